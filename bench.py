@@ -1,0 +1,510 @@
+#!/usr/bin/env python
+"""Benchmark: graph-batched stencil time stepping vs per-step launch on GB300.
+
+Default workload: 3D thermal 7-point stencil, 512x512x8 FP32, 1000
+iterations per step, seeded synthetic T ~ U[320,340], P ~ U[0,1e-3] on
+layer 0.  One bench "step" is one whole 1000-iteration run of the workload
+through the library's graph-batched path (gs_step with batch size S).
+L2 is flushed (256 MiB write) between timed steps, outside the timed events.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (the only comparison program there is:
+the paper ships no code).
+
+Other workloads (``--workload``): heat2d-512 (2D 512^2, 1000 iterations),
+heat2d-4096 (2D 4096^2, 200 iterations), fdtd-128 (Yee 128^3, 5000
+iterations).  Multi-GPU (torchrun): independent replicas, one per rank, no
+collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gs_inputs  # noqa: E402
+
+WORKLOADS = {
+    "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=1),
+    "heat2d-512": dict(kind="heat2d", nx=512, ny=512, nz=1, iters=1000, S=100, depth=1),
+    "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1),
+    "fdtd-128": dict(kind="fdtd", N=128, iters=5000, S=100, depth=1),
+}
+DEFAULT = "heat3d-512x512x8"
+METRIC = "cell-updates/s (graph-batched)"
+FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cells_of(w):
+    return w["N"] ** 3 if w["kind"] == "fdtd" else w["nx"] * w["ny"] * w["nz"]
+
+
+def algo_bytes_per_launch(w, depth, elem=4):
+    """Algorithmic DRAM bytes of one kernel launch.
+
+    Thermal depth-t launch: read T once, write T once, read the P plane once
+    (2D: P is the full plane), for t cell-updates per cell.  FDTD half-step
+    (H or E kernel): read 6 components, write 3, per cell."""
+    if w["kind"] == "fdtd":
+        return cells_of(w) * 9 * elem
+    plane = w["nx"] * w["ny"]
+    return cells_of(w) * 2 * elem + plane * elem
+
+
+# ------------------------------------------------------------ clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _smi_id():
+    import torch
+
+    try:
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return vis if vis.isdigit() else "0"
+
+
+# ------------------------------------------------------- oracle timing --
+def oracle_sample(w, budget_s=10.0):
+    """Time the FP64 oracle on a bounded sample of the workload.
+
+    Returns (cell-updates/s, sample description, threads, oracle result of
+    the full workload if it was run in full, else None)."""
+    import oracle
+
+    oracle.build()
+    threads = oracle.num_threads()
+    if w["kind"] == "fdtd":
+        N = w["N"]
+        f = oracle.fdtd_zero_fields(N)
+        n = 0
+        t0 = time.perf_counter()
+        chunk = 20
+        while n < w["iters"] and time.perf_counter() - t0 < budget_s:
+            oracle.fdtd_run(f, N, chunk, n0=n, src=(N // 2, N // 2, N // 2))
+            n += chunk
+        dt = time.perf_counter() - t0
+        full = f if n >= w["iters"] else None
+        return cells_of(w) * n / dt, f"FDTD {N}^3, first {n} of {w['iters']} steps", threads, full
+    T0, P = gs_inputs.heat_fields(w["nx"], w["ny"], w["nz"], seed=0)
+    coeffs = oracle.HEAT_COEFFS_2D if w["nz"] == 1 else oracle.HEAT_COEFFS_3D
+    T = T0
+    n = 0
+    chunk = 50
+    t0 = time.perf_counter()
+    while n < w["iters"] and time.perf_counter() - t0 < budget_s:
+        T = oracle.heat_run(T, P, chunk, coeffs)
+        n += chunk
+    dt = time.perf_counter() - t0
+    full = T if n >= w["iters"] else None
+    shape = "x".join(str(v) for v in (w["nx"], w["ny"], w["nz"]))
+    return cells_of(w) * n / dt, f"thermal {shape}, first {n} of {w['iters']} iterations", threads, full
+
+
+def run_reference(args, w, name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    sample = threads = None
+    for i in range(args.warmup + args.steps):
+        v, sample, threads, _ = oracle_sample(w, budget_s=max(1.0, 60.0 / (args.warmup + args.steps)))
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cells_of(w) * w["iters"] / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, **{k: v for k, v in w.items() if k not in ("S", "depth")}},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm --
+class Runner:
+    """One workload bound to a context on the current torch stream."""
+
+    def __init__(self, w, S, depth, plan_extra):
+        import torch
+
+        import paper_2501_09398_gb300 as g
+
+        self.g, self.w, self.S, self.depth = g, w, S, depth
+        self.stream = torch.cuda.current_stream()
+        h = self.stream.cuda_stream
+        if w["kind"] == "fdtd":
+            N = w["N"]
+            self.ctx = g.gs_create(g.GS_FDTD3D, N, N, N, g.GS_F32, g.GS_BC_PEC, h)
+            self.fields = g.FdtdFields(self.ctx, N)
+            g.gs_set_fdtd_params(self.ctx, courant=0.5, src_on=1, src=(N // 2, N // 2, N // 2))
+            self.host_in = []
+            self.out_shape = (N + 1,) * 3
+        else:
+            kind = g.GS_HEAT2D if w["kind"] == "heat2d" else g.GS_HEAT3D
+            self.ctx = g.gs_create(kind, w["nx"], w["ny"], w["nz"], g.GS_F32, g.GS_BC_CLAMP, h)
+            self.fields = g.HeatFields(self.ctx, w["nx"], w["ny"], w["nz"])
+            T0, P = gs_inputs.heat_fields(w["nx"], w["ny"], w["nz"], seed=0)
+            self.T0, self.P = T0, P
+            self.out_shape = T0.shape
+        plan = dict(temporal_depth=depth, **plan_extra)
+        g.gs_set_plan(self.ctx, **plan)
+        self.reset()
+
+    def reset(self):
+        g = self.g
+        if self.w["kind"] == "fdtd":
+            z = np.zeros(self.out_shape, dtype=np.float32)
+            for fid in g.FDTD_FIELDS:
+                g.gs_upload(self.ctx, fid, z)
+            g.gs_set_time(self.ctx, 0)
+        else:
+            g.gs_upload(self.ctx, g.GS_FIELD_T, self.T0)
+            g.gs_upload(self.ctx, g.GS_FIELD_P, self.P)
+
+    def step(self, S):
+        self.g.gs_step(self.ctx, self.w["iters"], S)
+
+    def read(self):
+        g = self.g
+        if self.w["kind"] == "fdtd":
+            return [g.gs_read_field(self.ctx, fid, np.empty(self.out_shape, dtype=np.float32)) for fid in g.FDTD_FIELDS]
+        return g.gs_read_field(self.ctx, g.GS_FIELD_T, np.empty(self.out_shape, dtype=np.float32))
+
+    def launches_per_step(self, S):
+        it = self.w["iters"]
+        if self.w["kind"] == "fdtd":
+            return 2 * it
+        t = self.depth
+        return it // t + it % t
+
+    def close(self):
+        self.g.gs_destroy(self.ctx)
+
+
+def timed_steps(run, S, K, W, flush):
+    """Device time of K steps (CUDA events on the launching stream), L2
+    flushed between steps outside the events.  Returns per-step ms list."""
+    import torch
+
+    st = run.stream
+    for _ in range(W):
+        flush.zero_()
+        run.step(S)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(st)
+        run.step(S)
+        b.record(st)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def kernel_avg_ms(run, flush, reps=6, per=16):
+    """Average duration of one launch of the dominant kernel: events around
+    single launches queued behind an L2-flush write so the GPU runs them back
+    to back (the host enqueues ahead while the flush runs)."""
+    import torch
+
+    g = run.g
+    st = run.stream
+    n_iter = 1 if run.w["kind"] == "fdtd" else run.depth
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(per)]
+        for a, b in evs:
+            a.record(st)
+            g.gs_step(run.ctx, n_iter, 0)
+            b.record(st)
+        torch.cuda.synchronize()
+        times += [a.elapsed_time(b) for a, b in evs]
+    # FDTD: one gs_step(1) is an H launch and an E launch; report per launch
+    div = 2 if run.w["kind"] == "fdtd" else 1
+    return statistics.median(times) / div
+
+
+def e2e_steps(run, S, K):
+    """Wall time per step through the public API with host buffers: upload
+    inputs from pinned host memory, step, read the result back."""
+    import torch
+
+    g = run.g
+    if run.w["kind"] == "fdtd":
+        hz = torch.zeros(run.out_shape, dtype=torch.float32).pin_memory().numpy()
+        h_in = [hz] * 6
+        fids = list(g.FDTD_FIELDS)
+    else:
+        h_in = [torch.from_numpy(run.T0).pin_memory().numpy(), torch.from_numpy(run.P).pin_memory().numpy()]
+        fids = [g.GS_FIELD_T, g.GS_FIELD_P]
+    h_out = torch.empty(run.out_shape, dtype=torch.float32).pin_memory().numpy()
+    out_fid = g.GS_FIELD_EZ if run.w["kind"] == "fdtd" else g.GS_FIELD_T
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        for fid, h in zip(fids, h_in):
+            g.gs_upload(run.ctx, fid, h)
+        if run.w["kind"] == "fdtd":
+            g.gs_set_time(run.ctx, 0)
+        run.step(S)
+        g.gs_read_field(run.ctx, out_fid, h_out)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / K
+    h2d = sum(h.nbytes for h in h_in)
+    return dt, h2d, h_out.nbytes
+
+
+def measure_workload(name, w, args, flush, with_e2e=True):
+    import torch
+
+    g_plan = {}
+    if args.block_x:
+        g_plan["block_x"] = args.block_x
+    if args.rows:
+        g_plan["rows"] = args.rows
+    if args.tile_x:
+        g_plan["tile_x"] = args.tile_x
+    if args.tile_y:
+        g_plan["tile_y"] = args.tile_y
+    if args.pdl:
+        g_plan["use_pdl"] = 1
+    if getattr(args, "kernel", 0):
+        g_plan["kernel"] = args.kernel
+    S = args.batch or w["S"]
+    depth = args.depth or w["depth"]
+    run = Runner(w, S, depth, g_plan)
+    try:
+        g = run.g
+        # paper convention (Sec. III-C): graph creation + execution of one run
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.gs_graph_destroy(run.ctx)
+        g.gs_graph_build(run.ctx, S)
+        run.step(S)
+        torch.cuda.synchronize()
+        paper_conv_ms = (time.perf_counter() - t0) * 1e3
+        build_s = g.gs_get_stats(run.ctx)["last_build_seconds"]
+        # steady state (graphs cached)
+        graph_ms = timed_steps(run, S, args.steps, args.warmup, flush)
+        per_step_ms = timed_steps(run, 0, args.steps, args.warmup, flush)
+        kern_ms = kernel_avg_ms(run, flush)
+        e2e = e2e_steps(run, S, max(3, min(args.steps, 20))) if with_e2e else None
+        # result after one clean run, for the error check
+        run.reset()
+        run.step(S)
+        result = run.read()
+    finally:
+        run.close()
+    return dict(S=S, depth=depth, graph_ms=graph_ms, per_step_ms=per_step_ms, kern_ms=kern_ms, e2e=e2e,
+                paper_conv_ms=paper_conv_ms, build_s=build_s, result=result,
+                launches=run.launches_per_step(S))
+
+
+def error_vs_oracle(w, result, full_ref):
+    if full_ref is None:
+        return None
+    if w["kind"] == "fdtd":
+        import oracle
+
+        ref = np.concatenate([full_ref[c].ravel() for c in oracle.FDTD_COMPONENTS])
+        got = np.concatenate([r.astype(np.float64).ravel() for r in result])
+        return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    return {"max_rel": float(np.max(np.abs(result.astype(np.float64) - full_ref) / np.abs(full_ref)))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="iteration batch size S (0: workload default)")
+    ap.add_argument("--depth", type=int, default=0, help="temporal depth t (0: workload default)")
+    ap.add_argument("--block-x", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=0)
+    ap.add_argument("--tile-x", type=int, default=0)
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--pdl", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0, help="thermal kernel variant (gs_kernel; 0 = auto)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 2D 512^2 / 4096^2 side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        run_reference(args, w, args.workload)
+        return
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    # All work (library, events, L2 flush) on one explicit stream: the
+    # default stream's handle is 0, which the library reads as "create your
+    # own stream", and events on another stream would not bracket its work.
+    torch.cuda.set_stream(torch.cuda.Stream())
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2501_09398_gb300  # noqa: F401  (fails loudly without the CUDA library)
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(_smi_id())
+    clocks.start()
+    m = measure_workload(args.workload, w, args, flush)
+    clk = clocks.stop()
+
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([sum(m["graph_ms"])], device="cuda", dtype=torch.float64)
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    else:
+        total_ms = sum(m["graph_ms"])
+
+    cells = cells_of(w)
+    ms_per_step = total_ms / args.steps
+    value = world * cells * w["iters"] * args.steps / (total_ms * 1e-3)
+    per_step_value = cells * w["iters"] / (statistics.mean(m["per_step_ms"]) * 1e-3)
+    peak, peak_kind = _peaks()
+    bytes_launch = algo_bytes_per_launch(w, m["depth"])
+    achieved = bytes_launch / (m["kern_ms"] * 1e-3) / 1e9
+    step_bw = bytes_launch * m["launches"] / (ms_per_step * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "iterations_per_step": w["iters"], "batch_size_S": m["S"],
+                   "temporal_depth": m["depth"], "parallelism": f"replicas x{world}" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel_ms": m["kern_ms"],
+                     "bytes_per_launch": bytes_launch, "in_step_GBps": step_bw},
+        "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
+                            "graph_speedup": per_step_value / (value / world)},
+        "paper_convention": {"ms_build_plus_run": m["paper_conv_ms"], "build_s": m["build_s"]},
+        "gpu_launches": m["launches"] * args.steps,
+        "clocks": clk,
+    }
+    if m["e2e"] is not None:
+        dt, h2d, d2h = m["e2e"]
+        line["e2e"] = {"value": cells * w["iters"] / dt, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, sample, threads, full = oracle_sample(w)
+        line["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+                                "sample": sample}
+        err = error_vs_oracle(w, m["result"], full)
+        if err is not None:
+            line["error_vs_oracle"] = err
+
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == DEFAULT:
+        extra = {}
+        a2 = argparse.Namespace(**{**vars(args), "batch": 0, "depth": 0, "block_x": 0, "rows": 0, "tile_x": 0,
+                                   "tile_y": 0, "pdl": False, "kernel": 0, "steps": 20})
+        for nm in ("heat2d-512", "heat2d-4096"):
+            ww = WORKLOADS[nm]
+            mm = measure_workload(nm, ww, a2, flush, with_e2e=False)
+            c = cells_of(ww) * ww["iters"]
+            gv = c / (statistics.mean(mm["graph_ms"]) * 1e-3)
+            pv = c / (statistics.mean(mm["per_step_ms"]) * 1e-3)
+            bl = algo_bytes_per_launch(ww, mm["depth"])
+            kbw = bl / (mm["kern_ms"] * 1e-3) / 1e9
+            extra[nm] = {"graph_value": gv, "per_step_value": pv, "graph_speedup": gv / pv, "S": mm["S"],
+                         "kernel_GBps": kbw, "kernel_frac": kbw / peak,
+                         "paper_convention_ms": mm["paper_conv_ms"]}
+        line["extra"] = extra
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

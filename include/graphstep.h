@@ -1,0 +1,284 @@
+/*
+ * graphstep — explicit iterative stencil time stepping on one GPU, with the
+ * per-iteration kernels grouped into iteration batches and unrolled into CUDA
+ * graphs ("Kernel Batching with CUDA Graphs", arXiv 2501.09398).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - an iterative solver launches the same kernel(s) once per iteration
+ *     (Sec. III-A, Listing 1); the launches are grouped into batches of S
+ *     (Listing 2) and each batch is unrolled into a static graph built by
+ *     manual graph creation: a linear chain of S kernel nodes, instantiated
+ *     and uploaded before the first launch (Listing 3, "Building");
+ *   - I_k iterations then take I = I_k / S graph launches (Eq. 4, Listing 3,
+ *     "Launching"); iteration counts that S does not divide are handled by a
+ *     peeled remainder graph (the fix the paper names in Sec. VI);
+ *   - the total time is graph creation plus execution, T = T_C + T_E
+ *     (Eqs. 1-6); gs_get_stats() reports the measured creation time T_C.
+ *
+ * Workloads (the paper's Sec. III-C applications):
+ *   GS_HEAT2D  2D 5-point thermal update (Rodinia Hotspot's role);
+ *   GS_HEAT3D  3D 7-point thermal update (Hotspot3D's role);
+ *   GS_FDTD3D  3D Yee FDTD Maxwell solver, one H kernel and one E kernel per
+ *              iteration.
+ * Thermal update (per cell, FP32 arithmetic):
+ *   T' = T + k*(P + cy*(T_N+T_S-2T) + cx*(T_E+T_W-2T) + cz*(t_amb-T)
+ *              [+ cz2*(T_U+T_D-2T) in 3D])
+ *   clamp boundary: a missing neighbour reads the cell itself (zero flux);
+ *   Dirichlet-0: it reads 0.  In 3D, P is one x-y plane acting on layer 0.
+ * FDTD update (normalised units, dx = 1, dt = courant number s):
+ *   H -= s*curl(E) (forward differences), then E += s*curl(H) (backward
+ *   differences, interior only: tangential E on the PEC walls stays 0), then
+ *   a soft source Ez[src] += amp*exp(-((n - delay)/width)^2) at step n.
+ *
+ * Conventions for every call:
+ *   - Every function returns gs_status; GS_OK is 0.  Nothing throws or aborts
+ *     across the boundary.  On failure, gs_last_error(ctx) holds a message.
+ *   - Device memory for fields is owned by the caller (e.g. allocated with
+ *     PyTorch) and borrowed by the context; it must stay valid while bound.
+ *     The context owns its graphs, its stream (only if it created one) and
+ *     small scratch buffers (FDTD step counter, conversion staging).
+ *   - Layout: x fastest, then y, then z.  A row holds `pitch` elements,
+ *     pitch >= row width and a multiple of 16 bytes (4 f32 or 8 bf16/f16
+ *     elements); the base pointer is 16-byte aligned; planes are pitch*rows
+ *     elements apart.  gs_required_pitch() returns the smallest valid pitch.
+ *   - All GPU work is asynchronous on the context's stream unless a call says
+ *     it synchronises.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef GRAPHSTEP_H
+#define GRAPHSTEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* bad handle, size, pointer, alignment or value */
+    GS_ERR_CUDA = 2,        /* a CUDA runtime call failed; see gs_last_error */
+    GS_ERR_OOM = 3,         /* a host or device allocation failed */
+    GS_ERR_STATE = 4,       /* call not valid in the current state (e.g. unbound field) */
+    GS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    GS_ERR_NUMERIC = 6,     /* non-finite values where finite ones are required */
+    GS_ERR_UNSUPPORTED = 7  /* valid request this build does not provide (e.g. plan too large) */
+} gs_status;
+
+typedef enum gs_kind { GS_HEAT2D = 0, GS_HEAT3D = 1, GS_FDTD3D = 2 } gs_kind;
+
+/* Storage type of the fields.  Arithmetic is always FP32. */
+typedef enum gs_dtype { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
+
+/* Boundary rule.  Thermal: CLAMP or DIRICHLET0.  FDTD: PEC only. */
+typedef enum gs_bc { GS_BC_CLAMP = 0, GS_BC_DIRICHLET0 = 1, GS_BC_PEC = 2 } gs_bc;
+
+typedef enum gs_field {
+    GS_FIELD_T0 = 0, /* thermal ping-pong buffer 0 (nz*ny rows of pitch) */
+    GS_FIELD_T1 = 1, /* thermal ping-pong buffer 1 */
+    GS_FIELD_P = 2,  /* thermal power map: one ny-row plane (layer 0 in 3D) */
+    GS_FIELD_EX = 3, /* FDTD components: (N+1)*(N+1) rows of pitch each */
+    GS_FIELD_EY = 4,
+    GS_FIELD_EZ = 5,
+    GS_FIELD_HX = 6,
+    GS_FIELD_HY = 7,
+    GS_FIELD_HZ = 8,
+    GS_FIELD_T = 9   /* alias: whichever of T0/T1 holds the current state */
+} gs_field;
+
+typedef struct gs_ctx gs_ctx;
+
+typedef struct gs_heat_coeffs {
+    float k, cx, cy, cz, cz2, t_amb;
+} gs_heat_coeffs;
+
+typedef struct gs_fdtd_params {
+    float courant;   /* s = c*dt/dx; stable for s < 1/sqrt(3) */
+    int32_t src_on;  /* 1: soft Ez source after each E update */
+    int64_t src_i, src_j, src_k;
+    float src_amp, src_delay, src_width; /* amp*exp(-((n-delay)/width)^2) */
+} gs_fdtd_params;
+
+/* Thermal kernel variants (gs_plan.kernel).
+ *   MARCH  depth 1 only: each thread marches a vector of cells down `rows`
+ *          rows; any nz.
+ *   WAVE   depth 1, 2 or 4, 2D or nz <= 16: each warp marches `rows` rows and
+ *          advances `temporal_depth` time levels in one pass (register
+ *          windows per level; block_x/32 warps per block in 2D, one warp
+ *          per plane in 3D).
+ *   TILE   depth 2 or 4: overlapped shared-memory tile of tile_x x tile_y
+ *          columns (all nz planes) with a t-wide halo.
+ *   AUTO   MARCH for depth 1, WAVE for depth > 1 where it applies, else TILE. */
+typedef enum gs_kernel { GS_KERNEL_AUTO = 0, GS_KERNEL_MARCH = 1, GS_KERNEL_WAVE = 2, GS_KERNEL_TILE = 3 } gs_kernel;
+
+/* Launch plan.  Zero fields select defaults.
+ *   block_x        threads along x per block (multiple of 32; <= 512 thermal,
+ *                  <= 256 FDTD)
+ *   rows           rows each block (or warp) marches along y; FDTD: k planes
+ *                  per block
+ *   tile_x, tile_y output tile of the TILE kernel
+ *   temporal_depth thermal steps fused in one launch: 1, 2 or 4; a depth-t
+ *                  launch is bit-identical to t depth-1 launches
+ *   use_pdl        1: graph nodes (and per-step launches) use programmatic
+ *                  dependent launch, so the next kernel's launch overlaps the
+ *                  tail of the previous one; results are unchanged
+ *   device_launch  1: instantiate graphs with cudaGraphInstantiateFlagDeviceLaunch
+ *                  as in the paper's Listing 3 (not combinable with use_pdl) */
+typedef struct gs_plan {
+    int32_t block_x;
+    int32_t rows;
+    int32_t tile_x;
+    int32_t tile_y;
+    int32_t temporal_depth;
+    int32_t use_pdl;
+    int32_t device_launch;
+    int32_t kernel; /* gs_kernel; thermal only (FDTD ignores it) */
+} gs_plan;
+
+typedef struct gs_stats {
+    double last_build_seconds;  /* host wall time of the last graph build:
+                                   create + add nodes + instantiate + upload
+                                   (the paper's T_C, Eq. 2, incl. upload) */
+    int64_t last_build_nodes;   /* kernel nodes in that graph */
+    int64_t graphs_built;       /* executable graphs built since creation */
+    int64_t graph_launches;     /* cudaGraphLaunch calls issued */
+    int64_t kernel_launches;    /* direct kernel launches issued */
+    int64_t iterations;         /* iterations issued (thermal steps / FDTD H+E pairs) */
+} gs_stats;
+
+/* ------------------------------------------------------------- basics -- */
+
+/* Library version as major*10000 + minor*100 + patch. */
+int gs_version(void);
+
+/* Static, human-readable name of a status code (never NULL). */
+const char *gs_status_string(gs_status s);
+
+/* Message of the last failed call on ctx ("" if none).  The pointer stays
+ * valid until the next call on ctx.  ctx == NULL gives the message of the
+ * last failed gs_create/gs_multi_create on this thread. */
+const char *gs_last_error(const gs_ctx *ctx);
+
+/* Smallest valid row pitch (elements) for rows of `width` elements of
+ * `dtype`: width rounded up to a multiple of 16 bytes.
+ * Errors: GS_ERR_INVALID_ARG for width < 1 or an unknown dtype. */
+gs_status gs_required_pitch(gs_dtype dtype, int64_t width, int64_t *pitch_out);
+
+/* ------------------------------------------------------ context set-up -- */
+
+/* Create a stepping context.
+ *   kind     GS_HEAT2D (nz must be 1), GS_HEAT3D, GS_FDTD3D (nx == ny == nz
+ *            == N cells; each component is an (N+1)^3 array)
+ *   nx,ny,nz grid size in cells, each in [1, 2^20], total < 2^31 elements
+ *   storage  field storage type
+ *   bc       GS_BC_CLAMP / GS_BC_DIRICHLET0 (thermal) or GS_BC_PEC (FDTD)
+ *   stream   cudaStream_t to run on, borrowed (cudaStreamLegacy and
+ *            cudaStreamPerThread are accepted); NULL: the context creates
+ *            (and later destroys) its own non-blocking stream, as the
+ *            paper's Listing 3 does.
+ * Defaults: thermal coefficients k=0.5, cx=cy=0.1, cz=0.01, cz2=0.05,
+ * t_amb=80; FDTD courant 0.5, source off; plan defaults, depth 1, no PDL.
+ * The CUDA device current on the calling thread is used.
+ * Errors: GS_ERR_INVALID_ARG (sizes, kind/bc mismatch), GS_ERR_CUDA,
+ * GS_ERR_OOM.  *out is NULL on failure. */
+gs_status gs_create(gs_ctx **out, gs_kind kind, int64_t nx, int64_t ny, int64_t nz,
+                    gs_dtype storage, gs_bc bc, void *stream);
+
+/* Destroy ctx: synchronises its stream, frees graphs and scratch, destroys
+ * the stream if the context created it.  Bound field memory is untouched.
+ * NULL is accepted (no-op). */
+gs_status gs_destroy(gs_ctx *ctx);
+
+/* Replace the thermal coefficients (GS_HEAT2D / GS_HEAT3D only).  Built
+ * graphs are discarded (their nodes hold the old values).  Non-finite
+ * values give GS_ERR_NUMERIC. */
+gs_status gs_set_heat_coeffs(gs_ctx *ctx, const gs_heat_coeffs *c);
+
+/* Replace the FDTD parameters (GS_FDTD3D only).  The source cell must lie
+ * inside the (N+1)^3 arrays.  Built graphs are discarded. */
+gs_status gs_set_fdtd_params(gs_ctx *ctx, const gs_fdtd_params *p);
+
+/* Replace the launch plan (see gs_plan).  Zero fields take defaults.  A plan
+ * the kernels cannot run on this grid (shared-memory tile too large,
+ * temporal depth on FDTD, bad block size) gives GS_ERR_UNSUPPORTED or
+ * GS_ERR_INVALID_ARG and leaves the old plan in place.  Built graphs are
+ * discarded. */
+gs_status gs_set_plan(gs_ctx *ctx, const gs_plan *plan);
+
+/* The plan in effect, with defaults filled in. */
+gs_status gs_get_plan(const gs_ctx *ctx, gs_plan *out);
+
+/* Bind caller-owned device memory to a field.
+ *   ptr    device pointer, 16-byte aligned; NULL unbinds
+ *   pitch  row pitch in elements (>= row width, multiple of 16 bytes)
+ * The buffer must hold rows*pitch elements: ny rows (2D, and P), nz*ny
+ * rows (3D thermal), (N+1)^2 rows of N+1 used elements (each FDTD
+ * component).  GS_FIELD_T binds the buffer that currently holds the state.
+ * Rebinding discards built graphs. */
+gs_status gs_bind_field(gs_ctx *ctx, gs_field id, void *ptr, int64_t pitch);
+
+/* Copy a dense float32 host array (x fastest, no padding) into a bound
+ * field, rounding to the storage type (round to nearest even).  n must be
+ * the field's dense element count.  Synchronises the context stream before
+ * returning, so the host buffer may be reused at once. */
+gs_status gs_upload(gs_ctx *ctx, gs_field id, const float *host, int64_t n);
+
+/* Copy a bound field into a dense float32 host array (widened from the
+ * storage type).  n must be the field's dense element count.  Synchronises
+ * the context stream (all queued steps finish first). */
+gs_status gs_read_field(gs_ctx *ctx, gs_field id, float *host_out, int64_t n);
+
+/* Which thermal buffer (0 or 1) holds the current state. */
+gs_status gs_get_parity(const gs_ctx *ctx, int32_t *parity_out);
+
+/* Declare which thermal buffer (0 or 1) holds the current state. */
+gs_status gs_set_parity(gs_ctx *ctx, int32_t parity);
+
+/* FDTD time index n of the next step (the source uses it).  gs_set_time
+ * writes it to the device counter on the context stream; it is ordered with
+ * the steps around it.  Thermal contexts only keep the host count. */
+gs_status gs_set_time(gs_ctx *ctx, int64_t n);
+gs_status gs_get_time(const gs_ctx *ctx, int64_t *n_out);
+
+/* ------------------------------------------------------------ stepping -- */
+
+/* Advance n_iters iterations (thermal steps, or FDTD H+E pairs).
+ *   batch_size == 0  per-step launches: one kernel launch per iteration
+ *                    (per fused group of temporal_depth iterations) — the
+ *                    paper's baseline, Listing 1;
+ *   batch_size  > 0  iteration batching: floor(n/S) launches of a graph of
+ *                    S iterations (Listing 3), then one launch of a cached
+ *                    remainder graph of n mod S iterations (loop peeling).
+ *                    Graphs are built on first use and cached per
+ *                    (S, buffer parity); two exec graphs exist when a batch
+ *                    flips the ping-pong parity.
+ * Results are bit-identical for every batch_size, temporal depth and PDL
+ * setting.  Asynchronous.  Errors: GS_ERR_STATE if a required field is
+ * unbound; GS_ERR_INVALID_ARG for n_iters < 0 or batch_size < 0. */
+gs_status gs_step(gs_ctx *ctx, int64_t n_iters, int64_t batch_size);
+
+/* Build, instantiate and upload the graph(s) for batches of S iterations
+ * starting from the current parity (and the other parity when S flips it),
+ * synchronously, timing the host wall clock into gs_stats.last_build_seconds.
+ * Replaces earlier graphs of the same S. */
+gs_status gs_graph_build(gs_ctx *ctx, int64_t batch_size);
+
+/* Launch the graph built by the last gs_graph_build n_launches times
+ * (S*n_launches iterations).  Asynchronous.  GS_ERR_STATE if none is built. */
+gs_status gs_graph_launch(gs_ctx *ctx, int64_t n_launches);
+
+/* Destroy every cached graph of ctx. */
+gs_status gs_graph_destroy(gs_ctx *ctx);
+
+/* Wait for all work queued on the context stream. */
+gs_status gs_sync(gs_ctx *ctx);
+
+/* Counters and the last measured graph build time. */
+gs_status gs_get_stats(const gs_ctx *ctx, gs_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPHSTEP_H */

@@ -1,0 +1,240 @@
+"""Python binding of libgraphstep (C ABI declared in include/graphstep.h).
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, converts Python/NumPy/PyTorch arguments to pointers and
+sizes, and raises ``GsError`` when the call returns a status other than
+GS_OK.  All stepping runs in the library's CUDA kernels; there is no CPU
+fallback, and importing this package fails if libgraphstep.so is missing
+(build it with ``python paper_2501_09398_gb300/build.py``).
+
+PyTorch is used only as a source of device memory and streams: pass
+``tensor.data_ptr()`` / ``torch.cuda.current_stream().cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgraphstep.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} not found: the CUDA library must be built first "
+        "(python paper_2501_09398_gb300/build.py)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------ constants --
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_STATE, GS_ERR_TIMEOUT, GS_ERR_NUMERIC, \
+    GS_ERR_UNSUPPORTED = range(8)
+GS_HEAT2D, GS_HEAT3D, GS_FDTD3D = range(3)
+GS_F32, GS_BF16, GS_F16 = range(3)
+GS_BC_CLAMP, GS_BC_DIRICHLET0, GS_BC_PEC = range(3)
+GS_KERNEL_AUTO, GS_KERNEL_MARCH, GS_KERNEL_WAVE, GS_KERNEL_TILE = range(4)
+(GS_FIELD_T0, GS_FIELD_T1, GS_FIELD_P, GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY,
+ GS_FIELD_HZ, GS_FIELD_T) = range(10)
+
+DTYPES = {"f32": GS_F32, "bf16": GS_BF16, "f16": GS_F16}
+FDTD_FIELDS = (GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY, GS_FIELD_HZ)
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.gs_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------- structs --
+class gs_heat_coeffs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("k", "cx", "cy", "cz", "cz2", "t_amb")]
+
+
+class gs_fdtd_params(ctypes.Structure):
+    _fields_ = [("courant", ctypes.c_float), ("src_on", ctypes.c_int32), ("src_i", ctypes.c_int64),
+                ("src_j", ctypes.c_int64), ("src_k", ctypes.c_int64), ("src_amp", ctypes.c_float),
+                ("src_delay", ctypes.c_float), ("src_width", ctypes.c_float)]
+
+
+class gs_plan(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "tile_x", "tile_y", "temporal_depth", "use_pdl",
+                                              "device_launch", "kernel")]
+
+
+class gs_stats(ctypes.Structure):
+    _fields_ = [("last_build_seconds", ctypes.c_double), ("last_build_nodes", ctypes.c_int64),
+                ("graphs_built", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("iterations", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("gs_version", [])
+_sig("gs_status_string", [ctypes.c_int], ctypes.c_char_p)
+_sig("gs_last_error", [_vp], ctypes.c_char_p)
+_sig("gs_required_pitch", [ctypes.c_int, _i64, ctypes.POINTER(_i64)])
+_sig("gs_create", [ctypes.POINTER(_vp), ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int, _vp])
+_sig("gs_destroy", [_vp])
+_sig("gs_set_heat_coeffs", [_vp, ctypes.POINTER(gs_heat_coeffs)])
+_sig("gs_set_fdtd_params", [_vp, ctypes.POINTER(gs_fdtd_params)])
+_sig("gs_set_plan", [_vp, ctypes.POINTER(gs_plan)])
+_sig("gs_get_plan", [_vp, ctypes.POINTER(gs_plan)])
+_sig("gs_bind_field", [_vp, ctypes.c_int, _vp, _i64])
+_sig("gs_upload", [_vp, ctypes.c_int, _fp, _i64])
+_sig("gs_read_field", [_vp, ctypes.c_int, _fp, _i64])
+_sig("gs_get_parity", [_vp, ctypes.POINTER(_i32)])
+_sig("gs_set_parity", [_vp, _i32])
+_sig("gs_set_time", [_vp, _i64])
+_sig("gs_get_time", [_vp, ctypes.POINTER(_i64)])
+_sig("gs_step", [_vp, _i64, _i64])
+_sig("gs_graph_build", [_vp, _i64])
+_sig("gs_graph_launch", [_vp, _i64])
+_sig("gs_graph_destroy", [_vp])
+_sig("gs_sync", [_vp])
+_sig("gs_get_stats", [_vp, ctypes.POINTER(gs_stats)])
+
+
+def _check(st: int, ctx=None):
+    if st != GS_OK:
+        raise GsError(st, _lib.gs_last_error(ctx).decode(errors="replace"))
+
+
+def _f32_ptr(a: np.ndarray):
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("need a C-contiguous float32 array")
+    return a.ctypes.data_as(_fp)
+
+
+# --------------------------------------------------------------- calls -----
+def gs_version() -> int:
+    return int(_lib.gs_version())
+
+
+def gs_status_string(status: int) -> str:
+    return _lib.gs_status_string(status).decode()
+
+
+def gs_last_error(ctx) -> str:
+    return _lib.gs_last_error(ctx).decode(errors="replace")
+
+
+def gs_required_pitch(dtype: int, width: int) -> int:
+    out = _i64()
+    _check(_lib.gs_required_pitch(dtype, width, ctypes.byref(out)))
+    return out.value
+
+
+def gs_create(kind: int, nx: int, ny: int, nz: int, dtype: int = GS_F32, bc: int = GS_BC_CLAMP, stream=None):
+    """Return an opaque context handle (ctypes.c_void_p)."""
+    h = _vp()
+    _check(_lib.gs_create(ctypes.byref(h), kind, nx, ny, nz, dtype, bc, _vp(stream) if stream else None))
+    return h
+
+
+def gs_destroy(ctx) -> None:
+    _check(_lib.gs_destroy(ctx))
+
+
+def gs_set_heat_coeffs(ctx, k=0.5, cx=0.1, cy=0.1, cz=0.01, cz2=0.05, t_amb=80.0) -> None:
+    c = gs_heat_coeffs(k, cx, cy, cz, cz2, t_amb)
+    _check(_lib.gs_set_heat_coeffs(ctx, ctypes.byref(c)), ctx)
+
+
+def gs_set_fdtd_params(ctx, courant=0.5, src_on=0, src=(0, 0, 0), amp=1.0, delay=60.0, width=20.0) -> None:
+    p = gs_fdtd_params(courant, src_on, src[0], src[1], src[2], amp, delay, width)
+    _check(_lib.gs_set_fdtd_params(ctx, ctypes.byref(p)), ctx)
+
+
+def gs_set_plan(ctx, block_x=0, rows=0, tile_x=0, tile_y=0, temporal_depth=0, use_pdl=0, device_launch=0,
+                kernel=0) -> None:
+    p = gs_plan(block_x, rows, tile_x, tile_y, temporal_depth, use_pdl, device_launch, kernel)
+    _check(_lib.gs_set_plan(ctx, ctypes.byref(p)), ctx)
+
+
+def gs_get_plan(ctx) -> dict:
+    p = gs_plan()
+    _check(_lib.gs_get_plan(ctx, ctypes.byref(p)), ctx)
+    return {n: getattr(p, n) for n, _ in gs_plan._fields_}
+
+
+def gs_bind_field(ctx, field: int, ptr: int, pitch: int) -> None:
+    _check(_lib.gs_bind_field(ctx, field, _vp(ptr) if ptr else None, pitch), ctx)
+
+
+def gs_upload(ctx, field: int, host: np.ndarray) -> None:
+    _check(_lib.gs_upload(ctx, field, _f32_ptr(host), host.size), ctx)
+
+
+def gs_read_field(ctx, field: int, out: np.ndarray) -> np.ndarray:
+    _check(_lib.gs_read_field(ctx, field, _f32_ptr(out), out.size), ctx)
+    return out
+
+
+def gs_get_parity(ctx) -> int:
+    v = _i32()
+    _check(_lib.gs_get_parity(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def gs_set_parity(ctx, parity: int) -> None:
+    _check(_lib.gs_set_parity(ctx, parity), ctx)
+
+
+def gs_set_time(ctx, n: int) -> None:
+    _check(_lib.gs_set_time(ctx, n), ctx)
+
+
+def gs_get_time(ctx) -> int:
+    v = _i64()
+    _check(_lib.gs_get_time(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def gs_step(ctx, n_iters: int, batch_size: int) -> None:
+    _check(_lib.gs_step(ctx, n_iters, batch_size), ctx)
+
+
+def gs_graph_build(ctx, batch_size: int) -> None:
+    _check(_lib.gs_graph_build(ctx, batch_size), ctx)
+
+
+def gs_graph_launch(ctx, n_launches: int) -> None:
+    _check(_lib.gs_graph_launch(ctx, n_launches), ctx)
+
+
+def gs_graph_destroy(ctx) -> None:
+    _check(_lib.gs_graph_destroy(ctx), ctx)
+
+
+def gs_sync(ctx) -> None:
+    _check(_lib.gs_sync(ctx), ctx)
+
+
+def gs_get_stats(ctx) -> dict:
+    s = gs_stats()
+    _check(_lib.gs_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {n: getattr(s, n) for n, _ in gs_stats._fields_}
+
+
+def raw_call(name: str, *args) -> int:
+    """Call a C entry point by name with ctypes arguments; returns its status
+    (no exception).  Used by tests that check error returns."""
+    return int(getattr(_lib, name)(*args))
+
+
+from .fields import HeatFields, FdtdFields  # noqa: E402  (device-memory helpers)
+
+__all__ = [n for n in dir() if n.startswith(("gs_", "GS_"))] + ["GsError", "HeatFields", "FdtdFields"]

@@ -1,0 +1,760 @@
+// C ABI of graphstep: contexts, field binding, per-step launches and the
+// iteration-batch graph unroller (the paper's Sec. III-A, Listings 1-3).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace gs;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;
+};
+
+}  // namespace
+
+struct gs_ctx {
+    gs_kind kind;
+    int64_t nx, ny, nz;
+    gs_dtype dt;
+    gs_bc bc;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    gs_heat_coeffs hc{0.5f, 0.1f, 0.1f, 0.01f, 0.05f, 80.0f};
+    gs_fdtd_params fp{};
+    gs_plan plan{};
+    void* ptr[9] = {};
+    int64_t pitch[9] = {};
+    int parity = 0;
+    int64_t time = 0;
+    long long* d_counter = nullptr;
+    float* staging = nullptr;
+    size_t staging_bytes = 0;
+    // Launch descriptors, valid while descs_ok: thermal [0]=depth 1,
+    // [1]=depth t, each per parity; FDTD [0][0]=H, [0][1]=E.
+    LaunchDesc desc[2][2];
+    bool descs_ok = false;
+    std::map<std::pair<int64_t, int>, GraphEntry> graphs;
+    int64_t built_S = 0;
+    gs_stats stats{};
+    std::string err;
+};
+
+// ------------------------------------------------------------ helpers ----
+
+namespace {
+
+gs_status fail(gs_ctx* c, gs_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+gs_status cuda_fail(gs_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA, m);
+}
+
+#define GS_CUDA(ctx, call)                                        \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+int vec_elems(gs_dtype dt) { return dt == GS_F32 ? 4 : 8; }
+constexpr int kTemporalThreads = 256;  // threads of a temporally blocked tile
+size_t elem_bytes(gs_dtype dt) { return dt == GS_F32 ? 4 : 2; }
+bool is_heat(const gs_ctx* c) { return c->kind == GS_HEAT2D || c->kind == GS_HEAT3D; }
+
+// Dense row width, row count and element count of a field.
+bool field_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows) {
+    if (is_heat(c)) {
+        if (id == GS_FIELD_T0 || id == GS_FIELD_T1) {
+            *width = c->nx;
+            *rows = c->ny * c->nz;
+            return true;
+        }
+        if (id == GS_FIELD_P) {
+            *width = c->nx;
+            *rows = c->ny;
+            return true;
+        }
+        return false;
+    }
+    if (id >= GS_FIELD_EX && id <= GS_FIELD_HZ) {
+        *width = c->nx + 1;
+        *rows = (c->nx + 1) * (c->nx + 1);
+        return true;
+    }
+    return false;
+}
+
+int resolve(const gs_ctx* c, int id) {
+    if (id == GS_FIELD_T) return c->parity ? GS_FIELD_T1 : GS_FIELD_T0;
+    return id;
+}
+
+void destroy_graphs(gs_ctx* c) {
+    for (auto& kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    c->graphs.clear();
+    c->built_S = 0;
+}
+
+void invalidate(gs_ctx* c) {
+    destroy_graphs(c);
+    c->descs_ok = false;
+}
+
+gs_plan default_plan(const gs_ctx* c) {
+    gs_plan p{};
+    if (c->kind == GS_FDTD3D) {
+        p.block_x = 32;
+        while (p.block_x * vec_elems(c->dt) < c->nx + 1 && p.block_x < 128) p.block_x += 32;
+        p.rows = 16;  // k planes per block
+        p.temporal_depth = 1;
+    } else if (c->kind == GS_HEAT2D) {
+        const bool small = c->nx * c->ny <= (1 << 20);
+        p.block_x = small ? 32 : 128;
+        p.rows = small ? 8 : 32;
+        p.tile_x = 64;
+        p.tile_y = 32;
+        p.temporal_depth = 1;
+        p.kernel = GS_KERNEL_MARCH;
+    } else {
+        p.block_x = 32;
+        p.rows = 16;
+        p.tile_x = 32;
+        p.tile_y = 32;
+        p.temporal_depth = 1;
+        p.kernel = GS_KERNEL_MARCH;
+    }
+    return p;
+}
+
+gs_status validate_plan(gs_ctx* c, gs_plan* p) {
+    const gs_plan d = default_plan(c);
+    if (p->block_x == 0) p->block_x = d.block_x;
+    if (p->rows == 0) p->rows = d.rows;
+    if (p->tile_x == 0) p->tile_x = d.tile_x;
+    if (p->tile_y == 0) p->tile_y = d.tile_y;
+    if (p->temporal_depth == 0) p->temporal_depth = 1;
+    if (p->block_x < 32 || p->block_x > 1024 || p->block_x % 32)
+        return fail(c, GS_ERR_INVALID_ARG, "plan.block_x must be a multiple of 32 in [32, 1024]");
+    if (p->rows < 1) return fail(c, GS_ERR_INVALID_ARG, "plan.rows must be >= 1");
+    if (c->kind == GS_FDTD3D && p->block_x > 256)
+        return fail(c, GS_ERR_INVALID_ARG, "FDTD: plan.block_x must be <= 256");
+    if (c->kind != GS_FDTD3D && p->block_x > 512)
+        return fail(c, GS_ERR_INVALID_ARG, "thermal: plan.block_x must be <= 512");
+    if (p->use_pdl != 0 && p->use_pdl != 1) return fail(c, GS_ERR_INVALID_ARG, "plan.use_pdl must be 0 or 1");
+    if (p->device_launch != 0 && p->device_launch != 1)
+        return fail(c, GS_ERR_INVALID_ARG, "plan.device_launch must be 0 or 1");
+    if (p->use_pdl && p->device_launch)
+        return fail(c, GS_ERR_INVALID_ARG, "plan.use_pdl and plan.device_launch cannot be combined");
+    const int t = p->temporal_depth;
+    if (t != 1 && t != 2 && t != 4) return fail(c, GS_ERR_INVALID_ARG, "plan.temporal_depth must be 1, 2 or 4");
+    if (c->kind == GS_FDTD3D && t != 1)
+        return fail(c, GS_ERR_UNSUPPORTED, "temporal blocking is provided for the thermal stencils only");
+    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_TILE)
+        return fail(c, GS_ERR_INVALID_ARG, "plan.kernel must be a gs_kernel value");
+    if (c->kind == GS_FDTD3D) p->kernel = GS_KERNEL_AUTO;
+    const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
+    if (is_heat(c) && p->kernel == GS_KERNEL_AUTO) p->kernel = (t == 1) ? GS_KERNEL_MARCH : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
+    if (p->kernel == GS_KERNEL_MARCH && t != 1)
+        return fail(c, GS_ERR_INVALID_ARG, "the MARCH kernel runs depth 1 only");
+    if (p->kernel == GS_KERNEL_TILE && t == 1)
+        return fail(c, GS_ERR_INVALID_ARG, "the TILE kernel runs depth 2 or 4 only");
+    if (p->kernel == GS_KERNEL_WAVE && !wave_ok)
+        return fail(c, GS_ERR_UNSUPPORTED, "the WAVE kernel needs nz <= 16 (all planes in one block)");
+    if (p->kernel == GS_KERNEL_WAVE && heat_wave_smem(c->kind == GS_HEAT3D ? (int)c->nz : 0, t, vec_elems(c->dt)) > 227 * 1024)
+        return fail(c, GS_ERR_UNSUPPORTED, "WAVE kernel shared memory too large");
+    if (t > 1 && p->kernel == GS_KERNEL_TILE) {
+        if (p->tile_x < 1 || p->tile_y < 1 || p->tile_x > 4096 || p->tile_y > 4096)
+            return fail(c, GS_ERR_INVALID_ARG, "plan.tile_x/tile_y must be in [1, 4096]");
+        const size_t sm = heat_temporal_smem(c->kind == GS_HEAT3D ? (int)c->nz : 1, p->tile_x, p->tile_y, t);
+        if (sm > 227 * 1024)
+            return fail(c, GS_ERR_UNSUPPORTED, "temporal tile needs " + std::to_string(sm) +
+                                                   " bytes of shared memory (limit 232448)");
+    }
+    if (c->kind == GS_HEAT3D && p->kernel == GS_KERNEL_MARCH) {
+        const int zb = (int)std::min<int64_t>(std::min<int64_t>(c->nz, 16), std::max(1, 512 / p->block_x));
+        if ((size_t)2 * (zb + 2) * p->block_x * vec_elems(c->dt) * 4 > 227 * 1024)
+            return fail(c, GS_ERR_UNSUPPORTED, "3D depth-1 block needs too much shared memory");
+    }
+    return GS_OK;
+}
+
+gs_status require_fields(gs_ctx* c) {
+    if (is_heat(c)) {
+        if (!c->ptr[GS_FIELD_T0] || !c->ptr[GS_FIELD_T1] || !c->ptr[GS_FIELD_P])
+            return fail(c, GS_ERR_STATE, "fields T0, T1 and P must be bound before stepping");
+        if (c->pitch[GS_FIELD_T0] != c->pitch[GS_FIELD_T1])
+            return fail(c, GS_ERR_STATE, "T0 and T1 must have the same pitch");
+    } else {
+        for (int f = GS_FIELD_EX; f <= GS_FIELD_HZ; ++f)
+            if (!c->ptr[f]) return fail(c, GS_ERR_STATE, "all six FDTD components must be bound before stepping");
+        for (int f = GS_FIELD_EY; f <= GS_FIELD_HZ; ++f)
+            if (c->pitch[f] != c->pitch[GS_FIELD_EX])
+                return fail(c, GS_ERR_STATE, "all six FDTD components must have the same pitch");
+    }
+    return GS_OK;
+}
+
+gs_status ensure_descs(gs_ctx* c) {
+    if (c->descs_ok) return GS_OK;
+    gs_status st = require_fields(c);
+    if (st != GS_OK) return st;
+    if (is_heat(c)) {
+        HeatArgs a{};
+        a.P = c->ptr[GS_FIELD_P];
+        a.nx = (int)c->nx;
+        a.ny = (int)c->ny;
+        a.nz = (int)c->nz;
+        a.rows = c->plan.rows;
+        a.pitch = c->pitch[GS_FIELD_T0];
+        a.plane = a.pitch * c->ny;
+        a.p_pitch = c->pitch[GS_FIELD_P];
+        a.tile_x = c->plan.tile_x;
+        a.tile_y = c->plan.tile_y;
+        a.c = HeatCoef{c->hc.k, c->hc.cx, c->hc.cy, c->hc.cz, c->hc.cz2, c->hc.t_amb};
+        const int t = c->plan.temporal_depth;
+        for (int par = 0; par < 2; ++par) {
+            a.Tin = c->ptr[par ? GS_FIELD_T1 : GS_FIELD_T0];
+            a.Tout = c->ptr[par ? GS_FIELD_T0 : GS_FIELD_T1];
+            // single-step launches (depth 1, and the peeled n mod t steps)
+            const int v1 = (c->plan.kernel == GS_KERNEL_WAVE) ? GS_KERNEL_WAVE : GS_KERNEL_MARCH;
+            cudaError_t e = heat_desc(c->kind, c->dt, c->bc, a, c->plan.block_x, 1, v1, &c->desc[0][par]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "thermal kernel set-up");
+            if (t > 1) {
+                const int bx = (c->plan.kernel == GS_KERNEL_TILE) ? kTemporalThreads : c->plan.block_x;
+                e = heat_desc(c->kind, c->dt, c->bc, a, bx, t, c->plan.kernel, &c->desc[1][par]);
+                if (e != cudaSuccess) return cuda_fail(c, e, "temporal kernel set-up");
+            }
+        }
+    } else {
+        FdtdArgs a{};
+        for (int f = 0; f < 6; ++f) a.f[f] = c->ptr[GS_FIELD_EX + f];
+        a.N = (int)c->nx;
+        a.kc = c->plan.rows;
+        a.pitch = c->pitch[GS_FIELD_EX];
+        a.plane = a.pitch * (c->nx + 1);
+        a.s = c->fp.courant;
+        a.src_on = c->fp.src_on;
+        a.si = (int)c->fp.src_i;
+        a.sj = (int)c->fp.src_j;
+        a.sk = (int)c->fp.src_k;
+        a.amp = c->fp.src_amp;
+        a.delay = c->fp.src_delay;
+        a.width = c->fp.src_width;
+        a.counter = c->d_counter;
+        cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, &c->desc[0][0]);
+        if (e == cudaSuccess) e = fdtd_desc(c->dt, true, a, c->plan.block_x, &c->desc[0][1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "FDTD kernel set-up");
+    }
+    c->descs_ok = true;
+    return GS_OK;
+}
+
+// The kernel sequence of n iterations starting at buffer parity p, in
+// order.  Thermal: n/t launches of depth t, then n%t of depth 1 (each flips
+// the parity).  FDTD: H, E per iteration.
+template <typename F>
+void for_each_launch(gs_ctx* c, int64_t n, int p, F&& f) {
+    if (is_heat(c)) {
+        const int t = c->plan.temporal_depth;
+        const int64_t q = (t > 1) ? n / t : 0;
+        const int64_t r = n - q * t;
+        for (int64_t i = 0; i < q; ++i) { f(c->desc[1][p]); p ^= 1; }
+        for (int64_t i = 0; i < r; ++i) { f(c->desc[0][p]); p ^= 1; }
+    } else {
+        for (int64_t i = 0; i < n; ++i) { f(c->desc[0][0]); f(c->desc[0][1]); }
+    }
+}
+
+int64_t launches_for(const gs_ctx* c, int64_t n) {
+    if (!is_heat(c)) return 2 * n;
+    const int t = c->plan.temporal_depth;
+    const int64_t q = (t > 1) ? n / t : 0;
+    return q + (n - q * t);
+}
+
+int flip_of(const gs_ctx* c, int64_t n) { return is_heat(c) ? (int)(launches_for(c, n) & 1) : 0; }
+
+cudaError_t launch_one(gs_ctx* c, LaunchDesc& d) {
+    void* args[1] = {d.arg_ptr()};
+    if (!c->plan.use_pdl) return cudaLaunchKernel(d.func, d.grid, d.block, args, d.smem, c->stream);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = d.grid;
+    cfg.blockDim = d.block;
+    cfg.dynamicSmemBytes = d.smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, d.func, args);
+}
+
+// Build one executable graph of S iterations from parity p: the paper's
+// manual creation of a linear chain (Listing 3, "Building"), optionally
+// with programmatic edges, then instantiate and upload.
+gs_status build_graph(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
+    cudaGraph_t g = nullptr;
+    GS_CUDA(c, cudaGraphCreate(&g, 0));
+    cudaGraphNode_t prev = nullptr;
+    int64_t nodes = 0;
+    cudaError_t err = cudaSuccess;
+    cudaGraphEdgeData edge{};
+    edge.from_port = cudaGraphKernelNodePortProgrammatic;
+    edge.to_port = 0;
+    edge.type = cudaGraphDependencyTypeProgrammatic;
+    for_each_launch(c, S, p, [&](LaunchDesc& d) {
+        if (err != cudaSuccess) return;
+        cudaKernelNodeParams np{};
+        void* args[1] = {d.arg_ptr()};
+        np.func = const_cast<void*>(d.func);
+        np.gridDim = d.grid;
+        np.blockDim = d.block;
+        np.sharedMemBytes = (unsigned)d.smem;
+        np.kernelParams = args;
+        np.extra = nullptr;
+        cudaGraphNode_t node;
+        if (c->plan.use_pdl && prev) {
+            err = cudaGraphAddKernelNode(&node, g, nullptr, 0, &np);
+            if (err == cudaSuccess) err = cudaGraphAddDependencies(g, &prev, &node, &edge, 1);
+        } else {
+            err = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &np);
+        }
+        prev = node;
+        ++nodes;
+    });
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, err, "cudaGraphAddKernelNode");
+    }
+    cudaGraphExec_t exec = nullptr;
+    const unsigned long long flags = c->plan.device_launch ? cudaGraphInstantiateFlagDeviceLaunch : 0;
+    err = cudaGraphInstantiateWithFlags(&exec, g, flags);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, err, "cudaGraphInstantiateWithFlags");
+    }
+    err = cudaGraphUpload(exec, c->stream);
+    if (err != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(g);
+        return cuda_fail(c, err, "cudaGraphUpload");
+    }
+    out->graph = g;
+    out->exec = exec;
+    out->nodes = nodes;
+    c->stats.graphs_built += 1;
+    return GS_OK;
+}
+
+gs_status ensure_graph(gs_ctx* c, int64_t S, int p, GraphEntry** out) {
+    auto key = std::make_pair(S, p);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        GraphEntry e;
+        gs_status st = build_graph(c, S, p, &e);
+        if (st != GS_OK) return st;
+        it = c->graphs.emplace(key, e).first;
+    }
+    *out = &it->second;
+    return GS_OK;
+}
+
+gs_status launch_graphs(gs_ctx* c, int64_t S, int64_t count) {
+    const int fl = flip_of(c, S);
+    for (int64_t i = 0; i < count; ++i) {
+        GraphEntry* e;
+        gs_status st = ensure_graph(c, S, c->parity, &e);
+        if (st != GS_OK) return st;
+        GS_CUDA(c, cudaGraphLaunch(e->exec, c->stream));
+        c->stats.graph_launches += 1;
+        c->parity ^= fl;
+    }
+    return GS_OK;
+}
+
+gs_status ensure_staging(gs_ctx* c, size_t bytes) {
+    if (c->staging_bytes >= bytes) return GS_OK;
+    if (c->staging) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->staging);
+        c->staging = nullptr;
+        c->staging_bytes = 0;
+    }
+    GS_CUDA(c, cudaMalloc(&c->staging, bytes));
+    c->staging_bytes = bytes;
+    return GS_OK;
+}
+
+bool finite_all(const float* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+namespace gs {
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+}  // namespace gs
+
+// ------------------------------------------------------------- C ABI -----
+
+extern "C" {
+
+int gs_version(void) { return 100; }
+
+const char* gs_status_string(gs_status s) {
+    switch (s) {
+        case GS_OK: return "GS_OK";
+        case GS_ERR_INVALID_ARG: return "GS_ERR_INVALID_ARG";
+        case GS_ERR_CUDA: return "GS_ERR_CUDA";
+        case GS_ERR_OOM: return "GS_ERR_OOM";
+        case GS_ERR_STATE: return "GS_ERR_STATE";
+        case GS_ERR_TIMEOUT: return "GS_ERR_TIMEOUT";
+        case GS_ERR_NUMERIC: return "GS_ERR_NUMERIC";
+        case GS_ERR_UNSUPPORTED: return "GS_ERR_UNSUPPORTED";
+    }
+    return "GS_ERR_UNKNOWN";
+}
+
+const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+gs_status gs_required_pitch(gs_dtype dtype, int64_t width, int64_t* pitch_out) {
+    if (!pitch_out || width < 1 || (dtype != GS_F32 && dtype != GS_BF16 && dtype != GS_F16))
+        return GS_ERR_INVALID_ARG;
+    const int64_t v = vec_elems(dtype);
+    *pitch_out = (width + v - 1) / v * v;
+    return GS_OK;
+}
+
+gs_status gs_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc,
+                    void* stream) {
+    if (!out) return fail(nullptr, GS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (kind != GS_HEAT2D && kind != GS_HEAT3D && kind != GS_FDTD3D)
+        return fail(nullptr, GS_ERR_INVALID_ARG, "unknown kind");
+    if (storage != GS_F32 && storage != GS_BF16 && storage != GS_F16)
+        return fail(nullptr, GS_ERR_INVALID_ARG, "unknown storage dtype");
+    const int64_t lim = int64_t(1) << 20;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > lim || ny > lim || nz > lim)
+        return fail(nullptr, GS_ERR_INVALID_ARG, "grid sizes must be in [1, 2^20]");
+    if (kind == GS_HEAT2D && nz != 1) return fail(nullptr, GS_ERR_INVALID_ARG, "GS_HEAT2D needs nz == 1");
+    if (kind == GS_FDTD3D && (nx != ny || ny != nz))
+        return fail(nullptr, GS_ERR_INVALID_ARG, "GS_FDTD3D needs a cubic grid (nx == ny == nz)");
+    const int64_t w = (kind == GS_FDTD3D) ? nx + 1 : nx;
+    const int64_t rows = (kind == GS_FDTD3D) ? (nx + 1) * (nx + 1) : ny * nz;
+    if ((double)(w + 8) * (double)rows >= 2147483647.0)
+        return fail(nullptr, GS_ERR_INVALID_ARG, "field too large (needs >= 2^31 elements)");
+    if (kind == GS_FDTD3D && bc != GS_BC_PEC) return fail(nullptr, GS_ERR_INVALID_ARG, "GS_FDTD3D needs GS_BC_PEC");
+    if (kind != GS_FDTD3D && bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0)
+        return fail(nullptr, GS_ERR_INVALID_ARG, "thermal kinds need GS_BC_CLAMP or GS_BC_DIRICHLET0");
+
+    gs_ctx* c = new (std::nothrow) gs_ctx();
+    if (!c) return fail(nullptr, GS_ERR_OOM, "host allocation failed");
+    c->kind = kind;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->dt = storage;
+    c->bc = bc;
+    c->fp = gs_fdtd_params{0.5f, 0, nx / 2, nx / 2, nx / 2, 1.0f, 60.0f, 20.0f};
+    c->plan = default_plan(c);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            c->stream = static_cast<cudaStream_t>(stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess && kind == GS_FDTD3D) {
+        e = cudaMalloc(&c->d_counter, sizeof(long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, sizeof(long long), c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e != cudaSuccess) {
+        gs_status st = cuda_fail(nullptr, e, "context set-up");
+        gs_destroy(c);
+        return st;
+    }
+    *out = c;
+    return GS_OK;
+}
+
+gs_status gs_destroy(gs_ctx* c) {
+    if (!c) return GS_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    destroy_graphs(c);
+    if (c->d_counter) cudaFree(c->d_counter);
+    if (c->staging) cudaFree(c->staging);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return GS_OK;
+}
+
+gs_status gs_set_heat_coeffs(gs_ctx* c, const gs_heat_coeffs* hc) {
+    if (!c || !hc) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    if (!is_heat(c)) return fail(c, GS_ERR_INVALID_ARG, "not a thermal context");
+    if (!finite_all(&hc->k, 6)) return fail(c, GS_ERR_NUMERIC, "non-finite coefficient");
+    c->hc = *hc;
+    invalidate(c);
+    return GS_OK;
+}
+
+gs_status gs_set_fdtd_params(gs_ctx* c, const gs_fdtd_params* p) {
+    if (!c || !p) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    if (c->kind != GS_FDTD3D) return fail(c, GS_ERR_INVALID_ARG, "not an FDTD context");
+    const float f[4] = {p->courant, p->src_amp, p->src_delay, p->src_width};
+    if (!finite_all(f, 4)) return fail(c, GS_ERR_NUMERIC, "non-finite parameter");
+    if (p->src_width == 0.0f) return fail(c, GS_ERR_INVALID_ARG, "src_width must be non-zero");
+    if (p->src_on != 0 && p->src_on != 1) return fail(c, GS_ERR_INVALID_ARG, "src_on must be 0 or 1");
+    const int64_t N = c->nx;
+    if (p->src_i < 0 || p->src_j < 0 || p->src_k < 0 || p->src_i > N || p->src_j > N || p->src_k > N)
+        return fail(c, GS_ERR_INVALID_ARG, "source cell outside the (N+1)^3 arrays");
+    c->fp = *p;
+    invalidate(c);
+    return GS_OK;
+}
+
+gs_status gs_set_plan(gs_ctx* c, const gs_plan* plan) {
+    if (!c || !plan) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    gs_plan p = *plan;
+    gs_status st = validate_plan(c, &p);
+    if (st != GS_OK) return st;
+    c->plan = p;
+    invalidate(c);
+    return GS_OK;
+}
+
+gs_status gs_get_plan(const gs_ctx* c, gs_plan* out) {
+    if (!c || !out) return GS_ERR_INVALID_ARG;
+    *out = c->plan;
+    return GS_OK;
+}
+
+gs_status gs_bind_field(gs_ctx* c, gs_field id, void* ptr, int64_t pitch) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    const int f = resolve(c, id);
+    int64_t width, rows;
+    if (f < 0 || f > GS_FIELD_HZ || !field_shape(c, f, &width, &rows))
+        return fail(c, GS_ERR_INVALID_ARG, "field id not valid for this context kind");
+    if (ptr) {
+        if (reinterpret_cast<uintptr_t>(ptr) % 16)
+            return fail(c, GS_ERR_INVALID_ARG, "field pointer must be 16-byte aligned");
+        if (pitch < width || pitch % vec_elems(c->dt))
+            return fail(c, GS_ERR_INVALID_ARG,
+                        "pitch must be >= " + std::to_string(width) + " and a multiple of 16 bytes");
+        cudaPointerAttributes attr;
+        cudaError_t e = cudaPointerGetAttributes(&attr, ptr);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaPointerGetAttributes");
+        if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+            return fail(c, GS_ERR_INVALID_ARG, "field pointer is not device memory");
+    }
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->ptr[f] = ptr;
+    c->pitch[f] = ptr ? pitch : 0;
+    invalidate(c);
+    return GS_OK;
+}
+
+gs_status gs_upload(gs_ctx* c, gs_field id, const float* host, int64_t n) {
+    if (!c || !host) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    const int f = resolve(c, id);
+    int64_t width, rows;
+    if (f < 0 || f > GS_FIELD_HZ || !field_shape(c, f, &width, &rows))
+        return fail(c, GS_ERR_INVALID_ARG, "field id not valid for this context kind");
+    if (!c->ptr[f]) return fail(c, GS_ERR_STATE, "field is not bound");
+    if (n != width * rows)
+        return fail(c, GS_ERR_INVALID_ARG, "n must equal the dense element count " + std::to_string(width * rows));
+    if (c->dt == GS_F32) {
+        GS_CUDA(c, cudaMemcpy2DAsync(c->ptr[f], c->pitch[f] * 4, host, width * 4, width * 4, rows,
+                                     cudaMemcpyHostToDevice, c->stream));
+    } else {
+        gs_status st = ensure_staging(c, (size_t)n * sizeof(float));
+        if (st != GS_OK) return st;
+        GS_CUDA(c, cudaMemcpyAsync(c->staging, host, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        GS_CUDA(c, convert_to_storage(c->dt, c->staging, c->ptr[f], width, rows, c->pitch[f], c->stream));
+    }
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+gs_status gs_read_field(gs_ctx* c, gs_field id, float* host_out, int64_t n) {
+    if (!c || !host_out) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    const int f = resolve(c, id);
+    int64_t width, rows;
+    if (f < 0 || f > GS_FIELD_HZ || !field_shape(c, f, &width, &rows))
+        return fail(c, GS_ERR_INVALID_ARG, "field id not valid for this context kind");
+    if (!c->ptr[f]) return fail(c, GS_ERR_STATE, "field is not bound");
+    if (n != width * rows)
+        return fail(c, GS_ERR_INVALID_ARG, "n must equal the dense element count " + std::to_string(width * rows));
+    if (c->dt == GS_F32) {
+        GS_CUDA(c, cudaMemcpy2DAsync(host_out, width * 4, c->ptr[f], c->pitch[f] * 4, width * 4, rows,
+                                     cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        gs_status st = ensure_staging(c, (size_t)n * sizeof(float));
+        if (st != GS_OK) return st;
+        GS_CUDA(c, convert_from_storage(c->dt, c->ptr[f], c->staging, width, rows, c->pitch[f], c->stream));
+        GS_CUDA(c, cudaMemcpyAsync(host_out, c->staging, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    }
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
+gs_status gs_get_parity(const gs_ctx* c, int32_t* out) {
+    if (!c || !out) return GS_ERR_INVALID_ARG;
+    *out = c->parity;
+    return GS_OK;
+}
+
+gs_status gs_set_parity(gs_ctx* c, int32_t parity) {
+    if (!c || (parity != 0 && parity != 1)) return fail(c, GS_ERR_INVALID_ARG, "parity must be 0 or 1");
+    if (!is_heat(c)) return fail(c, GS_ERR_INVALID_ARG, "parity applies to thermal contexts only");
+    c->parity = parity;
+    return GS_OK;
+}
+
+gs_status gs_set_time(gs_ctx* c, int64_t n) {
+    if (!c || n < 0) return fail(c, GS_ERR_INVALID_ARG, "time must be >= 0");
+    c->time = n;
+    if (c->d_counter) {
+        const long long v = n;
+        GS_CUDA(c, cudaMemcpyAsync(c->d_counter, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return GS_OK;
+}
+
+gs_status gs_get_time(const gs_ctx* c, int64_t* out) {
+    if (!c || !out) return GS_ERR_INVALID_ARG;
+    *out = c->time;
+    return GS_OK;
+}
+
+gs_status gs_step(gs_ctx* c, int64_t n_iters, int64_t batch_size) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (n_iters < 0 || batch_size < 0) return fail(c, GS_ERR_INVALID_ARG, "n_iters and batch_size must be >= 0");
+    gs_status st = ensure_descs(c);
+    if (st != GS_OK) return st;
+    if (n_iters == 0) return GS_OK;
+    if (batch_size == 0) {
+        // Listing 1: one launch per iteration (per fused group of depth t).
+        cudaError_t err = cudaSuccess;
+        int64_t launched = 0;
+        for_each_launch(c, n_iters, c->parity, [&](LaunchDesc& d) {
+            if (err == cudaSuccess) {
+                err = launch_one(c, d);
+                ++launched;
+            }
+        });
+        c->stats.kernel_launches += launched;
+        if (err != cudaSuccess) return cuda_fail(c, err, "kernel launch");
+        c->parity ^= flip_of(c, n_iters);
+    } else {
+        // Listing 3 plus loop peeling: floor(n/S) graph launches of S
+        // iterations, then one remainder graph of n mod S iterations.
+        const int64_t nb = n_iters / batch_size;
+        const int64_t r = n_iters - nb * batch_size;
+        if (nb > 0) {
+            st = launch_graphs(c, batch_size, nb);
+            if (st != GS_OK) return st;
+        }
+        if (r > 0) {
+            st = launch_graphs(c, r, 1);
+            if (st != GS_OK) return st;
+        }
+    }
+    c->time += n_iters;
+    c->stats.iterations += n_iters;
+    return GS_OK;
+}
+
+gs_status gs_graph_build(gs_ctx* c, int64_t S) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (S < 1) return fail(c, GS_ERR_INVALID_ARG, "batch_size must be >= 1");
+    gs_status st = ensure_descs(c);
+    if (st != GS_OK) return st;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int fl = flip_of(c, S);
+    for (int p = 0; p < 2; ++p) {
+        auto it = c->graphs.find(std::make_pair(S, p));
+        if (it != c->graphs.end()) {
+            cudaGraphExecDestroy(it->second.exec);
+            cudaGraphDestroy(it->second.graph);
+            c->graphs.erase(it);
+        }
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    GraphEntry* e = nullptr;
+    st = ensure_graph(c, S, c->parity, &e);
+    if (st == GS_OK && fl) st = ensure_graph(c, S, c->parity ^ 1, &e);
+    if (st != GS_OK) return st;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    const auto t1 = std::chrono::steady_clock::now();
+    c->stats.last_build_seconds = std::chrono::duration<double>(t1 - t0).count();
+    c->stats.last_build_nodes = e->nodes;
+    c->built_S = S;
+    return GS_OK;
+}
+
+gs_status gs_graph_launch(gs_ctx* c, int64_t n_launches) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (n_launches < 0) return fail(c, GS_ERR_INVALID_ARG, "n_launches must be >= 0");
+    if (c->built_S == 0) return fail(c, GS_ERR_STATE, "no graph built (call gs_graph_build first)");
+    gs_status st = launch_graphs(c, c->built_S, n_launches);
+    if (st != GS_OK) return st;
+    c->time += c->built_S * n_launches;
+    c->stats.iterations += c->built_S * n_launches;
+    return GS_OK;
+}
+
+gs_status gs_graph_destroy(gs_ctx* c) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    destroy_graphs(c);
+    return GS_OK;
+}
+
+gs_status gs_sync(gs_ctx* c) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    GS_CUDA(c, cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status gs_get_stats(const gs_ctx* c, gs_stats* out) {
+    if (!c || !out) return GS_ERR_INVALID_ARG;
+    *out = c->stats;
+    return GS_OK;
+}
+
+}  // extern "C"

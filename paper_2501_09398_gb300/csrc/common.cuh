@@ -1,0 +1,148 @@
+// Internal declarations shared by the library's translation units (not part
+// of the public C ABI; see include/graphstep.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "graphstep.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------- storage --
+// Fields are stored as f32, bf16 or f16; every kernel loads 16-byte vectors,
+// widens to f32, computes in f32 and rounds to nearest even on store.
+
+template <typename ST> struct Vec;  // elements per 16-byte vector
+
+template <> struct Vec<float> { static constexpr int N = 4; };
+template <> struct Vec<__nv_bfloat16> { static constexpr int N = 8; };
+template <> struct Vec<__half> { static constexpr int N = 8; };
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+template <typename ST> __device__ __forceinline__ ST from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// 16-byte vector load through the read-only path.
+template <typename ST>
+__device__ __forceinline__ void load_vec(const ST* __restrict__ p, float (&v)[Vec<ST>::N]) {
+    const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+    const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+    for (int i = 0; i < Vec<ST>::N; ++i) v[i] = to_f32(e[i]);
+}
+
+// 16-byte vector load through the coherent path (for in-place updates).
+template <typename ST>
+__device__ __forceinline__ void load_vec_rw(const ST* p, float (&v)[Vec<ST>::N]) {
+    const uint4 raw = *reinterpret_cast<const uint4*>(p);
+    const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+    for (int i = 0; i < Vec<ST>::N; ++i) v[i] = to_f32(e[i]);
+}
+
+// Store a vector; `n_valid` < N stores only the first n_valid elements.
+template <typename ST>
+__device__ __forceinline__ void store_vec(ST* p, const float (&v)[Vec<ST>::N], int n_valid) {
+    constexpr int N = Vec<ST>::N;
+    if (n_valid >= N) {
+        uint4 raw;
+        ST* e = reinterpret_cast<ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < N; ++i) e[i] = from_f32<ST>(v[i]);
+        *reinterpret_cast<uint4*>(p) = raw;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < n_valid) p[i] = from_f32<ST>(v[i]);
+    }
+}
+
+template <typename ST>
+__device__ __forceinline__ float load_scalar(const ST* p) { return to_f32(__ldg(p)); }
+
+// Programmatic dependent launch: a kernel first waits until the grid it
+// depends on has completed and its memory is visible, then lets its own
+// dependent start launching.  Waiting first keeps the early launch to one
+// kernel ahead (triggering first would let the whole chain launch at once
+// and fill the SMs with waiting blocks).  Both are no-ops when the launch
+// had no programmatic dependency.
+__device__ __forceinline__ void pdl_wait_then_trigger() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// ---------------------------------------------------------- kernel args --
+
+struct HeatCoef {
+    float k, cx, cy, cz, cz2, t_amb;
+};
+
+struct HeatArgs {
+    const void* Tin;
+    void* Tout;
+    const void* P;
+    int nx, ny, nz;
+    int rows;            // y rows per block (depth-1 kernels)
+    long long pitch;     // elements per row
+    long long plane;     // elements per z plane (pitch * ny)
+    long long p_pitch;   // elements per row of P
+    int tile_x, tile_y;  // output tile (temporal kernels)
+    HeatCoef c;
+};
+
+struct FdtdArgs {
+    void* f[6];           // Ex, Ey, Ez, Hx, Hy, Hz
+    int N;
+    int kc;               // k planes per block
+    long long pitch;      // elements per row (>= N+1)
+    long long plane;      // pitch * (N+1)
+    float s;              // courant number
+    int src_on;
+    int si, sj, sk;
+    float amp, delay, width;
+    long long* counter;   // device step counter (E kernel, source owner)
+};
+
+// A ready-to-launch kernel: host stub, launch shape and its single by-value
+// argument (every kernel here takes exactly one struct argument).
+struct LaunchDesc {
+    const void* func = nullptr;
+    dim3 grid, block;
+    size_t smem = 0;
+    alignas(16) unsigned char args[256];
+    size_t args_size = 0;
+
+    template <typename A> void set_args(const A& a) {
+        static_assert(sizeof(A) <= sizeof(args), "kernel args too large");
+        memcpy(args, &a, sizeof(A));
+        args_size = sizeof(A);
+    }
+    void* arg_ptr() { return args; }
+};
+
+// Kernel factories implemented in heat.cu / fdtd.cu / convert.cu.  They
+// return cudaSuccess or the first CUDA error (e.g. from setting the dynamic
+// shared memory limit), and cudaErrorInvalidValue for unsupported shapes.
+// Thermal kernel variants (gs_plan.kernel).
+constexpr int kWaveMaxNz = 16;  // wavefront kernel holds all planes in one block
+cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, int block_x, int depth, int variant,
+                      LaunchDesc* out);
+size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth);
+size_t heat_wave_smem(int nz3d, int depth, int vec);
+cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, LaunchDesc* out);
+cudaError_t convert_to_storage(gs_dtype dt, const float* src, void* dst, long long width, long long rows,
+                               long long pitch, cudaStream_t st);
+cudaError_t convert_from_storage(gs_dtype dt, const void* src, float* dst, long long width, long long rows,
+                                 long long pitch, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace gs

@@ -1,0 +1,526 @@
+// Thermal stencil kernels: 2D 5-point and 3D 7-point explicit updates (the
+// roles of Rodinia Hotspot / Hotspot3D in the paper's Sec. III-C), one step
+// per launch (depth 1) or t steps per launch on an overlapped shared-memory
+// tile (temporal blocking, depth 2 or 4).
+//
+// Update (per cell, FP32):
+//   T' = T + k*(P + cy*(N+S-2T) + cx*(E+W-2T) + cz*(t_amb-T) [+ cz2*(U+D-2T)])
+// Every kernel evaluates it through heat_cell(), whose operations are spelled
+// with explicit round-to-nearest intrinsics (no contraction or reassociation
+// is possible), so depth-1, temporally blocked, per-step and graph runs are
+// bit-identical.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gs {
+
+template <bool IS3D>
+__device__ __forceinline__ float heat_cell(float t, float n, float s, float w, float e, float d, float u, float p,
+                                           const HeatCoef& c) {
+    float acc = p;
+    acc = __fmaf_rn(c.cy, __fmaf_rn(-2.0f, t, __fadd_rn(n, s)), acc);
+    acc = __fmaf_rn(c.cx, __fmaf_rn(-2.0f, t, __fadd_rn(w, e)), acc);
+    acc = __fmaf_rn(c.cz, __fsub_rn(c.t_amb, t), acc);
+    if (IS3D) acc = __fmaf_rn(c.cz2, __fmaf_rn(-2.0f, t, __fadd_rn(d, u)), acc);
+    return __fmaf_rn(c.k, acc, t);
+}
+
+// 16-byte shared-memory row segments (V is 4 or 8 floats).
+template <int V>
+__device__ __forceinline__ void sm_put(float* p, const float (&v)[V]) {
+#pragma unroll
+    for (int i = 0; i < V; i += 4) *reinterpret_cast<float4*>(p + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
+template <int V>
+__device__ __forceinline__ void sm_get(const float* p, float (&v)[V]) {
+#pragma unroll
+    for (int i = 0; i < V; i += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p + i);
+        v[i] = q.x; v[i + 1] = q.y; v[i + 2] = q.z; v[i + 3] = q.w;
+    }
+}
+
+// Value a missing neighbour reads: the cell itself (clamp) or 0 (Dirichlet-0).
+template <int BC>
+__device__ __forceinline__ float bnd(float self) {
+    return BC == GS_BC_CLAMP ? self : 0.0f;
+}
+
+// ------------------------------------------------------------ depth 1 ----
+//
+// Block = blockDim.x threads along x (each owning one 16-byte vector of V
+// cells) x blockDim.y z-planes (3D).  The block marches `rows` rows in y;
+// each thread keeps rows y-1, y, y+1 of its vector in registers and issues
+// the loads of row y+2 (and P, edge scalars, z-halo rows of row y+1) one
+// iteration ahead.  x-neighbours come from warp shuffles (lanes 0/31 load
+// one scalar each); z-neighbours come from a double-buffered shared-memory
+// row per plane.
+template <typename ST, int BC, bool IS3D>
+__global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
+    constexpr int V = Vec<ST>::N;
+    extern __shared__ float zsm[];  // [2][ZB+2][BX*V] (3D only)
+    pdl_wait_then_trigger();
+
+    const int BX = blockDim.x;
+    const int tx = threadIdx.x;
+    const int lane = tx & 31;
+    const int x0 = (blockIdx.x * BX + tx) * V;
+    const int nx = a.nx, ny = a.ny;
+    const int ZB = IS3D ? (int)blockDim.y : 1;
+    const int tz = IS3D ? (int)threadIdx.y : 0;
+    const int z0 = IS3D ? (int)blockIdx.z * ZB : 0;
+    const int z = z0 + tz;
+    const bool act = (x0 < nx) && (!IS3D || z < a.nz);
+    const bool has_p = !IS3D || z == 0;
+    const bool dn_halo = IS3D && tz == 0 && z0 > 0 && x0 < nx;
+    const bool up_halo = IS3D && tz == ZB - 1 && z0 + ZB < a.nz && x0 < nx;
+    const int y0 = blockIdx.y * a.rows;
+    const int y1 = min(y0 + a.rows, ny);
+
+    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
+    ST* __restrict__ Tout = static_cast<ST*>(a.Tout);
+    const ST* __restrict__ P = static_cast<const ST*>(a.P);
+    const long long zoff = IS3D ? (long long)z * a.plane : 0;
+    const ST* col = Tin + zoff + x0;      // this thread's vector, row 0
+    const ST* pcol = P + x0;
+    const ST* dcol = Tin + zoff - a.plane + x0;  // plane z0-1 (tz == 0)
+    const ST* ucol = Tin + zoff + a.plane + x0;  // plane z0+ZB (tz == ZB-1)
+
+    float prv[V], cur[V], nxt[V], pc[V], dc[V], uc[V];
+    float wl = 0.f, er = 0.f;
+#pragma unroll
+    for (int i = 0; i < V; ++i) { cur[i] = 0.f; pc[i] = 0.f; dc[i] = 0.f; uc[i] = 0.f; }
+
+    // Prologue: rows y0-1, y0, y0+1 and the per-row extras of row y0.
+    if (act) load_vec(col + (long long)y0 * a.pitch, cur);
+    if (act && y0 > 0) {
+        load_vec(col + (long long)(y0 - 1) * a.pitch, prv);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) prv[i] = bnd<BC>(cur[i]);
+    }
+    if (act && y0 + 1 < ny) {
+        load_vec(col + (long long)(y0 + 1) * a.pitch, nxt);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) nxt[i] = bnd<BC>(cur[i]);
+    }
+    if (act && has_p) load_vec(pcol + (long long)y0 * a.p_pitch, pc);
+    if (act && lane == 0 && x0 > 0) wl = load_scalar(col + (long long)y0 * a.pitch - 1);
+    if (act && lane == 31 && x0 + V < nx) er = load_scalar(col + (long long)y0 * a.pitch + V);
+    if (dn_halo) load_vec(dcol + (long long)y0 * a.pitch, dc);
+    if (up_halo) load_vec(ucol + (long long)y0 * a.pitch, uc);
+
+    const int rowlen = BX * V;
+    for (int y = y0; y < y1; ++y) {
+        // Issue the loads the next iteration needs.
+        const bool more = (y + 1 < y1);
+        float nn[V], pn[V], dn[V], un[V];
+        float wln = 0.f, ern = 0.f;
+#pragma unroll
+        for (int i = 0; i < V; ++i) { nn[i] = 0.f; pn[i] = 0.f; dn[i] = 0.f; un[i] = 0.f; }
+        if (act && more && y + 2 < ny) load_vec(col + (long long)(y + 2) * a.pitch, nn);
+        if (act && more && has_p) load_vec(pcol + (long long)(y + 1) * a.p_pitch, pn);
+        if (act && more && lane == 0 && x0 > 0) wln = load_scalar(col + (long long)(y + 1) * a.pitch - 1);
+        if (act && more && lane == 31 && x0 + V < nx) ern = load_scalar(col + (long long)(y + 1) * a.pitch + V);
+        if (dn_halo && more) load_vec(dcol + (long long)(y + 1) * a.pitch, dn);
+        if (up_halo && more) load_vec(ucol + (long long)(y + 1) * a.pitch, un);
+
+        // x-neighbours across the vector edges.
+        float w0 = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+        float eV = __shfl_down_sync(0xffffffffu, cur[0], 1);
+        if (lane == 0) w0 = wl;
+        if (lane == 31) eV = er;
+
+        // z-neighbours through shared memory.
+        float dv[V], uv[V];
+        if (IS3D) {
+            float* buf = zsm + (size_t)(y & 1) * (ZB + 2) * rowlen + tx * V;
+            sm_put<V>(buf + (tz + 1) * rowlen, cur);
+            if (tz == 0) sm_put<V>(buf, dc);
+            if (tz == ZB - 1) sm_put<V>(buf + (ZB + 1) * rowlen, uc);
+            __syncthreads();
+            sm_get<V>(buf + tz * rowlen, dv);
+            sm_get<V>(buf + (tz + 2) * rowlen, uv);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if (z == 0) dv[i] = bnd<BC>(cur[i]);
+                if (z + 1 >= a.nz) uv[i] = bnd<BC>(cur[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) { dv[i] = 0.f; uv[i] = 0.f; }
+        }
+
+        if (act) {
+            float out[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const int x = x0 + i;
+                const float t = cur[i];
+                float w = (i == 0) ? w0 : cur[i - 1];
+                float e = (i == V - 1) ? eV : cur[i + 1];
+                if (x == 0) w = bnd<BC>(t);
+                if (x + 1 >= nx) e = bnd<BC>(t);
+                out[i] = heat_cell<IS3D>(t, prv[i], nxt[i], w, e, dv[i], uv[i], has_p ? pc[i] : 0.0f, a.c);
+            }
+            store_vec(Tout + zoff + (long long)y * a.pitch + x0, out, nx - x0);
+        }
+
+        // Rotate the row window.
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            prv[i] = cur[i];
+            cur[i] = nxt[i];
+            nxt[i] = (y + 2 < ny) ? nn[i] : bnd<BC>(cur[i]);
+            pc[i] = pn[i];
+            dc[i] = dn[i];
+            uc[i] = un[i];
+        }
+        wl = wln;
+        er = ern;
+    }
+}
+
+// ----------------------------------------------------- temporal blocking --
+//
+// One block owns an output tile of tile_x x tile_y columns (all nz layers).
+// It loads the tile plus a halo of width D into shared memory, advances D
+// steps there (the valid region shrinks by one cell per side per step), and
+// writes the tile interior.  Cells outside the grid are never read by valid
+// cells: boundary neighbours are selected by global coordinates exactly as
+// in the depth-1 kernel, and the same heat_cell() does the arithmetic, so
+// one depth-D launch equals D depth-1 launches bit for bit.
+//
+// Shared memory: two buffers of nz*(tile_y+2D)*(tile_x+2D) floats plus the
+// P tile of (tile_y+2D)*(tile_x+2D) floats.
+template <typename ST, int BC, bool IS3D, int D>
+__global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
+    extern __shared__ float tsm[];
+    pdl_wait_then_trigger();
+
+    const int IX = a.tile_x + 2 * D;
+    const int IY = a.tile_y + 2 * D;
+    const int nz = IS3D ? a.nz : 1;
+    const int area = IX * IY;
+    const int vol = area * nz;
+    float* bufA = tsm;
+    float* bufB = tsm + vol;
+    float* ptile = tsm + 2 * vol;
+    const int gx0 = blockIdx.x * a.tile_x - D;  // global x of local ix = 0
+    const int gy0 = blockIdx.y * a.tile_y - D;
+    const int nx = a.nx, ny = a.ny;
+    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
+    ST* __restrict__ Tout = static_cast<ST*>(a.Tout);
+    const ST* __restrict__ P = static_cast<const ST*>(a.P);
+    const int nthr = blockDim.x;
+
+    // Load the input region (cells outside the grid are left as 0).
+    for (int idx = threadIdx.x; idx < vol; idx += nthr) {
+        const int ix = idx % IX;
+        const int iy = (idx / IX) % IY;
+        const int iz = idx / area;
+        const int gx = gx0 + ix, gy = gy0 + iy;
+        float v = 0.f;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+            v = load_scalar(Tin + (long long)iz * a.plane + (long long)gy * a.pitch + gx);
+        bufA[idx] = v;
+    }
+    for (int idx = threadIdx.x; idx < area; idx += nthr) {
+        const int ix = idx % IX;
+        const int iy = idx / IX;
+        const int gx = gx0 + ix, gy = gy0 + iy;
+        float v = 0.f;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) v = load_scalar(P + (long long)gy * a.p_pitch + gx);
+        ptile[idx] = v;
+    }
+    __syncthreads();
+
+#pragma unroll 1
+    for (int s = 1; s <= D; ++s) {
+        const int wx = IX - 2 * s, wy = IY - 2 * s;
+        const int warea = wx * wy;
+        const int wvol = warea * nz;
+        for (int idx = threadIdx.x; idx < wvol; idx += nthr) {
+            const int ix = s + idx % wx;
+            const int iy = s + (idx / wx) % wy;
+            const int iz = idx / warea;
+            const int gx = gx0 + ix, gy = gy0 + iy;
+            if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
+            const int l = iz * area + iy * IX + ix;
+            const float t = bufA[l];
+            const float w = (gx > 0) ? bufA[l - 1] : bnd<BC>(t);
+            const float e = (gx + 1 < nx) ? bufA[l + 1] : bnd<BC>(t);
+            const float n = (gy > 0) ? bufA[l - IX] : bnd<BC>(t);
+            const float so = (gy + 1 < ny) ? bufA[l + IX] : bnd<BC>(t);
+            float d = 0.f, u = 0.f;
+            if (IS3D) {
+                d = (iz > 0) ? bufA[l - area] : bnd<BC>(t);
+                u = (iz + 1 < nz) ? bufA[l + area] : bnd<BC>(t);
+            }
+            const float p = (!IS3D || iz == 0) ? ptile[iy * IX + ix] : 0.0f;
+            bufB[l] = heat_cell<IS3D>(t, n, so, w, e, d, u, p, a.c);
+        }
+        __syncthreads();
+        float* sw = bufA;
+        bufA = bufB;
+        bufB = sw;
+    }
+
+    // Store the tile interior.
+    const int ovol = a.tile_x * a.tile_y * nz;
+    for (int idx = threadIdx.x; idx < ovol; idx += nthr) {
+        const int ox = idx % a.tile_x;
+        const int oy = (idx / a.tile_x) % a.tile_y;
+        const int iz = idx / (a.tile_x * a.tile_y);
+        const int gx = gx0 + D + ox, gy = gy0 + D + oy;
+        if (gx >= nx || gy >= ny) continue;
+        const float v = bufA[iz * area + (oy + D) * IX + (ox + D)];
+        Tout[(long long)iz * a.plane + (long long)gy * a.pitch + gx] = from_f32<ST>(v);
+    }
+}
+
+// ------------------------------------------------------------ wavefront --
+//
+// Temporal blocking without shared-memory tiles: each warp owns 32 vectors
+// of V cells along x (lanes 0 and 31 are halo lanes: loaded and computed but
+// never stored, so the stored span of a warp is 30*V cells and neighbouring
+// warps overlap by one vector on each side) and marches rows in y.  For
+// every time level s = 0..T-1 a thread keeps a 3-row window of its vector in
+// registers; at march step j (level-0 row r) level s computes row r - s from
+// level s-1's window, so one pass over the rows advances T steps.  The halo
+// lanes absorb the one cell of validity lost per level at each warp edge
+// (requires T <= V).  In 3D the block holds all nz planes (one warp row per
+// plane) and exchanges each level's newest row through a double-buffered
+// shared-memory row, with one barrier per march step.  A block marches
+// R + 2T level-0 rows to produce R output rows.
+//
+// Launch: 3D: block (32, nz), grid (x tiles, ceil(ny/R)).
+//         2D: block (32, WB) with WB independent warps stacked in y,
+//             grid (x tiles, ceil(ny/(R*WB))).
+template <typename ST, int BC, bool IS3D, int T>
+__global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
+    constexpr int V = Vec<ST>::N;
+    static_assert(T >= 1 && T <= V, "halo lane must cover T cells");
+    extern __shared__ float wsm[];  // 3D: [2][T][nz][32*V]
+    pdl_wait_then_trigger();
+
+    const int lane = threadIdx.x;
+    const int nx = a.nx, ny = a.ny;
+    const int R = a.rows;
+    const int stride = 30 * V;
+    const int xs = blockIdx.x * stride - V;       // global x of lane 0, element 0
+    const int x0 = xs + lane * V;                 // this lane's first cell
+    const int tz = IS3D ? (int)threadIdx.y : 0;
+    const int nz = IS3D ? a.nz : 1;
+    const int y0 = IS3D ? (int)blockIdx.y * R : ((int)blockIdx.y * (int)blockDim.y + (int)threadIdx.y) * R;
+    const bool has_p = !IS3D || tz == 0;
+    const bool ld_ok = (x0 >= 0) && (x0 < nx);   // vector lies (at least partly) in the grid
+    const bool st_lane = (lane >= 1) && (lane <= 30) && (x0 < nx);
+    const int rowlen = 32 * V;
+
+    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
+    ST* __restrict__ Tout = static_cast<ST*>(a.Tout);
+    const ST* __restrict__ P = static_cast<const ST*>(a.P);
+    const long long zoff = IS3D ? (long long)tz * a.plane : 0;
+    const ST* col = Tin + zoff + x0;
+    const ST* pcol = P + x0;
+
+    float win[T][3][V];
+    float pr[T + 1][V];
+#pragma unroll
+    for (int s = 0; s < T; ++s)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < V; ++i) win[s][k][i] = 0.f;
+#pragma unroll
+    for (int s = 0; s <= T; ++s)
+#pragma unroll
+        for (int i = 0; i < V; ++i) pr[s][i] = 0.f;
+
+    // prefetch of level-0 row r (and its P row)
+    float nrow[V], nprow[V];
+    const int rbeg = y0 - T;
+    const int nsteps = R + 2 * T;
+#pragma unroll
+    for (int i = 0; i < V; ++i) { nrow[i] = 0.f; nprow[i] = 0.f; }
+    if (ld_ok && rbeg >= 0 && rbeg < ny) {
+        load_vec(col + (long long)rbeg * a.pitch, nrow);
+        if (has_p) load_vec(pcol + (long long)rbeg * a.p_pitch, nprow);
+    }
+
+    for (int j = 0; j < nsteps; ++j) {
+        const int r = rbeg + j;
+        // shift in level-0 row r, issue the load of row r+1
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            win[0][0][i] = win[0][1][i];
+            win[0][1][i] = win[0][2][i];
+            win[0][2][i] = nrow[i];
+        }
+#pragma unroll
+        for (int s = T; s >= 1; --s)
+#pragma unroll
+            for (int i = 0; i < V; ++i) pr[s][i] = pr[s - 1][i];
+#pragma unroll
+        for (int i = 0; i < V; ++i) pr[0][i] = nprow[i];
+#pragma unroll
+        for (int i = 0; i < V; ++i) { nrow[i] = 0.f; nprow[i] = 0.f; }
+        if (ld_ok && r + 1 >= 0 && r + 1 < ny && j + 1 < nsteps) {
+            load_vec(col + (long long)(r + 1) * a.pitch, nrow);
+            if (has_p) load_vec(pcol + (long long)(r + 1) * a.p_pitch, nprow);
+        }
+
+        float* wbuf = nullptr;
+        const float* rbuf = nullptr;
+        if (IS3D) {
+            wbuf = wsm + (size_t)(j & 1) * T * nz * rowlen + lane * V;
+            rbuf = wsm + (size_t)((j + 1) & 1) * T * nz * rowlen + lane * V;
+            // After this barrier every thread has finished step j-1 (whose
+            // reads used buffer j&1) and the rows written at step j-1 (into
+            // buffer (j-1)&1) are visible.
+            __syncthreads();
+            sm_put<V>(wbuf + (size_t)tz * rowlen, win[0][2]);  // level 0, row r
+        }
+
+#pragma unroll
+        for (int s = 1; s <= T; ++s) {
+            const int q = r - s;  // row computed at this level
+            const float(&c)[V] = win[s - 1][1];
+            float w0 = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
+            float eV = __shfl_down_sync(0xffffffffu, c[0], 1);
+            float dv[V], uv[V];
+            if (IS3D) {
+                const float* lv = rbuf + (size_t)(s - 1) * nz * rowlen;
+                if (tz > 0) sm_get<V>(lv + (size_t)(tz - 1) * rowlen, dv);
+                if (tz + 1 < nz) sm_get<V>(lv + (size_t)(tz + 1) * rowlen, uv);
+            }
+            float out[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const int x = x0 + i;
+                const float t = c[i];
+                float w = (i == 0) ? w0 : c[i - 1];
+                float e = (i == V - 1) ? eV : c[i + 1];
+                if (x == 0) w = bnd<BC>(t);
+                if (x + 1 >= nx) e = bnd<BC>(t);
+                const float n = (q == 0) ? bnd<BC>(t) : win[s - 1][0][i];
+                const float so = (q + 1 >= ny) ? bnd<BC>(t) : win[s - 1][2][i];
+                float d = 0.f, u = 0.f;
+                if (IS3D) {
+                    d = (tz > 0) ? dv[i] : bnd<BC>(t);
+                    u = (tz + 1 < nz) ? uv[i] : bnd<BC>(t);
+                }
+                out[i] = heat_cell<IS3D>(t, n, so, w, e, d, u, has_p ? pr[s][i] : 0.0f, a.c);
+            }
+            if (s < T) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    win[s][0][i] = win[s][1][i];
+                    win[s][1][i] = win[s][2][i];
+                    win[s][2][i] = out[i];
+                }
+                if (IS3D) sm_put<V>(wbuf + ((size_t)s * nz + tz) * rowlen, out);
+            } else if (st_lane && q >= y0 && q < y0 + R && q < ny) {
+                store_vec(Tout + zoff + (long long)q * a.pitch + x0, out, nx - x0);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- factory ----
+
+size_t heat_wave_smem(int nz3d, int depth, int vec) {
+    return nz3d > 0 ? (size_t)2 * depth * nz3d * 32 * vec * sizeof(float) : 0;
+}
+
+size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth) {
+    const size_t area = (size_t)(tile_x + 2 * depth) * (tile_y + 2 * depth);
+    return (2 * area * (size_t)nz + area) * sizeof(float);
+}
+
+namespace {
+
+template <typename ST, int BC, bool IS3D>
+const void* pick_temporal(int depth) {
+    switch (depth) {
+        case 2: return (const void*)heat_temporal_kernel<ST, BC, IS3D, 2>;
+        case 4: return (const void*)heat_temporal_kernel<ST, BC, IS3D, 4>;
+        default: return nullptr;
+    }
+}
+
+template <typename ST, int BC, bool IS3D>
+const void* pick_wave(int depth) {
+    switch (depth) {
+        case 1: return (const void*)heat_wave_kernel<ST, BC, IS3D, 1>;
+        case 2: return (const void*)heat_wave_kernel<ST, BC, IS3D, 2>;
+        case 4: return (const void*)heat_wave_kernel<ST, BC, IS3D, 4>;
+        default: return nullptr;
+    }
+}
+
+template <typename ST, int BC>
+const void* pick(bool is3d, int depth, int variant) {
+    if (variant == GS_KERNEL_WAVE)
+        return is3d ? pick_wave<ST, BC, true>(depth) : pick_wave<ST, BC, false>(depth);
+    if (variant == GS_KERNEL_MARCH && depth == 1)
+        return is3d ? (const void*)heat_step_kernel<ST, BC, true> : (const void*)heat_step_kernel<ST, BC, false>;
+    if (variant == GS_KERNEL_TILE && depth > 1)
+        return is3d ? pick_temporal<ST, BC, true>(depth) : pick_temporal<ST, BC, false>(depth);
+    return nullptr;
+}
+
+template <typename ST>
+const void* pick_bc(gs_bc bc, bool is3d, int depth, int variant) {
+    return bc == GS_BC_CLAMP ? pick<ST, GS_BC_CLAMP>(is3d, depth, variant)
+                             : pick<ST, GS_BC_DIRICHLET0>(is3d, depth, variant);
+}
+
+int vec_elems(gs_dtype dt) { return dt == GS_F32 ? 4 : 8; }
+
+}  // namespace
+
+cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, int block_x, int depth, int variant,
+                      LaunchDesc* out) {
+    const bool is3d = (kind == GS_HEAT3D);
+    const void* f = nullptr;
+    switch (dt) {
+        case GS_F32: f = pick_bc<float>(bc, is3d, depth, variant); break;
+        case GS_BF16: f = pick_bc<__nv_bfloat16>(bc, is3d, depth, variant); break;
+        case GS_F16: f = pick_bc<__half>(bc, is3d, depth, variant); break;
+    }
+    if (!f) return cudaErrorInvalidValue;
+    out->func = f;
+    const int V = vec_elems(dt);
+    if (variant == GS_KERNEL_MARCH) {
+        const int zb = is3d ? std::min(std::min(a.nz, 16), std::max(1, 512 / block_x)) : 1;
+        out->block = dim3(block_x, zb, 1);
+        out->grid = dim3((a.nx + block_x * V - 1) / (block_x * V), (a.ny + a.rows - 1) / a.rows,
+                         is3d ? (a.nz + zb - 1) / zb : 1);
+        out->smem = is3d ? (size_t)2 * (zb + 2) * block_x * V * sizeof(float) : 0;
+    } else if (variant == GS_KERNEL_WAVE) {
+        if (is3d && a.nz > kWaveMaxNz) return cudaErrorInvalidValue;
+        const int stride = 30 * V;
+        const int wb = is3d ? a.nz : std::max(1, block_x / 32);
+        out->block = dim3(32, wb, 1);
+        const int ry = is3d ? a.rows : a.rows * wb;
+        out->grid = dim3((a.nx + stride - 1) / stride, (a.ny + ry - 1) / ry, 1);
+        out->smem = heat_wave_smem(is3d ? a.nz : 0, depth, V);
+    } else {
+        out->block = dim3(block_x, 1, 1);
+        out->grid = dim3((a.nx + a.tile_x - 1) / a.tile_x, (a.ny + a.tile_y - 1) / a.tile_y, 1);
+        out->smem = heat_temporal_smem(is3d ? a.nz : 1, a.tile_x, a.tile_y, depth);
+        if (out->smem > 227 * 1024) return cudaErrorInvalidValue;
+    }
+    if (out->smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+        if (e != cudaSuccess) return e;
+    }
+    out->set_args(a);
+    return cudaSuccess;
+}
+
+}  // namespace gs
