@@ -34,11 +34,17 @@ sys.path.insert(0, ROOT)
 
 import gs_inputs  # noqa: E402
 
+# Default launch plans per workload (the fastest measured on GB300; the
+# autotuner can re-derive them).  kernel: 1 = MARCH, 2 = WAVE.
 WORKLOADS = {
-    "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=1),
-    "heat2d-512": dict(kind="heat2d", nx=512, ny=512, nz=1, iters=1000, S=100, depth=1),
-    "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1),
-    "fdtd-128": dict(kind="fdtd", N=128, iters=5000, S=100, depth=1),
+    "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=1,
+                             plan=dict(kernel=1, block_x=64, rows=8)),
+    "heat2d-512": dict(kind="heat2d", nx=512, ny=512, nz=1, iters=1000, S=100, depth=1,
+                       plan=dict(kernel=1, block_x=64, rows=4)),
+    "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1,
+                        plan=dict(kernel=1, block_x=128, rows=32)),
+    "fdtd-128": dict(kind="fdtd", N=128, iters=5000, S=100, depth=1, plan={}),
+    "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=1, plan={}),
 }
 DEFAULT = "heat3d-512x512x8"
 METRIC = "cell-updates/s (graph-batched)"
@@ -54,7 +60,13 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def multi_sides(w):
+    return gs_inputs.instance_sides(w["n"], w["lo"], w["hi"], seed=0)
+
+
 def cells_of(w):
+    if w["kind"] == "multi":
+        return sum(s * s for s in multi_sides(w))
     return w["N"] ** 3 if w["kind"] == "fdtd" else w["nx"] * w["ny"] * w["nz"]
 
 
@@ -66,6 +78,8 @@ def algo_bytes_per_launch(w, depth, elem=4):
     (H or E kernel): read 6 components, write 3, per cell."""
     if w["kind"] == "fdtd":
         return cells_of(w) * 9 * elem
+    if w["kind"] == "multi":
+        return cells_of(w) * 3 * elem
     plane = w["nx"] * w["ny"]
     return cells_of(w) * 2 * elem + plane * elem
 
@@ -82,6 +96,12 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        if os.environ.get("CUDA_INJECTION64_PATH"):
+            # under a profiler's injection (ncu): numbers from such a run are
+            # not bench values, and the sampler would poll NVML during capture
+            self.proc = None
+            self.skipped = True
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -93,7 +113,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            why = "not sampled under a profiler" if getattr(self, "skipped", False) else "nvidia-smi unavailable"
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [why]}
         time.sleep(0.25)
         self.proc.terminate()
         try:
@@ -153,6 +174,20 @@ def oracle_sample(w, budget_s=10.0):
         dt = time.perf_counter() - t0
         full = f if n >= w["iters"] else None
         return cells_of(w) * n / dt, f"FDTD {N}^3, first {n} of {w['iters']} steps", threads, full
+    if w["kind"] == "multi":
+        sides = multi_sides(w)
+        fields = gs_inputs.instance_fields(sides)
+        n = 0
+        done = 0
+        t0 = time.perf_counter()
+        for (T, P) in fields:  # whole instances, smallest work first order as generated
+            if time.perf_counter() - t0 > budget_s:
+                break
+            oracle.heat_run(T, P, w["iters"], oracle.HEAT_COEFFS_2D)
+            n += T.size * w["iters"]
+            done += 1
+        dt = time.perf_counter() - t0
+        return n / dt, f"{done} of {len(sides)} instances, {w['iters']} iterations each", threads, None
     T0, P = gs_inputs.heat_fields(w["nx"], w["ny"], w["nz"], seed=0)
     coeffs = oracle.HEAT_COEFFS_2D if w["nz"] == 1 else oracle.HEAT_COEFFS_3D
     T = T0
@@ -183,7 +218,7 @@ def run_reference(args, w, name):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": cells_of(w) * w["iters"] / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, **{k: v for k, v in w.items() if k not in ("S", "depth")}},
+        "config": {"workload": name, **{k: v for k, v in w.items() if k not in ("S", "depth", "plan")}},
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -252,6 +287,58 @@ class Runner:
         self.g.gs_destroy(self.ctx)
 
 
+class MultiRunner:
+    """The uneven-instance batch: fused persistent kernel in captured graphs
+    (S > 0) against 64 separate per-step launch loops (S = 0)."""
+
+    def __init__(self, w, S, depth, plan_extra):
+        import torch
+
+        import paper_2501_09398_gb300 as g
+
+        self.g, self.w, self.S, self.depth = g, w, S, 1
+        self.stream = torch.cuda.current_stream()
+        self.sides = multi_sides(w)
+        self.m = g.gs_multi_create(self.sides, self.sides, g.GS_F32, g.GS_BC_CLAMP, self.stream.cuda_stream)
+        self.ctx = None
+        self.fields = g.MultiFields(self.m, self.sides, self.sides)
+        mp = {k: v for k, v in plan_extra.items() if k in ("block_x", "rows", "use_pdl")}
+        if mp:
+            g.gs_multi_set_plan(self.m, **mp)
+        self.inputs = gs_inputs.instance_fields(self.sides)
+        self.reset()
+
+    def reset(self):
+        g = self.g
+        for i, (T, P) in enumerate(self.inputs):
+            g.gs_multi_upload(self.m, i, g.GS_FIELD_T, T)
+            g.gs_multi_upload(self.m, i, g.GS_FIELD_P, P)
+
+    def step(self, S):
+        g = self.g
+        if S == 0:
+            g.gs_multi_step(self.m, self.w["iters"], 0, g.GS_MULTI_SEPARATE)
+        else:
+            g.gs_multi_step(self.m, self.w["iters"], S, g.GS_MULTI_FUSED)
+
+    def one_launch(self):
+        self.g.gs_multi_step(self.m, 1, 0, self.g.GS_MULTI_FUSED)
+
+    def read(self):
+        g = self.g
+        return [g.gs_multi_read_field(self.m, i, g.GS_FIELD_T, np.empty_like(T)) for i, (T, _) in
+                enumerate(self.inputs)]
+
+    def launches_per_step(self, S):
+        return self.w["iters"] if S > 0 else self.w["iters"] * len(self.sides)
+
+    def graph_build(self, S):
+        self.step(S)  # first use captures the graphs
+
+    def close(self):
+        self.g.gs_multi_destroy(self.m)
+
+
 def timed_steps(run, S, K, W, flush):
     """Device time of K steps (CUDA events on the launching stream), L2
     flushed between steps outside the events.  Returns per-step ms list."""
@@ -287,7 +374,10 @@ def kernel_avg_ms(run, flush, reps=6, per=16):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(per)]
         for a, b in evs:
             a.record(st)
-            g.gs_step(run.ctx, n_iter, 0)
+            if run.w["kind"] == "multi":
+                run.one_launch()
+            else:
+                g.gs_step(run.ctx, n_iter, 0)
             b.record(st)
         torch.cuda.synchronize()
         times += [a.elapsed_time(b) for a, b in evs]
@@ -302,6 +392,22 @@ def e2e_steps(run, S, K):
     import torch
 
     g = run.g
+    if run.w["kind"] == "multi":
+        pins = [(torch.from_numpy(T).pin_memory().numpy(), torch.from_numpy(P).pin_memory().numpy())
+                for T, P in run.inputs]
+        outs = [torch.empty(T.shape, dtype=torch.float32).pin_memory().numpy() for T, _ in run.inputs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            for i, (T, P) in enumerate(pins):
+                g.gs_multi_upload(run.m, i, g.GS_FIELD_T, T)
+                g.gs_multi_upload(run.m, i, g.GS_FIELD_P, P)
+            run.step(S)
+            for i, o in enumerate(outs):
+                g.gs_multi_read_field(run.m, i, g.GS_FIELD_T, o)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / K
+        return dt, sum(T.nbytes + P.nbytes for T, P in pins), sum(o.nbytes for o in outs)
     if run.w["kind"] == "fdtd":
         hz = torch.zeros(run.out_shape, dtype=torch.float32).pin_memory().numpy()
         h_in = [hz] * 6
@@ -329,7 +435,7 @@ def e2e_steps(run, S, K):
 def measure_workload(name, w, args, flush, with_e2e=True):
     import torch
 
-    g_plan = {}
+    g_plan = dict(w.get("plan", {}))
     if args.block_x:
         g_plan["block_x"] = args.block_x
     if args.rows:
@@ -344,18 +450,21 @@ def measure_workload(name, w, args, flush, with_e2e=True):
         g_plan["kernel"] = args.kernel
     S = args.batch or w["S"]
     depth = args.depth or w["depth"]
-    run = Runner(w, S, depth, g_plan)
+    run = (MultiRunner if w["kind"] == "multi" else Runner)(w, S, depth, g_plan)
     try:
         g = run.g
         # paper convention (Sec. III-C): graph creation + execution of one run
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g.gs_graph_destroy(run.ctx)
-        g.gs_graph_build(run.ctx, S)
-        run.step(S)
+        if run.ctx is not None:
+            g.gs_graph_destroy(run.ctx)
+            g.gs_graph_build(run.ctx, S)
+            run.step(S)
+        else:
+            run.graph_build(S)
         torch.cuda.synchronize()
         paper_conv_ms = (time.perf_counter() - t0) * 1e3
-        build_s = g.gs_get_stats(run.ctx)["last_build_seconds"]
+        build_s = g.gs_get_stats(run.ctx)["last_build_seconds"] if run.ctx is not None else None
         # steady state (graphs cached)
         graph_ms = timed_steps(run, S, args.steps, args.warmup, flush)
         per_step_ms = timed_steps(run, 0, args.steps, args.warmup, flush)
@@ -448,8 +557,12 @@ def main():
     per_step_value = cells * w["iters"] / (statistics.mean(m["per_step_ms"]) * 1e-3)
     peak, peak_kind = _peaks()
     bytes_launch = algo_bytes_per_launch(w, m["depth"])
-    achieved = bytes_launch / (m["kern_ms"] * 1e-3) / 1e9
-    step_bw = bytes_launch * m["launches"] / (ms_per_step * 1e-3) / 1e9
+    # average launch duration inside the timed region: CUDA events around
+    # each graph-batched step on the launching stream, divided by the
+    # kernel launches in it (so inter-node gaps are charged to the kernel)
+    launch_ms = ms_per_step / m["launches"]
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    isolated = bytes_launch / (m["kern_ms"] * 1e-3) / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
@@ -459,10 +572,11 @@ def main():
                    "temporal_depth": m["depth"], "parallelism": f"replicas x{world}" if world > 1 else "single",
                    "l2": "flushed between steps (256 MiB write)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel_ms": m["kern_ms"],
-                     "bytes_per_launch": bytes_launch, "in_step_GBps": step_bw},
+                     "traffic": None, "peak_kind": peak_kind, "launch_ms_in_step": launch_ms,
+                     "bytes_per_launch": bytes_launch, "isolated_launch_ms": m["kern_ms"],
+                     "isolated_GBps": isolated},
         "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
-                            "graph_speedup": per_step_value / (value / world)},
+                            "graph_speedup": (value / world) / per_step_value},
         "paper_convention": {"ms_build_plus_run": m["paper_conv_ms"], "build_s": m["build_s"]},
         "gpu_launches": m["launches"] * args.steps,
         "clocks": clk,
@@ -482,19 +596,25 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_extras and args.workload == DEFAULT:
         extra = {}
-        a2 = argparse.Namespace(**{**vars(args), "batch": 0, "depth": 0, "block_x": 0, "rows": 0, "tile_x": 0,
-                                   "tile_y": 0, "pdl": False, "kernel": 0, "steps": 20})
-        for nm in ("heat2d-512", "heat2d-4096"):
+        base = {**vars(args), "batch": 0, "depth": 0, "block_x": 0, "rows": 0, "tile_x": 0, "tile_y": 0,
+                "pdl": False, "kernel": 0, "steps": 20}
+        # 2D 512^2: graph-batched vs per-step launch of the same depth-1 kernel
+        # 2D 4096^2: HBM roofline of the depth-1 kernel, and the wavefront
+        # depth-4 kernel's throughput
+        for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(depth=4, kernel=2, rows=4), "wave4"),
+                              ("heat2d-4096", {}, "depth1"),
+                              ("heat2d-4096", dict(depth=4, kernel=2, rows=64, block_x=256), "wave4")):
             ww = WORKLOADS[nm]
-            mm = measure_workload(nm, ww, a2, flush, with_e2e=False)
+            mm = measure_workload(nm, ww, argparse.Namespace(**{**base, **over}), flush, with_e2e=False)
             c = cells_of(ww) * ww["iters"]
-            gv = c / (statistics.mean(mm["graph_ms"]) * 1e-3)
+            gms = statistics.mean(mm["graph_ms"])
+            gv = c / (gms * 1e-3)
             pv = c / (statistics.mean(mm["per_step_ms"]) * 1e-3)
             bl = algo_bytes_per_launch(ww, mm["depth"])
-            kbw = bl / (mm["kern_ms"] * 1e-3) / 1e9
-            extra[nm] = {"graph_value": gv, "per_step_value": pv, "graph_speedup": gv / pv, "S": mm["S"],
-                         "kernel_GBps": kbw, "kernel_frac": kbw / peak,
-                         "paper_convention_ms": mm["paper_conv_ms"]}
+            bw = bl / (gms / mm["launches"] * 1e-3) / 1e9
+            extra[f"{nm}/{tag}"] = {"graph_value": gv, "per_step_value": pv, "graph_speedup": gv / pv,
+                                    "S": mm["S"], "depth": mm["depth"], "in_step_GBps": bw,
+                                    "hbm_frac": bw / peak, "paper_convention_ms": mm["paper_conv_ms"]}
         line["extra"] = extra
 
     if world > 1:

@@ -277,6 +277,112 @@ gs_status gs_sync(gs_ctx *ctx);
 /* Counters and the last measured graph build time. */
 gs_status gs_get_stats(const gs_ctx *ctx, gs_stats *out);
 
+/* ------------------------------------------------------------ autotuner -- */
+
+typedef struct gs_tune_candidate {
+    gs_plan plan;        /* launch plan (zero fields: defaults) */
+    int64_t batch_size;  /* iteration batch size S; 0 = per-step launches */
+} gs_tune_candidate;
+
+typedef struct gs_tune_result {
+    gs_plan plan;             /* the plan as applied (defaults filled in) */
+    int64_t batch_size;
+    double build_seconds;     /* T_C: gs_graph_build host wall time (0 for S = 0) */
+    double exec_ms_per_iter;  /* T_E / n_iters, best of `reps` runs, CUDA events
+                                 on the context stream, graphs cached */
+    double total_ms;          /* build_seconds*1e3 + T_E of one n_iters run:
+                                 the paper's T = T_C + T_E (Eq. 1) */
+    int32_t status;           /* GS_OK, or why the candidate was skipped
+                                 (e.g. GS_ERR_UNSUPPORTED for a plan that does
+                                 not fit this grid) */
+    int32_t reserved;
+} gs_tune_result;
+
+/* Time every candidate on the context's own bound fields: set its plan,
+ * build its graphs (timed: T_C), run n_iters iterations once to warm up,
+ * then `reps` timed runs of n_iters iterations.  results[i] describes
+ * cands[i]; *best_index (may be NULL) receives the index with the smallest
+ * total_ms, the candidate that minimises T = T_C + T_E for a run of n_iters
+ * iterations (the paper's selection of the iteration batch size, Sec. III-B,
+ * extended to the launch plan).  The fields, buffer parity, time counter and
+ * plan are restored afterwards (the fields are snapshotted into temporary
+ * device memory first).  Synchronous.  Errors: GS_ERR_INVALID_ARG,
+ * GS_ERR_STATE (unbound fields), GS_ERR_CUDA, GS_ERR_OOM (snapshot),
+ * GS_ERR_UNSUPPORTED if no candidate could run. */
+gs_status gs_autotune(gs_ctx *ctx, int64_t n_iters, int32_t reps, const gs_tune_candidate *cands, int32_t n_cands,
+                      gs_tune_result *results, int32_t *best_index);
+
+/* ------------------------------------------------ uneven instance batch -- */
+
+/* Many independent 2D thermal grids of different sizes advanced together.
+ * Each instance behaves like a GS_HEAT2D context (same fields, layout and
+ * update); all instances share the stream, coefficients and buffer parity.
+ * This extends the paper's iteration batching (Sec. III-A) across problems:
+ * one launch per iteration covers every instance, and iteration batches of
+ * those launches are recorded into one graph. */
+typedef struct gs_multi gs_multi;
+
+typedef enum gs_multi_mode {
+    GS_MULTI_FUSED = 0,    /* one persistent kernel per iteration over all
+                              (instance, tile) work items, largest instances
+                              first; batch_size > 0 records batches into a
+                              graph by stream capture */
+    GS_MULTI_SEPARATE = 1  /* baseline: each instance stepped by its own
+                              launches (per-step, or its own graphs), one
+                              instance after another on the stream */
+} gs_multi_mode;
+
+typedef struct gs_multi_plan {
+    int32_t block_x; /* threads per block (multiple of 32, <= 512); default 64 */
+    int32_t rows;    /* rows per work item; default 8 */
+    int32_t blocks;  /* persistent grid size; 0: SM count x occupancy */
+    int32_t use_pdl; /* programmatic dependent launch between iterations */
+} gs_multi_plan;
+
+/* Create a batch of n instances, instance i of size nx[i] x ny[i] (each in
+ * [1, 2^20]).  storage/bc/stream as for gs_create (the batch's stream must
+ * be capturable, i.e. not the legacy default stream, for batch_size > 0 in
+ * GS_MULTI_FUSED mode).  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM;
+ * *out is NULL on failure. */
+gs_status gs_multi_create(gs_multi **out, int32_t n, const int64_t *nx, const int64_t *ny, gs_dtype storage,
+                          gs_bc bc, void *stream);
+
+/* Destroy the batch (synchronises; frees graphs, the device descriptor
+ * table and the instance contexts).  NULL is accepted. */
+gs_status gs_multi_destroy(gs_multi *m);
+
+/* Message of the last failed call on m ("" if none). */
+const char *gs_multi_last_error(const gs_multi *m);
+
+/* Thermal coefficients for every instance (default as gs_create). */
+gs_status gs_multi_set_heat_coeffs(gs_multi *m, const gs_heat_coeffs *c);
+
+/* Launch plan (zero fields take defaults).  Discards built graphs. */
+gs_status gs_multi_set_plan(gs_multi *m, const gs_multi_plan *p);
+
+/* Bind caller-owned device memory to field T0, T1 or P of instance i (as
+ * gs_bind_field; GS_FIELD_T is not accepted here). */
+gs_status gs_multi_bind_field(gs_multi *m, int32_t i, gs_field id, void *ptr, int64_t pitch);
+
+/* Upload / read back a field of instance i (as gs_upload / gs_read_field;
+ * GS_FIELD_T is the current buffer). */
+gs_status gs_multi_upload(gs_multi *m, int32_t i, gs_field id, const float *host, int64_t n);
+gs_status gs_multi_read_field(gs_multi *m, int32_t i, gs_field id, float *host_out, int64_t n);
+
+/* Advance every instance by n_iters iterations (see gs_multi_mode).  Results
+ * are bit-identical across modes and batch sizes.  Asynchronous.
+ * GS_ERR_STATE if a field of some instance is unbound. */
+gs_status gs_multi_step(gs_multi *m, int64_t n_iters, int64_t batch_size, gs_multi_mode mode);
+
+/* Buffer parity shared by all instances (0: T0 holds the state). */
+gs_status gs_multi_get_parity(const gs_multi *m, int32_t *parity_out);
+
+/* Wait for the batch's stream. */
+gs_status gs_multi_sync(gs_multi *m);
+
+/* Counters summed over the fused kernel and every instance context. */
+gs_status gs_multi_get_stats(const gs_multi *m, gs_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

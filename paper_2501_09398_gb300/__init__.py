@@ -63,6 +63,20 @@ class gs_plan(ctypes.Structure):
                                               "device_launch", "kernel")]
 
 
+class gs_multi_plan(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "blocks", "use_pdl")]
+
+
+class gs_tune_candidate(ctypes.Structure):
+    _fields_ = [("plan", gs_plan), ("batch_size", ctypes.c_int64)]
+
+
+class gs_tune_result(ctypes.Structure):
+    _fields_ = [("plan", gs_plan), ("batch_size", ctypes.c_int64), ("build_seconds", ctypes.c_double),
+                ("exec_ms_per_iter", ctypes.c_double), ("total_ms", ctypes.c_double), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class gs_stats(ctypes.Structure):
     _fields_ = [("last_build_seconds", ctypes.c_double), ("last_build_nodes", ctypes.c_int64),
                 ("graphs_built", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
@@ -105,6 +119,21 @@ _sig("gs_graph_launch", [_vp, _i64])
 _sig("gs_graph_destroy", [_vp])
 _sig("gs_sync", [_vp])
 _sig("gs_get_stats", [_vp, ctypes.POINTER(gs_stats)])
+_i64p = ctypes.POINTER(_i64)
+_sig("gs_autotune", [_vp, _i64, _i32, ctypes.POINTER(gs_tune_candidate), _i32, ctypes.POINTER(gs_tune_result),
+                     ctypes.POINTER(_i32)])
+_sig("gs_multi_create", [ctypes.POINTER(_vp), _i32, _i64p, _i64p, ctypes.c_int, ctypes.c_int, _vp])
+_sig("gs_multi_destroy", [_vp])
+_sig("gs_multi_last_error", [_vp], ctypes.c_char_p)
+_sig("gs_multi_set_heat_coeffs", [_vp, ctypes.POINTER(gs_heat_coeffs)])
+_sig("gs_multi_set_plan", [_vp, ctypes.POINTER(gs_multi_plan)])
+_sig("gs_multi_bind_field", [_vp, _i32, ctypes.c_int, _vp, _i64])
+_sig("gs_multi_upload", [_vp, _i32, ctypes.c_int, _fp, _i64])
+_sig("gs_multi_read_field", [_vp, _i32, ctypes.c_int, _fp, _i64])
+_sig("gs_multi_step", [_vp, _i64, _i64, ctypes.c_int])
+_sig("gs_multi_get_parity", [_vp, ctypes.POINTER(_i32)])
+_sig("gs_multi_sync", [_vp])
+_sig("gs_multi_get_stats", [_vp, ctypes.POINTER(gs_stats)])
 
 
 def _check(st: int, ctx=None):
@@ -229,12 +258,104 @@ def gs_get_stats(ctx) -> dict:
     return {n: getattr(s, n) for n, _ in gs_stats._fields_}
 
 
+def _plan_dict(p) -> dict:
+    return {n: getattr(p, n) for n, _ in gs_plan._fields_}
+
+
+def gs_autotune(ctx, n_iters: int, candidates, reps: int = 3):
+    """candidates: list of (plan dict, batch_size).  Returns (results, best
+    index); each result is a dict with the plan as applied, batch_size,
+    build_seconds, exec_ms_per_iter, total_ms and status."""
+    n = len(candidates)
+    arr = (gs_tune_candidate * n)()
+    for i, (plan, S) in enumerate(candidates):
+        arr[i].plan = gs_plan(*[int(plan.get(f, 0)) for f, _ in gs_plan._fields_])
+        arr[i].batch_size = int(S)
+    res = (gs_tune_result * n)()
+    best = _i32(-1)
+    _check(_lib.gs_autotune(ctx, n_iters, reps, arr, n, res, ctypes.byref(best)), ctx)
+    out = [dict(plan=_plan_dict(r.plan), batch_size=r.batch_size, build_seconds=r.build_seconds,
+                exec_ms_per_iter=r.exec_ms_per_iter, total_ms=r.total_ms, status=r.status) for r in res]
+    return out, best.value
+
+
+# ----------------------------------------------------- instance batches --
+GS_MULTI_FUSED, GS_MULTI_SEPARATE = range(2)
+
+
+def _mcheck(st: int, m):
+    if st != GS_OK:
+        raise GsError(st, _lib.gs_multi_last_error(m).decode(errors="replace") if m else "")
+
+
+def gs_multi_create(nx, ny, dtype: int = GS_F32, bc: int = GS_BC_CLAMP, stream=None):
+    n = len(nx)
+    ax = (_i64 * n)(*[int(v) for v in nx])
+    ay = (_i64 * n)(*[int(v) for v in ny])
+    h = _vp()
+    st = _lib.gs_multi_create(ctypes.byref(h), n, ax, ay, dtype, bc, _vp(stream) if stream else None)
+    if st != GS_OK:
+        raise GsError(st, "gs_multi_create failed: " + _lib.gs_last_error(None).decode(errors="replace"))
+    return h
+
+
+def gs_multi_destroy(m) -> None:
+    _mcheck(_lib.gs_multi_destroy(m), None)
+
+
+def gs_multi_last_error(m) -> str:
+    return _lib.gs_multi_last_error(m).decode(errors="replace")
+
+
+def gs_multi_set_heat_coeffs(m, k=0.5, cx=0.1, cy=0.1, cz=0.01, cz2=0.05, t_amb=80.0) -> None:
+    c = gs_heat_coeffs(k, cx, cy, cz, cz2, t_amb)
+    _mcheck(_lib.gs_multi_set_heat_coeffs(m, ctypes.byref(c)), m)
+
+
+def gs_multi_set_plan(m, block_x=0, rows=0, blocks=0, use_pdl=0) -> None:
+    p = gs_multi_plan(block_x, rows, blocks, use_pdl)
+    _mcheck(_lib.gs_multi_set_plan(m, ctypes.byref(p)), m)
+
+
+def gs_multi_bind_field(m, i: int, field: int, ptr: int, pitch: int) -> None:
+    _mcheck(_lib.gs_multi_bind_field(m, i, field, _vp(ptr) if ptr else None, pitch), m)
+
+
+def gs_multi_upload(m, i: int, field: int, host: np.ndarray) -> None:
+    _mcheck(_lib.gs_multi_upload(m, i, field, _f32_ptr(host), host.size), m)
+
+
+def gs_multi_read_field(m, i: int, field: int, out: np.ndarray) -> np.ndarray:
+    _mcheck(_lib.gs_multi_read_field(m, i, field, _f32_ptr(out), out.size), m)
+    return out
+
+
+def gs_multi_step(m, n_iters: int, batch_size: int, mode: int = GS_MULTI_FUSED) -> None:
+    _mcheck(_lib.gs_multi_step(m, n_iters, batch_size, mode), m)
+
+
+def gs_multi_get_parity(m) -> int:
+    v = _i32()
+    _mcheck(_lib.gs_multi_get_parity(m, ctypes.byref(v)), m)
+    return v.value
+
+
+def gs_multi_sync(m) -> None:
+    _mcheck(_lib.gs_multi_sync(m), m)
+
+
+def gs_multi_get_stats(m) -> dict:
+    s = gs_stats()
+    _mcheck(_lib.gs_multi_get_stats(m, ctypes.byref(s)), m)
+    return {n: getattr(s, n) for n, _ in gs_stats._fields_}
+
+
 def raw_call(name: str, *args) -> int:
     """Call a C entry point by name with ctypes arguments; returns its status
     (no exception).  Used by tests that check error returns."""
     return int(getattr(_lib, name)(*args))
 
 
-from .fields import HeatFields, FdtdFields  # noqa: E402  (device-memory helpers)
+from .fields import FdtdFields, HeatFields, MultiFields  # noqa: E402  (device-memory helpers)
 
-__all__ = [n for n in dir() if n.startswith(("gs_", "GS_"))] + ["GsError", "HeatFields", "FdtdFields"]
+__all__ = [n for n in dir() if n.startswith(("gs_", "GS_"))] + ["GsError", "HeatFields", "FdtdFields", "MultiFields"]

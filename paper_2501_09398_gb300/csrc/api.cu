@@ -417,6 +417,16 @@ bool finite_all(const float* v, int n) {
 }  // namespace
 
 namespace gs {
+void ctx_field(const gs_ctx* c, int id, void** ptr, int64_t* pitch) {
+    *ptr = c->ptr[id];
+    *pitch = c->pitch[id];
+}
+bool ctx_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows) { return field_shape(c, id, width, rows); }
+size_t ctx_elem_bytes(const gs_ctx* c) { return elem_bytes(c->dt); }
+bool ctx_is_heat(const gs_ctx* c) { return is_heat(c); }
+cudaStream_t ctx_stream(const gs_ctx* c) { return c->stream; }
+gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg) { return fail(c, s, msg); }
+
 int device_sm_count() {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;

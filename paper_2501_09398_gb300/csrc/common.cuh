@@ -7,6 +7,9 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <cstring>
+#include <string>
+
 #include "graphstep.h"
 
 namespace gs {
@@ -111,6 +114,26 @@ struct FdtdArgs {
     long long* counter;   // device step counter (E kernel, source owner)
 };
 
+// One instance of the persistent multi-instance kernel (device table row).
+struct MultiInstance {
+    void* T0;
+    void* T1;
+    const void* P;
+    long long pitch, p_pitch;
+    int nx, ny;
+    int first_item;  // index of this instance's first (x tile, y tile) item
+    int n_items;
+};
+
+struct MultiArgs {
+    const MultiInstance* desc;  // device table, n_inst rows, largest first
+    int n_inst;
+    int total_items;
+    int rows;
+    int parity;  // 0: read T0, write T1; 1: the reverse
+    HeatCoef c;
+};
+
 // A ready-to-launch kernel: host stub, launch shape and its single by-value
 // argument (every kernel here takes exactly one struct argument).
 struct LaunchDesc {
@@ -137,6 +160,7 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
                       LaunchDesc* out);
 size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth);
 size_t heat_wave_smem(int nz3d, int depth, int vec);
+const void* heat_multi_func(gs_dtype dt, gs_bc bc);  // heat_multi_kernel<dt, bc>
 cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, LaunchDesc* out);
 cudaError_t convert_to_storage(gs_dtype dt, const float* src, void* dst, long long width, long long rows,
                                long long pitch, cudaStream_t st);
@@ -144,5 +168,13 @@ cudaError_t convert_from_storage(gs_dtype dt, const void* src, float* dst, long 
                                  long long pitch, cudaStream_t st);
 
 int device_sm_count();
+
+// Accessors of a context for the other translation units.
+void ctx_field(const gs_ctx* c, int id, void** ptr, int64_t* pitch);  // NULL / 0 if unbound
+bool ctx_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows);
+size_t ctx_elem_bytes(const gs_ctx* c);
+bool ctx_is_heat(const gs_ctx* c);
+cudaStream_t ctx_stream(const gs_ctx* c);
+gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg);  // records msg, returns s
 
 }  // namespace gs

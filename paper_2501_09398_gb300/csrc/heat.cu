@@ -56,26 +56,26 @@ __device__ __forceinline__ float bnd(float self) {
 // iteration ahead.  x-neighbours come from warp shuffles (lanes 0/31 load
 // one scalar each); z-neighbours come from a double-buffered shared-memory
 // row per plane.
+// One block's share of a depth-1 step: the tile (bx, by[, bz]) of the grid
+// described by `a`.  Shared by the single-grid kernel and the persistent
+// multi-instance kernel.
 template <typename ST, int BC, bool IS3D>
-__global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
+__device__ __forceinline__ void heat_march_tile(const HeatArgs& a, int bx, int by, int bz, float* zsm) {
     constexpr int V = Vec<ST>::N;
-    extern __shared__ float zsm[];  // [2][ZB+2][BX*V] (3D only)
-    pdl_wait_then_trigger();
-
     const int BX = blockDim.x;
     const int tx = threadIdx.x;
     const int lane = tx & 31;
-    const int x0 = (blockIdx.x * BX + tx) * V;
+    const int x0 = (bx * BX + tx) * V;
     const int nx = a.nx, ny = a.ny;
     const int ZB = IS3D ? (int)blockDim.y : 1;
     const int tz = IS3D ? (int)threadIdx.y : 0;
-    const int z0 = IS3D ? (int)blockIdx.z * ZB : 0;
+    const int z0 = IS3D ? bz * ZB : 0;
     const int z = z0 + tz;
     const bool act = (x0 < nx) && (!IS3D || z < a.nz);
     const bool has_p = !IS3D || z == 0;
     const bool dn_halo = IS3D && tz == 0 && z0 > 0 && x0 < nx;
     const bool up_halo = IS3D && tz == ZB - 1 && z0 + ZB < a.nz && x0 < nx;
-    const int y0 = blockIdx.y * a.rows;
+    const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, ny);
 
     const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
@@ -180,6 +180,52 @@ __global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
         }
         wl = wln;
         er = ern;
+    }
+}
+
+template <typename ST, int BC, bool IS3D>
+__global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
+    extern __shared__ float zsm[];  // [2][ZB+2][BX*V] (3D only)
+    pdl_wait_then_trigger();
+    heat_march_tile<ST, BC, IS3D>(a, blockIdx.x, blockIdx.y, blockIdx.z, zsm);
+}
+
+// ------------------------------------------------- multi-instance (2D) ----
+//
+// Persistent kernel over many independent 2D grids: the work list is every
+// (instance, x tile, y tile) of the depth-1 march, instances ordered largest
+// first; block b takes items b, b + gridDim.x, ...  The descriptor table
+// (per instance: both buffers, P, sizes, pitches, first work item) lives in
+// device memory; `parity` selects which buffer is read.
+template <typename ST, int BC>
+__global__ void __launch_bounds__(512) heat_multi_kernel(const MultiArgs m) {
+    pdl_wait_then_trigger();
+    const int V = Vec<ST>::N;
+    const int span = blockDim.x * V;
+    for (int w = blockIdx.x; w < m.total_items; w += gridDim.x) {
+        // binary search: last instance whose first item <= w
+        int lo = 0, hi = m.n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (m.desc[mid].first_item <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const MultiInstance& d = m.desc[lo];
+        HeatArgs a{};
+        a.Tin = m.parity ? d.T1 : d.T0;
+        a.Tout = m.parity ? d.T0 : d.T1;
+        a.P = d.P;
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.nz = 1;
+        a.rows = m.rows;
+        a.pitch = d.pitch;
+        a.plane = d.pitch * d.ny;
+        a.p_pitch = d.p_pitch;
+        a.c = m.c;
+        const int ntx = (d.nx + span - 1) / span;
+        const int item = w - d.first_item;
+        heat_march_tile<ST, BC, false>(a, item % ntx, item / ntx, 0, nullptr);
     }
 }
 
@@ -431,6 +477,19 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
 }
 
 // ------------------------------------------------------------- factory ----
+
+const void* heat_multi_func(gs_dtype dt, gs_bc bc) {
+    const bool cl = (bc == GS_BC_CLAMP);
+    switch (dt) {
+        case GS_F32: return cl ? (const void*)heat_multi_kernel<float, GS_BC_CLAMP>
+                               : (const void*)heat_multi_kernel<float, GS_BC_DIRICHLET0>;
+        case GS_BF16: return cl ? (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_CLAMP>
+                                : (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_DIRICHLET0>;
+        case GS_F16: return cl ? (const void*)heat_multi_kernel<__half, GS_BC_CLAMP>
+                               : (const void*)heat_multi_kernel<__half, GS_BC_DIRICHLET0>;
+    }
+    return nullptr;
+}
 
 size_t heat_wave_smem(int nz3d, int depth, int vec) {
     return nz3d > 0 ? (size_t)2 * depth * nz3d * 32 * vec * sizeof(float) : 0;

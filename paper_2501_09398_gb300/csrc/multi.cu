@@ -1,0 +1,394 @@
+// Many independent 2D thermal grids of uneven sizes advanced together.
+//
+// GS_MULTI_FUSED: one persistent kernel per iteration covers every
+// (instance, tile) work item (largest instances first); with batch_size S > 0
+// the S launches are recorded into a graph by stream capture (the paper's
+// Sec. II alternative to manual creation) and replayed, with a cached
+// remainder graph for n mod S.
+// GS_MULTI_SEPARATE: the baseline, each instance stepped by its own per-step
+// (or graph-batched) launches, instance after instance on the same stream.
+// Both give bit-identical results: the fused kernel runs the same tile code.
+#include <algorithm>
+#include <map>
+#include <new>
+#include <numeric>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace gs;
+
+struct gs_multi {
+    std::vector<gs_ctx*> inst;
+    std::vector<int64_t> nx, ny;
+    gs_dtype dt;
+    gs_bc bc;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    gs_heat_coeffs hc{0.5f, 0.1f, 0.1f, 0.01f, 0.05f, 80.0f};
+    gs_multi_plan plan{};
+    int parity = 0;
+    MultiInstance* d_desc = nullptr;  // device descriptor table
+    int total_items = 0;
+    bool table_ok = false;
+    LaunchDesc desc[2];
+    std::map<std::pair<int64_t, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
+    gs_stats stats{};
+    std::string err;
+};
+
+namespace {
+
+gs_status mfail(gs_multi* m, gs_status s, const std::string& msg) {
+    if (m) m->err = msg;
+    return s;
+}
+
+gs_status mcuda(gs_multi* m, cudaError_t e, const char* what) {
+    return mfail(m, e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define GS_MCUDA(m, call)                                       \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return mcuda((m), e_, #call);    \
+    } while (0)
+
+gs_status from_ctx(gs_multi* m, gs_status st, int i) {
+    if (st != GS_OK) m->err = "instance " + std::to_string(i) + ": " + gs_last_error(m->inst[i]);
+    return st;
+}
+
+void drop_graphs(gs_multi* m) {
+    for (auto& kv : m->graphs) {
+        cudaGraphExecDestroy(kv.second.second);
+        cudaGraphDestroy(kv.second.first);
+    }
+    m->graphs.clear();
+}
+
+void invalidate(gs_multi* m) {
+    drop_graphs(m);
+    m->table_ok = false;
+}
+
+int vec_elems(gs_dtype dt) { return dt == GS_F32 ? 4 : 8; }
+
+// Build the descriptor table (largest instances first) and the two launch
+// descriptors (one per buffer parity).
+gs_status ensure_table(gs_multi* m) {
+    if (m->table_ok) return GS_OK;
+    const int n = (int)m->inst.size();
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return m->nx[a] * m->ny[a] > m->nx[b] * m->ny[b]; });
+    const int span = m->plan.block_x * vec_elems(m->dt);
+    std::vector<MultiInstance> host(n);
+    int item = 0;
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        void* t0;
+        void* t1;
+        void* p;
+        int64_t pt0, pt1, pp;
+        ctx_field(m->inst[i], GS_FIELD_T0, &t0, &pt0);
+        ctx_field(m->inst[i], GS_FIELD_T1, &t1, &pt1);
+        ctx_field(m->inst[i], GS_FIELD_P, &p, &pp);
+        if (!t0 || !t1 || !p)
+            return mfail(m, GS_ERR_STATE, "instance " + std::to_string(i) + ": T0, T1 and P must be bound");
+        if (pt0 != pt1) return mfail(m, GS_ERR_STATE, "instance " + std::to_string(i) + ": T0/T1 pitch differ");
+        MultiInstance& d = host[k];
+        d.T0 = t0;
+        d.T1 = t1;
+        d.P = p;
+        d.pitch = pt0;
+        d.p_pitch = pp;
+        d.nx = (int)m->nx[i];
+        d.ny = (int)m->ny[i];
+        const int ntx = (d.nx + span - 1) / span;
+        const int nty = (d.ny + m->plan.rows - 1) / m->plan.rows;
+        d.first_item = item;
+        d.n_items = ntx * nty;
+        item += d.n_items;
+    }
+    if (!m->d_desc) GS_MCUDA(m, cudaMalloc(&m->d_desc, sizeof(MultiInstance) * n));
+    GS_MCUDA(m, cudaMemcpyAsync(m->d_desc, host.data(), sizeof(MultiInstance) * n, cudaMemcpyHostToDevice,
+                                m->stream));
+    GS_MCUDA(m, cudaStreamSynchronize(m->stream));
+    m->total_items = item;
+    const void* f = heat_multi_func(m->dt, m->bc);
+    int blocks = m->plan.blocks;
+    if (blocks <= 0) {
+        int occ = 0;
+        GS_MCUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, m->plan.block_x, 0));
+        blocks = std::max(1, occ) * device_sm_count();
+    }
+    blocks = std::max(1, std::min(blocks, item));
+    for (int par = 0; par < 2; ++par) {
+        MultiArgs a{};
+        a.desc = m->d_desc;
+        a.n_inst = n;
+        a.total_items = item;
+        a.rows = m->plan.rows;
+        a.parity = par;
+        a.c = HeatCoef{m->hc.k, m->hc.cx, m->hc.cy, m->hc.cz, m->hc.cz2, m->hc.t_amb};
+        LaunchDesc& d = m->desc[par];
+        d.func = f;
+        d.grid = dim3(blocks, 1, 1);
+        d.block = dim3(m->plan.block_x, 1, 1);
+        d.smem = 0;
+        d.set_args(a);
+    }
+    m->table_ok = true;
+    return GS_OK;
+}
+
+cudaError_t launch_fused(gs_multi* m, int parity) {
+    LaunchDesc& d = m->desc[parity];
+    void* args[1] = {d.arg_ptr()};
+    if (!m->plan.use_pdl) return cudaLaunchKernel(d.func, d.grid, d.block, args, d.smem, m->stream);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = d.grid;
+    cfg.blockDim = d.block;
+    cfg.dynamicSmemBytes = d.smem;
+    cfg.stream = m->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, d.func, args);
+}
+
+// Record S fused launches from parity p into a graph by stream capture.
+gs_status capture_graph(gs_multi* m, int64_t S, int p, cudaGraphExec_t* out) {
+    auto key = std::make_pair(S, p);
+    auto it = m->graphs.find(key);
+    if (it != m->graphs.end()) {
+        *out = it->second.second;
+        return GS_OK;
+    }
+    GS_MCUDA(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int64_t i = 0; i < S && err == cudaSuccess; ++i) err = launch_fused(m, (p + (int)(i & 1)) & 1);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(m->stream, &g);
+    if (err != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return mcuda(m, err != cudaSuccess ? err : e2, "stream capture of the fused multi-instance launches");
+    }
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiateWithFlags(&exec, g, 0);
+    if (err == cudaSuccess) err = cudaGraphUpload(exec, m->stream);
+    if (err != cudaSuccess) {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(g);
+        return mcuda(m, err, "instantiate/upload of the captured graph");
+    }
+    m->graphs[key] = std::make_pair(g, exec);
+    m->stats.graphs_built += 1;
+    *out = exec;
+    return GS_OK;
+}
+
+gs_status check_inst(gs_multi* m, int32_t i) {
+    if (!m) return GS_ERR_INVALID_ARG;
+    if (i < 0 || i >= (int32_t)m->inst.size()) return mfail(m, GS_ERR_INVALID_ARG, "instance index out of range");
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_multi_create(gs_multi** out, int32_t n, const int64_t* nx, const int64_t* ny, gs_dtype storage,
+                          gs_bc bc, void* stream) {
+    if (!out || !nx || !ny || n < 1) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (storage != GS_F32 && storage != GS_BF16 && storage != GS_F16) return GS_ERR_INVALID_ARG;
+    if (bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0) return GS_ERR_INVALID_ARG;
+    int64_t items = 0;
+    for (int i = 0; i < n; ++i) {
+        if (nx[i] < 1 || ny[i] < 1 || nx[i] > (1 << 20) || ny[i] > (1 << 20)) return GS_ERR_INVALID_ARG;
+        items += (nx[i] + 127) / 128 * ny[i];
+    }
+    if (items >= (int64_t(1) << 31)) return GS_ERR_INVALID_ARG;
+    gs_multi* m = new (std::nothrow) gs_multi();
+    if (!m) return GS_ERR_OOM;
+    m->dt = storage;
+    m->bc = bc;
+    m->plan.block_x = 64;
+    m->plan.rows = 8;
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        m->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        m->own_stream = (e == cudaSuccess);
+    }
+    if (e != cudaSuccess) {
+        gs_multi_destroy(m);
+        return GS_ERR_CUDA;
+    }
+    for (int i = 0; i < n; ++i) {
+        gs_ctx* c = nullptr;
+        gs_status st = gs_create(&c, GS_HEAT2D, nx[i], ny[i], 1, storage, bc, m->stream);
+        if (st != GS_OK) {
+            gs_multi_destroy(m);
+            return st;
+        }
+        m->inst.push_back(c);
+        m->nx.push_back(nx[i]);
+        m->ny.push_back(ny[i]);
+    }
+    *out = m;
+    return GS_OK;
+}
+
+gs_status gs_multi_destroy(gs_multi* m) {
+    if (!m) return GS_OK;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    drop_graphs(m);
+    for (gs_ctx* c : m->inst) gs_destroy(c);
+    if (m->d_desc) cudaFree(m->d_desc);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+    return GS_OK;
+}
+
+const char* gs_multi_last_error(const gs_multi* m) { return m ? m->err.c_str() : ""; }
+
+gs_status gs_multi_set_heat_coeffs(gs_multi* m, const gs_heat_coeffs* c) {
+    if (!m || !c) return GS_ERR_INVALID_ARG;
+    for (size_t i = 0; i < m->inst.size(); ++i) {
+        gs_status st = gs_set_heat_coeffs(m->inst[i], c);
+        if (st != GS_OK) return from_ctx(m, st, (int)i);
+    }
+    m->hc = *c;
+    invalidate(m);
+    return GS_OK;
+}
+
+gs_status gs_multi_set_plan(gs_multi* m, const gs_multi_plan* p) {
+    if (!m || !p) return GS_ERR_INVALID_ARG;
+    gs_multi_plan q = *p;
+    if (q.block_x == 0) q.block_x = 64;
+    if (q.rows == 0) q.rows = 8;
+    if (q.block_x < 32 || q.block_x > 512 || q.block_x % 32)
+        return mfail(m, GS_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [32, 512]");
+    if (q.rows < 1 || q.blocks < 0 || (q.use_pdl != 0 && q.use_pdl != 1))
+        return mfail(m, GS_ERR_INVALID_ARG, "rows >= 1, blocks >= 0, use_pdl in {0, 1}");
+    gs_plan sp{};
+    sp.block_x = q.block_x;
+    sp.rows = q.rows;
+    sp.temporal_depth = 1;
+    sp.use_pdl = q.use_pdl;
+    sp.kernel = GS_KERNEL_MARCH;
+    for (size_t i = 0; i < m->inst.size(); ++i) {
+        gs_status st = gs_set_plan(m->inst[i], &sp);
+        if (st != GS_OK) return from_ctx(m, st, (int)i);
+    }
+    m->plan = q;
+    invalidate(m);
+    return GS_OK;
+}
+
+gs_status gs_multi_bind_field(gs_multi* m, int32_t i, gs_field id, void* ptr, int64_t pitch) {
+    gs_status st = check_inst(m, i);
+    if (st != GS_OK) return st;
+    if (id == GS_FIELD_T) return mfail(m, GS_ERR_INVALID_ARG, "bind T0/T1 explicitly");
+    st = gs_bind_field(m->inst[i], id, ptr, pitch);
+    if (st != GS_OK) return from_ctx(m, st, i);
+    invalidate(m);
+    return GS_OK;
+}
+
+gs_status gs_multi_upload(gs_multi* m, int32_t i, gs_field id, const float* host, int64_t n) {
+    gs_status st = check_inst(m, i);
+    if (st != GS_OK) return st;
+    return from_ctx(m, gs_upload(m->inst[i], id, host, n), i);
+}
+
+gs_status gs_multi_read_field(gs_multi* m, int32_t i, gs_field id, float* host_out, int64_t n) {
+    gs_status st = check_inst(m, i);
+    if (st != GS_OK) return st;
+    return from_ctx(m, gs_read_field(m->inst[i], id, host_out, n), i);
+}
+
+gs_status gs_multi_get_parity(const gs_multi* m, int32_t* out) {
+    if (!m || !out) return GS_ERR_INVALID_ARG;
+    *out = m->parity;
+    return GS_OK;
+}
+
+gs_status gs_multi_step(gs_multi* m, int64_t n_iters, int64_t batch_size, gs_multi_mode mode) {
+    if (!m) return GS_ERR_INVALID_ARG;
+    if (n_iters < 0 || batch_size < 0) return mfail(m, GS_ERR_INVALID_ARG, "n_iters and batch_size must be >= 0");
+    if (mode != GS_MULTI_FUSED && mode != GS_MULTI_SEPARATE) return mfail(m, GS_ERR_INVALID_ARG, "unknown mode");
+    if (n_iters == 0) return GS_OK;
+    if (mode == GS_MULTI_SEPARATE) {
+        for (size_t i = 0; i < m->inst.size(); ++i) {
+            gs_status st = gs_step(m->inst[i], n_iters, batch_size);
+            if (st != GS_OK) return from_ctx(m, st, (int)i);
+        }
+        m->parity ^= (int)(n_iters & 1);
+        m->stats.iterations += n_iters;
+        return GS_OK;
+    }
+    gs_status st = ensure_table(m);
+    if (st != GS_OK) return st;
+    if (batch_size == 0) {
+        for (int64_t k = 0; k < n_iters; ++k) {
+            GS_MCUDA(m, launch_fused(m, m->parity));
+            m->parity ^= 1;
+        }
+        m->stats.kernel_launches += n_iters;
+    } else {
+        const int64_t nb = n_iters / batch_size, r = n_iters % batch_size;
+        for (int64_t b = 0; b < nb; ++b) {
+            cudaGraphExec_t ex;
+            st = capture_graph(m, batch_size, m->parity, &ex);
+            if (st != GS_OK) return st;
+            GS_MCUDA(m, cudaGraphLaunch(ex, m->stream));
+            m->stats.graph_launches += 1;
+            m->parity ^= (int)(batch_size & 1);
+        }
+        if (r) {
+            cudaGraphExec_t ex;
+            st = capture_graph(m, r, m->parity, &ex);
+            if (st != GS_OK) return st;
+            GS_MCUDA(m, cudaGraphLaunch(ex, m->stream));
+            m->stats.graph_launches += 1;
+            m->parity ^= (int)(r & 1);
+        }
+    }
+    // keep each instance context's view of the current buffer in step
+    for (gs_ctx* c : m->inst) gs_set_parity(c, m->parity);
+    m->stats.iterations += n_iters;
+    return GS_OK;
+}
+
+gs_status gs_multi_sync(gs_multi* m) {
+    if (!m) return GS_ERR_INVALID_ARG;
+    GS_MCUDA(m, cudaStreamSynchronize(m->stream));
+    return GS_OK;
+}
+
+gs_status gs_multi_get_stats(const gs_multi* m, gs_stats* out) {
+    if (!m || !out) return GS_ERR_INVALID_ARG;
+    *out = m->stats;
+    for (gs_ctx* c : m->inst) {
+        gs_stats s;
+        gs_get_stats(c, &s);
+        out->kernel_launches += s.kernel_launches;
+        out->graph_launches += s.graph_launches;
+        out->graphs_built += s.graphs_built;
+    }
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -9,7 +9,7 @@ from __future__ import annotations
 import torch
 
 from . import (GS_BF16, GS_F16, GS_F32, GS_FIELD_P, GS_FIELD_T0, GS_FIELD_T1, FDTD_FIELDS, gs_bind_field,
-               gs_required_pitch)
+               gs_multi_bind_field, gs_required_pitch)
 
 _TORCH = {GS_F32: torch.float32, GS_BF16: torch.bfloat16, GS_F16: torch.float16}
 
@@ -56,3 +56,18 @@ class FdtdFields:
 
     def bytes(self) -> int:
         return sum(t.numel() * t.element_size() for t in self.f)
+
+
+class MultiFields:
+    """T0, T1, P of every instance of a gs_multi batch (2D, square or not)."""
+
+    def __init__(self, m, nx, ny, dtype: int = GS_F32, device="cuda"):
+        self.bufs = []
+        for i, (w, h) in enumerate(zip(nx, ny)):
+            pitch = gs_required_pitch(dtype, w)
+            t0, t1, p = (_alloc(h, pitch, dtype, device) for _ in range(3))
+            gs_multi_bind_field(m, i, GS_FIELD_T0, t0.data_ptr(), pitch)
+            gs_multi_bind_field(m, i, GS_FIELD_T1, t1.data_ptr(), pitch)
+            gs_multi_bind_field(m, i, GS_FIELD_P, p.data_ptr(), pitch)
+            self.bufs.append((t0, t1, p))
+        _ready(device)

@@ -19,3 +19,10 @@ def oracle():
 
     _oracle.build()
     return _oracle
+
+
+@pytest.fixture(scope="session")
+def fdtd_config2_ref(oracle):
+    """FP64 oracle of the 128^3 driven cavity after 5000 steps (computed once)."""
+    N, n, src = 128, 5000, (64, 64, 64)
+    return oracle.fdtd_run(oracle.fdtd_zero_fields(N), N, n, src=src)

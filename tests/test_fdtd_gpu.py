@@ -156,11 +156,11 @@ def test_step_counter_and_resume():
         del fields
 
 
-def test_config2_full_size(oracle):
+def test_config2_full_size(fdtd_config2_ref):
     # 128^3 cells, courant 0.5, PEC, soft Ez source at the centre, 5000 steps
     N, n = 128, 5000
     src = (64, 64, 64)
-    ref = _oracle_run(oracle, N, n, src=src)
+    ref = fdtd_config2_ref
     got = _gpu_run(N, n, 100, src=src)
     err = rel_l2(fdtd_concat(got), fdtd_concat(ref))
     print(f"config2 f32 rel L2 {err:.3e}")

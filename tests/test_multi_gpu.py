@@ -1,0 +1,94 @@
+"""Uneven instance batches: the fused persistent kernel (per-step and in
+stream-captured graphs) against per-instance launches and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import gs_inputs
+from gsutil import HEAT_RTOL, max_rel, stream_handle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_09398_gb300  # noqa: F401
+
+
+def _run(sides, fields_np, n, S, mode, plan=None, stream=None, dims=None):
+    import torch
+
+    import paper_2501_09398_gb300 as g
+
+    nx = [d[0] for d in dims] if dims else sides
+    ny = [d[1] for d in dims] if dims else sides
+    if stream is None:
+        stream = torch.cuda.Stream()
+    m = g.gs_multi_create(nx, ny, g.GS_F32, g.GS_BC_CLAMP, stream.cuda_stream)
+    bufs = g.MultiFields(m, nx, ny)
+    try:
+        if plan:
+            g.gs_multi_set_plan(m, **plan)
+        for i, (T, P) in enumerate(fields_np):
+            g.gs_multi_upload(m, i, g.GS_FIELD_T, T)
+            g.gs_multi_upload(m, i, g.GS_FIELD_P, P)
+        g.gs_multi_step(m, n, S, mode)
+        out = [g.gs_multi_read_field(m, i, g.GS_FIELD_T, np.empty_like(T)) for i, (T, _) in enumerate(fields_np)]
+        return out, g.gs_multi_get_stats(m)
+    finally:
+        g.gs_multi_destroy(m)
+        del bufs
+
+
+def test_small_batch_all_modes_bit_identical(oracle):
+    import paper_2501_09398_gb300 as g
+
+    dims = [(130, 17), (5, 9), (64, 64), (200, 3), (1, 1), (77, 120)]
+    fields_np = [gs_inputs.heat_fields(w, h, 1, seed=300 + i) for i, (w, h) in enumerate(dims)]
+    n = 23
+    base, _ = _run(None, fields_np, n, 0, g.GS_MULTI_SEPARATE, dims=dims)
+    for i, (T, P) in enumerate(fields_np):
+        assert max_rel(base[i], oracle.heat_run(T, P, n, oracle.HEAT_COEFFS_2D)) <= HEAT_RTOL
+    for S, mode, plan in ((0, g.GS_MULTI_FUSED, None), (7, g.GS_MULTI_FUSED, None), (23, g.GS_MULTI_FUSED, None),
+                          (5, g.GS_MULTI_FUSED, dict(block_x=32, rows=3, blocks=7)),
+                          (4, g.GS_MULTI_FUSED, dict(use_pdl=1)), (6, g.GS_MULTI_SEPARATE, None)):
+        got, st = _run(None, fields_np, n, S, mode, plan=plan, dims=dims)
+        assert all(np.array_equal(a, b) for a, b in zip(got, base)), (S, mode, plan)
+        if mode == g.GS_MULTI_FUSED and S > 0:
+            assert st["graph_launches"] == n // S + (1 if n % S else 0)
+
+
+def test_unbound_instance_is_a_state_error():
+    import torch
+
+    import paper_2501_09398_gb300 as g
+
+    m = g.gs_multi_create([16, 8], [16, 8], g.GS_F32, g.GS_BC_CLAMP, torch.cuda.Stream().cuda_stream)
+    try:
+        with pytest.raises(g.GsError) as e:
+            g.gs_multi_step(m, 3, 0, g.GS_MULTI_FUSED)
+        assert e.value.status == g.GS_ERR_STATE
+        with pytest.raises(g.GsError) as e:
+            g.gs_multi_bind_field(m, 5, g.GS_FIELD_T0, 0, 16)
+        assert e.value.status == g.GS_ERR_INVALID_ARG
+    finally:
+        g.gs_multi_destroy(m)
+
+
+def test_config3_batch(oracle):
+    # 64 square grids, sides log-uniform in [64, 1024], seeds 1000+k, 2000 iterations
+    import paper_2501_09398_gb300 as g
+
+    sides = gs_inputs.instance_sides(64, 64, 1024, seed=0)
+    fields_np = gs_inputs.instance_fields(sides)
+    n = 2000
+    fused, _ = _run(sides, fields_np, n, 100, g.GS_MULTI_FUSED)
+    sep, _ = _run(sides, fields_np, n, 0, g.GS_MULTI_SEPARATE)
+    assert all(np.array_equal(a, b) for a, b in zip(fused, sep))
+    order = np.argsort(sides)
+    for i in list(order[:6]) + [order[-1]]:
+        T, P = fields_np[i]
+        err = max_rel(fused[i], oracle.heat_run(T, P, n, oracle.HEAT_COEFFS_2D))
+        assert err <= HEAT_RTOL, (i, sides[i], err)
