@@ -383,6 +383,49 @@ gs_status gs_multi_sync(gs_multi *m);
 /* Counters summed over the fused kernel and every instance context. */
 gs_status gs_multi_get_stats(const gs_multi *m, gs_stats *out);
 
+/* -------------------------------------------- step without allocation -- */
+
+/* The paper has no counterpart to this entry point: it serves callers that
+ * cannot call cudaMalloc.  Code whose device memory all comes from its own
+ * allocator or a fixed budget (a framework that forbids raw allocations
+ * outside its memory manager), or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit device synchronisation, can still advance a batch of
+ * 2D grids with the GS_MULTI_FUSED kernel here: the call allocates nothing.
+ * Its descriptor table lives in a fixed array of GS_NOALLOC_MAX_INSTANCES
+ * rows in device memory that belongs to the loaded library (every GPU that
+ * loads the library holds it, about 14 KiB, until the process exits). */
+#define GS_NOALLOC_MAX_INSTANCES 256
+
+typedef struct gs_instance {
+    void *T0;         /* ping-pong buffers, ny rows of `pitch` elements */
+    void *T1;
+    const void *P;    /* power map, ny rows of `p_pitch` elements */
+    int64_t nx, ny;   /* grid size, each in [1, 2^20] */
+    int64_t pitch;    /* elements per row of T0/T1 (>= nx, multiple of 16 bytes) */
+    int64_t p_pitch;  /* elements per row of P (same rules) */
+} gs_instance;
+
+/* Advance n_inst independent 2D thermal grids by n_iters iterations, one
+ * fused launch per iteration (block 64 threads, 8 rows per work item), on
+ * `stream` (NULL: the legacy default stream).  parity: which buffer holds
+ * the current state of every instance (0: T0); *parity_out (may be NULL)
+ * receives the parity after the call.  Same update and results, bit for bit,
+ * as gs_multi_step in GS_MULTI_FUSED mode.  Asynchronous.
+ * Set-up: the first call on a device resolves the table's device address
+ * (cudaGetSymbolAddress) with that device current, so make the first call on
+ * each device before relying on the call doing no set-up work.
+ * Sharing: every call writes the same table (stream-ordered on its own
+ * stream) and the table keeps the last call's contents; calls that overlap
+ * on the GPU (different streams, or host threads racing) race on it.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Errors (message in gs_last_error(NULL)): GS_ERR_INVALID_ARG for n_inst
+ * outside [1, GS_NOALLOC_MAX_INSTANCES], bad pointers, sizes or pitches, or
+ * more than 2^31 work items; GS_ERR_NUMERIC for non-finite coefficients;
+ * GS_ERR_CUDA if a CUDA call fails. */
+gs_status gs_multi_step_noalloc(const gs_instance *inst, int32_t n_inst, int32_t parity, int64_t n_iters,
+                                const gs_heat_coeffs *coeffs, gs_dtype storage, gs_bc bc, void *stream,
+                                int32_t *parity_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -350,6 +350,34 @@ def gs_multi_get_stats(m) -> dict:
     return {n: getattr(s, n) for n, _ in gs_stats._fields_}
 
 
+# ------------------------------------------------- step without allocation --
+GS_NOALLOC_MAX_INSTANCES = 256
+
+
+class gs_instance(ctypes.Structure):
+    _fields_ = [("T0", _vp), ("T1", _vp), ("P", _vp), ("nx", _i64), ("ny", _i64), ("pitch", _i64),
+                ("p_pitch", _i64)]
+
+
+_sig("gs_multi_step_noalloc", [ctypes.POINTER(gs_instance), _i32, _i32, _i64, ctypes.POINTER(gs_heat_coeffs),
+                               ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_i32)])
+
+
+def gs_multi_step_noalloc(instances, parity: int, n_iters: int, coeffs=None, dtype: int = GS_F32,
+                          bc: int = GS_BC_CLAMP, stream=None) -> int:
+    """instances: list of dicts with T0, T1, P (device pointers), nx, ny,
+    pitch, p_pitch.  Returns the parity after the call."""
+    n = len(instances)
+    arr = (gs_instance * max(n, 1))()
+    for i, d in enumerate(instances):
+        arr[i] = gs_instance(d["T0"], d["T1"], d["P"], d["nx"], d["ny"], d["pitch"], d["p_pitch"])
+    c = gs_heat_coeffs(**(coeffs or dict(k=0.5, cx=0.1, cy=0.1, cz=0.01, cz2=0.05, t_amb=80.0)))
+    out = _i32(parity)
+    _check(_lib.gs_multi_step_noalloc(arr, n, parity, n_iters, ctypes.byref(c), dtype, bc,
+                                      _vp(stream) if stream else None, ctypes.byref(out)))
+    return out.value
+
+
 def raw_call(name: str, *args) -> int:
     """Call a C entry point by name with ctypes arguments; returns its status
     (no exception).  Used by tests that check error returns."""

@@ -426,6 +426,7 @@ size_t ctx_elem_bytes(const gs_ctx* c) { return elem_bytes(c->dt); }
 bool ctx_is_heat(const gs_ctx* c) { return is_heat(c); }
 cudaStream_t ctx_stream(const gs_ctx* c) { return c->stream; }
 gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg) { return fail(c, s, msg); }
+gs_status global_fail(gs_status s, const std::string& msg) { return fail(nullptr, s, msg); }
 
 int device_sm_count() {
     int dev = 0, n = 0;

@@ -176,5 +176,6 @@ size_t ctx_elem_bytes(const gs_ctx* c);
 bool ctx_is_heat(const gs_ctx* c);
 cudaStream_t ctx_stream(const gs_ctx* c);
 gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg);  // records msg, returns s
+gs_status global_fail(gs_status s, const std::string& msg);  // message for gs_last_error(NULL)
 
 }  // namespace gs
