@@ -312,6 +312,40 @@ typedef struct gs_tune_result {
 gs_status gs_autotune(gs_ctx *ctx, int64_t n_iters, int32_t reps, const gs_tune_candidate *cands, int32_t n_cands,
                       gs_tune_result *results, int32_t *best_index);
 
+/* ------------------------------------------------------ analytic model -- */
+
+/* The paper's performance model (Sec. III-B): T = T_C + T_E (Eq. 1),
+ * T_C = k_c*S + b_c (Eq. 2), T_E = a/S + b (Eq. 6, from Eqs. 3-5 with
+ * a = I_k(T_a - T_i), b = I_k(T_k + T_i) - T_a + T_l), all in seconds for a
+ * run of I_k iterations.  mae_* are the fits' mean absolute errors (the
+ * paper's Table I reports the same quantities). */
+typedef struct gs_model {
+    double k_c, b_c;  /* Eq. 2 */
+    double a, b;      /* Eq. 6 */
+    double mae_create, mae_exec;
+} gs_model;
+
+/* Least-squares fit of Eq. 2 to (S[i], t_create[i]) and of Eq. 6 to
+ * (S[i], t_exec[i]), n >= 2 points with at least two distinct S >= 1.
+ * Host only (no GPU needed).  Errors: GS_ERR_INVALID_ARG, GS_ERR_NUMERIC;
+ * message in gs_last_error(NULL). */
+gs_status gs_model_fit(const double *S, const double *t_create, const double *t_exec, int32_t n, gs_model *out);
+
+/* Eq. 1 for batch size S >= 1: k_c*S + b_c + a/S + b. */
+gs_status gs_model_total(const gs_model *m, double S, double *total_out);
+
+/* The batch size among cands[0..n) (each >= 1, e.g. the divisors of I_k the
+ * paper admits, Sec. III-B) that minimises Eq. 1; ties go to the smaller S.
+ * *best_T (may be NULL) receives the model's total. */
+gs_status gs_model_pick(const gs_model *m, const int64_t *cands, int32_t n, int64_t *best_S, double *best_T);
+
+/* Measure T_C and T_E on the context for each S in S_list (runs of n_iters
+ * iterations with the context's current plan, via gs_autotune, so the fields
+ * are restored) and fit the model.  Choose S values that divide n_iters so
+ * that T_E holds no remainder graph. */
+gs_status gs_model_calibrate(gs_ctx *ctx, int64_t n_iters, const int64_t *S_list, int32_t n, int32_t reps,
+                             gs_model *out);
+
 /* ------------------------------------------------ uneven instance batch -- */
 
 /* Many independent 2D thermal grids of different sizes advanced together.

@@ -77,6 +77,10 @@ class gs_tune_result(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class gs_model(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("k_c", "b_c", "a", "b", "mae_create", "mae_exec")]
+
+
 class gs_stats(ctypes.Structure):
     _fields_ = [("last_build_seconds", ctypes.c_double), ("last_build_nodes", ctypes.c_int64),
                 ("graphs_built", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
@@ -277,6 +281,51 @@ def gs_autotune(ctx, n_iters: int, candidates, reps: int = 3):
     out = [dict(plan=_plan_dict(r.plan), batch_size=r.batch_size, build_seconds=r.build_seconds,
                 exec_ms_per_iter=r.exec_ms_per_iter, total_ms=r.total_ms, status=r.status) for r in res]
     return out, best.value
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_sig("gs_model_fit", [_dp, _dp, _dp, _i32, ctypes.POINTER(gs_model)])
+_sig("gs_model_total", [ctypes.POINTER(gs_model), ctypes.c_double, _dp])
+_sig("gs_model_pick", [ctypes.POINTER(gs_model), ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i64), _dp])
+_sig("gs_model_calibrate", [_vp, _i64, ctypes.POINTER(_i64), _i32, _i32, ctypes.POINTER(gs_model)])
+
+
+def _model_dict(m) -> dict:
+    return {n: getattr(m, n) for n, _ in gs_model._fields_}
+
+
+def _model_struct(d) -> "gs_model":
+    return gs_model(*[float(d.get(n, 0.0)) for n, _ in gs_model._fields_])
+
+
+def gs_model_fit(S, t_create, t_exec) -> dict:
+    n = len(S)
+    arr = lambda v: (ctypes.c_double * n)(*[float(x) for x in v])  # noqa: E731
+    out = gs_model()
+    _check(_lib.gs_model_fit(arr(S), arr(t_create), arr(t_exec), n, ctypes.byref(out)))
+    return _model_dict(out)
+
+
+def gs_model_total(model: dict, S: float) -> float:
+    out = ctypes.c_double()
+    _check(_lib.gs_model_total(ctypes.byref(_model_struct(model)), float(S), ctypes.byref(out)))
+    return out.value
+
+
+def gs_model_pick(model: dict, candidates):
+    n = len(candidates)
+    c = (_i64 * n)(*[int(v) for v in candidates])
+    best, tot = _i64(), ctypes.c_double()
+    _check(_lib.gs_model_pick(ctypes.byref(_model_struct(model)), c, n, ctypes.byref(best), ctypes.byref(tot)))
+    return best.value, tot.value
+
+
+def gs_model_calibrate(ctx, n_iters: int, S_list, reps: int = 2) -> dict:
+    n = len(S_list)
+    c = (_i64 * n)(*[int(v) for v in S_list])
+    out = gs_model()
+    _check(_lib.gs_model_calibrate(ctx, n_iters, c, n, reps, ctypes.byref(out)), ctx)
+    return _model_dict(out)
 
 
 # ----------------------------------------------------- instance batches --

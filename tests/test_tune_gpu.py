@@ -82,3 +82,25 @@ def test_autotune_needs_bound_fields():
         assert e.value.status == g.GS_ERR_STATE
     finally:
         g.gs_destroy(ctx)
+
+
+def test_model_calibrate_on_gpu():
+    # Fit Eqs. 2 and 6 on a small 2D grid.  Graph creation grows with the
+    # node count (k_c > 0), and on GB300 the time between nodes inside a
+    # graph is shorter than between graph launches (Obs. I: a > 0).
+    import paper_2501_09398_gb300 as g
+
+    T0, P = gs_inputs.heat_fields(256, 256, 1, seed=33)
+    ctx, fields = heat_setup(256, 256)
+    try:
+        heat_upload(ctx, T0, P)
+        before = heat_read(ctx, T0.shape)
+        m = g.gs_model_calibrate(ctx, 1000, [1, 10, 50, 100, 500, 1000], reps=2)
+        assert all(np.isfinite(v) for v in m.values())
+        assert m["k_c"] > 0 and m["a"] > 0, m
+        best, total = g.gs_model_pick(m, [1, 10, 50, 100, 500, 1000])
+        assert best in (10, 50, 100, 500, 1000)
+        assert np.array_equal(heat_read(ctx, T0.shape), before)
+    finally:
+        g.gs_destroy(ctx)
+        del fields
