@@ -346,6 +346,77 @@ gs_status gs_model_pick(const gs_model *m, const int64_t *cands, int32_t n, int6
 gs_status gs_model_calibrate(gs_ctx *ctx, int64_t n_iters, const int64_t *S_list, int32_t n, int32_t reps,
                              gs_model *out);
 
+/* ------------------------------------------------- learned cost model -- */
+
+/* A small MLP that predicts log(milliseconds per iteration) of running a
+ * workload with a candidate (launch plan, batch size S), trained on timings
+ * the library sweeps itself (gs_autotune), used to pick the candidate with
+ * the smallest prediction.  This takes the place of the paper's analytic
+ * model (Sec. III-B) in choosing S, and extends the choice to the launch
+ * plan and temporal depth — the automatic characterisation and batch-size
+ * selection the paper leaves as future work (Sec. VI).
+ * Network: GS_MLP_INPUTS -> GS_MLP_HIDDEN -> GS_MLP_HIDDEN -> 1, ReLU, one
+ * flat FP32 parameter array: W1[32][16] | b1[32] | W2[32][32] | b2[32] |
+ * W3[32] | b3.  Inputs are standardised inside the kernels with a stored
+ * per-feature mean and 1/std.  Loss: mean squared error.  Training: Adam
+ * (0.9, 0.999, 1e-8), minibatches in row order; one epoch is replayed as a
+ * CUDA graph.  All arrays passed as X / y are device memory, X row-major
+ * [n_rows][GS_MLP_INPUTS] float32, y [n_rows] float32. */
+#define GS_MLP_INPUTS 16
+#define GS_MLP_HIDDEN 32
+#define GS_MLP_PARAMS 1633
+
+typedef struct gs_mlp gs_mlp;
+
+/* Describes a stepping problem for the feature vector. */
+typedef struct gs_workload {
+    int32_t kind;     /* gs_kind */
+    int32_t dtype;    /* gs_dtype */
+    int64_t nx, ny, nz;
+    int64_t n_iters;  /* iterations of the run (the paper's I_k) */
+} gs_workload;
+
+/* Feature vectors (n x GS_MLP_INPUTS floats, host memory) of a workload
+ * with each candidate: log2 nx, log2 ny, log2 nz, one-hot kind (3), kernels
+ * per iteration, log2 n_iters, one-hot dtype (3), log2 S (0 for S = 0),
+ * [S == 0], log2 block_x, log2 rows, temporal depth.  Candidates must give
+ * block_x, rows and temporal_depth explicitly.  Host only. */
+gs_status gs_features(const gs_workload *w, const gs_tune_candidate *c, int32_t n, float *out);
+
+/* Create a model with Glorot-uniform weights drawn from splitmix64(seed),
+ * zero biases, identity normalisation, on `stream` (NULL: own stream). */
+gs_status gs_mlp_create(gs_mlp **out, uint64_t seed, void *stream);
+gs_status gs_mlp_destroy(gs_mlp *m);
+const char *gs_mlp_last_error(const gs_mlp *m);
+
+/* Parameters (GS_MLP_PARAMS floats, host).  Setting them resets Adam. */
+gs_status gs_mlp_set_params(gs_mlp *m, const float *host, int64_t n);
+gs_status gs_mlp_get_params(gs_mlp *m, float *host, int64_t n);
+
+/* Feature standardisation: fit mean and 1/std (population) of X's columns
+ * on the GPU, or set / get them (GS_MLP_INPUTS floats each, host). */
+gs_status gs_mlp_fit_normalization(gs_mlp *m, const float *X, int64_t n_rows);
+gs_status gs_mlp_set_normalization(gs_mlp *m, const float *mean, const float *inv_std);
+gs_status gs_mlp_get_normalization(gs_mlp *m, float *mean, float *inv_std);
+
+/* Mean squared error over the rows and its gradient with respect to the
+ * parameters (grad_host: GS_MLP_PARAMS floats or NULL).  Synchronous. */
+gs_status gs_mlp_loss_grad(gs_mlp *m, const float *X, const float *y, int64_t n_rows, float *loss_out,
+                           float *grad_host);
+
+/* `epochs` passes of Adam over minibatches of batch_rows rows at learning
+ * rate lr; *final_loss (may be NULL) gets the loss over all rows after
+ * training.  Synchronous. */
+gs_status gs_mlp_train(gs_mlp *m, const float *X, const float *y, int64_t n_rows, int32_t epochs, int32_t batch_rows,
+                       float lr, float *final_loss);
+
+/* Predictions for n_rows rows into device memory `pred`.  Asynchronous. */
+gs_status gs_mlp_predict(gs_mlp *m, const float *X, int64_t n_rows, float *pred);
+
+/* The row with the smallest prediction (ties: lowest row) and its value.
+ * Synchronous. */
+gs_status gs_mlp_argmin(gs_mlp *m, const float *X, int64_t n_rows, int64_t *best_row, float *best_pred);
+
 /* ------------------------------------------------ uneven instance batch -- */
 
 /* Many independent 2D thermal grids of different sizes advanced together.

@@ -328,6 +328,113 @@ def gs_model_calibrate(ctx, n_iters: int, S_list, reps: int = 2) -> dict:
     return _model_dict(out)
 
 
+# ------------------------------------------------------- cost model --
+GS_MLP_INPUTS, GS_MLP_HIDDEN, GS_MLP_PARAMS = 16, 32, 1633
+
+
+class gs_workload(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("dtype", _i32), ("nx", _i64), ("ny", _i64), ("nz", _i64), ("n_iters", _i64)]
+
+
+_sig("gs_features", [ctypes.POINTER(gs_workload), ctypes.POINTER(gs_tune_candidate), _i32, _fp])
+_sig("gs_mlp_create", [ctypes.POINTER(_vp), ctypes.c_uint64, _vp])
+_sig("gs_mlp_destroy", [_vp])
+_sig("gs_mlp_last_error", [_vp], ctypes.c_char_p)
+_sig("gs_mlp_set_params", [_vp, _fp, _i64])
+_sig("gs_mlp_get_params", [_vp, _fp, _i64])
+_sig("gs_mlp_fit_normalization", [_vp, _vp, _i64])
+_sig("gs_mlp_set_normalization", [_vp, _fp, _fp])
+_sig("gs_mlp_get_normalization", [_vp, _fp, _fp])
+_sig("gs_mlp_loss_grad", [_vp, _vp, _vp, _i64, _fp, _fp])
+_sig("gs_mlp_train", [_vp, _vp, _vp, _i64, _i32, _i32, ctypes.c_float, _fp])
+_sig("gs_mlp_predict", [_vp, _vp, _i64, _vp])
+_sig("gs_mlp_argmin", [_vp, _vp, _i64, ctypes.POINTER(_i64), _fp])
+
+
+def _lcheck(st: int, m):
+    if st != GS_OK:
+        msg = _lib.gs_mlp_last_error(m).decode(errors="replace") if m else ""
+        raise GsError(st, msg or _lib.gs_last_error(None).decode(errors="replace"))
+
+
+def gs_features(workload: dict, candidates) -> np.ndarray:
+    """Feature matrix (len(candidates) x 16, float32) of a workload dict
+    (kind, dtype, nx, ny, nz, n_iters) with (plan dict, S) candidates."""
+    w = gs_workload(*[int(workload[k]) for k, _ in gs_workload._fields_])
+    n = len(candidates)
+    arr = (gs_tune_candidate * n)()
+    for i, (plan, S) in enumerate(candidates):
+        arr[i].plan = gs_plan(*[int(plan.get(f, 0)) for f, _ in gs_plan._fields_])
+        arr[i].batch_size = int(S)
+    out = np.empty((n, GS_MLP_INPUTS), dtype=np.float32)
+    _check(_lib.gs_features(ctypes.byref(w), arr, n, _f32_ptr(out)))
+    return out
+
+
+def gs_mlp_create(seed: int = 0, stream=None):
+    h = _vp()
+    _lcheck(_lib.gs_mlp_create(ctypes.byref(h), seed, _vp(stream) if stream else None), None)
+    return h
+
+
+def gs_mlp_destroy(m) -> None:
+    _lcheck(_lib.gs_mlp_destroy(m), None)
+
+
+def gs_mlp_last_error(m) -> str:
+    return _lib.gs_mlp_last_error(m).decode(errors="replace")
+
+
+def gs_mlp_set_params(m, params: np.ndarray) -> None:
+    _lcheck(_lib.gs_mlp_set_params(m, _f32_ptr(params), params.size), m)
+
+
+def gs_mlp_get_params(m) -> np.ndarray:
+    out = np.empty(GS_MLP_PARAMS, dtype=np.float32)
+    _lcheck(_lib.gs_mlp_get_params(m, _f32_ptr(out), out.size), m)
+    return out
+
+
+def gs_mlp_fit_normalization(m, X_dev_ptr: int, n_rows: int) -> None:
+    _lcheck(_lib.gs_mlp_fit_normalization(m, _vp(X_dev_ptr), n_rows), m)
+
+
+def gs_mlp_set_normalization(m, mean: np.ndarray, inv_std: np.ndarray) -> None:
+    _lcheck(_lib.gs_mlp_set_normalization(m, _f32_ptr(mean), _f32_ptr(inv_std)), m)
+
+
+def gs_mlp_get_normalization(m):
+    mean = np.empty(GS_MLP_INPUTS, dtype=np.float32)
+    inv = np.empty(GS_MLP_INPUTS, dtype=np.float32)
+    _lcheck(_lib.gs_mlp_get_normalization(m, _f32_ptr(mean), _f32_ptr(inv)), m)
+    return mean, inv
+
+
+def gs_mlp_loss_grad(m, X_dev_ptr: int, y_dev_ptr: int, n_rows: int):
+    loss = ctypes.c_float()
+    grad = np.empty(GS_MLP_PARAMS, dtype=np.float32)
+    _lcheck(_lib.gs_mlp_loss_grad(m, _vp(X_dev_ptr), _vp(y_dev_ptr), n_rows, ctypes.byref(loss), _f32_ptr(grad)), m)
+    return loss.value, grad
+
+
+def gs_mlp_train(m, X_dev_ptr: int, y_dev_ptr: int, n_rows: int, epochs: int, batch_rows: int, lr: float) -> float:
+    loss = ctypes.c_float()
+    _lcheck(_lib.gs_mlp_train(m, _vp(X_dev_ptr), _vp(y_dev_ptr), n_rows, epochs, batch_rows, lr, ctypes.byref(loss)),
+            m)
+    return loss.value
+
+
+def gs_mlp_predict(m, X_dev_ptr: int, n_rows: int, pred_dev_ptr: int) -> None:
+    _lcheck(_lib.gs_mlp_predict(m, _vp(X_dev_ptr), n_rows, _vp(pred_dev_ptr)), m)
+
+
+def gs_mlp_argmin(m, X_dev_ptr: int, n_rows: int):
+    idx = _i64()
+    val = ctypes.c_float()
+    _lcheck(_lib.gs_mlp_argmin(m, _vp(X_dev_ptr), n_rows, ctypes.byref(idx), ctypes.byref(val)), m)
+    return idx.value, val.value
+
+
 # ----------------------------------------------------- instance batches --
 GS_MULTI_FUSED, GS_MULTI_SEPARATE = range(2)
 

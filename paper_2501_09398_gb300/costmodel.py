@@ -1,0 +1,303 @@
+"""Learned choice of iteration batch size, launch plan and temporal depth.
+
+The paper picks the batch size S from a fitted analytic model (Sec. III-B,
+Eqs. 1-6) and names automatic characterisation and selection as future work
+(Sec. VI).  This module drives the library's own calls to do that with a
+learned model:
+
+1. ``sample_workloads``: seeded stepping problems over 2D 64^2-4096^2, 3D
+   64^3-256^3 and thin 3D stacks, Yee FDTD 32^3-160^3, three storage types,
+   run lengths I_k of 100-10000 iterations.
+2. ``candidates``: per workload, the launch plans x batch sizes
+   S in {per-step, 1, 10, 50, 100, 500, 1000}.
+3. ``sweep``: times every candidate on the GPU with ``gs_autotune`` (graph
+   build time T_C and milliseconds per iteration); the swept table is both
+   the training data and the judge.
+4. ``train``: fits the MLP (``gs_mlp_*``: the library's CUDA forward,
+   backward and Adam kernels) to log(ms per iteration of the whole run),
+   total = T_C + I_k * ms_per_iter.
+5. ``evaluate``: on held-out workloads, the regret of a pick is
+   T(pick) / T(best in the sweep) - 1, for the learned picker, the paper's
+   analytic picker (Eqs. 2 and 6 fitted to the same sweep at the default
+   launch plan) and a fixed S = 100 ("approximately 100 nodes", Sec. IV-A).
+
+Run ``python -m paper_2501_09398_gb300.costmodel --help``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import (GS_BC_CLAMP, GS_BC_PEC, GS_F32, GS_FDTD3D, GS_FIELD_P, GS_FIELD_T, GS_HEAT2D, GS_HEAT3D,
+               GS_KERNEL_MARCH, GS_KERNEL_WAVE, FDTD_FIELDS, FdtdFields, HeatFields, gs_autotune, gs_create,
+               gs_destroy, gs_features, gs_model_fit, gs_model_pick, gs_mlp_argmin, gs_mlp_create,
+               gs_mlp_destroy, gs_mlp_fit_normalization, gs_mlp_loss_grad, gs_mlp_train, gs_set_fdtd_params,
+               gs_upload)
+
+S_LIST = (0, 1, 10, 50, 100, 500, 1000)
+KINDS = ("heat2d", "heat3d", "fdtd")
+KIND_ID = {"heat2d": GS_HEAT2D, "heat3d": GS_HEAT3D, "fdtd": GS_FDTD3D}
+
+
+DATA = __import__("os").path.join(__import__("os").path.dirname(__file__), "data", "costmodel_sweep_gb300.json.gz")
+
+
+def load_tables(path: str = DATA):
+    """Swept (workload, table) pairs: the GB300 sweep shipped with the
+    package (150 training workloads, seed 1; 200 held-out, seed 4242), or a
+    file written by --dataset.  Returns (train_pairs, heldout_pairs)."""
+    import gzip
+
+    opener = gzip.open if path.endswith(".gz") else open
+    with opener(path, "rt") as f:
+        d = json.load(f)
+    for split in ("train", "heldout"):
+        for _, tab in d[split]:
+            for r in tab:
+                if r["ms_per_iter"] is None:
+                    r["ms_per_iter"] = float("inf")
+    return [tuple(p) for p in d["train"]], [tuple(p) for p in d["heldout"]]
+
+
+def sample_workloads(n: int, seed: int):
+    """n seeded workloads (dicts with kind, dtype, nx, ny, nz, n_iters)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        kind = KINDS[int(rng.integers(0, 3))]
+        dtype = int(rng.integers(0, 3))
+        n_iters = int(round(math.exp(rng.uniform(math.log(100), math.log(10000)))))
+        lu = lambda lo, hi: int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))  # noqa: E731
+        if kind == "heat2d":
+            nx, ny, nz = lu(64, 4096), lu(64, 4096), 1
+        elif kind == "heat3d":
+            if rng.uniform() < 0.5:
+                nx, ny, nz = lu(64, 256), lu(64, 256), lu(64, 256)
+            else:  # thin stack (Hotspot3D-like chips): few layers, wide planes
+                nx, ny, nz = lu(128, 1024), lu(128, 1024), int(rng.choice([2, 4, 8, 16]))
+        else:
+            nx = ny = nz = lu(32, 160)
+        out.append(dict(kind=kind, dtype=dtype, nx=nx, ny=ny, nz=nz, n_iters=n_iters))
+    return out
+
+
+def default_plan(w):
+    """The launch plan the analytic and fixed pickers use."""
+    if w["kind"] == "fdtd":
+        return dict(block_x=64, rows=16, temporal_depth=1)
+    return dict(block_x=64, rows=8, temporal_depth=1, kernel=GS_KERNEL_MARCH)
+
+
+def candidates(w):
+    """(plan, S) pairs for a workload; every plan field explicit."""
+    shapes = []
+    if w["kind"] == "fdtd":
+        for bx in (32, 64, 128):
+            for rows in (4, 16):
+                shapes.append(dict(block_x=bx, rows=rows, temporal_depth=1))
+    else:
+        bxs = (32, 64, 128) if w["kind"] == "heat2d" else (32, 64)
+        for bx in bxs:
+            for rows in (4, 16):
+                shapes.append(dict(block_x=bx, rows=rows, temporal_depth=1, kernel=GS_KERNEL_MARCH))
+        if w["kind"] == "heat2d" or w["nz"] <= 16:
+            for t in (2, 4):
+                for rows in (4, 16):
+                    shapes.append(dict(block_x=64, rows=rows, temporal_depth=t, kernel=GS_KERNEL_WAVE))
+    if default_plan(w) not in shapes:
+        shapes.append(default_plan(w))
+    return [(dict(p), S) for p in shapes for S in S_LIST]
+
+
+def _context(w, stream):
+    """A context for the workload with seeded fields; returns (ctx, keepalive)."""
+    import gs_inputs
+
+    kind = KIND_ID[w["kind"]]
+    if w["kind"] == "fdtd":
+        N = w["nx"]
+        ctx = gs_create(kind, N, N, N, w["dtype"], GS_BC_PEC, stream)
+        f = FdtdFields(ctx, N, w["dtype"])
+        gs_set_fdtd_params(ctx, courant=0.5, src_on=1, src=(N // 2, N // 2, N // 2))
+        return ctx, f
+    ctx = gs_create(kind, w["nx"], w["ny"], w["nz"], w["dtype"], GS_BC_CLAMP, stream)
+    f = HeatFields(ctx, w["nx"], w["ny"], w["nz"], w["dtype"])
+    T, P = gs_inputs.heat_fields(w["nx"], w["ny"], w["nz"], seed=0)
+    gs_upload(ctx, GS_FIELD_T, T)
+    gs_upload(ctx, GS_FIELD_P, P)
+    return ctx, f
+
+
+def sweep(w, n_meas: int = 1000, reps: int = 1, stream=None):
+    """Time every candidate of w; returns a list of dicts (plan, S,
+    build_seconds, ms_per_iter, status)."""
+    ctx, keep = _context(w, stream)
+    try:
+        cands = candidates(w)
+        res, _ = gs_autotune(ctx, n_meas, cands, reps=reps)
+    finally:
+        gs_destroy(ctx)
+        del keep
+    out = []
+    for (plan, S), r in zip(cands, res):
+        out.append(dict(plan=plan, S=S, build_seconds=r["build_seconds"], ms_per_iter=r["exec_ms_per_iter"],
+                        status=r["status"]))
+    return out
+
+
+def run_ms(row, n_iters):
+    """Modelled wall time of an n_iters run of a swept candidate:
+    graph creation plus n_iters steady-state iterations."""
+    return row["build_seconds"] * 1e3 + n_iters * row["ms_per_iter"]
+
+
+def _fw(w):
+    """The workload as gs_features takes it (numeric kind)."""
+    return dict(w, kind=KIND_ID[w["kind"]])
+
+
+def rows_for(w, table, n_iters_list=None):
+    """Training rows (features, log ms per iteration) of a swept workload."""
+    ok = [r for r in table if r["status"] == 0 and math.isfinite(r["ms_per_iter"])]
+    feats, ys = [], []
+    for n in (n_iters_list or [w["n_iters"]]):
+        F = gs_features(_fw(dict(w, n_iters=n)), [(r["plan"], r["S"]) for r in ok])
+        feats.append(F)
+        ys.append(np.array([math.log(run_ms(r, n) / n) for r in ok], dtype=np.float32))
+    return np.concatenate(feats), np.concatenate(ys)
+
+
+# Run lengths each swept workload contributes rows for (besides its own):
+# the table gives T_C and ms per iteration, so any run length can be
+# composed; spreading them teaches the model how T_C amortises.
+AUG_ITERS = tuple(int(v) for v in np.geomspace(100, 10000, 7))
+
+
+def training_set(pairs):
+    """Stack the training rows of (workload, table) pairs."""
+    Xs, ys = [], []
+    for w, tab in pairs:
+        X, y = rows_for(w, tab, [w["n_iters"], *AUG_ITERS])
+        Xs.append(X)
+        ys.append(y)
+    return np.concatenate(Xs), np.concatenate(ys)
+
+
+def train(X: np.ndarray, y: np.ndarray, epochs: int = 2000, batch_rows: int = 1024, lr: float = 3e-3, seed: int = 0,
+          stream=None):
+    """Fit the MLP on device copies of (X, y); returns (model handle, loss)."""
+    import torch
+
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).cuda()
+    torch.cuda.synchronize()
+    m = gs_mlp_create(seed=seed, stream=stream)
+    gs_mlp_fit_normalization(m, Xd.data_ptr(), X.shape[0])
+    l0, _ = gs_mlp_loss_grad(m, Xd.data_ptr(), yd.data_ptr(), X.shape[0])
+    loss = gs_mlp_train(m, Xd.data_ptr(), yd.data_ptr(), X.shape[0], epochs, batch_rows, lr)
+    return m, l0, loss
+
+
+def pick_learned(m, w, table):
+    """The swept candidate the model predicts fastest (among runnable ones)."""
+    import torch
+
+    ok = [r for r in table if r["status"] == 0 and math.isfinite(r["ms_per_iter"])]
+    F = gs_features(_fw(w), [(r["plan"], r["S"]) for r in ok])
+    Fd = torch.from_numpy(F).cuda()
+    torch.cuda.synchronize()
+    idx, _ = gs_mlp_argmin(m, Fd.data_ptr(), F.shape[0])
+    return ok[idx]
+
+
+def pick_analytic(w, table):
+    """The paper's method: at the default launch plan, fit Eq. 2 to the
+    measured build times and Eq. 6 to the measured execution times of the
+    graph batch sizes, then take the S minimising Eq. 1 for I_k = n_iters."""
+    dp = default_plan(w)
+    rows = [r for r in table if r["plan"] == dp and r["S"] > 0 and r["status"] == 0]
+    S = [r["S"] for r in rows]
+    tc = [r["build_seconds"] for r in rows]
+    te = [w["n_iters"] * r["ms_per_iter"] * 1e-3 for r in rows]
+    model = gs_model_fit(S, tc, te)
+    best, _ = gs_model_pick(model, S)
+    return next(r for r in rows if r["S"] == best)
+
+
+def pick_fixed(w, table, S=100):
+    dp = default_plan(w)
+    return next(r for r in table if r["plan"] == dp and r["S"] == S and r["status"] == 0)
+
+
+def regret(w, table, row):
+    ok = [r for r in table if r["status"] == 0 and math.isfinite(r["ms_per_iter"])]
+    best = min(run_ms(r, w["n_iters"]) for r in ok)
+    return run_ms(row, w["n_iters"]) / best - 1.0
+
+
+def evaluate(m, held):
+    """held: list of (workload, table).  Returns per-picker regrets."""
+    out = {"learned": [], "analytic": [], "fixed_S100": []}
+    for w, table in held:
+        out["learned"].append(regret(w, table, pick_learned(m, w, table)))
+        out["analytic"].append(regret(w, table, pick_analytic(w, table)))
+        out["fixed_S100"].append(regret(w, table, pick_fixed(w, table)))
+    return out
+
+
+def summarize(reg):
+    return {k: dict(mean=float(np.mean(v)), median=float(np.median(v)), p95=float(np.percentile(v, 95)),
+                    max=float(np.max(v)), within_5pct=float(np.mean(np.array(v) <= 0.05))) for k, v in reg.items()}
+
+
+def main():
+    import torch
+
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--train", type=int, default=150, help="training workloads (seed 1)")
+    ap.add_argument("--heldout", type=int, default=200, help="held-out workloads (seed 4242)")
+    ap.add_argument("--n-meas", type=int, default=1000, help="iterations per timed run in the sweep")
+    ap.add_argument("--epochs", type=int, default=2000)
+    ap.add_argument("--out", default="costmodel_report.json")
+    ap.add_argument("--dataset", default="", help="write the swept tables here (json)")
+    ap.add_argument("--tables", default="",
+                    help="read swept tables instead of sweeping: a --dataset file, or 'packaged' for the GB300 sweep")
+    ap.add_argument("--batch-rows", type=int, default=1024)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    args = ap.parse_args()
+    torch.cuda.set_device(0)
+    st = torch.cuda.Stream()
+    torch.cuda.set_stream(st)
+    t0 = time.time()
+    if args.tables:
+        train_pairs, held_pairs = load_tables(DATA if args.tables == "packaged" else args.tables)
+        train_pairs, held_pairs = train_pairs[:args.train], held_pairs[:args.heldout]
+    else:
+        train_w = sample_workloads(args.train, seed=1)
+        held_w = sample_workloads(args.heldout, seed=4242)
+        train_pairs = [(w, sweep(w, args.n_meas, stream=st.cuda_stream)) for w in train_w]
+        held_pairs = [(w, sweep(w, args.n_meas, stream=st.cuda_stream)) for w in held_w]
+        if args.dataset:
+            with open(args.dataset, "w") as f:
+                json.dump(dict(train=train_pairs, heldout=held_pairs), f)
+    t_sweep = time.time() - t0
+    X, y = training_set(train_pairs)
+    m, l0, loss = train(X, y, epochs=args.epochs, batch_rows=args.batch_rows, lr=args.lr)
+    try:
+        reg = evaluate(m, held_pairs)
+    finally:
+        gs_mlp_destroy(m)
+    report = dict(train_workloads=len(train_pairs), heldout_workloads=len(held_pairs), rows=int(X.shape[0]),
+                  epochs=args.epochs, batch_rows=args.batch_rows, lr=args.lr,
+                  loss_initial=l0, loss_final=loss, sweep_seconds=t_sweep, regret=summarize(reg))
+    with open(args.out, "w") as f:
+        json.dump(report, f, indent=1)
+    print(json.dumps(report))
+
+
+if __name__ == "__main__":
+    main()
