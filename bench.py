@@ -35,14 +35,15 @@ sys.path.insert(0, ROOT)
 import gs_inputs  # noqa: E402
 
 # Default launch plans per workload (the fastest measured on GB300; the
-# autotuner can re-derive them).  kernel: 1 = MARCH, 2 = WAVE.
+# autotuner can re-derive them).  kernel: 1 = MARCH, 2 = WAVE, 4 = COLUMN.
+# The per-step baseline always uses plain launches (use_pdl forced off).
 WORKLOADS = {
     "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=1,
-                             plan=dict(kernel=1, block_x=64, rows=8)),
+                             plan=dict(kernel=4, rows=4, use_pdl=1)),
     "heat2d-512": dict(kind="heat2d", nx=512, ny=512, nz=1, iters=1000, S=100, depth=1,
-                       plan=dict(kernel=1, block_x=64, rows=4)),
+                       plan=dict(kernel=4, rows=4)),
     "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1,
-                        plan=dict(kernel=1, block_x=128, rows=32)),
+                        plan=dict(kernel=4, rows=8)),
     "fdtd-128": dict(kind="fdtd", N=128, iters=5000, S=100, depth=1, plan={}),
     "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=1, plan={}),
 }
@@ -467,7 +468,13 @@ def measure_workload(name, w, args, flush, with_e2e=True):
         build_s = g.gs_get_stats(run.ctx)["last_build_seconds"] if run.ctx is not None else None
         # steady state (graphs cached)
         graph_ms = timed_steps(run, S, args.steps, args.warmup, flush)
+        # the per-step baseline is the paper's Listing 1: plain launches
+        if g_plan.get("use_pdl") and run.ctx is not None:
+            g.gs_set_plan(run.ctx, temporal_depth=depth, **{k: v for k, v in g_plan.items() if k != "use_pdl"})
         per_step_ms = timed_steps(run, 0, args.steps, args.warmup, flush)
+        if g_plan.get("use_pdl") and run.ctx is not None:
+            g.gs_set_plan(run.ctx, temporal_depth=depth, **g_plan)
+            g.gs_graph_build(run.ctx, S)
         kern_ms = kernel_avg_ms(run, flush)
         e2e = e2e_steps(run, S, max(3, min(args.steps, 20))) if with_e2e else None
         # result after one clean run, for the error check
@@ -601,8 +608,7 @@ def main():
         # 2D 512^2: graph-batched vs per-step launch of the same depth-1 kernel
         # 2D 4096^2: HBM roofline of the depth-1 kernel, and the wavefront
         # depth-4 kernel's throughput
-        for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(depth=4, kernel=2, rows=4), "wave4"),
-                              ("heat2d-4096", {}, "depth1"),
+        for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-4096", {}, "depth1"),
                               ("heat2d-4096", dict(depth=4, kernel=2, rows=64, block_x=256), "wave4")):
             ww = WORKLOADS[nm]
             mm = measure_workload(nm, ww, argparse.Namespace(**{**base, **over}), flush, with_e2e=False)

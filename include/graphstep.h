@@ -109,8 +109,18 @@ typedef struct gs_fdtd_params {
  *          per plane in 3D).
  *   TILE   depth 2 or 4: overlapped shared-memory tile of tile_x x tile_y
  *          columns (all nz planes) with a t-wide halo.
- *   AUTO   MARCH for depth 1, WAVE for depth > 1 where it applies, else TILE. */
-typedef enum gs_kernel { GS_KERNEL_AUTO = 0, GS_KERNEL_MARCH = 1, GS_KERNEL_WAVE = 2, GS_KERNEL_TILE = 3 } gs_kernel;
+ *   COLUMN depth 1 only, 2D or nz <= 8: each thread owns one vector of cells
+ *          at one y with every plane of its column in registers (no march,
+ *          no shared memory); `rows` (<= 8) warps per block stacked in y.
+ *   AUTO   depth 1: COLUMN for 2D and nz <= 8, else MARCH; depth > 1: WAVE
+ *          for 2D and nz <= 16, else TILE. */
+typedef enum gs_kernel {
+    GS_KERNEL_AUTO = 0,
+    GS_KERNEL_MARCH = 1,
+    GS_KERNEL_WAVE = 2,
+    GS_KERNEL_TILE = 3,
+    GS_KERNEL_COLUMN = 4
+} gs_kernel;
 
 /* Launch plan.  Zero fields select defaults.
  *   block_x        threads along x per block (multiple of 32; <= 512 thermal,

@@ -129,14 +129,16 @@ gs_plan default_plan(const gs_ctx* c) {
         while (p.block_x * vec_elems(c->dt) < c->nx + 1 && p.block_x < 128) p.block_x += 32;
         p.rows = 16;  // k planes per block
         p.temporal_depth = 1;
-    } else if (c->kind == GS_HEAT2D) {
-        const bool small = c->nx * c->ny <= (1 << 20);
-        p.block_x = small ? 32 : 128;
-        p.rows = small ? 8 : 32;
-        p.tile_x = 64;
+    } else if (c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz) {
+        // the column kernel (measured fastest at depth 1 for 2D and thin
+        // stacks); rows = warps per block stacked in y
+        const bool small = c->nx * c->ny * c->nz <= (1 << 22);
+        p.block_x = 64;
+        p.rows = small ? 4 : 8;
+        p.tile_x = c->kind == GS_HEAT2D ? 64 : 32;
         p.tile_y = 32;
         p.temporal_depth = 1;
-        p.kernel = GS_KERNEL_MARCH;
+        p.kernel = GS_KERNEL_COLUMN;
     } else {
         p.block_x = 32;
         p.rows = 16;
@@ -171,15 +173,22 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     if (t != 1 && t != 2 && t != 4) return fail(c, GS_ERR_INVALID_ARG, "plan.temporal_depth must be 1, 2 or 4");
     if (c->kind == GS_FDTD3D && t != 1)
         return fail(c, GS_ERR_UNSUPPORTED, "temporal blocking is provided for the thermal stencils only");
-    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_TILE)
+    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_COLUMN)
         return fail(c, GS_ERR_INVALID_ARG, "plan.kernel must be a gs_kernel value");
     if (c->kind == GS_FDTD3D) p->kernel = GS_KERNEL_AUTO;
     const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
-    if (is_heat(c) && p->kernel == GS_KERNEL_AUTO) p->kernel = (t == 1) ? GS_KERNEL_MARCH : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
+    const bool column_ok = (c->kind == GS_HEAT2D) || (c->nz <= kColumnMaxNz);
+    if (is_heat(c) && p->kernel == GS_KERNEL_AUTO)
+        p->kernel = (t == 1) ? (column_ok ? GS_KERNEL_COLUMN : GS_KERNEL_MARCH)
+                             : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
     if (p->kernel == GS_KERNEL_MARCH && t != 1)
         return fail(c, GS_ERR_INVALID_ARG, "the MARCH kernel runs depth 1 only");
     if (p->kernel == GS_KERNEL_TILE && t == 1)
         return fail(c, GS_ERR_INVALID_ARG, "the TILE kernel runs depth 2 or 4 only");
+    if (p->kernel == GS_KERNEL_COLUMN && t != 1)
+        return fail(c, GS_ERR_INVALID_ARG, "the COLUMN kernel runs depth 1 only");
+    if (p->kernel == GS_KERNEL_COLUMN && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
+        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernel needs nz <= 8");
     if (p->kernel == GS_KERNEL_WAVE && !wave_ok)
         return fail(c, GS_ERR_UNSUPPORTED, "the WAVE kernel needs nz <= 16 (all planes in one block)");
     if (p->kernel == GS_KERNEL_WAVE && heat_wave_smem(c->kind == GS_HEAT3D ? (int)c->nz : 0, t, vec_elems(c->dt)) > 227 * 1024)
@@ -238,7 +247,9 @@ gs_status ensure_descs(gs_ctx* c) {
             a.Tin = c->ptr[par ? GS_FIELD_T1 : GS_FIELD_T0];
             a.Tout = c->ptr[par ? GS_FIELD_T0 : GS_FIELD_T1];
             // single-step launches (depth 1, and the peeled n mod t steps)
-            const int v1 = (c->plan.kernel == GS_KERNEL_WAVE) ? GS_KERNEL_WAVE : GS_KERNEL_MARCH;
+            const int v1 = (c->plan.kernel == GS_KERNEL_WAVE || c->plan.kernel == GS_KERNEL_COLUMN)
+                               ? c->plan.kernel
+                               : GS_KERNEL_MARCH;
             cudaError_t e = heat_desc(c->kind, c->dt, c->bc, a, c->plan.block_x, 1, v1, &c->desc[0][par]);
             if (e != cudaSuccess) return cuda_fail(c, e, "thermal kernel set-up");
             if (t > 1) {

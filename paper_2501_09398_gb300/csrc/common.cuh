@@ -155,7 +155,8 @@ struct LaunchDesc {
 // return cudaSuccess or the first CUDA error (e.g. from setting the dynamic
 // shared memory limit), and cudaErrorInvalidValue for unsupported shapes.
 // Thermal kernel variants (gs_plan.kernel).
-constexpr int kWaveMaxNz = 16;  // wavefront kernel holds all planes in one block
+constexpr int kWaveMaxNz = 16;   // wavefront kernel holds all planes in one block
+constexpr int kColumnMaxNz = 8;  // column kernel holds all planes in registers
 cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, int block_x, int depth, int variant,
                       LaunchDesc* out);
 size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth);

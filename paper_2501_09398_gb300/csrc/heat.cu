@@ -59,6 +59,108 @@ __device__ __forceinline__ float bnd(float self) {
 // One block's share of a depth-1 step: the tile (bx, by[, bz]) of the grid
 // described by `a`.  Shared by the single-grid kernel and the persistent
 // multi-instance kernel.
+//
+// The row window (rows y-1, y, y+1 and the prefetch target y+2) is a ring of
+// four register arrays rotated by a 4-way manual unroll, so the march moves
+// no data between registers.  z-boundaries need no per-cell select: the
+// thread on the bottom (top) plane writes the boundary value of its own row
+// into the shared row below (above) it, and threads past nz write nothing.
+// x-boundaries are handled per cell only in warps that touch the grid's x
+// edges; interior warps take a select-free path (a warp-uniform branch with
+// no barrier inside).  Planes without a source keep P at zero.
+template <typename ST, int BC, bool IS3D>
+struct MarchTile {
+    static constexpr int V = Vec<ST>::N;
+    const HeatArgs& a;
+    const ST* col;   // this thread's vector in row 0 of its plane
+    const ST* pcol;  // P, row 0
+    const ST* dcol;  // plane z0-1 (tz == 0 halo)
+    const ST* ucol;  // plane z0+ZB (tz == ZB-1 halo)
+    ST* ocol;        // output, row 0 of this plane
+    float* zsm;
+    int lane, tx, tz, ZB, z, x0, nx, ny, y1, rowlen;
+    bool act, has_p, dn_halo, up_halo, fast_x;
+
+    __device__ __forceinline__ void fill_bnd(float (&dst)[V], const float (&src)[V]) const {
+#pragma unroll
+        for (int i = 0; i < V; ++i) dst[i] = bnd<BC>(src[i]);
+    }
+
+    // One output row y.  prv/cur/nxt hold rows y-1, y, y+1 (boundary rows
+    // materialised); nn receives row y+2; pc/dc/uc/wl/er are row y's P,
+    // z-halos and x-edge scalars, pn/dn/un/wln/ern receive row y+1's.
+    __device__ __forceinline__ void step(int y, float (&prv)[V], float (&cur)[V], float (&nxt)[V], float (&nn)[V],
+                                         float (&pc)[V], float (&pn)[V], float (&dc)[V], float (&dn)[V],
+                                         float (&uc)[V], float (&un)[V], float& wl, float& wln, float& er,
+                                         float& ern) const {
+        const bool more = (y + 1 < y1);
+        const long long pitch = a.pitch;
+#pragma unroll
+        for (int i = 0; i < V; ++i) { pn[i] = 0.f; dn[i] = 0.f; un[i] = 0.f; }
+        wln = 0.f;
+        ern = 0.f;
+        if (act && more && y + 2 < ny) load_vec(col + (long long)(y + 2) * pitch, nn);
+        if (act && more && has_p) load_vec(pcol + (long long)(y + 1) * a.p_pitch, pn);
+        if (act && more && lane == 0 && x0 > 0) wln = load_scalar(col + (long long)(y + 1) * pitch - 1);
+        if (act && more && lane == 31 && x0 + V < nx) ern = load_scalar(col + (long long)(y + 1) * pitch + V);
+        if (dn_halo && more) load_vec(dcol + (long long)(y + 1) * pitch, dn);
+        if (up_halo && more) load_vec(ucol + (long long)(y + 1) * pitch, un);
+
+        float w0 = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+        float eV = __shfl_down_sync(0xffffffffu, cur[0], 1);
+        if (lane == 0) w0 = wl;
+        if (lane == 31) eV = er;
+
+        float dv[V], uv[V];
+        if (IS3D) {
+            float* buf = zsm + (size_t)(y & 1) * (ZB + 2) * rowlen + tx * V;
+            if (z < a.nz) sm_put<V>(buf + (tz + 1) * rowlen, cur);
+            if (dn_halo) sm_put<V>(buf, dc);
+            if (tz == ZB - 1 && up_halo) sm_put<V>(buf + (ZB + 1) * rowlen, uc);
+            if (z == 0 || z + 1 == a.nz) {
+                float b[V];
+                fill_bnd(b, cur);
+                if (z == 0) sm_put<V>(buf + tz * rowlen, b);
+                if (z + 1 == a.nz) sm_put<V>(buf + (tz + 2) * rowlen, b);
+            }
+            __syncthreads();
+            sm_get<V>(buf + tz * rowlen, dv);
+            sm_get<V>(buf + (tz + 2) * rowlen, uv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) { dv[i] = 0.f; uv[i] = 0.f; }
+        }
+
+        if (act) {
+            float out[V];
+            if (fast_x) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const float w = (i == 0) ? w0 : cur[i - 1];
+                    const float e = (i == V - 1) ? eV : cur[i + 1];
+                    out[i] = heat_cell<IS3D>(cur[i], prv[i], nxt[i], w, e, dv[i], uv[i], pc[i], a.c);
+                }
+                store_vec(ocol + (long long)y * pitch, out, V);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const int x = x0 + i;
+                    const float t = cur[i];
+                    float w = (i == 0) ? w0 : cur[i - 1];
+                    float e = (i == V - 1) ? eV : cur[i + 1];
+                    if (x == 0) w = bnd<BC>(t);
+                    if (x + 1 >= nx) e = bnd<BC>(t);
+                    out[i] = heat_cell<IS3D>(t, prv[i], nxt[i], w, e, dv[i], uv[i], pc[i], a.c);
+                }
+                store_vec(ocol + (long long)y * pitch, out, nx - x0);
+            }
+        }
+        // the row after nxt is nn; past the last row it is the boundary row
+        if (y + 2 >= ny) fill_bnd(nn, nxt);
+    }
+
+};
+
 template <typename ST, int BC, bool IS3D>
 __device__ __forceinline__ void heat_march_tile(const HeatArgs& a, int bx, int by, int bz, float* zsm) {
     constexpr int V = Vec<ST>::N;
@@ -71,115 +173,61 @@ __device__ __forceinline__ void heat_march_tile(const HeatArgs& a, int bx, int b
     const int tz = IS3D ? (int)threadIdx.y : 0;
     const int z0 = IS3D ? bz * ZB : 0;
     const int z = z0 + tz;
-    const bool act = (x0 < nx) && (!IS3D || z < a.nz);
-    const bool has_p = !IS3D || z == 0;
-    const bool dn_halo = IS3D && tz == 0 && z0 > 0 && x0 < nx;
-    const bool up_halo = IS3D && tz == ZB - 1 && z0 + ZB < a.nz && x0 < nx;
     const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, ny);
-
-    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
-    ST* __restrict__ Tout = static_cast<ST*>(a.Tout);
-    const ST* __restrict__ P = static_cast<const ST*>(a.P);
     const long long zoff = IS3D ? (long long)z * a.plane : 0;
-    const ST* col = Tin + zoff + x0;      // this thread's vector, row 0
-    const ST* pcol = P + x0;
-    const ST* dcol = Tin + zoff - a.plane + x0;  // plane z0-1 (tz == 0)
-    const ST* ucol = Tin + zoff + a.plane + x0;  // plane z0+ZB (tz == ZB-1)
+    const ST* Tin = static_cast<const ST*>(a.Tin);
 
-    float prv[V], cur[V], nxt[V], pc[V], dc[V], uc[V];
-    float wl = 0.f, er = 0.f;
-#pragma unroll
-    for (int i = 0; i < V; ++i) { cur[i] = 0.f; pc[i] = 0.f; dc[i] = 0.f; uc[i] = 0.f; }
+    MarchTile<ST, BC, IS3D> m{a};
+    m.col = Tin + zoff + x0;
+    m.pcol = static_cast<const ST*>(a.P) + x0;
+    m.dcol = Tin + zoff - a.plane + x0;
+    m.ucol = Tin + zoff + a.plane + x0;
+    m.ocol = static_cast<ST*>(a.Tout) + zoff + x0;
+    m.zsm = zsm;
+    m.lane = lane;
+    m.tx = tx;
+    m.tz = tz;
+    m.ZB = ZB;
+    m.z = z;
+    m.x0 = x0;
+    m.nx = nx;
+    m.ny = ny;
+    m.y1 = y1;
+    m.rowlen = BX * V;
+    m.act = (x0 < nx) && (!IS3D || z < a.nz);
+    m.has_p = !IS3D || z == 0;
+    m.dn_halo = IS3D && tz == 0 && z0 > 0 && x0 < nx;
+    m.up_halo = IS3D && tz == ZB - 1 && z0 + ZB < a.nz && x0 < nx;
+    m.fast_x = __all_sync(0xffffffffu, x0 > 0 && x0 + V < nx);
 
-    // Prologue: rows y0-1, y0, y0+1 and the per-row extras of row y0.
-    if (act) load_vec(col + (long long)y0 * a.pitch, cur);
-    if (act && y0 > 0) {
-        load_vec(col + (long long)(y0 - 1) * a.pitch, prv);
-    } else {
+    float A[V], B[V], C[V], D[V], PA[V], PB[V], DA[V], DB[V], UA[V], UB[V];
+    float WA = 0.f, WB = 0.f, EA = 0.f, EB = 0.f;
 #pragma unroll
-        for (int i = 0; i < V; ++i) prv[i] = bnd<BC>(cur[i]);
-    }
-    if (act && y0 + 1 < ny) {
-        load_vec(col + (long long)(y0 + 1) * a.pitch, nxt);
-    } else {
-#pragma unroll
-        for (int i = 0; i < V; ++i) nxt[i] = bnd<BC>(cur[i]);
-    }
-    if (act && has_p) load_vec(pcol + (long long)y0 * a.p_pitch, pc);
-    if (act && lane == 0 && x0 > 0) wl = load_scalar(col + (long long)y0 * a.pitch - 1);
-    if (act && lane == 31 && x0 + V < nx) er = load_scalar(col + (long long)y0 * a.pitch + V);
-    if (dn_halo) load_vec(dcol + (long long)y0 * a.pitch, dc);
-    if (up_halo) load_vec(ucol + (long long)y0 * a.pitch, uc);
+    for (int i = 0; i < V; ++i) { B[i] = 0.f; D[i] = 0.f; PA[i] = 0.f; DA[i] = 0.f; UA[i] = 0.f; }
+    // Prologue: A = row y0-1, B = row y0, C = row y0+1 (boundary rows
+    // materialised) and row y0's P, z-halos and x-edge scalars.
+    const long long pitch = a.pitch;
+    if (m.act) load_vec(m.col + (long long)y0 * pitch, B);
+    if (m.act && y0 > 0) load_vec(m.col + (long long)(y0 - 1) * pitch, A);
+    else m.fill_bnd(A, B);
+    if (m.act && y0 + 1 < ny) load_vec(m.col + (long long)(y0 + 1) * pitch, C);
+    else m.fill_bnd(C, B);
+    if (m.act && m.has_p) load_vec(m.pcol + (long long)y0 * a.p_pitch, PA);
+    if (m.act && lane == 0 && x0 > 0) WA = load_scalar(m.col + (long long)y0 * pitch - 1);
+    if (m.act && lane == 31 && x0 + V < nx) EA = load_scalar(m.col + (long long)y0 * pitch + V);
+    if (m.dn_halo) load_vec(m.dcol + (long long)y0 * pitch, DA);
+    if (m.up_halo) load_vec(m.ucol + (long long)y0 * pitch, UA);
 
-    const int rowlen = BX * V;
-    for (int y = y0; y < y1; ++y) {
-        // Issue the loads the next iteration needs.
-        const bool more = (y + 1 < y1);
-        float nn[V], pn[V], dn[V], un[V];
-        float wln = 0.f, ern = 0.f;
-#pragma unroll
-        for (int i = 0; i < V; ++i) { nn[i] = 0.f; pn[i] = 0.f; dn[i] = 0.f; un[i] = 0.f; }
-        if (act && more && y + 2 < ny) load_vec(col + (long long)(y + 2) * a.pitch, nn);
-        if (act && more && has_p) load_vec(pcol + (long long)(y + 1) * a.p_pitch, pn);
-        if (act && more && lane == 0 && x0 > 0) wln = load_scalar(col + (long long)(y + 1) * a.pitch - 1);
-        if (act && more && lane == 31 && x0 + V < nx) ern = load_scalar(col + (long long)(y + 1) * a.pitch + V);
-        if (dn_halo && more) load_vec(dcol + (long long)(y + 1) * a.pitch, dn);
-        if (up_halo && more) load_vec(ucol + (long long)(y + 1) * a.pitch, un);
-
-        // x-neighbours across the vector edges.
-        float w0 = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
-        float eV = __shfl_down_sync(0xffffffffu, cur[0], 1);
-        if (lane == 0) w0 = wl;
-        if (lane == 31) eV = er;
-
-        // z-neighbours through shared memory.
-        float dv[V], uv[V];
-        if (IS3D) {
-            float* buf = zsm + (size_t)(y & 1) * (ZB + 2) * rowlen + tx * V;
-            sm_put<V>(buf + (tz + 1) * rowlen, cur);
-            if (tz == 0) sm_put<V>(buf, dc);
-            if (tz == ZB - 1) sm_put<V>(buf + (ZB + 1) * rowlen, uc);
-            __syncthreads();
-            sm_get<V>(buf + tz * rowlen, dv);
-            sm_get<V>(buf + (tz + 2) * rowlen, uv);
-#pragma unroll
-            for (int i = 0; i < V; ++i) {
-                if (z == 0) dv[i] = bnd<BC>(cur[i]);
-                if (z + 1 >= a.nz) uv[i] = bnd<BC>(cur[i]);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < V; ++i) { dv[i] = 0.f; uv[i] = 0.f; }
-        }
-
-        if (act) {
-            float out[V];
-#pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const int x = x0 + i;
-                const float t = cur[i];
-                float w = (i == 0) ? w0 : cur[i - 1];
-                float e = (i == V - 1) ? eV : cur[i + 1];
-                if (x == 0) w = bnd<BC>(t);
-                if (x + 1 >= nx) e = bnd<BC>(t);
-                out[i] = heat_cell<IS3D>(t, prv[i], nxt[i], w, e, dv[i], uv[i], has_p ? pc[i] : 0.0f, a.c);
-            }
-            store_vec(Tout + zoff + (long long)y * a.pitch + x0, out, nx - x0);
-        }
-
-        // Rotate the row window.
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            prv[i] = cur[i];
-            cur[i] = nxt[i];
-            nxt[i] = (y + 2 < ny) ? nn[i] : bnd<BC>(cur[i]);
-            pc[i] = pn[i];
-            dc[i] = dn[i];
-            uc[i] = un[i];
-        }
-        wl = wln;
-        er = ern;
+    for (int y = y0; y < y1;) {
+        m.step(y, A, B, C, D, PA, PB, DA, DB, UA, UB, WA, WB, EA, EB);
+        if (++y >= y1) break;
+        m.step(y, B, C, D, A, PB, PA, DB, DA, UB, UA, WB, WA, EB, EA);
+        if (++y >= y1) break;
+        m.step(y, C, D, A, B, PA, PB, DA, DB, UA, UB, WA, WB, EA, EB);
+        if (++y >= y1) break;
+        m.step(y, D, A, B, C, PB, PA, DB, DA, UB, UA, WB, WA, EB, EA);
+        ++y;
     }
 }
 
@@ -324,6 +372,87 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
         if (gx >= nx || gy >= ny) continue;
         const float v = bufA[iz * area + (oy + D) * IX + (ox + D)];
         Tout[(long long)iz * a.plane + (long long)gy * a.pitch + gx] = from_f32<ST>(v);
+    }
+}
+
+// --------------------------------------------------------------- column --
+//
+// Depth 1 without a march: each thread owns one 16-byte vector along x at
+// one y and keeps every plane of its column (nz <= NZM) in registers, so
+// one round of independent loads (rows y-1, y, y+1 of every plane, the P
+// row, and the x-edge scalars of lanes 0 and 31) feeds the whole update.
+// x-neighbours come from warp shuffles, y- and z-neighbours from registers;
+// no shared memory and no barrier.  Vertical reuse between the rows of a
+// block goes through L1 (read-only path).  Block (32, rows).
+template <typename ST, int BC, int NZM>
+__global__ void __launch_bounds__(256) heat_column_kernel(const HeatArgs a) {
+    constexpr int V = Vec<ST>::N;
+    pdl_wait_then_trigger();
+    const int lane = threadIdx.x;
+    const int x0 = (blockIdx.x * 32 + lane) * V;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool act = (x0 < nx) && (y < ny);
+    const bool fast_x = __all_sync(0xffffffffu, x0 > 0 && x0 + V < nx);
+    const long long pitch = a.pitch, plane = a.plane;
+    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
+    const ST* base = Tin + (long long)min(y, ny - 1) * pitch + x0;
+
+    float c[NZM][V], n[NZM][V], so[NZM][V], p[V];
+    float wl[NZM], er[NZM];
+#pragma unroll
+    for (int z = 0; z < NZM; ++z) {
+        wl[z] = 0.f;
+        er[z] = 0.f;
+#pragma unroll
+        for (int i = 0; i < V; ++i) { c[z][i] = 0.f; n[z][i] = 0.f; so[z][i] = 0.f; }
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) p[i] = 0.f;
+    if (act) {
+#pragma unroll
+        for (int z = 0; z < NZM; ++z) {
+            if (z < nz) {
+                const ST* q = base + z * plane;
+                load_vec(q, c[z]);
+                if (y > 0) load_vec(q - pitch, n[z]);
+                if (y + 1 < ny) load_vec(q + pitch, so[z]);
+                if (lane == 0 && x0 > 0) wl[z] = load_scalar(q - 1);
+                if (lane == 31 && x0 + V < nx) er[z] = load_scalar(q + V);
+            }
+        }
+        load_vec(static_cast<const ST*>(a.P) + (long long)y * a.p_pitch + x0, p);
+    }
+#pragma unroll
+    for (int z = 0; z < NZM; ++z) {
+        if (z < nz) {  // warp-uniform
+            float w0 = __shfl_up_sync(0xffffffffu, c[z][V - 1], 1);
+            float eV = __shfl_down_sync(0xffffffffu, c[z][0], 1);
+            if (lane == 0) w0 = wl[z];
+            if (lane == 31) eV = er[z];
+            if (!act) continue;
+            float out[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const float t = c[z][i];
+                float w = (i == 0) ? w0 : c[z][i - 1];
+                float e = (i == V - 1) ? eV : c[z][i + 1];
+                if (!fast_x) {
+                    if (x0 + i == 0) w = bnd<BC>(t);
+                    if (x0 + i + 1 >= nx) e = bnd<BC>(t);
+                }
+                const float nv = (y > 0) ? n[z][i] : bnd<BC>(t);
+                const float sv = (y + 1 < ny) ? so[z][i] : bnd<BC>(t);
+                float d = 0.f, u = 0.f;
+                if (NZM > 1) {
+                    d = (z > 0) ? c[z > 0 ? z - 1 : 0][i] : bnd<BC>(t);
+                    u = (z + 1 < nz) ? c[z + 1 < NZM ? z + 1 : z][i] : bnd<BC>(t);
+                }
+                out[i] = heat_cell<(NZM > 1)>(t, nv, sv, w, e, d, u, (z == 0) ? p[i] : 0.0f, a.c);
+            }
+            store_vec(static_cast<ST*>(a.Tout) + (long long)z * plane + (long long)y * pitch + x0, out,
+                      fast_x ? V : nx - x0);
+        }
     }
 }
 
@@ -523,6 +652,9 @@ const void* pick_wave(int depth) {
 
 template <typename ST, int BC>
 const void* pick(bool is3d, int depth, int variant) {
+    if (variant == GS_KERNEL_COLUMN && depth == 1)
+        return is3d ? (const void*)heat_column_kernel<ST, BC, kColumnMaxNz>
+                    : (const void*)heat_column_kernel<ST, BC, 1>;
     if (variant == GS_KERNEL_WAVE)
         return is3d ? pick_wave<ST, BC, true>(depth) : pick_wave<ST, BC, false>(depth);
     if (variant == GS_KERNEL_MARCH && depth == 1)
@@ -560,6 +692,12 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
         out->grid = dim3((a.nx + block_x * V - 1) / (block_x * V), (a.ny + a.rows - 1) / a.rows,
                          is3d ? (a.nz + zb - 1) / zb : 1);
         out->smem = is3d ? (size_t)2 * (zb + 2) * block_x * V * sizeof(float) : 0;
+    } else if (variant == GS_KERNEL_COLUMN) {
+        if (is3d && a.nz > kColumnMaxNz) return cudaErrorInvalidValue;
+        const int by = std::max(1, std::min(a.rows, 8));
+        out->block = dim3(32, by, 1);
+        out->grid = dim3((a.nx + 32 * V - 1) / (32 * V), (a.ny + by - 1) / by, 1);
+        out->smem = 0;
     } else if (variant == GS_KERNEL_WAVE) {
         if (is3d && a.nz > kWaveMaxNz) return cudaErrorInvalidValue;
         const int stride = 30 * V;

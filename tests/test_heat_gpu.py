@@ -54,7 +54,12 @@ def test_heat3d_parity_small(oracle, shape, bc):
     nx, ny, nz = shape
     T0, P = gs_inputs.heat_fields(nx, ny, nz, seed=8)
     ref = oracle.heat_run(T0, P, 40, oracle.HEAT_COEFFS_3D, bc)
-    for plan in (None, dict(block_x=64, rows=2)):
+    import paper_2501_09398_gb300 as g
+
+    plans = [None, dict(block_x=64, rows=2)]
+    if nz <= 8:
+        plans.append(dict(kernel=g.GS_KERNEL_COLUMN, rows=3))
+    for plan in plans:
         got = heat_gpu(T0, P, 40, S=0, bc=bc, plan=plan)
         assert np.max(np.abs(got - ref)) <= HEAT_RTOL * np.max(np.abs(ref))
 
@@ -95,6 +100,15 @@ def test_temporal_blocking_bit_identical(shape, depth):
         plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_WAVE, rows=rows, block_x=bx)
         assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"wave rows={rows} bx={bx}"
         assert np.array_equal(heat_gpu(T0, P, n, S=6, plan=plan), base), f"wave graph rows={rows} bx={bx}"
+    if depth == 1:  # column kernel: every plane of a column in registers (nz <= 8)
+        for rows in (1, 4, 8):
+            plan = dict(kernel=g.GS_KERNEL_COLUMN, rows=rows)
+            if nz > 8:
+                with pytest.raises(g.GsError):
+                    heat_gpu(T0, P, n, S=0, plan=plan)
+                continue
+            assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"column rows={rows}"
+            assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column graph rows={rows}"
     if depth > 1:  # overlapped shared-memory tiles
         for tile in ((32, 32), (16, 8), (13, 7)):
             plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_TILE, tile_x=tile[0], tile_y=tile[1])
