@@ -44,7 +44,7 @@ WORKLOADS = {
                        plan=dict(kernel=4, rows=4)),
     "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1,
                         plan=dict(kernel=4, rows=8)),
-    "fdtd-128": dict(kind="fdtd", N=128, iters=5000, S=100, depth=1, plan={}),
+    "fdtd-128": dict(kind="fdtd", N=128, iters=5000, S=100, depth=1, plan=dict(kernel=4, rows=2)),
     "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=1, plan={}),
 }
 DEFAULT = "heat3d-512x512x8"
@@ -303,7 +303,7 @@ class MultiRunner:
         self.m = g.gs_multi_create(self.sides, self.sides, g.GS_F32, g.GS_BC_CLAMP, self.stream.cuda_stream)
         self.ctx = None
         self.fields = g.MultiFields(self.m, self.sides, self.sides)
-        mp = {k: v for k, v in plan_extra.items() if k in ("block_x", "rows", "use_pdl")}
+        mp = {k: v for k, v in plan_extra.items() if k in ("block_x", "rows", "use_pdl", "kernel")}
         if mp:
             g.gs_multi_set_plan(self.m, **mp)
         self.inputs = gs_inputs.instance_fields(self.sides)

@@ -143,7 +143,9 @@ typedef struct gs_plan {
     int32_t temporal_depth;
     int32_t use_pdl;
     int32_t device_launch;
-    int32_t kernel; /* gs_kernel; thermal only (FDTD ignores it) */
+    int32_t kernel; /* gs_kernel; FDTD: COLUMN (default: one vector per thread,
+                       block 32 x rows x 8/rows) or MARCH (block_x threads
+                       marching `rows` k planes) */
 } gs_plan;
 
 typedef struct gs_stats {
@@ -448,10 +450,13 @@ typedef enum gs_multi_mode {
 } gs_multi_mode;
 
 typedef struct gs_multi_plan {
-    int32_t block_x; /* threads per block (multiple of 32, <= 512); default 64 */
-    int32_t rows;    /* rows per work item; default 8 */
+    int32_t block_x; /* MARCH tiles: threads per block (multiple of 32, <= 512); default 64 */
+    int32_t rows;    /* rows per work item (COLUMN: <= 8); default 8 (MARCH), 4 (COLUMN) */
     int32_t blocks;  /* persistent grid size; 0: SM count x occupancy */
     int32_t use_pdl; /* programmatic dependent launch between iterations */
+    int32_t kernel;  /* work-item tile: GS_KERNEL_MARCH (default; block_x threads
+                        marching `rows` rows) or GS_KERNEL_COLUMN (32 x rows
+                        threads, one row per warp row) */
 } gs_multi_plan;
 
 /* Create a batch of n instances, instance i of size nx[i] x ny[i] (each in

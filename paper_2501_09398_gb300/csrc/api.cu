@@ -127,8 +127,9 @@ gs_plan default_plan(const gs_ctx* c) {
     if (c->kind == GS_FDTD3D) {
         p.block_x = 32;
         while (p.block_x * vec_elems(c->dt) < c->nx + 1 && p.block_x < 128) p.block_x += 32;
-        p.rows = 16;  // k planes per block
+        p.rows = 4;  // COLUMN: j rows per block (k planes per block for MARCH)
         p.temporal_depth = 1;
+        p.kernel = GS_KERNEL_COLUMN;
     } else if (c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz) {
         // the column kernel (measured fastest at depth 1 for 2D and thin
         // stacks); rows = warps per block stacked in y
@@ -175,7 +176,11 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
         return fail(c, GS_ERR_UNSUPPORTED, "temporal blocking is provided for the thermal stencils only");
     if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_COLUMN)
         return fail(c, GS_ERR_INVALID_ARG, "plan.kernel must be a gs_kernel value");
-    if (c->kind == GS_FDTD3D) p->kernel = GS_KERNEL_AUTO;
+    if (c->kind == GS_FDTD3D) {
+        if (p->kernel == GS_KERNEL_AUTO) p->kernel = GS_KERNEL_COLUMN;
+        if (p->kernel != GS_KERNEL_COLUMN && p->kernel != GS_KERNEL_MARCH)
+            return fail(c, GS_ERR_INVALID_ARG, "FDTD kernels: GS_KERNEL_COLUMN or GS_KERNEL_MARCH");
+    }
     const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
     const bool column_ok = (c->kind == GS_HEAT2D) || (c->nz <= kColumnMaxNz);
     if (is_heat(c) && p->kernel == GS_KERNEL_AUTO)
@@ -274,8 +279,8 @@ gs_status ensure_descs(gs_ctx* c) {
         a.delay = c->fp.src_delay;
         a.width = c->fp.src_width;
         a.counter = c->d_counter;
-        cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, &c->desc[0][0]);
-        if (e == cudaSuccess) e = fdtd_desc(c->dt, true, a, c->plan.block_x, &c->desc[0][1]);
+        cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, c->plan.kernel, &c->desc[0][0]);
+        if (e == cudaSuccess) e = fdtd_desc(c->dt, true, a, c->plan.block_x, c->plan.kernel, &c->desc[0][1]);
         if (e != cudaSuccess) return cuda_fail(c, e, "FDTD kernel set-up");
     }
     c->descs_ok = true;

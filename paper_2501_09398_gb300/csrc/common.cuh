@@ -161,8 +161,12 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
                       LaunchDesc* out);
 size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth);
 size_t heat_wave_smem(int nz3d, int depth, int vec);
-const void* heat_multi_func(gs_dtype dt, gs_bc bc);  // heat_multi_kernel<dt, bc>
-cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, LaunchDesc* out);
+// heat_multi_kernel for (dt, bc) with MARCH tiles (blockDim.x threads x
+// `rows` rows) or COLUMN tiles (32 x `rows` threads, one row per warp row).
+const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant);
+// FDTD H (e_half false) or E kernel; variant GS_KERNEL_COLUMN (no march,
+// block (32, kc, 8/kc)) or GS_KERNEL_MARCH (block_x threads marching kc planes).
+cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out);
 cudaError_t convert_to_storage(gs_dtype dt, const float* src, void* dst, long long width, long long rows,
                                long long pitch, cudaStream_t st);
 cudaError_t convert_from_storage(gs_dtype dt, const void* src, float* dst, long long width, long long rows,

@@ -22,6 +22,15 @@ namespace gs {
 
 enum { EX = 0, EY = 1, EZ = 2, HX = 3, HY = 4, HZ = 5 };
 
+// f -/+ s*((a - b) - (c - d)) with every rounding spelled out, so that both
+// kernel variants produce the same bits.
+__device__ __forceinline__ float curl_sub(float f, float s, float a, float b, float c, float d) {
+    return __fmaf_rn(-s, __fsub_rn(__fsub_rn(a, b), __fsub_rn(c, d)), f);
+}
+__device__ __forceinline__ float curl_add(float f, float s, float a, float b, float c, float d) {
+    return __fmaf_rn(s, __fsub_rn(__fsub_rn(a, b), __fsub_rn(c, d)), f);
+}
+
 template <typename ST>
 __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
     constexpr int V = Vec<ST>::N;
@@ -85,9 +94,9 @@ __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
                 const int i = i0 + e;
                 const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
                 const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
-                if (j < N && k < N) hx[e] -= s * ((ezj1[e] - ez[e]) - (eyk1[e] - eyk[e]));
-                if (i < N && k < N) hy[e] -= s * ((exk1[e] - exk[e]) - (ez_ip - ez[e]));
-                if (i < N && j < N) hz[e] -= s * ((ey_ip - eyk[e]) - (exj1[e] - exk[e]));
+                if (j < N && k < N) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
+                if (i < N && k < N) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
+                if (i < N && j < N) hz[e] = curl_sub(hz[e], s, ey_ip, eyk[e], exj1[e], exk[e]);
             }
             store_vec(Hx + o, hx, nv);
             store_vec(Hy + o, hy, nv);
@@ -162,19 +171,19 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
                 const bool i_int = (i >= 1 && i <= N - 1);
                 const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
                 const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
-                if (i < N && j_int && k_int) ex[e] += s * ((hz[e] - hzj_1[e]) - (hy[e] - hyk_1[e]));
-                if (j < N && i_int && k_int) ey[e] += s * ((hx[e] - hxk_1[e]) - (hz[e] - hz_im));
-                if (k < N && i_int && j_int) ez[e] += s * ((hy[e] - hy_im) - (hx[e] - hxj_1[e]));
+                if (i < N && j_int && k_int) ex[e] = curl_add(ex[e], s, hz[e], hzj_1[e], hy[e], hyk_1[e]);
+                if (j < N && i_int && k_int) ey[e] = curl_add(ey[e], s, hx[e], hxk_1[e], hz[e], hz_im);
+                if (k < N && i_int && j_int) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
             }
             // The one thread that owns cell (si, sj, sk) keeps the device
             // step counter n and, if the source is on, adds it to Ez there.
             if (j == a.sj && k == a.sk && a.si >= i0 && a.si < i0 + V) {
                 const long long n = *a.counter;
                 if (a.src_on) {
-                    const float u = ((float)n - a.delay) / a.width;
+                    const float u = __fdiv_rn(__fsub_rn((float)n, a.delay), a.width);
 #pragma unroll
                     for (int e = 0; e < V; ++e)
-                        if (i0 + e == a.si) ez[e] += a.amp * expf(-u * u);
+                        if (i0 + e == a.si) ez[e] = __fadd_rn(ez[e], __fmul_rn(a.amp, expf(-u * u)));
                 }
                 *a.counter = n + 1;
             }
@@ -187,20 +196,187 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
     }
 }
 
-cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, LaunchDesc* out) {
+// ------------------------------------------------------------- column ----
+//
+// No march: each thread owns one 16-byte vector along i at one (j, k) and
+// issues all of its loads at once (own components, the k+1 / j+1 (H) or
+// k-1 / j-1 (E) neighbour vectors, and the i-edge scalars of lanes 31 / 0).
+// Block (32, by, bz); neighbour vectors are re-read through L1/L2.
+template <typename ST>
+__global__ void __launch_bounds__(256) fdtd_h_column_kernel(const FdtdArgs a) {
+    constexpr int V = Vec<ST>::N;
+    pdl_wait_then_trigger();
+    const int N = a.N, M = N + 1;
+    const int lane = threadIdx.x;
+    const int i0 = (blockIdx.x * 32 + lane) * V;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const bool act = (i0 < M) && (j < M) && (k < M);
+    const ST* Ex = static_cast<const ST*>(a.f[EX]);
+    const ST* Ey = static_cast<const ST*>(a.f[EY]);
+    const ST* Ez = static_cast<const ST*>(a.f[EZ]);
+    ST* Hx = static_cast<ST*>(a.f[HX]);
+    ST* Hy = static_cast<ST*>(a.f[HY]);
+    ST* Hz = static_cast<ST*>(a.f[HZ]);
+    const float s = a.s;
+    const long long o = act ? (long long)k * a.plane + (long long)j * a.pitch + i0 : 0;
+    float exk[V], eyk[V], ez[V], exk1[V], eyk1[V], ezj1[V], exj1[V], hx[V], hy[V], hz[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        exk[e] = 0.f; eyk[e] = 0.f; ez[e] = 0.f; exk1[e] = 0.f; eyk1[e] = 0.f; ezj1[e] = 0.f; exj1[e] = 0.f;
+        hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f;
+    }
+    float ez_r = 0.f, ey_r = 0.f;
+    if (act) {
+        load_vec(Ex + o, exk);
+        load_vec(Ey + o, eyk);
+        load_vec(Ez + o, ez);
+        if (k + 1 < M) {
+            load_vec(Ex + o + a.plane, exk1);
+            load_vec(Ey + o + a.plane, eyk1);
+        }
+        if (j + 1 < M) {
+            load_vec(Ez + o + a.pitch, ezj1);
+            load_vec(Ex + o + a.pitch, exj1);
+        }
+        load_vec_rw(Hx + o, hx);
+        load_vec_rw(Hy + o, hy);
+        load_vec_rw(Hz + o, hz);
+        if (lane == 31 && i0 + V < M) {
+            ez_r = load_scalar(Ez + o + V);
+            ey_r = load_scalar(Ey + o + V);
+        }
+    }
+    const float ez_n = __shfl_down_sync(0xffffffffu, ez[0], 1);
+    const float ey_n = __shfl_down_sync(0xffffffffu, eyk[0], 1);
+    if (!act) return;
+    const float ez_last = (lane == 31) ? ez_r : ez_n;
+    const float ey_last = (lane == 31) ? ey_r : ey_n;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
+        const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
+        if (j < N && k < N) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
+        if (i < N && k < N) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
+        if (i < N && j < N) hz[e] = curl_sub(hz[e], s, ey_ip, eyk[e], exj1[e], exk[e]);
+    }
+    const int nv = M - i0;
+    store_vec(Hx + o, hx, nv);
+    store_vec(Hy + o, hy, nv);
+    store_vec(Hz + o, hz, nv);
+}
+
+template <typename ST>
+__global__ void __launch_bounds__(256) fdtd_e_column_kernel(const FdtdArgs a) {
+    constexpr int V = Vec<ST>::N;
+    pdl_wait_then_trigger();
+    const int N = a.N, M = N + 1;
+    const int lane = threadIdx.x;
+    const int i0 = (blockIdx.x * 32 + lane) * V;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const bool act = (i0 < M) && (j < M) && (k < M);
+    ST* Ex = static_cast<ST*>(a.f[EX]);
+    ST* Ey = static_cast<ST*>(a.f[EY]);
+    ST* Ez = static_cast<ST*>(a.f[EZ]);
+    const ST* Hx = static_cast<const ST*>(a.f[HX]);
+    const ST* Hy = static_cast<const ST*>(a.f[HY]);
+    const ST* Hz = static_cast<const ST*>(a.f[HZ]);
+    const float s = a.s;
+    const long long o = act ? (long long)k * a.plane + (long long)j * a.pitch + i0 : 0;
+    float hx[V], hy[V], hz[V], hxk_1[V], hyk_1[V], hzj_1[V], hxj_1[V], ex[V], ey[V], ez[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f; hxk_1[e] = 0.f; hyk_1[e] = 0.f; hzj_1[e] = 0.f; hxj_1[e] = 0.f;
+        ex[e] = 0.f; ey[e] = 0.f; ez[e] = 0.f;
+    }
+    float hz_l = 0.f, hy_l = 0.f;
+    if (act) {
+        load_vec(Hx + o, hx);
+        load_vec(Hy + o, hy);
+        load_vec(Hz + o, hz);
+        if (k >= 1) {
+            load_vec(Hx + o - a.plane, hxk_1);
+            load_vec(Hy + o - a.plane, hyk_1);
+        }
+        if (j >= 1) {
+            load_vec(Hz + o - a.pitch, hzj_1);
+            load_vec(Hx + o - a.pitch, hxj_1);
+        }
+        load_vec_rw(Ex + o, ex);
+        load_vec_rw(Ey + o, ey);
+        load_vec_rw(Ez + o, ez);
+        if (lane == 0 && i0 >= 1) {
+            hz_l = load_scalar(Hz + o - 1);
+            hy_l = load_scalar(Hy + o - 1);
+        }
+    }
+    const float hz_p = __shfl_up_sync(0xffffffffu, hz[V - 1], 1);
+    const float hy_p = __shfl_up_sync(0xffffffffu, hy[V - 1], 1);
+    if (!act) return;
+    const float hz_first = (lane == 0) ? hz_l : hz_p;
+    const float hy_first = (lane == 0) ? hy_l : hy_p;
+    const bool j_int = (j >= 1 && j <= N - 1);
+    const bool k_int = (k >= 1 && k <= N - 1);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        const bool i_int = (i >= 1 && i <= N - 1);
+        const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
+        const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
+        if (i < N && j_int && k_int) ex[e] = curl_add(ex[e], s, hz[e], hzj_1[e], hy[e], hyk_1[e]);
+        if (j < N && i_int && k_int) ey[e] = curl_add(ey[e], s, hx[e], hxk_1[e], hz[e], hz_im);
+        if (k < N && i_int && j_int) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
+    }
+    if (j == a.sj && k == a.sk && a.si >= i0 && a.si < i0 + V) {
+        const long long n = *a.counter;
+        if (a.src_on) {
+            const float u = __fdiv_rn(__fsub_rn((float)n, a.delay), a.width);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (i0 + e == a.si) ez[e] = __fadd_rn(ez[e], __fmul_rn(a.amp, expf(-u * u)));
+        }
+        *a.counter = n + 1;
+    }
+    const int nv = M - i0;
+    store_vec(Ex + o, ex, nv);
+    store_vec(Ey + o, ey, nv);
+    store_vec(Ez + o, ez, nv);
+}
+
+cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out) {
     const int V = (dt == GS_F32) ? 4 : 8;
     const int M = a.N + 1;
+    const bool col = (variant == GS_KERNEL_COLUMN);
     switch (dt) {
-        case GS_F32: out->func = e_half ? (const void*)fdtd_e_kernel<float> : (const void*)fdtd_h_kernel<float>; break;
-        case GS_BF16:
-            out->func = e_half ? (const void*)fdtd_e_kernel<__nv_bfloat16> : (const void*)fdtd_h_kernel<__nv_bfloat16>;
+        case GS_F32:
+            out->func = col ? (e_half ? (const void*)fdtd_e_column_kernel<float> : (const void*)fdtd_h_column_kernel<float>)
+                            : (e_half ? (const void*)fdtd_e_kernel<float> : (const void*)fdtd_h_kernel<float>);
             break;
-        case GS_F16: out->func = e_half ? (const void*)fdtd_e_kernel<__half> : (const void*)fdtd_h_kernel<__half>; break;
+        case GS_BF16:
+            out->func = col ? (e_half ? (const void*)fdtd_e_column_kernel<__nv_bfloat16>
+                                      : (const void*)fdtd_h_column_kernel<__nv_bfloat16>)
+                            : (e_half ? (const void*)fdtd_e_kernel<__nv_bfloat16>
+                                      : (const void*)fdtd_h_kernel<__nv_bfloat16>);
+            break;
+        case GS_F16:
+            out->func = col ? (e_half ? (const void*)fdtd_e_column_kernel<__half> : (const void*)fdtd_h_column_kernel<__half>)
+                            : (e_half ? (const void*)fdtd_e_kernel<__half> : (const void*)fdtd_h_kernel<__half>);
+            break;
         default: return cudaErrorInvalidValue;
     }
-    const int by = std::max(1, 256 / block_x);
-    out->block = dim3(block_x, by, 1);
-    out->grid = dim3((M + block_x * V - 1) / (block_x * V), (M + by - 1) / by, (M + a.kc - 1) / a.kc);
+    if (col) {
+        // block (32, by, bz): a.kc rows of j per block (<= 8), 256/(32*by) planes of k
+        const int by = std::max(1, std::min(a.kc, 8));
+        const int bz = std::max(1, 8 / by);
+        out->block = dim3(32, by, bz);
+        out->grid = dim3((M + 32 * V - 1) / (32 * V), (M + by - 1) / by, (M + bz - 1) / bz);
+    } else {
+        const int by = std::max(1, 256 / block_x);
+        out->block = dim3(block_x, by, 1);
+        out->grid = dim3((M + block_x * V - 1) / (block_x * V), (M + by - 1) / by, (M + a.kc - 1) / a.kc);
+    }
     out->smem = 0;
     out->set_args(a);
     return cudaSuccess;

@@ -238,6 +238,9 @@ __global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
     heat_march_tile<ST, BC, IS3D>(a, blockIdx.x, blockIdx.y, blockIdx.z, zsm);
 }
 
+template <typename ST, int BC, int NZM>
+__device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int by);
+
 // ------------------------------------------------- multi-instance (2D) ----
 //
 // Persistent kernel over many independent 2D grids: the work list is every
@@ -245,11 +248,11 @@ __global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
 // first; block b takes items b, b + gridDim.x, ...  The descriptor table
 // (per instance: both buffers, P, sizes, pitches, first work item) lives in
 // device memory; `parity` selects which buffer is read.
-template <typename ST, int BC>
+template <typename ST, int BC, bool COL>
 __global__ void __launch_bounds__(512) heat_multi_kernel(const MultiArgs m) {
     pdl_wait_then_trigger();
     const int V = Vec<ST>::N;
-    const int span = blockDim.x * V;
+    const int span = (COL ? 32 : blockDim.x) * V;
     for (int w = blockIdx.x; w < m.total_items; w += gridDim.x) {
         // binary search: last instance whose first item <= w
         int lo = 0, hi = m.n_inst - 1;
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(512) heat_multi_kernel(const MultiArgs m) {
         a.c = m.c;
         const int ntx = (d.nx + span - 1) / span;
         const int item = w - d.first_item;
-        heat_march_tile<ST, BC, false>(a, item % ntx, item / ntx, 0, nullptr);
+        if (COL) heat_column_tile<ST, BC, 1>(a, item % ntx, item / ntx);
+        else heat_march_tile<ST, BC, false>(a, item % ntx, item / ntx, 0, nullptr);
     }
 }
 
@@ -385,12 +389,11 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
 // no shared memory and no barrier.  Vertical reuse between the rows of a
 // block goes through L1 (read-only path).  Block (32, rows).
 template <typename ST, int BC, int NZM>
-__global__ void __launch_bounds__(256) heat_column_kernel(const HeatArgs a) {
+__device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int by) {
     constexpr int V = Vec<ST>::N;
-    pdl_wait_then_trigger();
     const int lane = threadIdx.x;
-    const int x0 = (blockIdx.x * 32 + lane) * V;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x0 = (bx * 32 + lane) * V;
+    const int y = by * blockDim.y + threadIdx.y;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const bool act = (x0 < nx) && (y < ny);
     const bool fast_x = __all_sync(0xffffffffu, x0 > 0 && x0 + V < nx);
@@ -454,6 +457,12 @@ __global__ void __launch_bounds__(256) heat_column_kernel(const HeatArgs a) {
                       fast_x ? V : nx - x0);
         }
     }
+}
+
+template <typename ST, int BC, int NZM>
+__global__ void __launch_bounds__(256) heat_column_kernel(const HeatArgs a) {
+    pdl_wait_then_trigger();
+    heat_column_tile<ST, BC, NZM>(a, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------ wavefront --
@@ -607,17 +616,24 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
 
 // ------------------------------------------------------------- factory ----
 
-const void* heat_multi_func(gs_dtype dt, gs_bc bc) {
+namespace {
+template <bool COL>
+const void* multi_func(gs_dtype dt, gs_bc bc) {
     const bool cl = (bc == GS_BC_CLAMP);
     switch (dt) {
-        case GS_F32: return cl ? (const void*)heat_multi_kernel<float, GS_BC_CLAMP>
-                               : (const void*)heat_multi_kernel<float, GS_BC_DIRICHLET0>;
-        case GS_BF16: return cl ? (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_CLAMP>
-                                : (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_DIRICHLET0>;
-        case GS_F16: return cl ? (const void*)heat_multi_kernel<__half, GS_BC_CLAMP>
-                               : (const void*)heat_multi_kernel<__half, GS_BC_DIRICHLET0>;
+        case GS_F32: return cl ? (const void*)heat_multi_kernel<float, GS_BC_CLAMP, COL>
+                               : (const void*)heat_multi_kernel<float, GS_BC_DIRICHLET0, COL>;
+        case GS_BF16: return cl ? (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_CLAMP, COL>
+                                : (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_DIRICHLET0, COL>;
+        case GS_F16: return cl ? (const void*)heat_multi_kernel<__half, GS_BC_CLAMP, COL>
+                               : (const void*)heat_multi_kernel<__half, GS_BC_DIRICHLET0, COL>;
     }
     return nullptr;
+}
+}  // namespace
+
+const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant) {
+    return variant == GS_KERNEL_COLUMN ? multi_func<true>(dt, bc) : multi_func<false>(dt, bc);
 }
 
 size_t heat_wave_smem(int nz3d, int depth, int vec) {

@@ -86,7 +86,8 @@ gs_status ensure_table(gs_multi* m) {
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return m->nx[a] * m->ny[a] > m->nx[b] * m->ny[b]; });
-    const int span = m->plan.block_x * vec_elems(m->dt);
+    const bool col = (m->plan.kernel == GS_KERNEL_COLUMN);
+    const int span = (col ? 32 : m->plan.block_x) * vec_elems(m->dt);
     std::vector<MultiInstance> host(n);
     int item = 0;
     for (int k = 0; k < n; ++k) {
@@ -120,11 +121,12 @@ gs_status ensure_table(gs_multi* m) {
                                 m->stream));
     GS_MCUDA(m, cudaStreamSynchronize(m->stream));
     m->total_items = item;
-    const void* f = heat_multi_func(m->dt, m->bc);
+    const void* f = heat_multi_func(m->dt, m->bc, m->plan.kernel);
+    const dim3 block = col ? dim3(32, m->plan.rows, 1) : dim3(m->plan.block_x, 1, 1);
     int blocks = m->plan.blocks;
     if (blocks <= 0) {
         int occ = 0;
-        GS_MCUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, m->plan.block_x, 0));
+        GS_MCUDA(m, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, (int)(block.x * block.y), 0));
         blocks = std::max(1, occ) * device_sm_count();
     }
     blocks = std::max(1, std::min(blocks, item));
@@ -139,7 +141,7 @@ gs_status ensure_table(gs_multi* m) {
         LaunchDesc& d = m->desc[par];
         d.func = f;
         d.grid = dim3(blocks, 1, 1);
-        d.block = dim3(m->plan.block_x, 1, 1);
+        d.block = block;
         d.smem = 0;
         d.set_args(a);
     }
@@ -223,6 +225,7 @@ gs_status gs_multi_create(gs_multi** out, int32_t n, const int64_t* nx, const in
     m->bc = bc;
     m->plan.block_x = 64;
     m->plan.rows = 8;
+    m->plan.kernel = GS_KERNEL_MARCH;
     cudaError_t e = cudaSuccess;
     if (stream) {
         m->stream = static_cast<cudaStream_t>(stream);
@@ -276,10 +279,17 @@ gs_status gs_multi_set_heat_coeffs(gs_multi* m, const gs_heat_coeffs* c) {
 gs_status gs_multi_set_plan(gs_multi* m, const gs_multi_plan* p) {
     if (!m || !p) return GS_ERR_INVALID_ARG;
     gs_multi_plan q = *p;
+    // MARCH tiles measured faster here: a persistent loop over small column
+    // tiles exposes one full load round trip per work item
+    if (q.kernel == GS_KERNEL_AUTO) q.kernel = GS_KERNEL_MARCH;
+    if (q.kernel != GS_KERNEL_COLUMN && q.kernel != GS_KERNEL_MARCH)
+        return mfail(m, GS_ERR_INVALID_ARG, "kernel must be GS_KERNEL_COLUMN or GS_KERNEL_MARCH");
     if (q.block_x == 0) q.block_x = 64;
-    if (q.rows == 0) q.rows = 8;
+    if (q.rows == 0) q.rows = (q.kernel == GS_KERNEL_COLUMN) ? 4 : 8;
     if (q.block_x < 32 || q.block_x > 512 || q.block_x % 32)
         return mfail(m, GS_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [32, 512]");
+    if (q.kernel == GS_KERNEL_COLUMN && q.rows > 8)
+        return mfail(m, GS_ERR_INVALID_ARG, "COLUMN tiles take rows <= 8");
     if (q.rows < 1 || q.blocks < 0 || (q.use_pdl != 0 && q.use_pdl != 1))
         return mfail(m, GS_ERR_INVALID_ARG, "rows >= 1, blocks >= 0, use_pdl in {0, 1}");
     gs_plan sp{};

@@ -136,7 +136,7 @@ extern "C" gs_status gs_multi_step_noalloc(const gs_instance* inst, int32_t n_in
     e = cudaMemcpyAsync(ds.desc, rows, sizeof(MultiInstance) * n_inst, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return global_fail(GS_ERR_CUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
 
-    const void* f = heat_multi_func(storage, bc);
+    const void* f = heat_multi_func(storage, bc, GS_KERNEL_MARCH);
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kBlockX, 0);
     if (e != cudaSuccess) return global_fail(GS_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));

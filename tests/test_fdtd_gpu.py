@@ -66,7 +66,11 @@ def test_graph_bit_identical_and_plans():
     for S in (1, 4, 7, 45, 60):
         got = _gpu_run(N, 45, S, src=src)
         assert all(np.array_equal(got[k], base[k]) for k in FDTD_NAMES), f"S={S}"
-    for plan in (dict(use_pdl=1), dict(block_x=32, rows=3), dict(block_x=128, rows=40), dict(device_launch=1)):
+    import paper_2501_09398_gb300 as g
+
+    for plan in (dict(use_pdl=1), dict(rows=1), dict(rows=3), dict(rows=8), dict(device_launch=1),
+                 dict(kernel=g.GS_KERNEL_MARCH, block_x=32, rows=3),
+                 dict(kernel=g.GS_KERNEL_MARCH, block_x=128, rows=40)):
         got = _gpu_run(N, 45, 9, src=src, plan=plan)
         assert all(np.array_equal(got[k], base[k]) for k in FDTD_NAMES), str(plan)
 

@@ -52,7 +52,9 @@ def test_small_batch_all_modes_bit_identical(oracle):
     for i, (T, P) in enumerate(fields_np):
         assert max_rel(base[i], oracle.heat_run(T, P, n, oracle.HEAT_COEFFS_2D)) <= HEAT_RTOL
     for S, mode, plan in ((0, g.GS_MULTI_FUSED, None), (7, g.GS_MULTI_FUSED, None), (23, g.GS_MULTI_FUSED, None),
-                          (5, g.GS_MULTI_FUSED, dict(block_x=32, rows=3, blocks=7)),
+                          (5, g.GS_MULTI_FUSED, dict(block_x=32, rows=3, blocks=7, kernel=g.GS_KERNEL_MARCH)),
+                          (5, g.GS_MULTI_FUSED, dict(rows=8, blocks=5, kernel=g.GS_KERNEL_COLUMN)),
+                          (0, g.GS_MULTI_FUSED, dict(rows=1, kernel=g.GS_KERNEL_COLUMN)),
                           (4, g.GS_MULTI_FUSED, dict(use_pdl=1)), (6, g.GS_MULTI_SEPARATE, None)):
         got, st = _run(None, fields_np, n, S, mode, plan=plan, dims=dims)
         assert all(np.array_equal(a, b) for a, b in zip(got, base)), (S, mode, plan)
