@@ -65,6 +65,33 @@ def multi_sides(w):
     return gs_inputs.instance_sides(w["n"], w["lo"], w["hi"], seed=0)
 
 
+def kernel_sha():
+    """First 16 hex digits of sha256 over the thermal kernel sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("heat.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2501_09398_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summaries, if they were
+    taken on the current kernel sources (else None)."""
+    import glob
+    import re
+
+    sha = kernel_sha()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as f:
+            for line in f:
+                m = re.match(r"bench-traffic: workload=(\S+) kernel=\S+ sha256=(\w+) bytes=(\d+)", line)
+                if m and m.group(1) == workload and m.group(2) == sha:
+                    return int(m.group(3))
+    return None
+
+
 def cells_of(w):
     if w["kind"] == "multi":
         return sum(s * s for s in multi_sides(w))
@@ -579,7 +606,8 @@ def main():
                    "temporal_depth": m["depth"], "parallelism": f"replicas x{world}" if world > 1 else "single",
                    "l2": "flushed between steps (256 MiB write)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "launch_ms_in_step": launch_ms,
+                     "traffic": recorded_traffic(args.workload), "peak_kind": peak_kind,
+                     "launch_ms_in_step": launch_ms,
                      "bytes_per_launch": bytes_launch, "isolated_launch_ms": m["kern_ms"],
                      "isolated_GBps": isolated},
         "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
