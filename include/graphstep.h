@@ -112,6 +112,9 @@ typedef struct gs_fdtd_params {
  *   COLUMN depth 1 only, 2D or nz <= 8: each thread owns one vector of cells
  *          at one y with every plane of its column in registers (no march,
  *          no shared memory); `rows` (<= 8) warps per block stacked in y.
+ *   COLUMN_SMEM  as COLUMN, but each thread loads only its own row of every
+ *          plane; rows y-1 / y+1 come from shared memory after one barrier
+ *          (fewer registers and L2 requests).
  *   AUTO   depth 1: COLUMN for 2D and nz <= 8, else MARCH; depth > 1: WAVE
  *          for 2D and nz <= 16, else TILE. */
 typedef enum gs_kernel {
@@ -119,7 +122,8 @@ typedef enum gs_kernel {
     GS_KERNEL_MARCH = 1,
     GS_KERNEL_WAVE = 2,
     GS_KERNEL_TILE = 3,
-    GS_KERNEL_COLUMN = 4
+    GS_KERNEL_COLUMN = 4,
+    GS_KERNEL_COLUMN_SMEM = 5
 } gs_kernel;
 
 /* Launch plan.  Zero fields select defaults.

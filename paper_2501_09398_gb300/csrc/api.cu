@@ -174,7 +174,7 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     if (t != 1 && t != 2 && t != 4) return fail(c, GS_ERR_INVALID_ARG, "plan.temporal_depth must be 1, 2 or 4");
     if (c->kind == GS_FDTD3D && t != 1)
         return fail(c, GS_ERR_UNSUPPORTED, "temporal blocking is provided for the thermal stencils only");
-    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_COLUMN)
+    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_COLUMN_SMEM)
         return fail(c, GS_ERR_INVALID_ARG, "plan.kernel must be a gs_kernel value");
     if (c->kind == GS_FDTD3D) {
         if (p->kernel == GS_KERNEL_AUTO) p->kernel = GS_KERNEL_COLUMN;
@@ -190,10 +190,10 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
         return fail(c, GS_ERR_INVALID_ARG, "the MARCH kernel runs depth 1 only");
     if (p->kernel == GS_KERNEL_TILE && t == 1)
         return fail(c, GS_ERR_INVALID_ARG, "the TILE kernel runs depth 2 or 4 only");
-    if (p->kernel == GS_KERNEL_COLUMN && t != 1)
-        return fail(c, GS_ERR_INVALID_ARG, "the COLUMN kernel runs depth 1 only");
-    if (p->kernel == GS_KERNEL_COLUMN && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
-        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernel needs nz <= 8");
+    const bool colv = (p->kernel == GS_KERNEL_COLUMN || p->kernel == GS_KERNEL_COLUMN_SMEM);
+    if (colv && t != 1) return fail(c, GS_ERR_INVALID_ARG, "the COLUMN kernels run depth 1 only");
+    if (colv && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
+        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernels need nz <= 8");
     if (p->kernel == GS_KERNEL_WAVE && !wave_ok)
         return fail(c, GS_ERR_UNSUPPORTED, "the WAVE kernel needs nz <= 16 (all planes in one block)");
     if (p->kernel == GS_KERNEL_WAVE && heat_wave_smem(c->kind == GS_HEAT3D ? (int)c->nz : 0, t, vec_elems(c->dt)) > 227 * 1024)
@@ -252,7 +252,8 @@ gs_status ensure_descs(gs_ctx* c) {
             a.Tin = c->ptr[par ? GS_FIELD_T1 : GS_FIELD_T0];
             a.Tout = c->ptr[par ? GS_FIELD_T0 : GS_FIELD_T1];
             // single-step launches (depth 1, and the peeled n mod t steps)
-            const int v1 = (c->plan.kernel == GS_KERNEL_WAVE || c->plan.kernel == GS_KERNEL_COLUMN)
+            const int v1 = (c->plan.kernel == GS_KERNEL_WAVE || c->plan.kernel == GS_KERNEL_COLUMN ||
+                            c->plan.kernel == GS_KERNEL_COLUMN_SMEM)
                                ? c->plan.kernel
                                : GS_KERNEL_MARCH;
             cudaError_t e = heat_desc(c->kind, c->dt, c->bc, a, c->plan.block_x, 1, v1, &c->desc[0][par]);

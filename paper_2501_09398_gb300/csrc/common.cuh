@@ -161,6 +161,7 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
                       LaunchDesc* out);
 size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth);
 size_t heat_wave_smem(int nz3d, int depth, int vec);
+size_t heat_scol_smem(int nzm, int rows, int vec);
 // heat_multi_kernel for (dt, bc) with MARCH tiles (blockDim.x threads x
 // `rows` rows) or COLUMN tiles (32 x `rows` threads, one row per warp row).
 const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant);

@@ -465,6 +465,120 @@ __global__ void __launch_bounds__(256) heat_column_kernel(const HeatArgs a) {
     heat_column_tile<ST, BC, NZM>(a, blockIdx.x, blockIdx.y);
 }
 
+// ------------------------------------------- column, rows in shared memory --
+//
+// COLUMN with the y-neighbour rows staged in shared memory: each thread loads
+// only its own row of every plane (the block's first and last thread rows
+// also load the halo rows above and below the block), stores it to shared
+// memory, and after one barrier reads rows y-1 and y+1 from there.  Fewer
+// registers and L2 requests than COLUMN; z-neighbours from registers, x by
+// shuffle.  Block (32, rows); shared memory (rows + 2) x NZM x 32 x V floats.
+template <typename ST, int BC, int NZM>
+__global__ void __launch_bounds__(256) heat_scol_kernel(const HeatArgs a) {
+    constexpr int V = Vec<ST>::N;
+    extern __shared__ float ssm[];
+    pdl_wait_then_trigger();
+    const int lane = threadIdx.x, ty = threadIdx.y, BY = blockDim.y;
+    const int x0 = (blockIdx.x * 32 + lane) * V;
+    const int y0 = blockIdx.y * BY;
+    const int y = y0 + ty;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool xin = x0 < nx;
+    const bool act = xin && (y < ny);
+    const bool fast_x = __all_sync(0xffffffffu, x0 > 0 && x0 + V < nx);
+    const long long pitch = a.pitch, plane = a.plane;
+    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
+    const ST* base = Tin + (long long)min(y, ny - 1) * pitch + x0;
+    const int slabf = 32 * V;  // floats of one (row, plane) slab
+    float* mine = ssm + lane * V;
+
+    float c[NZM][V], p[V], wl[NZM], er[NZM];
+#pragma unroll
+    for (int z = 0; z < NZM; ++z) {
+        wl[z] = 0.f;
+        er[z] = 0.f;
+#pragma unroll
+        for (int i = 0; i < V; ++i) c[z][i] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) p[i] = 0.f;
+    if (act) {
+#pragma unroll
+        for (int z = 0; z < NZM; ++z) {
+            if (z < nz) {
+                const ST* q = base + z * plane;
+                load_vec(q, c[z]);
+                if (lane == 0 && x0 > 0) wl[z] = load_scalar(q - 1);
+                if (lane == 31 && x0 + V < nx) er[z] = load_scalar(q + V);
+            }
+        }
+        load_vec(static_cast<const ST*>(a.P) + (long long)y * a.p_pitch + x0, p);
+    }
+    // halo rows, each with its own condition (with one thread row per block
+    // the same thread loads both): y0 - 1 into slab row 0 when it exists,
+    // y0 + BY into slab row BY + 1 when it exists
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const bool want = side == 0 ? (ty == 0 && y0 > 0) : (ty == BY - 1 && y0 + BY < ny);
+        if (!(xin && want)) continue;
+        const int hy = side == 0 ? y0 - 1 : y0 + BY;
+        const int hr = side == 0 ? 0 : BY + 1;
+        const ST* hb = Tin + (long long)hy * pitch + x0;
+#pragma unroll
+        for (int z = 0; z < NZM; ++z) {
+            if (z < nz) {
+                float h[V];
+                load_vec(hb + z * plane, h);
+                sm_put<V>(mine + ((size_t)hr * NZM + z) * slabf, h);
+            }
+        }
+    }
+    if (act) {
+#pragma unroll
+        for (int z = 0; z < NZM; ++z)
+            if (z < nz) sm_put<V>(mine + ((size_t)(ty + 1) * NZM + z) * slabf, c[z]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int z = 0; z < NZM; ++z) {
+        if (z < nz) {  // warp-uniform
+            float w0 = __shfl_up_sync(0xffffffffu, c[z][V - 1], 1);
+            float eV = __shfl_down_sync(0xffffffffu, c[z][0], 1);
+            if (lane == 0) w0 = wl[z];
+            if (lane == 31) eV = er[z];
+            if (!act) continue;
+            float nv[V], sv[V];
+            if (y > 0) sm_get<V>(mine + ((size_t)ty * NZM + z) * slabf, nv);
+            else
+#pragma unroll
+                for (int i = 0; i < V; ++i) nv[i] = bnd<BC>(c[z][i]);
+            if (y + 1 < ny) sm_get<V>(mine + ((size_t)(ty + 2) * NZM + z) * slabf, sv);
+            else
+#pragma unroll
+                for (int i = 0; i < V; ++i) sv[i] = bnd<BC>(c[z][i]);
+            float out[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const float t = c[z][i];
+                float w = (i == 0) ? w0 : c[z][i - 1];
+                float e = (i == V - 1) ? eV : c[z][i + 1];
+                if (!fast_x) {
+                    if (x0 + i == 0) w = bnd<BC>(t);
+                    if (x0 + i + 1 >= nx) e = bnd<BC>(t);
+                }
+                float d = 0.f, u = 0.f;
+                if (NZM > 1) {
+                    d = (z > 0) ? c[z > 0 ? z - 1 : 0][i] : bnd<BC>(t);
+                    u = (z + 1 < nz) ? c[z + 1 < NZM ? z + 1 : z][i] : bnd<BC>(t);
+                }
+                out[i] = heat_cell<(NZM > 1)>(t, nv[i], sv[i], w, e, d, u, (z == 0) ? p[i] : 0.0f, a.c);
+            }
+            store_vec(static_cast<ST*>(a.Tout) + (long long)z * plane + (long long)y * pitch + x0, out,
+                      fast_x ? V : nx - x0);
+        }
+    }
+}
+
 // ------------------------------------------------------------ wavefront --
 //
 // Temporal blocking without shared-memory tiles: each warp owns 32 vectors
@@ -636,6 +750,8 @@ const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant) {
     return variant == GS_KERNEL_COLUMN ? multi_func<true>(dt, bc) : multi_func<false>(dt, bc);
 }
 
+size_t heat_scol_smem(int nzm, int rows, int vec) { return (size_t)(rows + 2) * nzm * 32 * vec * sizeof(float); }
+
 size_t heat_wave_smem(int nz3d, int depth, int vec) {
     return nz3d > 0 ? (size_t)2 * depth * nz3d * 32 * vec * sizeof(float) : 0;
 }
@@ -671,6 +787,9 @@ const void* pick(bool is3d, int depth, int variant) {
     if (variant == GS_KERNEL_COLUMN && depth == 1)
         return is3d ? (const void*)heat_column_kernel<ST, BC, kColumnMaxNz>
                     : (const void*)heat_column_kernel<ST, BC, 1>;
+    if (variant == GS_KERNEL_COLUMN_SMEM && depth == 1)
+        return is3d ? (const void*)heat_scol_kernel<ST, BC, kColumnMaxNz>
+                    : (const void*)heat_scol_kernel<ST, BC, 1>;
     if (variant == GS_KERNEL_WAVE)
         return is3d ? pick_wave<ST, BC, true>(depth) : pick_wave<ST, BC, false>(depth);
     if (variant == GS_KERNEL_MARCH && depth == 1)
@@ -714,6 +833,12 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
         out->block = dim3(32, by, 1);
         out->grid = dim3((a.nx + 32 * V - 1) / (32 * V), (a.ny + by - 1) / by, 1);
         out->smem = 0;
+    } else if (variant == GS_KERNEL_COLUMN_SMEM) {
+        if (is3d && a.nz > kColumnMaxNz) return cudaErrorInvalidValue;
+        const int by = std::max(1, std::min(a.rows, 8));
+        out->block = dim3(32, by, 1);
+        out->grid = dim3((a.nx + 32 * V - 1) / (32 * V), (a.ny + by - 1) / by, 1);
+        out->smem = heat_scol_smem(is3d ? kColumnMaxNz : 1, by, V);
     } else if (variant == GS_KERNEL_WAVE) {
         if (is3d && a.nz > kWaveMaxNz) return cudaErrorInvalidValue;
         const int stride = 30 * V;

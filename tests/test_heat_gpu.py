@@ -101,14 +101,15 @@ def test_temporal_blocking_bit_identical(shape, depth):
         assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"wave rows={rows} bx={bx}"
         assert np.array_equal(heat_gpu(T0, P, n, S=6, plan=plan), base), f"wave graph rows={rows} bx={bx}"
     if depth == 1:  # column kernel: every plane of a column in registers (nz <= 8)
-        for rows in (1, 4, 8):
-            plan = dict(kernel=g.GS_KERNEL_COLUMN, rows=rows)
+        for rows, kern in ((1, g.GS_KERNEL_COLUMN), (4, g.GS_KERNEL_COLUMN), (8, g.GS_KERNEL_COLUMN),
+                           (1, g.GS_KERNEL_COLUMN_SMEM), (3, g.GS_KERNEL_COLUMN_SMEM), (8, g.GS_KERNEL_COLUMN_SMEM)):
+            plan = dict(kernel=kern, rows=rows)
             if nz > 8:
                 with pytest.raises(g.GsError):
                     heat_gpu(T0, P, n, S=0, plan=plan)
                 continue
-            assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"column rows={rows}"
-            assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column graph rows={rows}"
+            assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"column {kern} rows={rows}"
+            assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column {kern} graph rows={rows}"
     if depth > 1:  # overlapped shared-memory tiles
         for tile in ((32, 32), (16, 8), (13, 7)):
             plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_TILE, tile_x=tile[0], tile_y=tile[1])
