@@ -66,7 +66,10 @@ typedef enum gs_status {
     GS_ERR_UNSUPPORTED = 7  /* valid request this build does not provide (e.g. plan too large) */
 } gs_status;
 
-typedef enum gs_kind { GS_HEAT2D = 0, GS_HEAT3D = 1, GS_FDTD3D = 2 } gs_kind;
+/* GS_SKELETON is the paper's skeleton application (Sec. III-C): a vector of
+ * nx elements multiplied in place by a constant c, one kernel per iteration
+ * (ny = nz = 1; field GS_FIELD_X; gs_set_scale sets c, default 1). */
+typedef enum gs_kind { GS_HEAT2D = 0, GS_HEAT3D = 1, GS_FDTD3D = 2, GS_SKELETON = 3 } gs_kind;
 
 /* Storage type of the fields.  Arithmetic is always FP32. */
 typedef enum gs_dtype { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
@@ -84,7 +87,8 @@ typedef enum gs_field {
     GS_FIELD_HX = 6,
     GS_FIELD_HY = 7,
     GS_FIELD_HZ = 8,
-    GS_FIELD_T = 9   /* alias: whichever of T0/T1 holds the current state */
+    GS_FIELD_T = 9,  /* alias: whichever of T0/T1 holds the current state */
+    GS_FIELD_X = 10  /* skeleton vector: one row of nx elements */
 } gs_field;
 
 typedef struct gs_ctx gs_ctx;
@@ -185,10 +189,12 @@ gs_status gs_required_pitch(gs_dtype dtype, int64_t width, int64_t *pitch_out);
 
 /* Create a stepping context.
  *   kind     GS_HEAT2D (nz must be 1), GS_HEAT3D, GS_FDTD3D (nx == ny == nz
- *            == N cells; each component is an (N+1)^3 array)
+ *            == N cells; each component is an (N+1)^3 array), GS_SKELETON
+ *            (ny == nz == 1; nx elements, up to 2^31)
  *   nx,ny,nz grid size in cells, each in [1, 2^20], total < 2^31 elements
  *   storage  field storage type
- *   bc       GS_BC_CLAMP / GS_BC_DIRICHLET0 (thermal) or GS_BC_PEC (FDTD)
+ *   bc       GS_BC_CLAMP / GS_BC_DIRICHLET0 (thermal), GS_BC_PEC (FDTD);
+ *            ignored for GS_SKELETON
  *   stream   cudaStream_t to run on, borrowed (cudaStreamLegacy and
  *            cudaStreamPerThread are accepted); NULL: the context creates
  *            (and later destroys) its own non-blocking stream, as the
@@ -214,6 +220,10 @@ gs_status gs_set_heat_coeffs(gs_ctx *ctx, const gs_heat_coeffs *c);
 /* Replace the FDTD parameters (GS_FDTD3D only).  The source cell must lie
  * inside the (N+1)^3 arrays.  Built graphs are discarded. */
 gs_status gs_set_fdtd_params(gs_ctx *ctx, const gs_fdtd_params *p);
+
+/* The skeleton application's constant c (GS_SKELETON only); non-finite c
+ * gives GS_ERR_NUMERIC.  Built graphs are discarded. */
+gs_status gs_set_scale(gs_ctx *ctx, float c);
 
 /* Replace the launch plan (see gs_plan).  Zero fields take defaults.  A plan
  * the kernels cannot run on this grid (shared-memory tile too large,

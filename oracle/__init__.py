@@ -153,3 +153,12 @@ def fdtd_run(fields: dict, N: int, n_steps: int, courant: float = 0.5, n0: int =
     _load().or_fdtd_run(N, int(n0), int(n_steps), float(courant), *[_dptr(a) for a in arrs],
                         1 if src is not None else 0, si, sj, sk, float(amp), float(delay), float(width))
     return fields
+
+
+def skeleton_run(x0, c: float, n_steps: int) -> np.ndarray:
+    """The paper's skeleton application (Sec. III-C): the vector multiplied
+    by the constant c once per iteration, n_steps times, in float64."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    for _ in range(int(n_steps)):
+        x = c * x
+    return x

@@ -30,12 +30,12 @@ _lib = ctypes.CDLL(LIB_PATH)
 # ------------------------------------------------------------ constants --
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_STATE, GS_ERR_TIMEOUT, GS_ERR_NUMERIC, \
     GS_ERR_UNSUPPORTED = range(8)
-GS_HEAT2D, GS_HEAT3D, GS_FDTD3D = range(3)
+GS_HEAT2D, GS_HEAT3D, GS_FDTD3D, GS_SKELETON = range(4)
 GS_F32, GS_BF16, GS_F16 = range(3)
 GS_BC_CLAMP, GS_BC_DIRICHLET0, GS_BC_PEC = range(3)
 GS_KERNEL_AUTO, GS_KERNEL_MARCH, GS_KERNEL_WAVE, GS_KERNEL_TILE, GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM = range(6)
 (GS_FIELD_T0, GS_FIELD_T1, GS_FIELD_P, GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY,
- GS_FIELD_HZ, GS_FIELD_T) = range(10)
+ GS_FIELD_HZ, GS_FIELD_T, GS_FIELD_X) = range(11)
 
 DTYPES = {"f32": GS_F32, "bf16": GS_BF16, "f16": GS_F16}
 FDTD_FIELDS = (GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY, GS_FIELD_HZ)
@@ -109,6 +109,7 @@ _sig("gs_destroy", [_vp])
 _sig("gs_set_heat_coeffs", [_vp, ctypes.POINTER(gs_heat_coeffs)])
 _sig("gs_set_fdtd_params", [_vp, ctypes.POINTER(gs_fdtd_params)])
 _sig("gs_set_plan", [_vp, ctypes.POINTER(gs_plan)])
+_sig("gs_set_scale", [_vp, ctypes.c_float])
 _sig("gs_get_plan", [_vp, ctypes.POINTER(gs_plan)])
 _sig("gs_bind_field", [_vp, ctypes.c_int, _vp, _i64])
 _sig("gs_upload", [_vp, ctypes.c_int, _fp, _i64])
@@ -189,6 +190,10 @@ def gs_set_heat_coeffs(ctx, k=0.5, cx=0.1, cy=0.1, cz=0.01, cz2=0.05, t_amb=80.0
 def gs_set_fdtd_params(ctx, courant=0.5, src_on=0, src=(0, 0, 0), amp=1.0, delay=60.0, width=20.0) -> None:
     p = gs_fdtd_params(courant, src_on, src[0], src[1], src[2], amp, delay, width)
     _check(_lib.gs_set_fdtd_params(ctx, ctypes.byref(p)), ctx)
+
+
+def gs_set_scale(ctx, c: float) -> None:
+    _check(_lib.gs_set_scale(ctx, c), ctx)
 
 
 def gs_set_plan(ctx, block_x=0, rows=0, tile_x=0, tile_y=0, temporal_depth=0, use_pdl=0, device_launch=0,

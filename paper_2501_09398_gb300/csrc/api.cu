@@ -36,9 +36,10 @@ struct gs_ctx {
     bool own_stream = false;
     gs_heat_coeffs hc{0.5f, 0.1f, 0.1f, 0.01f, 0.05f, 80.0f};
     gs_fdtd_params fp{};
+    float scale = 1.0f;
     gs_plan plan{};
-    void* ptr[9] = {};
-    int64_t pitch[9] = {};
+    void* ptr[11] = {};
+    int64_t pitch[11] = {};
     int parity = 0;
     int64_t time = 0;
     long long* d_counter = nullptr;
@@ -79,6 +80,7 @@ int vec_elems(gs_dtype dt) { return dt == GS_F32 ? 4 : 8; }
 constexpr int kTemporalThreads = 256;  // threads of a temporally blocked tile
 size_t elem_bytes(gs_dtype dt) { return dt == GS_F32 ? 4 : 2; }
 bool is_heat(const gs_ctx* c) { return c->kind == GS_HEAT2D || c->kind == GS_HEAT3D; }
+bool is_skel(const gs_ctx* c) { return c->kind == GS_SKELETON; }
 
 // Dense row width, row count and element count of a field.
 bool field_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows) {
@@ -94,6 +96,12 @@ bool field_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows) {
             return true;
         }
         return false;
+    }
+    if (is_skel(c)) {
+        if (id != GS_FIELD_X) return false;
+        *width = c->nx;
+        *rows = 1;
+        return true;
     }
     if (id >= GS_FIELD_EX && id <= GS_FIELD_HZ) {
         *width = c->nx + 1;
@@ -124,6 +132,12 @@ void invalidate(gs_ctx* c) {
 
 gs_plan default_plan(const gs_ctx* c) {
     gs_plan p{};
+    if (is_skel(c)) {
+        p.block_x = 256;
+        p.rows = 1;
+        p.temporal_depth = 1;
+        return p;
+    }
     if (c->kind == GS_FDTD3D) {
         p.block_x = 32;
         while (p.block_x * vec_elems(c->dt) < c->nx + 1 && p.block_x < 128) p.block_x += 32;
@@ -161,8 +175,18 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     if (p->block_x < 32 || p->block_x > 1024 || p->block_x % 32)
         return fail(c, GS_ERR_INVALID_ARG, "plan.block_x must be a multiple of 32 in [32, 1024]");
     if (p->rows < 1) return fail(c, GS_ERR_INVALID_ARG, "plan.rows must be >= 1");
-    if (c->kind == GS_FDTD3D && p->block_x > 256)
-        return fail(c, GS_ERR_INVALID_ARG, "FDTD: plan.block_x must be <= 256");
+    if ((c->kind == GS_FDTD3D || is_skel(c)) && p->block_x > 256)
+        return fail(c, GS_ERR_INVALID_ARG, "FDTD / skeleton: plan.block_x must be <= 256");
+    if (is_skel(c)) {
+        if (p->temporal_depth > 1) return fail(c, GS_ERR_UNSUPPORTED, "the skeleton kernel has no temporal blocking");
+        if (p->use_pdl != 0 && p->use_pdl != 1) return fail(c, GS_ERR_INVALID_ARG, "plan.use_pdl must be 0 or 1");
+        if (p->device_launch != 0 && p->device_launch != 1)
+            return fail(c, GS_ERR_INVALID_ARG, "plan.device_launch must be 0 or 1");
+        if (p->use_pdl && p->device_launch)
+            return fail(c, GS_ERR_INVALID_ARG, "plan.use_pdl and plan.device_launch cannot be combined");
+        p->kernel = GS_KERNEL_AUTO;
+        return GS_OK;
+    }
     if (c->kind != GS_FDTD3D && p->block_x > 512)
         return fail(c, GS_ERR_INVALID_ARG, "thermal: plan.block_x must be <= 512");
     if (p->use_pdl != 0 && p->use_pdl != 1) return fail(c, GS_ERR_INVALID_ARG, "plan.use_pdl must be 0 or 1");
@@ -215,6 +239,10 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
 }
 
 gs_status require_fields(gs_ctx* c) {
+    if (is_skel(c)) {
+        if (!c->ptr[GS_FIELD_X]) return fail(c, GS_ERR_STATE, "field X must be bound before stepping");
+        return GS_OK;
+    }
     if (is_heat(c)) {
         if (!c->ptr[GS_FIELD_T0] || !c->ptr[GS_FIELD_T1] || !c->ptr[GS_FIELD_P])
             return fail(c, GS_ERR_STATE, "fields T0, T1 and P must be bound before stepping");
@@ -234,6 +262,13 @@ gs_status ensure_descs(gs_ctx* c) {
     if (c->descs_ok) return GS_OK;
     gs_status st = require_fields(c);
     if (st != GS_OK) return st;
+    if (is_skel(c)) {
+        SkeletonArgs a{c->ptr[GS_FIELD_X], (long long)c->nx, c->scale};
+        cudaError_t e = skeleton_desc(c->dt, a, c->plan.block_x, &c->desc[0][0]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "skeleton kernel set-up");
+        c->descs_ok = true;
+        return GS_OK;
+    }
     if (is_heat(c)) {
         HeatArgs a{};
         a.P = c->ptr[GS_FIELD_P];
@@ -293,6 +328,10 @@ gs_status ensure_descs(gs_ctx* c) {
 // the parity).  FDTD: H, E per iteration.
 template <typename F>
 void for_each_launch(gs_ctx* c, int64_t n, int p, F&& f) {
+    if (is_skel(c)) {
+        for (int64_t i = 0; i < n; ++i) f(c->desc[0][0]);
+        return;
+    }
     if (is_heat(c)) {
         const int t = c->plan.temporal_depth;
         const int64_t q = (t > 1) ? n / t : 0;
@@ -305,6 +344,7 @@ void for_each_launch(gs_ctx* c, int64_t n, int p, F&& f) {
 }
 
 int64_t launches_for(const gs_ctx* c, int64_t n) {
+    if (is_skel(c)) return n;
     if (!is_heat(c)) return 2 * n;
     const int t = c->plan.temporal_depth;
     const int64_t q = (t > 1) ? n / t : 0;
@@ -441,6 +481,7 @@ void ctx_field(const gs_ctx* c, int id, void** ptr, int64_t* pitch) {
 bool ctx_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows) { return field_shape(c, id, width, rows); }
 size_t ctx_elem_bytes(const gs_ctx* c) { return elem_bytes(c->dt); }
 bool ctx_is_heat(const gs_ctx* c) { return is_heat(c); }
+bool ctx_is_skel(const gs_ctx* c) { return is_skel(c); }
 cudaStream_t ctx_stream(const gs_ctx* c) { return c->stream; }
 gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg) { return fail(c, s, msg); }
 gs_status global_fail(gs_status s, const std::string& msg) { return fail(nullptr, s, msg); }
@@ -487,22 +528,24 @@ gs_status gs_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t 
                     void* stream) {
     if (!out) return fail(nullptr, GS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (kind != GS_HEAT2D && kind != GS_HEAT3D && kind != GS_FDTD3D)
+    if (kind != GS_HEAT2D && kind != GS_HEAT3D && kind != GS_FDTD3D && kind != GS_SKELETON)
         return fail(nullptr, GS_ERR_INVALID_ARG, "unknown kind");
+    if (kind == GS_SKELETON && (ny != 1 || nz != 1 || nx < 1 || nx >= (int64_t(1) << 31)))
+        return fail(nullptr, GS_ERR_INVALID_ARG, "GS_SKELETON needs ny == nz == 1 and 1 <= nx < 2^31");
     if (storage != GS_F32 && storage != GS_BF16 && storage != GS_F16)
         return fail(nullptr, GS_ERR_INVALID_ARG, "unknown storage dtype");
     const int64_t lim = int64_t(1) << 20;
-    if (nx < 1 || ny < 1 || nz < 1 || nx > lim || ny > lim || nz > lim)
+    if (kind != GS_SKELETON && (nx < 1 || ny < 1 || nz < 1 || nx > lim || ny > lim || nz > lim))
         return fail(nullptr, GS_ERR_INVALID_ARG, "grid sizes must be in [1, 2^20]");
     if (kind == GS_HEAT2D && nz != 1) return fail(nullptr, GS_ERR_INVALID_ARG, "GS_HEAT2D needs nz == 1");
     if (kind == GS_FDTD3D && (nx != ny || ny != nz))
         return fail(nullptr, GS_ERR_INVALID_ARG, "GS_FDTD3D needs a cubic grid (nx == ny == nz)");
     const int64_t w = (kind == GS_FDTD3D) ? nx + 1 : nx;
     const int64_t rows = (kind == GS_FDTD3D) ? (nx + 1) * (nx + 1) : ny * nz;
-    if ((double)(w + 8) * (double)rows >= 2147483647.0)
+    if (kind != GS_SKELETON && (double)(w + 8) * (double)rows >= 2147483647.0)
         return fail(nullptr, GS_ERR_INVALID_ARG, "field too large (needs >= 2^31 elements)");
     if (kind == GS_FDTD3D && bc != GS_BC_PEC) return fail(nullptr, GS_ERR_INVALID_ARG, "GS_FDTD3D needs GS_BC_PEC");
-    if (kind != GS_FDTD3D && bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0)
+    if ((kind == GS_HEAT2D || kind == GS_HEAT3D) && bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0)
         return fail(nullptr, GS_ERR_INVALID_ARG, "thermal kinds need GS_BC_CLAMP or GS_BC_DIRICHLET0");
 
     gs_ctx* c = new (std::nothrow) gs_ctx();
@@ -558,6 +601,15 @@ gs_status gs_set_heat_coeffs(gs_ctx* c, const gs_heat_coeffs* hc) {
     return GS_OK;
 }
 
+gs_status gs_set_scale(gs_ctx* c, float scale) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!is_skel(c)) return fail(c, GS_ERR_INVALID_ARG, "not a skeleton context");
+    if (!std::isfinite(scale)) return fail(c, GS_ERR_NUMERIC, "non-finite scale");
+    c->scale = scale;
+    invalidate(c);
+    return GS_OK;
+}
+
 gs_status gs_set_fdtd_params(gs_ctx* c, const gs_fdtd_params* p) {
     if (!c || !p) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
     if (c->kind != GS_FDTD3D) return fail(c, GS_ERR_INVALID_ARG, "not an FDTD context");
@@ -593,7 +645,7 @@ gs_status gs_bind_field(gs_ctx* c, gs_field id, void* ptr, int64_t pitch) {
     if (!c) return GS_ERR_INVALID_ARG;
     const int f = resolve(c, id);
     int64_t width, rows;
-    if (f < 0 || f > GS_FIELD_HZ || !field_shape(c, f, &width, &rows))
+    if (f < 0 || f > GS_FIELD_X || f == GS_FIELD_T || !field_shape(c, f, &width, &rows))
         return fail(c, GS_ERR_INVALID_ARG, "field id not valid for this context kind");
     if (ptr) {
         if (reinterpret_cast<uintptr_t>(ptr) % 16)
@@ -618,7 +670,7 @@ gs_status gs_upload(gs_ctx* c, gs_field id, const float* host, int64_t n) {
     if (!c || !host) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
     const int f = resolve(c, id);
     int64_t width, rows;
-    if (f < 0 || f > GS_FIELD_HZ || !field_shape(c, f, &width, &rows))
+    if (f < 0 || f > GS_FIELD_X || f == GS_FIELD_T || !field_shape(c, f, &width, &rows))
         return fail(c, GS_ERR_INVALID_ARG, "field id not valid for this context kind");
     if (!c->ptr[f]) return fail(c, GS_ERR_STATE, "field is not bound");
     if (n != width * rows)
@@ -640,7 +692,7 @@ gs_status gs_read_field(gs_ctx* c, gs_field id, float* host_out, int64_t n) {
     if (!c || !host_out) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
     const int f = resolve(c, id);
     int64_t width, rows;
-    if (f < 0 || f > GS_FIELD_HZ || !field_shape(c, f, &width, &rows))
+    if (f < 0 || f > GS_FIELD_X || f == GS_FIELD_T || !field_shape(c, f, &width, &rows))
         return fail(c, GS_ERR_INVALID_ARG, "field id not valid for this context kind");
     if (!c->ptr[f]) return fail(c, GS_ERR_STATE, "field is not bound");
     if (n != width * rows)

@@ -114,6 +114,12 @@ struct FdtdArgs {
     long long* counter;   // device step counter (E kernel, source owner)
 };
 
+struct SkeletonArgs {
+    void* x;
+    long long n;
+    float c;
+};
+
 // One instance of the persistent multi-instance kernel (device table row).
 struct MultiInstance {
     void* T0;
@@ -173,6 +179,8 @@ cudaError_t convert_to_storage(gs_dtype dt, const float* src, void* dst, long lo
 cudaError_t convert_from_storage(gs_dtype dt, const void* src, float* dst, long long width, long long rows,
                                  long long pitch, cudaStream_t st);
 
+cudaError_t skeleton_desc(gs_dtype dt, const SkeletonArgs& a, int block_x, LaunchDesc* out);
+
 int device_sm_count();
 
 // Accessors of a context for the other translation units.
@@ -180,6 +188,7 @@ void ctx_field(const gs_ctx* c, int id, void** ptr, int64_t* pitch);  // NULL / 
 bool ctx_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows);
 size_t ctx_elem_bytes(const gs_ctx* c);
 bool ctx_is_heat(const gs_ctx* c);
+bool ctx_is_skel(const gs_ctx* c);
 cudaStream_t ctx_stream(const gs_ctx* c);
 gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg);  // records msg, returns s
 gs_status global_fail(gs_status s, const std::string& msg);  // message for gs_last_error(NULL)

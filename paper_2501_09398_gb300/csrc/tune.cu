@@ -35,6 +35,7 @@ cudaError_t take(gs_ctx* c, Snapshot* s) {
     const bool heat = ctx_is_heat(c);
     std::vector<int> ids;
     if (heat) ids = {s->parity ? GS_FIELD_T1 : GS_FIELD_T0};
+    else if (ctx_is_skel(c)) ids = {GS_FIELD_X};
     else ids = {GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY, GS_FIELD_HZ};
     cudaStream_t st = ctx_stream(c);
     for (int id : ids) {
@@ -67,7 +68,7 @@ cudaError_t restore(gs_ctx* c, Snapshot* s) {
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     for (void* b : s->bufs) cudaFree(b);
     s->bufs.clear();
-    if (!ctx_is_heat(c)) gs_set_time(c, s->time);
+    if (!ctx_is_heat(c) && !ctx_is_skel(c)) gs_set_time(c, s->time);
     return err;
 }
 
@@ -79,7 +80,9 @@ extern "C" gs_status gs_autotune(gs_ctx* ctx, int64_t n_iters, int32_t reps, con
         return ctx_fail(ctx, GS_ERR_INVALID_ARG, "gs_autotune: NULL pointer, or n_cands/n_iters/reps < 1");
     {
         const bool heat = ctx_is_heat(ctx);
-        const int lo = heat ? GS_FIELD_T0 : GS_FIELD_EX, hi = heat ? GS_FIELD_P : GS_FIELD_HZ;
+        const bool skel = ctx_is_skel(ctx);
+        const int lo = heat ? GS_FIELD_T0 : (skel ? GS_FIELD_X : GS_FIELD_EX);
+        const int hi = heat ? GS_FIELD_P : (skel ? GS_FIELD_X : GS_FIELD_HZ);
         for (int id = lo; id <= hi; ++id) {
             void* p;
             int64_t pitch;

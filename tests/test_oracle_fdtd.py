@@ -133,3 +133,12 @@ def test_driven_cavity_symmetries(oracle):
     assert np.max(np.abs(Ex[:, :, :N] + Ex[:, :, N - 1::-1])) <= tol
     # the driven field reached the walls' neighbourhood (the run is not trivial)
     assert np.max(np.abs(Ez[:, :, 1])) > 1e-8 * scale
+
+
+def test_skeleton_oracle_closed_forms(oracle):
+    # the skeleton kernel of Sec. III-C: x <- c x per iteration, so x_n = c^n x_0
+    x0 = np.array([1.5, -3.0, 0.25, 7.0])
+    assert np.array_equal(oracle.skeleton_run(x0, -1.0, 7), -x0)
+    assert np.array_equal(oracle.skeleton_run(x0, 2.0, 10), x0 * 1024.0)
+    c = 1.0 + 2.0 ** -8
+    np.testing.assert_allclose(oracle.skeleton_run(x0, c, 300), x0 * c ** 300, rtol=1e-13)
