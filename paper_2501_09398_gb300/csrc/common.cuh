@@ -71,6 +71,46 @@ __device__ __forceinline__ void store_vec(ST* p, const float (&v)[Vec<ST>::N], i
 template <typename ST>
 __device__ __forceinline__ float load_scalar(const ST* p) { return to_f32(__ldg(p)); }
 
+// W elements per access, W * sizeof(ST) = 8 or 16 bytes (read-only path).
+template <typename ST, int W>
+__device__ __forceinline__ void load_vecw(const ST* __restrict__ p, float (&v)[W]) {
+    static_assert(W * sizeof(ST) == 8 || W * sizeof(ST) == 16, "8- or 16-byte access");
+    if constexpr (W * sizeof(ST) == 16) {
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
+    } else {
+        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
+    }
+}
+
+template <typename ST, int W>
+__device__ __forceinline__ void store_vecw(ST* p, const float (&v)[W], int n_valid) {
+    if (n_valid >= W) {
+        if constexpr (W * sizeof(ST) == 16) {
+            uint4 raw;
+            ST* e = reinterpret_cast<ST*>(&raw);
+#pragma unroll
+            for (int i = 0; i < W; ++i) e[i] = from_f32<ST>(v[i]);
+            *reinterpret_cast<uint4*>(p) = raw;
+        } else {
+            uint2 raw;
+            ST* e = reinterpret_cast<ST*>(&raw);
+#pragma unroll
+            for (int i = 0; i < W; ++i) e[i] = from_f32<ST>(v[i]);
+            *reinterpret_cast<uint2*>(p) = raw;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            if (i < n_valid) p[i] = from_f32<ST>(v[i]);
+    }
+}
+
 // Programmatic dependent launch: a kernel first waits until the grid it
 // depends on has completed and its memory is visible, then lets its own
 // dependent start launching.  Waiting first keeps the early launch to one

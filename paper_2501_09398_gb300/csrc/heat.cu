@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
     heat_march_tile<ST, BC, IS3D>(a, blockIdx.x, blockIdx.y, blockIdx.z, zsm);
 }
 
-template <typename ST, int BC, int NZM>
+template <typename ST, int BC, int NZM, int W = Vec<ST>::N>
 __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int by);
 
 // ------------------------------------------------- multi-instance (2D) ----
@@ -379,6 +379,14 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
     }
 }
 
+// Cells per thread of the COLUMN kernel: a full 16-byte vector in 2D; in 3D
+// (every plane of the column in registers) a half vector, which halves the
+// register arrays and doubles the threads in flight.
+template <typename ST>
+constexpr int column_width(bool is3d) {
+    return is3d ? Vec<ST>::N / 2 : Vec<ST>::N;
+}
+
 // --------------------------------------------------------------- column --
 //
 // Depth 1 without a march: each thread owns one 16-byte vector along x at
@@ -388,9 +396,9 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
 // x-neighbours come from warp shuffles, y- and z-neighbours from registers;
 // no shared memory and no barrier.  Vertical reuse between the rows of a
 // block goes through L1 (read-only path).  Block (32, rows).
-template <typename ST, int BC, int NZM>
+template <typename ST, int BC, int NZM, int W>
 __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int by) {
-    constexpr int V = Vec<ST>::N;
+    constexpr int V = W;  // cells per thread (a 16- or 8-byte access)
     const int lane = threadIdx.x;
     const int x0 = (bx * 32 + lane) * V;
     const int y = by * blockDim.y + threadIdx.y;
@@ -417,14 +425,14 @@ __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int 
         for (int z = 0; z < NZM; ++z) {
             if (z < nz) {
                 const ST* q = base + z * plane;
-                load_vec(q, c[z]);
-                if (y > 0) load_vec(q - pitch, n[z]);
-                if (y + 1 < ny) load_vec(q + pitch, so[z]);
+                load_vecw<ST, V>(q, c[z]);
+                if (y > 0) load_vecw<ST, V>(q - pitch, n[z]);
+                if (y + 1 < ny) load_vecw<ST, V>(q + pitch, so[z]);
                 if (lane == 0 && x0 > 0) wl[z] = load_scalar(q - 1);
                 if (lane == 31 && x0 + V < nx) er[z] = load_scalar(q + V);
             }
         }
-        load_vec(static_cast<const ST*>(a.P) + (long long)y * a.p_pitch + x0, p);
+        load_vecw<ST, V>(static_cast<const ST*>(a.P) + (long long)y * a.p_pitch + x0, p);
     }
 #pragma unroll
     for (int z = 0; z < NZM; ++z) {
@@ -453,16 +461,16 @@ __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int 
                 }
                 out[i] = heat_cell<(NZM > 1)>(t, nv, sv, w, e, d, u, (z == 0) ? p[i] : 0.0f, a.c);
             }
-            store_vec(static_cast<ST*>(a.Tout) + (long long)z * plane + (long long)y * pitch + x0, out,
+            store_vecw<ST, V>(static_cast<ST*>(a.Tout) + (long long)z * plane + (long long)y * pitch + x0, out,
                       fast_x ? V : nx - x0);
         }
     }
 }
 
-template <typename ST, int BC, int NZM>
+template <typename ST, int BC, int NZM, int W>
 __global__ void __launch_bounds__(256) heat_column_kernel(const HeatArgs a) {
     pdl_wait_then_trigger();
-    heat_column_tile<ST, BC, NZM>(a, blockIdx.x, blockIdx.y);
+    heat_column_tile<ST, BC, NZM, W>(a, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------- column, rows in shared memory --
@@ -785,8 +793,8 @@ const void* pick_wave(int depth) {
 template <typename ST, int BC>
 const void* pick(bool is3d, int depth, int variant) {
     if (variant == GS_KERNEL_COLUMN && depth == 1)
-        return is3d ? (const void*)heat_column_kernel<ST, BC, kColumnMaxNz>
-                    : (const void*)heat_column_kernel<ST, BC, 1>;
+        return is3d ? (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, column_width<ST>(true)>
+                    : (const void*)heat_column_kernel<ST, BC, 1, column_width<ST>(false)>;
     if (variant == GS_KERNEL_COLUMN_SMEM && depth == 1)
         return is3d ? (const void*)heat_scol_kernel<ST, BC, kColumnMaxNz>
                     : (const void*)heat_scol_kernel<ST, BC, 1>;
@@ -830,8 +838,9 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
     } else if (variant == GS_KERNEL_COLUMN) {
         if (is3d && a.nz > kColumnMaxNz) return cudaErrorInvalidValue;
         const int by = std::max(1, std::min(a.rows, 8));
+        const int cw = (dt == GS_F32) ? column_width<float>(is3d) : column_width<__half>(is3d);
         out->block = dim3(32, by, 1);
-        out->grid = dim3((a.nx + 32 * V - 1) / (32 * V), (a.ny + by - 1) / by, 1);
+        out->grid = dim3((a.nx + 32 * cw - 1) / (32 * cw), (a.ny + by - 1) / by, 1);
         out->smem = 0;
     } else if (variant == GS_KERNEL_COLUMN_SMEM) {
         if (is3d && a.nz > kColumnMaxNz) return cudaErrorInvalidValue;
