@@ -231,6 +231,33 @@ def oracle_sample(w, budget_s=10.0):
     return cells_of(w) * n / dt, f"thermal {shape}, first {n} of {w['iters']} iterations", threads, full
 
 
+def config_of(name, w, S, depth, world):
+    """The bench line's config (same keys on both arms)."""
+    return {"workload": name, "iterations_per_step": w["iters"], "batch_size_S": S, "temporal_depth": depth,
+            "parallelism": f"replicas x{world}" if world > 1 else "single",
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+def aggregate(step_ms, units_per_step, group=None):
+    """Whole-job throughput of independent replicas: each rank timed its own
+    steps (step_ms, device milliseconds); the job time is the maximum over
+    ranks of their summed step times and the work is every rank's units.
+    Returns (value in units/s, job milliseconds, world size)."""
+    import torch
+
+    world = 1
+    total = float(sum(step_ms))
+    if group is not None or (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        import torch.distributed as dist
+
+        world = dist.get_world_size(group)
+        dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+        total = float(t.item())
+    return world * units_per_step * len(step_ms) / (total * 1e-3), total, world
+
+
 def run_reference(args, w, name):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -246,7 +273,7 @@ def run_reference(args, w, name):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": cells_of(w) * w["iters"] / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, **{k: v for k, v in w.items() if k not in ("S", "depth", "plan")}},
+        "config": config_of(name, w, w["S"], w["depth"], args.gpus),
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -476,6 +503,8 @@ def measure_workload(name, w, args, flush, with_e2e=True):
         g_plan["use_pdl"] = 1
     if getattr(args, "kernel", 0):
         g_plan["kernel"] = args.kernel
+    if getattr(args, "loop", False):
+        g_plan["graph_loop"] = 1
     S = args.batch or w["S"]
     depth = args.depth or w["depth"]
     run = (MultiRunner if w["kind"] == "multi" else Runner)(w, S, depth, g_plan)
@@ -542,6 +571,8 @@ def main():
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--pdl", action="store_true")
     ap.add_argument("--kernel", type=int, default=0, help="thermal kernel variant (gs_kernel; 0 = auto)")
+    ap.add_argument("--loop", action="store_true",
+                    help="run the batches as one device-side loop (conditional while node) per step")
     ap.add_argument("--no-extras", action="store_true", help="skip the 2D 512^2 / 4096^2 side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     args = ap.parse_args()
@@ -578,16 +609,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
 
-        t = torch.tensor([sum(m["graph_ms"])], device="cuda", dtype=torch.float64)
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    else:
-        total_ms = sum(m["graph_ms"])
-
     cells = cells_of(w)
+    value, total_ms, _ = aggregate(m["graph_ms"], cells * w["iters"])
     ms_per_step = total_ms / args.steps
-    value = world * cells * w["iters"] * args.steps / (total_ms * 1e-3)
     per_step_value = cells * w["iters"] / (statistics.mean(m["per_step_ms"]) * 1e-3)
     peak, peak_kind = _peaks()
     bytes_launch = algo_bytes_per_launch(w, m["depth"])
@@ -602,9 +627,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "iterations_per_step": w["iters"], "batch_size_S": m["S"],
-                   "temporal_depth": m["depth"], "parallelism": f"replicas x{world}" if world > 1 else "single",
-                   "l2": "flushed between steps (256 MiB write)"},
+        "config": config_of(args.workload, w, m["S"], m["depth"], world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": recorded_traffic(args.workload), "peak_kind": peak_kind,
                      "launch_ms_in_step": launch_ms,
@@ -632,11 +655,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras and args.workload == DEFAULT:
         extra = {}
         base = {**vars(args), "batch": 0, "depth": 0, "block_x": 0, "rows": 0, "tile_x": 0, "tile_y": 0,
-                "pdl": False, "kernel": 0, "steps": 20}
+                "pdl": False, "kernel": 0, "loop": False, "steps": 20}
         # 2D 512^2: graph-batched vs per-step launch of the same depth-1 kernel
         # 2D 4096^2: HBM roofline of the depth-1 kernel, and the wavefront
         # depth-4 kernel's throughput
-        for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-4096", {}, "depth1"),
+        for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(loop=True), "device_loop"),
+                              ("heat2d-4096", {}, "depth1"),
                               ("heat2d-4096", dict(depth=4, kernel=2, rows=64, block_x=256), "wave4")):
             ww = WORKLOADS[nm]
             mm = measure_workload(nm, ww, argparse.Namespace(**{**base, **over}), flush, with_e2e=False)

@@ -154,6 +154,17 @@ typedef struct gs_plan {
     int32_t kernel; /* gs_kernel; FDTD: COLUMN (default: one vector per thread,
                        block 32 x rows x 8/rows) or MARCH (block_x threads
                        marching `rows` k planes) */
+    int32_t graph_loop; /* 0: the floor(n/S) batches are floor(n/S) graph
+                           launches (Listing 3).  1: one launch of a graph
+                           whose conditional while node repeats the batch on
+                           the device (Sec. V's conditional nodes): a small
+                           kernel at the end of each trip counts the trips
+                           down and clears the condition after the last; when
+                           a batch flips the buffer parity the loop body is
+                           two batches and an odd last batch runs as a plain
+                           batch graph.  Same results bit for bit.  Not with
+                           device_launch (a device-launch graph holds no
+                           conditional node): GS_ERR_UNSUPPORTED. */
 } gs_plan;
 
 typedef struct gs_stats {
@@ -388,9 +399,9 @@ gs_status gs_model_calibrate(gs_ctx *ctx, int64_t n_iters, const int64_t *S_list
  * (0.9, 0.999, 1e-8), minibatches in row order; one epoch is replayed as a
  * CUDA graph.  All arrays passed as X / y are device memory, X row-major
  * [n_rows][GS_MLP_INPUTS] float32, y [n_rows] float32. */
-#define GS_MLP_INPUTS 16
+#define GS_MLP_INPUTS 18
 #define GS_MLP_HIDDEN 32
-#define GS_MLP_PARAMS 1633
+#define GS_MLP_PARAMS 1697
 
 typedef struct gs_mlp gs_mlp;
 
@@ -405,8 +416,10 @@ typedef struct gs_workload {
 /* Feature vectors (n x GS_MLP_INPUTS floats, host memory) of a workload
  * with each candidate: log2 nx, log2 ny, log2 nz, one-hot kind (3), kernels
  * per iteration, log2 n_iters, one-hot dtype (3), log2 S (0 for S = 0),
- * [S == 0], log2 block_x, log2 rows, temporal depth.  Candidates must give
- * block_x, rows and temporal_depth explicitly.  Host only. */
+ * [S == 0], log2 block_x, log2 rows, temporal depth, [kernel is COLUMN or
+ * COLUMN_SMEM], [kernel is COLUMN_SMEM] (GS_KERNEL_AUTO resolved as
+ * gs_set_plan does).  Candidates must give block_x, rows and
+ * temporal_depth explicitly.  Host only. */
 gs_status gs_features(const gs_workload *w, const gs_tune_candidate *c, int32_t n, float *out);
 
 /* Create a model with Glorot-uniform weights drawn from splitmix64(seed),

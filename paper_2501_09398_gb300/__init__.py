@@ -60,7 +60,7 @@ class gs_fdtd_params(ctypes.Structure):
 
 class gs_plan(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "tile_x", "tile_y", "temporal_depth", "use_pdl",
-                                              "device_launch", "kernel")]
+                                              "device_launch", "kernel", "graph_loop")]
 
 
 class gs_multi_plan(ctypes.Structure):
@@ -197,8 +197,8 @@ def gs_set_scale(ctx, c: float) -> None:
 
 
 def gs_set_plan(ctx, block_x=0, rows=0, tile_x=0, tile_y=0, temporal_depth=0, use_pdl=0, device_launch=0,
-                kernel=0) -> None:
-    p = gs_plan(block_x, rows, tile_x, tile_y, temporal_depth, use_pdl, device_launch, kernel)
+                kernel=0, graph_loop=0) -> None:
+    p = gs_plan(block_x, rows, tile_x, tile_y, temporal_depth, use_pdl, device_launch, kernel, graph_loop)
     _check(_lib.gs_set_plan(ctx, ctypes.byref(p)), ctx)
 
 
@@ -334,7 +334,7 @@ def gs_model_calibrate(ctx, n_iters: int, S_list, reps: int = 2) -> dict:
 
 
 # ------------------------------------------------------- cost model --
-GS_MLP_INPUTS, GS_MLP_HIDDEN, GS_MLP_PARAMS = 16, 32, 1633
+GS_MLP_INPUTS, GS_MLP_HIDDEN, GS_MLP_PARAMS = 18, 32, 1697
 
 
 class gs_workload(ctypes.Structure):
@@ -363,7 +363,7 @@ def _lcheck(st: int, m):
 
 
 def gs_features(workload: dict, candidates) -> np.ndarray:
-    """Feature matrix (len(candidates) x 16, float32) of a workload dict
+    """Feature matrix (len(candidates) x GS_MLP_INPUTS, float32) of a workload dict
     (kind, dtype, nx, ny, nz, n_iters) with (plan dict, S) candidates."""
     w = gs_workload(*[int(workload[k]) for k, _ in gs_workload._fields_])
     n = len(candidates)

@@ -22,7 +22,29 @@ struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t nodes = 0;
+    // Device-loop graphs only: the node that sets the trip count, and the
+    // trip count it currently holds.
+    cudaGraphNode_t init_node = nullptr;
+    unsigned long long trip = 0;
 };
+
+// Device-side loop control of the while-node graphs.  The parent graph runs
+// loop_init once (remaining = trip) and then the conditional node; the last
+// node of the body runs loop_ctl, which counts one trip off and keeps the
+// condition set while trips remain.  loop_ctl ends the loop on any value
+// <= 1, so the loop stops after at most the stored count whatever it holds.
+__global__ void loop_init_kernel(unsigned long long* remaining, unsigned long long trip) { *remaining = trip; }
+
+__global__ void loop_ctl_kernel(cudaGraphConditionalHandle h, unsigned long long* remaining) {
+    const unsigned long long left = *remaining;
+    if (left <= 1) {
+        *remaining = 0;
+        cudaGraphSetConditional(h, 0u);
+    } else {
+        *remaining = left - 1;
+        cudaGraphSetConditional(h, 1u);
+    }
+}
 
 }  // namespace
 
@@ -43,6 +65,7 @@ struct gs_ctx {
     int parity = 0;
     int64_t time = 0;
     long long* d_counter = nullptr;
+    unsigned long long* d_loop = nullptr;  // trips left of the device loop
     float* staging = nullptr;
     size_t staging_bytes = 0;
     // Launch descriptors, valid while descs_ok: thermal [0]=depth 1,
@@ -50,6 +73,7 @@ struct gs_ctx {
     LaunchDesc desc[2][2];
     bool descs_ok = false;
     std::map<std::pair<int64_t, int>, GraphEntry> graphs;
+    std::map<std::pair<int64_t, int>, GraphEntry> loops;  // device-loop graphs
     int64_t built_S = 0;
     gs_stats stats{};
     std::string err;
@@ -117,11 +141,13 @@ int resolve(const gs_ctx* c, int id) {
 }
 
 void destroy_graphs(gs_ctx* c) {
-    for (auto& kv : c->graphs) {
-        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    for (auto* m : {&c->graphs, &c->loops}) {
+        for (auto& kv : *m) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        m->clear();
     }
-    c->graphs.clear();
     c->built_S = 0;
 }
 
@@ -172,6 +198,9 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     if (p->tile_x == 0) p->tile_x = d.tile_x;
     if (p->tile_y == 0) p->tile_y = d.tile_y;
     if (p->temporal_depth == 0) p->temporal_depth = 1;
+    if (p->graph_loop != 0 && p->graph_loop != 1) return fail(c, GS_ERR_INVALID_ARG, "plan.graph_loop must be 0 or 1");
+    if (p->graph_loop && p->device_launch)
+        return fail(c, GS_ERR_UNSUPPORTED, "a device-launch graph cannot hold the conditional node of plan.graph_loop");
     if (p->block_x < 32 || p->block_x > 1024 || p->block_x % 32)
         return fail(c, GS_ERR_INVALID_ARG, "plan.block_x must be a multiple of 32 in [32, 1024]");
     if (p->rows < 1) return fail(c, GS_ERR_INVALID_ARG, "plan.rows must be >= 1");
@@ -369,14 +398,10 @@ cudaError_t launch_one(gs_ctx* c, LaunchDesc& d) {
     return cudaLaunchKernelExC(&cfg, d.func, args);
 }
 
-// Build one executable graph of S iterations from parity p: the paper's
-// manual creation of a linear chain (Listing 3, "Building"), optionally
-// with programmatic edges, then instantiate and upload.
-gs_status build_graph(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
-    cudaGraph_t g = nullptr;
-    GS_CUDA(c, cudaGraphCreate(&g, 0));
-    cudaGraphNode_t prev = nullptr;
-    int64_t nodes = 0;
+// Append the kernel nodes of S iterations from parity p to g as a linear
+// chain after *prev (none if NULL), with programmatic edges when the plan
+// asks for PDL.  *prev becomes the last node added.
+cudaError_t add_chain(gs_ctx* c, cudaGraph_t g, int64_t S, int p, cudaGraphNode_t* prev, int64_t* nodes) {
     cudaError_t err = cudaSuccess;
     cudaGraphEdgeData edge{};
     edge.from_port = cudaGraphKernelNodePortProgrammatic;
@@ -393,22 +418,22 @@ gs_status build_graph(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
         np.kernelParams = args;
         np.extra = nullptr;
         cudaGraphNode_t node;
-        if (c->plan.use_pdl && prev) {
+        if (c->plan.use_pdl && *prev) {
             err = cudaGraphAddKernelNode(&node, g, nullptr, 0, &np);
-            if (err == cudaSuccess) err = cudaGraphAddDependencies(g, &prev, &node, &edge, 1);
+            if (err == cudaSuccess) err = cudaGraphAddDependencies(g, prev, &node, &edge, 1);
         } else {
-            err = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &np);
+            err = cudaGraphAddKernelNode(&node, g, *prev ? prev : nullptr, *prev ? 1 : 0, &np);
         }
-        prev = node;
-        ++nodes;
+        *prev = node;
+        ++*nodes;
     });
-    if (err != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return cuda_fail(c, err, "cudaGraphAddKernelNode");
-    }
+    return err;
+}
+
+gs_status instantiate(gs_ctx* c, cudaGraph_t g, GraphEntry* out) {
     cudaGraphExec_t exec = nullptr;
     const unsigned long long flags = c->plan.device_launch ? cudaGraphInstantiateFlagDeviceLaunch : 0;
-    err = cudaGraphInstantiateWithFlags(&exec, g, flags);
+    cudaError_t err = cudaGraphInstantiateWithFlags(&exec, g, flags);
     if (err != cudaSuccess) {
         cudaGraphDestroy(g);
         return cuda_fail(c, err, "cudaGraphInstantiateWithFlags");
@@ -421,9 +446,78 @@ gs_status build_graph(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
     }
     out->graph = g;
     out->exec = exec;
-    out->nodes = nodes;
     c->stats.graphs_built += 1;
     return GS_OK;
+}
+
+// Build one executable graph of S iterations from parity p: the paper's
+// manual creation of a linear chain (Listing 3, "Building"), optionally
+// with programmatic edges, then instantiate and upload.
+gs_status build_graph(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
+    cudaGraph_t g = nullptr;
+    GS_CUDA(c, cudaGraphCreate(&g, 0));
+    cudaGraphNode_t prev = nullptr;
+    int64_t nodes = 0;
+    cudaError_t err = add_chain(c, g, S, p, &prev, &nodes);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, err, "cudaGraphAddKernelNode");
+    }
+    out->nodes = nodes;
+    return instantiate(c, g, out);
+}
+
+// Build the device-loop graph of batches of S from parity p: loop_init,
+// then a while node whose body is one batch (two when a batch flips the
+// parity, so every trip starts at p) followed by loop_ctl.  One launch runs
+// `trip` bodies with no host launch between them; the trip count is a
+// parameter of the init node, changed in the executable graph per launch.
+gs_status build_loop(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
+    if (!c->d_loop) GS_CUDA(c, cudaMalloc(&c->d_loop, sizeof(unsigned long long)));
+    cudaGraph_t g = nullptr;
+    GS_CUDA(c, cudaGraphCreate(&g, 0));
+    cudaError_t err = cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNode_t init = nullptr, loop = nullptr;
+    unsigned long long trip = 1;
+    void* init_args[2] = {&c->d_loop, &trip};
+    cudaKernelNodeParams ip{};
+    ip.func = (void*)loop_init_kernel;
+    ip.gridDim = dim3(1);
+    ip.blockDim = dim3(1);
+    ip.kernelParams = init_args;
+    err = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (err == cudaSuccess) err = cudaGraphAddKernelNode(&init, g, nullptr, 0, &ip);
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (err == cudaSuccess) err = cudaGraphAddNode(&loop, g, &init, nullptr, 1, &cp);
+    int64_t nodes = 0;
+    if (err == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t prev = nullptr;
+        const int fl = flip_of(c, S);
+        err = add_chain(c, body, S, p, &prev, &nodes);
+        if (err == cudaSuccess && fl) err = add_chain(c, body, S, p ^ 1, &prev, &nodes);
+        void* ctl_args[2] = {&h, &c->d_loop};
+        cudaKernelNodeParams kp{};
+        kp.func = (void*)loop_ctl_kernel;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.kernelParams = ctl_args;
+        cudaGraphNode_t ctl;
+        if (err == cudaSuccess) err = cudaGraphAddKernelNode(&ctl, body, &prev, 1, &kp);
+    }
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, err, "device-loop graph construction");
+    }
+    out->nodes = nodes;
+    out->init_node = init;
+    out->trip = trip;
+    return instantiate(c, g, out);
 }
 
 gs_status ensure_graph(gs_ctx* c, int64_t S, int p, GraphEntry** out) {
@@ -437,6 +531,54 @@ gs_status ensure_graph(gs_ctx* c, int64_t S, int p, GraphEntry** out) {
     }
     *out = &it->second;
     return GS_OK;
+}
+
+gs_status ensure_loop(gs_ctx* c, int64_t S, int p, GraphEntry** out) {
+    auto key = std::make_pair(S, p);
+    auto it = c->loops.find(key);
+    if (it == c->loops.end()) {
+        GraphEntry e;
+        gs_status st = build_loop(c, S, p, &e);
+        if (st != GS_OK) return st;
+        it = c->loops.emplace(key, e).first;
+    }
+    *out = &it->second;
+    return GS_OK;
+}
+
+gs_status launch_graphs(gs_ctx* c, int64_t S, int64_t count);
+
+// Run `count` batches of S with the device loop: one launch of the loop
+// graph for the whole bodies (count, or count/2 when a batch flips the
+// parity), then the odd batch, if any, as a plain batch graph.
+gs_status launch_loop(gs_ctx* c, int64_t S, int64_t count) {
+    const int fl = flip_of(c, S);
+    const int64_t trips = fl ? count / 2 : count;
+    if (trips > 0) {
+        GraphEntry* e;
+        gs_status st = ensure_loop(c, S, c->parity, &e);
+        if (st != GS_OK) return st;
+        if (e->trip != (unsigned long long)trips) {
+            unsigned long long trip = (unsigned long long)trips;
+            void* args[2] = {&c->d_loop, &trip};
+            cudaKernelNodeParams ip{};
+            ip.func = (void*)loop_init_kernel;
+            ip.gridDim = dim3(1);
+            ip.blockDim = dim3(1);
+            ip.kernelParams = args;
+            GS_CUDA(c, cudaGraphExecKernelNodeSetParams(e->exec, e->init_node, &ip));
+            e->trip = trip;
+        }
+        GS_CUDA(c, cudaGraphLaunch(e->exec, c->stream));
+        c->stats.graph_launches += 1;
+    }
+    if (fl && (count & 1)) return launch_graphs(c, S, 1);
+    return GS_OK;
+}
+
+// `count` batches of S: graph launches (Listing 3) or the device loop.
+gs_status run_batches(gs_ctx* c, int64_t S, int64_t count) {
+    return c->plan.graph_loop ? launch_loop(c, S, count) : launch_graphs(c, S, count);
 }
 
 gs_status launch_graphs(gs_ctx* c, int64_t S, int64_t count) {
@@ -586,6 +728,7 @@ gs_status gs_destroy(gs_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     destroy_graphs(c);
     if (c->d_counter) cudaFree(c->d_counter);
+    if (c->d_loop) cudaFree(c->d_loop);
     if (c->staging) cudaFree(c->staging);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -765,7 +908,7 @@ gs_status gs_step(gs_ctx* c, int64_t n_iters, int64_t batch_size) {
         const int64_t nb = n_iters / batch_size;
         const int64_t r = n_iters - nb * batch_size;
         if (nb > 0) {
-            st = launch_graphs(c, batch_size, nb);
+            st = run_batches(c, batch_size, nb);
             if (st != GS_OK) return st;
         }
         if (r > 0) {
@@ -793,10 +936,22 @@ gs_status gs_graph_build(gs_ctx* c, int64_t S) {
             c->graphs.erase(it);
         }
     }
+    {
+        auto it = c->loops.find(std::make_pair(S, c->parity));
+        if (it != c->loops.end()) {
+            cudaGraphExecDestroy(it->second.exec);
+            cudaGraphDestroy(it->second.graph);
+            c->loops.erase(it);
+        }
+    }
     const auto t0 = std::chrono::steady_clock::now();
     GraphEntry* e = nullptr;
-    st = ensure_graph(c, S, c->parity, &e);
-    if (st == GS_OK && fl) st = ensure_graph(c, S, c->parity ^ 1, &e);
+    if (c->plan.graph_loop) {
+        st = ensure_loop(c, S, c->parity, &e);
+    } else {
+        st = ensure_graph(c, S, c->parity, &e);
+        if (st == GS_OK && fl) st = ensure_graph(c, S, c->parity ^ 1, &e);
+    }
     if (st != GS_OK) return st;
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     const auto t1 = std::chrono::steady_clock::now();
@@ -810,7 +965,7 @@ gs_status gs_graph_launch(gs_ctx* c, int64_t n_launches) {
     if (!c) return GS_ERR_INVALID_ARG;
     if (n_launches < 0) return fail(c, GS_ERR_INVALID_ARG, "n_launches must be >= 0");
     if (c->built_S == 0) return fail(c, GS_ERR_STATE, "no graph built (call gs_graph_build first)");
-    gs_status st = launch_graphs(c, c->built_S, n_launches);
+    gs_status st = run_batches(c, c->built_S, n_launches);
     if (st != GS_OK) return st;
     c->time += c->built_S * n_launches;
     c->stats.iterations += c->built_S * n_launches;
