@@ -11,7 +11,11 @@ are not available; these distributions stand in for them:
 * uneven instance batches: square grids with side round(exp(U[ln 64, ln 1024])),
   instance k seeded with 1000 + k;
 * FDTD: zero fields (the soft source drives the cavity) or, for the
-  source-free pins, a random interior E field.
+  source-free pins, a random interior E field;
+* FDTD media (the cavity filled with objects): material 0 is vacuum, the
+  other materials are axis-aligned boxes placed at random (later boxes
+  overwrite earlier ones) with eps_r ~ U[1.5, 8], mu_r ~ U[1, 2], and, for
+  lossy materials, sigma ~ U[0, 0.05] and sigma_m ~ U[0, 0.02].
 """
 from __future__ import annotations
 
@@ -65,6 +69,34 @@ def fdtd_random_e(N: int, seed: int = DEFAULT_SEED):
         a[~mask] = 0.0
         out[name] = a
     return out
+
+
+def fdtd_media(N: int, n_mat: int = 4, n_boxes: int = 8, lossy: bool = True, seed: int = DEFAULT_SEED,
+               swap_symmetric: bool = False):
+    """A material map (uint8, (N+1)^3, [k][j][i]) and its table of
+    (eps_r, sigma, mu_r, sigma_m) rows; row 0 is vacuum.
+
+    ``swap_symmetric`` mirrors every box across the plane i = j, so that the
+    map is unchanged when i and j are swapped."""
+    rng = np.random.default_rng(seed)
+    table = [(1.0, 0.0, 1.0, 0.0)]
+    for _ in range(1, n_mat):
+        eps_r = float(np.float32(rng.uniform(1.5, 8.0)))
+        mu_r = float(np.float32(rng.uniform(1.0, 2.0)))
+        sigma = float(np.float32(rng.uniform(0.0, 0.05))) if lossy else 0.0
+        sigma_m = float(np.float32(rng.uniform(0.0, 0.02))) if lossy else 0.0
+        table.append((eps_r, sigma, mu_r, sigma_m))
+    m = N + 1
+    mat = np.zeros((m, m, m), dtype=np.uint8)
+    for _ in range(n_boxes):
+        lo = rng.integers(0, m, size=3)
+        ext = rng.integers(1, max(2, m // 2), size=3)
+        hi = np.minimum(lo + ext, m)
+        mid = int(rng.integers(1, n_mat)) if n_mat > 1 else 0
+        mat[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = mid
+        if swap_symmetric:
+            mat[lo[2]:hi[2], lo[0]:hi[0], lo[1]:hi[1]] = mid
+    return mat, table
 
 
 def round_to(arr: np.ndarray, dtype: str) -> np.ndarray:

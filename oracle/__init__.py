@@ -14,15 +14,18 @@ What it computes (all in float64, plain loops in ``oracle.c``):
   in 3D.
 * ``fdtd_run``: n Yee leapfrog steps (H update, then E update, then a soft
   Ez point source), the paper's FDTD Maxwell solver with its two kernels per
-  step (Sec. III-C), PEC cavity, normalised units.
+  step (Sec. III-C), PEC cavity, normalised units; optionally in linear,
+  lossy media given by a per-cell material map (the textbook lossy-medium
+  Yee update).
 * Batching iterations into graphs (Sec. III-A, Listings 1-3) does not change
   the result, so no oracle function models graphs: the oracle of a batched run
   is the plain run.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms (heat eigenmode decay, uniform relaxation, Yee energy
-invariance, Yee cavity dispersion), invariants and a brute-force matrix
-restatement.  The source-driven FDTD field has no closed form; it is pinned
+invariance, Yee cavity dispersion, the cavity-mode recurrence in a uniform
+lossy medium), invariants (the permittivity-weighted Yee energy in a
+lossless heterogeneous medium) and a brute-force matrix restatement.  The source-driven FDTD field has no closed form; it is pinned
 through the source value, the mirror/swap symmetries and the same scheme's
 source-free pins.
 """
@@ -78,6 +81,10 @@ def _load():
             lib.or_fdtd_run.argtypes = [i64, i64, i64, ctypes.c_double] + [dp] * 6 + [
                 ctypes.c_int, i64, i64, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             lib.or_fdtd_run.restype = None
+            lib.or_fdtd_run_media.argtypes = [i64, i64, i64, ctypes.c_double] + [dp] * 6 + [
+                ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, dp, dp, dp, dp,
+                ctypes.c_int, i64, i64, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.or_fdtd_run_media.restype = ctypes.c_int
             lib.or_fdtd_source.argtypes = [ctypes.c_double] * 4
             lib.or_fdtd_source.restype = ctypes.c_double
             lib.or_num_threads.argtypes = []
@@ -136,12 +143,15 @@ def fdtd_source(n, amp=1.0, delay=60.0, width=20.0) -> float:
 
 
 def fdtd_run(fields: dict, N: int, n_steps: int, courant: float = 0.5, n0: int = 0,
-             src=None, amp=1.0, delay=60.0, width=20.0) -> dict:
+             src=None, amp=1.0, delay=60.0, width=20.0, media=None) -> dict:
     """Advance the six Yee components in place by ``n_steps`` leapfrog steps.
 
     ``fields``: dict of six float64 (N+1)^3 arrays (see ``FDTD_COMPONENTS``),
     H holding H^{n0-1/2} and E holding E^{n0}.  ``src``: (i, j, k) of the soft
-    Ez source, or None for a source-free run.  Returns ``fields``.
+    Ez source, or None for a source-free run.  ``media``: None (vacuum) or
+    ``(mat, table)`` with ``mat`` a uint8 (N+1)^3 material-id array indexed
+    [k][j][i] and ``table`` a sequence of (eps_r, sigma, mu_r, sigma_m) rows
+    (at most 256; ids past the table are vacuum).  Returns ``fields``.
     """
     arrs = []
     for c in FDTD_COMPONENTS:
@@ -150,8 +160,24 @@ def fdtd_run(fields: dict, N: int, n_steps: int, courant: float = 0.5, n0: int =
             raise ValueError(f"{c}: need a C-contiguous float64 array of shape {(N + 1,) * 3}")
         arrs.append(a)
     si, sj, sk = src if src is not None else (0, 0, 0)
-    _load().or_fdtd_run(N, int(n0), int(n_steps), float(courant), *[_dptr(a) for a in arrs],
-                        1 if src is not None else 0, si, sj, sk, float(amp), float(delay), float(width))
+    if media is None:
+        _load().or_fdtd_run(N, int(n0), int(n_steps), float(courant), *[_dptr(a) for a in arrs],
+                            1 if src is not None else 0, si, sj, sk, float(amp), float(delay), float(width))
+        return fields
+    mat, table = media
+    mat = np.ascontiguousarray(mat, dtype=np.uint8)
+    if mat.shape != (N + 1,) * 3:
+        raise ValueError(f"material map: need shape {(N + 1,) * 3}")
+    tab = np.array(table, dtype=np.float64).reshape(-1, 4)
+    if len(tab) > 256:
+        raise ValueError("at most 256 materials")
+    cols = [np.ascontiguousarray(tab[:, q]) for q in range(4)]
+    rc = _load().or_fdtd_run_media(N, int(n0), int(n_steps), float(courant), *[_dptr(a) for a in arrs],
+                                   mat.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(tab),
+                                   *[_dptr(c) for c in cols], 1 if src is not None else 0, si, sj, sk,
+                                   float(amp), float(delay), float(width))
+    if rc != 0:
+        raise ValueError("bad material table")
     return fields
 
 

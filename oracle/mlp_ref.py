@@ -1,7 +1,7 @@
 """FP64 oracle of the learned cost model's network (test infrastructure only).
 
-Network 16 -> 32 -> 32 -> 1 with ReLU, flat parameters
-W1[32][16] | b1[32] | W2[32][32] | b2[32] | W3[32] | b3, inputs standardised
+Network 18 -> 32 -> 32 -> 1 with ReLU, flat parameters
+W1[32][18] | b1[32] | W2[32][32] | b2[32] | W3[32] | b3, inputs standardised
 with (x - mean) * inv_std, loss L = mean((pred - y)^2).  The gradient is the
 chain rule written out layer by layer; Adam is the published update (Kingma
 & Ba 2015) with bias correction, beta1 0.9, beta2 0.999, eps 1e-8.  Pinned
@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import numpy as np
 
-NI, NH = 16, 32
+NI, NH = 18, 32
 NP = NH * NI + NH + NH * NH + NH + NH + 1
 
 

@@ -37,6 +37,10 @@
  *    Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2), Hz(i+1/2,j+1/2,k); every
  *    component is stored in a dense (N+1)^3 array indexed [k][j][i].
  *
+ *  - The same scheme in linear, possibly lossy media with a per-cell
+ *    material map (or_fdtd_run_media; the paper's solver models a vacuum
+ *    cavity, this is the general-medium form of the same Yee update).
+ *
  * All arrays here are dense (no pitch), x fastest.  Floating point
  * contraction is disabled at build time (-ffp-contract=off) so that results
  * are the same on x86-64 and aarch64 hosts.  The OpenMP pragmas only split
@@ -215,6 +219,111 @@ void or_fdtd_run(int64_t N, int64_t n0, int64_t n_steps, double s, double *Ex,
         if (src_on)
             Ez[yee(N, si, sj, sk)] += or_fdtd_source((double)n, amp, delay, width);
     }
+}
+
+/* ---------------------------------------------------------------------
+ * Yee leapfrog in linear, possibly lossy media (the textbook lossy-medium
+ * update with the conduction term averaged over the two time levels,
+ * Taflove & Hagness, Computational Electrodynamics, Ch. 3), normalised as
+ * above (eps0 = mu0 = c = 1, dx = 1, dt = s).  Material m has relative
+ * permittivity eps_r, conductivity sigma, relative permeability mu_r and
+ * magnetic conductivity sigma_m; with
+ *   a_e = sigma s / (2 eps_r),   a_h = sigma_m s / (2 mu_r):
+ *   E^{n+1}   = ca E^n       + cb curl H^{n+1/2},
+ *               ca = (1 - a_e)/(1 + a_e),  cb = (s/eps_r)/(1 + a_e);
+ *   H^{n+1/2} = da H^{n-1/2} - db curl E^n,
+ *               da = (1 - a_h)/(1 + a_h),  db = (s/mu_r)/(1 + a_h).
+ * Every component at array index c = [k][j][i] takes the material mat[c]
+ * (the cell whose lower corner is (i, j, k)); ids >= n_mat are vacuum.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    double ca, cb, da, db;
+} or_medium;
+
+static or_medium or_medium_of(double s, double eps_r, double sigma, double mu_r, double sigma_m)
+{
+    or_medium m;
+    const double ae = sigma * s / (2.0 * eps_r);
+    const double ah = sigma_m * s / (2.0 * mu_r);
+    m.ca = (1.0 - ae) / (1.0 + ae);
+    m.cb = (s / eps_r) / (1.0 + ae);
+    m.da = (1.0 - ah) / (1.0 + ah);
+    m.db = (s / mu_r) / (1.0 + ah);
+    return m;
+}
+
+static void or_fdtd_h_media(int64_t N, const or_medium *tab, const uint8_t *mat,
+                            const double *Ex, const double *Ey, const double *Ez,
+                            double *Hx, double *Hy, double *Hz)
+{
+    int64_t k;
+#pragma omp parallel for schedule(static)
+    for (k = 0; k <= N; ++k) {
+        for (int64_t j = 0; j <= N; ++j) {
+            for (int64_t i = 0; i <= N; ++i) {
+                const int64_t c = yee(N, i, j, k);
+                const or_medium m = tab[mat[c]];
+                if (j < N && k < N)
+                    Hx[c] = m.da * Hx[c] - m.db * ((Ez[yee(N, i, j + 1, k)] - Ez[c])
+                                                   - (Ey[yee(N, i, j, k + 1)] - Ey[c]));
+                if (i < N && k < N)
+                    Hy[c] = m.da * Hy[c] - m.db * ((Ex[yee(N, i, j, k + 1)] - Ex[c])
+                                                   - (Ez[yee(N, i + 1, j, k)] - Ez[c]));
+                if (i < N && j < N)
+                    Hz[c] = m.da * Hz[c] - m.db * ((Ey[yee(N, i + 1, j, k)] - Ey[c])
+                                                   - (Ex[yee(N, i, j + 1, k)] - Ex[c]));
+            }
+        }
+    }
+}
+
+static void or_fdtd_e_media(int64_t N, const or_medium *tab, const uint8_t *mat,
+                            double *Ex, double *Ey, double *Ez,
+                            const double *Hx, const double *Hy, const double *Hz)
+{
+    int64_t k;
+#pragma omp parallel for schedule(static)
+    for (k = 0; k <= N; ++k) {
+        for (int64_t j = 0; j <= N; ++j) {
+            for (int64_t i = 0; i <= N; ++i) {
+                const int64_t c = yee(N, i, j, k);
+                const or_medium m = tab[mat[c]];
+                if (i < N && j >= 1 && j <= N - 1 && k >= 1 && k <= N - 1)
+                    Ex[c] = m.ca * Ex[c] + m.cb * ((Hz[c] - Hz[yee(N, i, j - 1, k)])
+                                                   - (Hy[c] - Hy[yee(N, i, j, k - 1)]));
+                if (j < N && i >= 1 && i <= N - 1 && k >= 1 && k <= N - 1)
+                    Ey[c] = m.ca * Ey[c] + m.cb * ((Hx[c] - Hx[yee(N, i, j, k - 1)])
+                                                   - (Hz[c] - Hz[yee(N, i - 1, j, k)]));
+                if (k < N && i >= 1 && i <= N - 1 && j >= 1 && j <= N - 1)
+                    Ez[c] = m.ca * Ez[c] + m.cb * ((Hy[c] - Hy[yee(N, i - 1, j, k)])
+                                                   - (Hx[c] - Hx[yee(N, i, j - 1, k)]));
+            }
+        }
+    }
+}
+
+/* or_fdtd_run in media: mat is an (N+1)^3 array of material ids; the
+ * material table has n_mat (<= 256) rows given as four arrays. */
+int or_fdtd_run_media(int64_t N, int64_t n0, int64_t n_steps, double s, double *Ex,
+                      double *Ey, double *Ez, double *Hx, double *Hy, double *Hz,
+                      const uint8_t *mat, int n_mat, const double *eps_r,
+                      const double *sigma, const double *mu_r, const double *sigma_m,
+                      int src_on, int64_t si, int64_t sj, int64_t sk, double amp,
+                      double delay, double width)
+{
+    or_medium tab[256];
+    if (n_mat < 0 || n_mat > 256)
+        return 1;
+    for (int m = 0; m < 256; ++m)
+        tab[m] = (m < n_mat) ? or_medium_of(s, eps_r[m], sigma[m], mu_r[m], sigma_m[m])
+                             : or_medium_of(s, 1.0, 0.0, 1.0, 0.0);
+    for (int64_t n = n0; n < n0 + n_steps; ++n) {
+        or_fdtd_h_media(N, tab, mat, Ex, Ey, Ez, Hx, Hy, Hz);
+        or_fdtd_e_media(N, tab, mat, Ex, Ey, Ez, Hx, Hy, Hz);
+        if (src_on)
+            Ez[yee(N, si, sj, sk)] += or_fdtd_source((double)n, amp, delay, width);
+    }
+    return 0;
 }
 
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */

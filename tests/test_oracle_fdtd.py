@@ -142,3 +142,111 @@ def test_skeleton_oracle_closed_forms(oracle):
     assert np.array_equal(oracle.skeleton_run(x0, 2.0, 10), x0 * 1024.0)
     c = 1.0 + 2.0 ** -8
     np.testing.assert_allclose(oracle.skeleton_run(x0, c, 300), x0 * c ** 300, rtol=1e-13)
+
+
+# ----------------------------------------------------------- media pins --
+#
+# The lossy-medium Yee update is pinned without restating its coefficients:
+# * a table of vacuum rows gives the vacuum scheme bit for bit;
+# * in a uniform lossless medium a cavity mode obeys the Yee dispersion with
+#   the wave speed 1/sqrt(eps_r mu_r): sin^2 terms scaled by s^2/(eps_r mu_r);
+# * in any heterogeneous lossy medium the discrete Poynting theorem holds
+#   exactly: with W^n = sum eps |E^n|^2 + sum mu H^{n-1/2} . H^{n+1/2},
+#   W^{n+1} - W^n = -(s/2) [ sum sigma (E^{n+1} + E^n)^2
+#                            + sum sigma_m H^{n+1/2} (H^{n+3/2} + 2 H^{n+1/2} + H^{n-1/2}) ]
+#   (Joule heating of the time-averaged fields), eps, mu, sigma, sigma_m taken
+#   at each component's own location; a wrong coefficient, sign, or material
+#   lookup breaks it;
+# * a swap-symmetric medium keeps the driven field's x <-> y symmetry.
+
+def _per_location(mat, table, q):
+    return np.array([row[q] for row in table] + [(1.0, 0.0, 1.0, 0.0)[q]] * (256 - len(table)))[mat]
+
+
+def test_media_vacuum_table_is_the_vacuum_scheme(oracle):
+    N = 10
+    mat, _ = gs_inputs.fdtd_media(N, n_mat=3, seed=5)
+    f = _fields_from_e(oracle, N, gs_inputs.fdtd_random_e(N, 2))
+    g = {k: v.copy() for k, v in f.items()}
+    oracle.fdtd_run(f, N, 30, src=(5, 5, 5))
+    oracle.fdtd_run(g, N, 30, src=(5, 5, 5), media=(mat, [(1.0, 0.0, 1.0, 0.0)] * 3))
+    assert all(np.array_equal(f[c], g[c]) for c in oracle.FDTD_COMPONENTS)
+
+
+@pytest.mark.parametrize("eps_r,mu_r", [(2.5, 1.5), (6.0, 1.0)])
+def test_media_uniform_dielectric_dispersion(oracle, eps_r, mu_r):
+    N, s = 16, 0.5
+    mode = _mode_field(N, "Ez", 2, 1)
+    f = oracle.fdtd_zero_fields(N)
+    f["Ez"][...] = mode
+    media = (np.ones((N + 1,) * 3, dtype=np.uint8), [(1.0, 0.0, 1.0, 0.0), (eps_r, 0.0, mu_r, 0.0)])
+    a = [float(np.sum(f["Ez"] * mode))]
+    for _ in range(60):
+        oracle.fdtd_run(f, N, 1, courant=s, media=media)
+        a.append(float(np.sum(f["Ez"] * mode)))
+    cos_pred = 1.0 - 2.0 * s * s / (eps_r * mu_r) * (math.sin(math.pi * 2 / (2 * N)) ** 2
+                                                     + math.sin(math.pi * 1 / (2 * N)) ** 2)
+    amp = max(abs(v) for v in a)
+    checked = 0
+    for n in range(1, len(a) - 1):
+        if abs(a[n]) > 0.2 * amp:
+            assert abs((a[n + 1] + a[n - 1]) / (2.0 * a[n]) - cos_pred) <= 1e-10
+            checked += 1
+    assert checked > 20
+
+
+@pytest.mark.parametrize("lossy", [True, False])
+def test_media_discrete_poynting_theorem(oracle, lossy):
+    N, s = 9, 0.5
+    mat, table = gs_inputs.fdtd_media(N, n_mat=4, n_boxes=10, lossy=lossy, seed=11)
+    assert len(np.unique(mat)) >= 3
+    if lossy:
+        assert all(r[1] > 0 and r[3] > 0 for r in table[1:])
+    eps, sig, mu, sigm = (_per_location(mat, table, q) for q in range(4))
+    E = ("Ex", "Ey", "Ez")
+    H = ("Hx", "Hy", "Hz")
+    f = _fields_from_e(oracle, N, gs_inputs.fdtd_random_e(N, 4))
+    e_hist = [{c: f[c].copy() for c in E}]  # e_hist[n] = E^n
+    h_hist = [{c: f[c].copy() for c in H}]  # h_hist[n] = H^{n-1/2}; H^{-1/2} = 0
+    for _ in range(40):
+        oracle.fdtd_run(f, N, 1, courant=s, media=(mat, table))
+        e_hist.append({c: f[c].copy() for c in E})
+        h_hist.append({c: f[c].copy() for c in H})
+
+    def W(n):  # sum eps |E^n|^2 + sum mu H^{n-1/2} . H^{n+1/2}
+        return (sum(float(np.sum(eps * e_hist[n][c] ** 2)) for c in E)
+                + sum(float(np.sum(mu * h_hist[n][c] * h_hist[n + 1][c])) for c in H))
+
+    W0 = W(0)
+    assert W0 > 0
+    drop = 0.0
+    for n in range(0, 38):
+        joule = (sum(float(np.sum(sig * (e_hist[n + 1][c] + e_hist[n][c]) ** 2)) for c in E)
+                 + sum(float(np.sum(sigm * h_hist[n + 1][c] * (h_hist[n + 2][c] + 2 * h_hist[n + 1][c]
+                                                                + h_hist[n][c]))) for c in H))
+        assert abs((W(n + 1) - W(n)) + 0.5 * s * joule) <= 1e-12 * W0, n
+        drop += W(n) - W(n + 1)
+    if lossy:
+        assert drop > 1e-4 * W0  # the losses are visible
+    else:
+        assert abs(drop) <= 1e-12 * W0
+
+
+def test_media_swap_symmetry(oracle):
+    N = 12
+    c = N // 2
+    mat, table = gs_inputs.fdtd_media(N, n_mat=4, n_boxes=6, seed=8, swap_symmetric=True)
+    f = oracle.fdtd_zero_fields(N)
+    oracle.fdtd_run(f, N, 90, src=(c, c, c), media=(mat, table))
+    Ex, Ey, Ez, Hx, Hy, Hz = (f[k] for k in oracle.FDTD_COMPONENTS)
+    scale = np.max(np.abs(Ez))
+    sw = lambda a: np.transpose(a, (0, 2, 1))
+    tol = 1e-12 * scale
+    assert np.max(np.abs(Ez - sw(Ez))) <= tol
+    assert np.max(np.abs(Ex - sw(Ey))) <= tol
+    assert np.max(np.abs(Hx + sw(Hy))) <= tol
+    assert np.max(np.abs(Hz + sw(Hz))) <= tol
+    # the medium changes the field: it differs from the vacuum run
+    g = oracle.fdtd_zero_fields(N)
+    oracle.fdtd_run(g, N, 90, src=(c, c, c))
+    assert np.max(np.abs(g["Ez"] - Ez)) > 1e-3 * scale
