@@ -456,6 +456,14 @@ gs_status gs_mlp_predict(gs_mlp *m, const float *X, int64_t n_rows, float *pred)
  * Synchronous. */
 gs_status gs_mlp_argmin(gs_mlp *m, const float *X, int64_t n_rows, int64_t *best_row, float *best_pred);
 
+/* As gs_mlp_argmin for an ensemble of k models: the row with the smallest
+ * mean prediction of models[0..k-1] (each with its own normalisation), and
+ * that mean.  Runs on models[0]'s stream after waiting for the others'.
+ * Synchronous.  Errors are reported through gs_mlp_last_error(models[0])
+ * for CUDA failures, gs_last_error(NULL) for bad arguments. */
+gs_status gs_mlp_argmin_ensemble(gs_mlp *const *models, int32_t k, const float *X, int64_t n_rows,
+                                 int64_t *best_row, float *best_pred);
+
 /* ------------------------------------------------ uneven instance batch -- */
 
 /* Many independent 2D thermal grids of different sizes advanced together.

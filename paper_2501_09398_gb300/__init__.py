@@ -354,6 +354,7 @@ _sig("gs_mlp_loss_grad", [_vp, _vp, _vp, _i64, _fp, _fp])
 _sig("gs_mlp_train", [_vp, _vp, _vp, _i64, _i32, _i32, ctypes.c_float, _fp])
 _sig("gs_mlp_predict", [_vp, _vp, _i64, _vp])
 _sig("gs_mlp_argmin", [_vp, _vp, _i64, ctypes.POINTER(_i64), _fp])
+_sig("gs_mlp_argmin_ensemble", [ctypes.POINTER(_vp), ctypes.c_int32, _vp, _i64, ctypes.POINTER(_i64), _fp])
 
 
 def _lcheck(st: int, m):
@@ -437,6 +438,16 @@ def gs_mlp_argmin(m, X_dev_ptr: int, n_rows: int):
     idx = _i64()
     val = ctypes.c_float()
     _lcheck(_lib.gs_mlp_argmin(m, _vp(X_dev_ptr), n_rows, ctypes.byref(idx), ctypes.byref(val)), m)
+    return idx.value, val.value
+
+
+def gs_mlp_argmin_ensemble(models, X_dev_ptr: int, n_rows: int):
+    """Row with the smallest mean prediction of several models, and that mean."""
+    arr = (_vp * len(models))(*models)
+    idx = _i64()
+    val = ctypes.c_float()
+    _lcheck(_lib.gs_mlp_argmin_ensemble(arr, len(models), _vp(X_dev_ptr), n_rows, ctypes.byref(idx),
+                                        ctypes.byref(val)), models[0] if models else None)
     return idx.value, val.value
 
 

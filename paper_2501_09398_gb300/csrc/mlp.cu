@@ -20,9 +20,9 @@ using namespace gs;
 
 namespace {
 
-constexpr int NI = GS_MLP_INPUTS;   // 16
+constexpr int NI = GS_MLP_INPUTS;   // 18
 constexpr int NH = GS_MLP_HIDDEN;   // 32
-constexpr int NP = GS_MLP_PARAMS;   // 1633
+constexpr int NP = GS_MLP_PARAMS;   // 1697
 constexpr int OW1 = 0, OB1 = OW1 + NH * NI, OW2 = OB1 + NH, OB2 = OW2 + NH * NH, OW3 = OB2 + NH, OB3 = OW3 + NH;
 static_assert(OB3 + 1 == NP, "parameter layout");
 constexpr int ROWS = 128;           // rows per block (threads per block)
@@ -179,6 +179,8 @@ __global__ void __launch_bounds__(256) mlp_reduce_adam_kernel(const ReduceAdamAr
     }
 }
 
+// ACC: add the prediction to out[r] (ensemble sums) instead of storing it.
+template <bool ACC>
 __global__ void __launch_bounds__(256) mlp_predict_kernel(const float* __restrict__ params,
                                                           const float* __restrict__ mean,
                                                           const float* __restrict__ inv_std,
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(256) mlp_predict_kernel(const float* __restric
         for (int j = 0; j < NH; ++j) acc = fmaf(P[OW2 + i * NH + j], h1[j], acc);
         pred = fmaf(P[OW3 + i], fmaxf(acc, 0.f), pred);
     }
-    out[r] = pred;
+    out[r] = ACC ? out[r] + pred : pred;
 }
 
 // Single block: index of the smallest value (ties: smallest index).
@@ -570,27 +572,28 @@ gs_status gs_mlp_train(gs_mlp* m, const float* X, const float* y, int64_t n_rows
 gs_status gs_mlp_predict(gs_mlp* m, const float* X, int64_t n_rows, float* pred) {
     if (!m || !dev_ptr_ok(X) || !dev_ptr_ok(pred) || n_rows < 1)
         return mlp_fail(m, GS_ERR_INVALID_ARG, "gs_mlp_predict: bad args");
-    mlp_predict_kernel<<<(unsigned)((n_rows + 255) / 256), 256, 0, m->stream>>>(m->params, m->norm, m->norm + NI, X,
-                                                                              n_rows, pred);
+    mlp_predict_kernel<false><<<(unsigned)((n_rows + 255) / 256), 256, 0, m->stream>>>(m->params, m->norm,
+                                                                                     m->norm + NI, X, n_rows, pred);
     GS_MLPC(m, cudaGetLastError());
     return GS_OK;
 }
 
-gs_status gs_mlp_argmin(gs_mlp* m, const float* X, int64_t n_rows, int64_t* best_row, float* best_pred) {
-    if (!m || !dev_ptr_ok(X) || n_rows < 1 || !best_row)
-        return mlp_fail(m, GS_ERR_INVALID_ARG, "gs_mlp_argmin: bad args");
-    if (n_rows > m->pred_cap) {
-        if (m->pred) {
-            cudaStreamSynchronize(m->stream);
-            cudaFree(m->pred);
-            m->pred = nullptr;
-            m->pred_cap = 0;
-        }
-        GS_MLPC(m, cudaMalloc(&m->pred, (size_t)n_rows * sizeof(float)));
-        m->pred_cap = n_rows;
+namespace {
+
+gs_status ensure_pred(gs_mlp* m, int64_t n_rows) {
+    if (n_rows <= m->pred_cap) return GS_OK;
+    if (m->pred) {
+        cudaStreamSynchronize(m->stream);
+        cudaFree(m->pred);
+        m->pred = nullptr;
+        m->pred_cap = 0;
     }
-    gs_status st = gs_mlp_predict(m, X, n_rows, m->pred);
-    if (st != GS_OK) return st;
+    GS_MLPC(m, cudaMalloc(&m->pred, (size_t)n_rows * sizeof(float)));
+    m->pred_cap = n_rows;
+    return GS_OK;
+}
+
+gs_status finish_argmin(gs_mlp* m, int64_t n_rows, float scale, int64_t* best_row, float* best_pred) {
     argmin_kernel<<<1, 1024, 0, m->stream>>>(m->pred, n_rows, m->amin_idx, m->amin_val);
     GS_MLPC(m, cudaGetLastError());
     long long idx = -1;
@@ -599,8 +602,44 @@ gs_status gs_mlp_argmin(gs_mlp* m, const float* X, int64_t n_rows, int64_t* best
     GS_MLPC(m, cudaMemcpyAsync(&val, m->amin_val, sizeof(val), cudaMemcpyDeviceToHost, m->stream));
     GS_MLPC(m, cudaStreamSynchronize(m->stream));
     *best_row = idx;
-    if (best_pred) *best_pred = val;
+    if (best_pred) *best_pred = val * scale;
     return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_mlp_argmin(gs_mlp* m, const float* X, int64_t n_rows, int64_t* best_row, float* best_pred) {
+    if (!m || !dev_ptr_ok(X) || n_rows < 1 || !best_row)
+        return mlp_fail(m, GS_ERR_INVALID_ARG, "gs_mlp_argmin: bad args");
+    gs_status st = ensure_pred(m, n_rows);
+    if (st == GS_OK) st = gs_mlp_predict(m, X, n_rows, m->pred);
+    if (st != GS_OK) return st;
+    return finish_argmin(m, n_rows, 1.0f, best_row, best_pred);
+}
+
+gs_status gs_mlp_argmin_ensemble(gs_mlp* const* models, int32_t k, const float* X, int64_t n_rows,
+                                 int64_t* best_row, float* best_pred) {
+    if (!models || k < 1 || !dev_ptr_ok(X) || n_rows < 1 || !best_row)
+        return mlp_fail(nullptr, GS_ERR_INVALID_ARG, "gs_mlp_argmin_ensemble: bad args");
+    for (int32_t i = 0; i < k; ++i)
+        if (!models[i]) return mlp_fail(nullptr, GS_ERR_INVALID_ARG, "gs_mlp_argmin_ensemble: NULL model");
+    gs_mlp* m0 = models[0];
+    for (int32_t i = 1; i < k; ++i) GS_MLPC(m0, cudaStreamSynchronize(models[i]->stream));
+    gs_status st = ensure_pred(m0, n_rows);
+    if (st != GS_OK) return st;
+    const unsigned grid = (unsigned)((n_rows + 255) / 256);
+    // sum of the members' predictions in member order, on the first member's stream
+    for (int32_t i = 0; i < k; ++i) {
+        const gs_mlp* mi = models[i];
+        if (i == 0)
+            mlp_predict_kernel<false><<<grid, 256, 0, m0->stream>>>(mi->params, mi->norm, mi->norm + NI, X, n_rows,
+                                                                    m0->pred);
+        else
+            mlp_predict_kernel<true><<<grid, 256, 0, m0->stream>>>(mi->params, mi->norm, mi->norm + NI, X, n_rows,
+                                                                   m0->pred);
+        GS_MLPC(m0, cudaGetLastError());
+    }
+    return finish_argmin(m0, n_rows, 1.0f / (float)k, best_row, best_pred);
 }
 
 gs_status gs_features(const gs_workload* w, const gs_tune_candidate* c, int32_t n, float* out) {
@@ -631,6 +670,16 @@ gs_status gs_features(const gs_workload* w, const gs_tune_candidate* c, int32_t 
         f[13] = (float)std::log2((double)p.block_x);
         f[14] = (float)std::log2((double)p.rows);
         f[15] = (float)p.temporal_depth;
+        // kernel variant, with AUTO resolved as the context resolves it
+        int k = p.kernel;
+        if (k == GS_KERNEL_AUTO) {
+            const bool thin = w->kind != GS_HEAT3D || w->nz <= kColumnMaxNz;
+            k = (p.temporal_depth == 1) ? (thin ? GS_KERNEL_COLUMN : GS_KERNEL_MARCH)
+                                        : ((w->kind == GS_HEAT2D || w->nz <= kWaveMaxNz) ? GS_KERNEL_WAVE
+                                                                                          : GS_KERNEL_TILE);
+        }
+        f[16] = (k == GS_KERNEL_COLUMN || k == GS_KERNEL_COLUMN_SMEM);
+        f[17] = (k == GS_KERNEL_COLUMN_SMEM);
     }
     return GS_OK;
 }

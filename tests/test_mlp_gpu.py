@@ -118,3 +118,32 @@ def test_predict_and_argmin():
         assert idx == int(np.argmin(got)) and val == pytest.approx(got[idx])
     finally:
         g.gs_mlp_destroy(m)
+
+
+def test_argmin_ensemble_matches_oracle_mean():
+    import paper_2501_09398_gb300 as g
+
+    X, _ = _data(2500, 44)
+    Xd, X2d = _dev(X), _dev(X * 2.0 + 1.0)
+    models = [g.gs_mlp_create(seed=s) for s in (21, 22, 23)]
+    try:
+        refs = []
+        for i, m in enumerate(models):
+            # members standardise with their own statistics
+            g.gs_mlp_fit_normalization(m, (X2d if i == 1 else Xd).data_ptr(), X.shape[0])
+            mean, inv = (a.astype(np.float64) for a in g.gs_mlp_get_normalization(m))
+            refs.append(mr.forward(g.gs_mlp_get_params(m).astype(np.float64), X, mean, inv)[0])
+        ref = np.mean(refs, axis=0)
+        idx, val = g.gs_mlp_argmin_ensemble(models, Xd.data_ptr(), X.shape[0])
+        scale = max(1.0, float(np.max(np.abs(ref))))
+        # the pick is a minimum of the oracle mean up to FP32 rounding
+        assert ref[idx] <= ref.min() + 1e-5 * scale
+        assert abs(val - ref[idx]) <= 1e-5 * scale
+        # one member alone is that member's own argmin
+        i1, _ = g.gs_mlp_argmin_ensemble(models[:1], Xd.data_ptr(), X.shape[0])
+        assert i1 == g.gs_mlp_argmin(models[0], Xd.data_ptr(), X.shape[0])[0]
+        with pytest.raises(g.GsError):
+            g.gs_mlp_argmin_ensemble([], Xd.data_ptr(), X.shape[0])
+    finally:
+        for m in models:
+            g.gs_mlp_destroy(m)

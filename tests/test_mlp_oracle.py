@@ -66,12 +66,23 @@ def test_feature_layout(g):
     w = dict(kind=g.GS_HEAT2D, dtype=g.GS_F32, nx=512, ny=256, nz=1, n_iters=1000)
     f = g.gs_features(w, [(dict(block_x=64, rows=4, temporal_depth=1), 100),
                           (dict(block_x=128, rows=32, temporal_depth=4), 0)])
-    expect0 = [9, 8, 0, 1, 0, 0, 1, math.log2(1000), 1, 0, 0, math.log2(100), 0, 6, 2, 1]
-    expect1 = [9, 8, 0, 1, 0, 0, 1, math.log2(1000), 1, 0, 0, 0, 1, 7, 5, 4]
+    # the last two inputs flag the kernel variant: AUTO resolves to COLUMN
+    # at depth 1 in 2D and to the wavefront kernel at depth 4
+    expect0 = [9, 8, 0, 1, 0, 0, 1, math.log2(1000), 1, 0, 0, math.log2(100), 0, 6, 2, 1, 1, 0]
+    expect1 = [9, 8, 0, 1, 0, 0, 1, math.log2(1000), 1, 0, 0, 0, 1, 7, 5, 4, 0, 0]
     np.testing.assert_allclose(f[0], expect0, rtol=1e-6)
     np.testing.assert_allclose(f[1], expect1, rtol=1e-6)
     w3 = dict(kind=g.GS_FDTD3D, dtype=g.GS_BF16, nx=128, ny=128, nz=128, n_iters=5000)
     f3 = g.gs_features(w3, [(dict(block_x=64, rows=16, temporal_depth=1), 50)])[0]
-    assert list(f3[3:7]) == [0, 0, 1, 2] and list(f3[8:11]) == [0, 1, 0]
+    assert list(f3[3:7]) == [0, 0, 1, 2] and list(f3[8:11]) == [0, 1, 0] and list(f3[16:]) == [1, 0]
+    deep = dict(kind=g.GS_HEAT3D, dtype=g.GS_F32, nx=64, ny=64, nz=16, n_iters=100)
+    thin = dict(deep, nz=8)
+    one = (dict(block_x=32, rows=16, temporal_depth=1), 10)
+    assert list(g.gs_features(deep, [one])[0][16:]) == [0, 0]  # AUTO -> MARCH above 8 planes
+    assert list(g.gs_features(thin, [one])[0][16:]) == [1, 0]
+    smem = (dict(block_x=64, rows=4, temporal_depth=1, kernel=g.GS_KERNEL_COLUMN_SMEM), 10)
+    march = (dict(block_x=64, rows=4, temporal_depth=1, kernel=g.GS_KERNEL_MARCH), 10)
+    assert list(g.gs_features(thin, [smem])[0][16:]) == [1, 1]
+    assert list(g.gs_features(thin, [march])[0][16:]) == [0, 0]
     with pytest.raises(g.GsError):
         g.gs_features(w, [(dict(block_x=0, rows=4, temporal_depth=1), 10)])
