@@ -45,6 +45,10 @@ WORKLOADS = {
     "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1,
                         plan=dict(kernel=4, rows=8)),
     "fdtd-128": dict(kind="fdtd", N=128, iters=5000, S=100, depth=1, plan=dict(kernel=4, rows=2)),
+    # larger cavities (HBM-bound), in vacuum and filled with lossy objects
+    "fdtd-256": dict(kind="fdtd", N=256, iters=500, S=100, depth=1, plan=dict(kernel=4, rows=2)),
+    "fdtd-media-256": dict(kind="fdtd", N=256, iters=500, S=100, depth=1, plan=dict(kernel=4, rows=2),
+                           media=dict(n_mat=8, n_boxes=24, seed=0)),
     "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=1, plan={}),
 }
 DEFAULT = "heat3d-512x512x8"
@@ -103,9 +107,10 @@ def algo_bytes_per_launch(w, depth, elem=4):
 
     Thermal depth-t launch: read T once, write T once, read the P plane once
     (2D: P is the full plane), for t cell-updates per cell.  FDTD half-step
-    (H or E kernel): read 6 components, write 3, per cell."""
+    (H or E kernel): read 6 components, write 3, per cell, plus the 1-byte
+    material id in media."""
     if w["kind"] == "fdtd":
-        return cells_of(w) * 9 * elem
+        return cells_of(w) * (9 * elem + (1 if w.get("media") else 0))
     if w["kind"] == "multi":
         return cells_of(w) * 3 * elem
     plane = w["nx"] * w["ny"]
@@ -193,15 +198,17 @@ def oracle_sample(w, budget_s=10.0):
     if w["kind"] == "fdtd":
         N = w["N"]
         f = oracle.fdtd_zero_fields(N)
+        media = gs_inputs.fdtd_media(N, **w["media"]) if w.get("media") else None
         n = 0
         t0 = time.perf_counter()
         chunk = 20
         while n < w["iters"] and time.perf_counter() - t0 < budget_s:
-            oracle.fdtd_run(f, N, chunk, n0=n, src=(N // 2, N // 2, N // 2))
+            oracle.fdtd_run(f, N, chunk, n0=n, src=(N // 2, N // 2, N // 2), media=media)
             n += chunk
         dt = time.perf_counter() - t0
         full = f if n >= w["iters"] else None
-        return cells_of(w) * n / dt, f"FDTD {N}^3, first {n} of {w['iters']} steps", threads, full
+        what = "FDTD in media" if media else "FDTD"
+        return cells_of(w) * n / dt, f"{what} {N}^3, first {n} of {w['iters']} steps", threads, full
     if w["kind"] == "multi":
         sides = multi_sides(w)
         fields = gs_inputs.instance_fields(sides)
@@ -296,8 +303,12 @@ class Runner:
         if w["kind"] == "fdtd":
             N = w["N"]
             self.ctx = g.gs_create(g.GS_FDTD3D, N, N, N, g.GS_F32, g.GS_BC_PEC, h)
-            self.fields = g.FdtdFields(self.ctx, N)
+            self.fields = g.FdtdFields(self.ctx, N, media=bool(w.get("media")))
             g.gs_set_fdtd_params(self.ctx, courant=0.5, src_on=1, src=(N // 2, N // 2, N // 2))
+            if w.get("media"):
+                mat, table = gs_inputs.fdtd_media(N, **w["media"])
+                g.gs_set_fdtd_media(self.ctx, table)
+                g.gs_upload_u8(self.ctx, g.GS_FIELD_MAT, mat)
             self.host_in = []
             self.out_shape = (N + 1,) * 3
         else:
@@ -660,6 +671,7 @@ def main():
         # 2D 4096^2: HBM roofline of the depth-1 kernel, and the wavefront
         # depth-4 kernel's throughput
         for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(loop=True), "device_loop"),
+                              ("fdtd-256", {}, "column"), ("fdtd-media-256", {}, "column"),
                               ("heat2d-4096", {}, "depth1"),
                               ("heat2d-4096", dict(depth=4, kernel=2, rows=64, block_x=256), "wave4")):
             ww = WORKLOADS[nm]

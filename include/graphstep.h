@@ -88,7 +88,10 @@ typedef enum gs_field {
     GS_FIELD_HY = 7,
     GS_FIELD_HZ = 8,
     GS_FIELD_T = 9,  /* alias: whichever of T0/T1 holds the current state */
-    GS_FIELD_X = 10  /* skeleton vector: one row of nx elements */
+    GS_FIELD_X = 10, /* skeleton vector: one row of nx elements */
+    GS_FIELD_MAT = 11 /* FDTD material map: uint8 ids, (N+1)*(N+1) rows with
+                         the same pitch (in elements) as the six components;
+                         read only while a media table is set */
 } gs_field;
 
 typedef struct gs_ctx gs_ctx;
@@ -103,6 +106,20 @@ typedef struct gs_fdtd_params {
     int64_t src_i, src_j, src_k;
     float src_amp, src_delay, src_width; /* amp*exp(-((n-delay)/width)^2) */
 } gs_fdtd_params;
+
+/* One row of an FDTD media table: relative permittivity, conductivity,
+ * relative permeability and magnetic conductivity, in the normalised units
+ * of the FDTD context (eps0 = mu0 = c = 1, dx = 1, dt = courant).  With
+ * a_e = sigma*s/(2 eps_r), a_h = sigma_m*s/(2 mu_r), each step is the
+ * textbook lossy-medium Yee update
+ *   H <- da*H - db*curl(E),  da = (1 - a_h)/(1 + a_h), db = (s/mu_r)/(1 + a_h)
+ *   E <- ca*E + cb*curl(H),  ca = (1 - a_e)/(1 + a_e), cb = (s/eps_r)/(1 + a_e)
+ * (coefficients computed in double, stored as float). */
+typedef struct gs_medium {
+    float eps_r, sigma, mu_r, sigma_m;
+} gs_medium;
+
+#define GS_MAX_MEDIA 256
 
 /* Thermal kernel variants (gs_plan.kernel).
  *   MARCH  depth 1 only: each thread marches a vector of cells down `rows`
@@ -232,6 +249,17 @@ gs_status gs_set_heat_coeffs(gs_ctx *ctx, const gs_heat_coeffs *c);
  * inside the (N+1)^3 arrays.  Built graphs are discarded. */
 gs_status gs_set_fdtd_params(gs_ctx *ctx, const gs_fdtd_params *p);
 
+/* FDTD in linear, possibly lossy media (an extension of the paper's vacuum
+ * cavity solver, Sec. III-C): every component at element offset c takes
+ * the material GS_FIELD_MAT[c] (the cell whose lower corner is its index
+ * (i, j, k)); ids >= n are vacuum.  n = 0 returns to vacuum (the map is
+ * then not read).  Rows need finite eps_r > 0, mu_r > 0, sigma >= 0,
+ * sigma_m >= 0 (else GS_ERR_INVALID_ARG / GS_ERR_NUMERIC); n > 256 gives
+ * GS_ERR_INVALID_ARG.  Stepping with a table needs the map bound
+ * (GS_ERR_STATE) and the COLUMN kernels (GS_ERR_UNSUPPORTED for MARCH).
+ * The table is copied; built graphs are discarded. */
+gs_status gs_set_fdtd_media(gs_ctx *ctx, const gs_medium *table, int32_t n);
+
 /* The skeleton application's constant c (GS_SKELETON only); non-finite c
  * gives GS_ERR_NUMERIC.  Built graphs are discarded. */
 gs_status gs_set_scale(gs_ctx *ctx, float c);
@@ -260,6 +288,10 @@ gs_status gs_bind_field(gs_ctx *ctx, gs_field id, void *ptr, int64_t pitch);
  * the field's dense element count.  Synchronises the context stream before
  * returning, so the host buffer may be reused at once. */
 gs_status gs_upload(gs_ctx *ctx, gs_field id, const float *host, int64_t n);
+
+/* Copy a dense uint8 host array ((N+1)^3 ids, i fastest) into the bound
+ * GS_FIELD_MAT of an FDTD context.  Synchronous. */
+gs_status gs_upload_u8(gs_ctx *ctx, gs_field id, const uint8_t *host, int64_t n);
 
 /* Copy a bound field into a dense float32 host array (widened from the
  * storage type).  n must be the field's dense element count.  Synchronises

@@ -35,7 +35,8 @@ GS_F32, GS_BF16, GS_F16 = range(3)
 GS_BC_CLAMP, GS_BC_DIRICHLET0, GS_BC_PEC = range(3)
 GS_KERNEL_AUTO, GS_KERNEL_MARCH, GS_KERNEL_WAVE, GS_KERNEL_TILE, GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM = range(6)
 (GS_FIELD_T0, GS_FIELD_T1, GS_FIELD_P, GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY,
- GS_FIELD_HZ, GS_FIELD_T, GS_FIELD_X) = range(11)
+ GS_FIELD_HZ, GS_FIELD_T, GS_FIELD_X, GS_FIELD_MAT) = range(12)
+GS_MAX_MEDIA = 256
 
 DTYPES = {"f32": GS_F32, "bf16": GS_BF16, "f16": GS_F16}
 FDTD_FIELDS = (GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY, GS_FIELD_HZ)
@@ -56,6 +57,10 @@ class gs_fdtd_params(ctypes.Structure):
     _fields_ = [("courant", ctypes.c_float), ("src_on", ctypes.c_int32), ("src_i", ctypes.c_int64),
                 ("src_j", ctypes.c_int64), ("src_k", ctypes.c_int64), ("src_amp", ctypes.c_float),
                 ("src_delay", ctypes.c_float), ("src_width", ctypes.c_float)]
+
+
+class gs_medium(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("eps_r", "sigma", "mu_r", "sigma_m")]
 
 
 class gs_plan(ctypes.Structure):
@@ -108,6 +113,8 @@ _sig("gs_create", [ctypes.POINTER(_vp), ctypes.c_int, _i64, _i64, _i64, ctypes.c
 _sig("gs_destroy", [_vp])
 _sig("gs_set_heat_coeffs", [_vp, ctypes.POINTER(gs_heat_coeffs)])
 _sig("gs_set_fdtd_params", [_vp, ctypes.POINTER(gs_fdtd_params)])
+_sig("gs_set_fdtd_media", [_vp, ctypes.POINTER(gs_medium), ctypes.c_int32])
+_sig("gs_upload_u8", [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), _i64])
 _sig("gs_set_plan", [_vp, ctypes.POINTER(gs_plan)])
 _sig("gs_set_scale", [_vp, ctypes.c_float])
 _sig("gs_get_plan", [_vp, ctypes.POINTER(gs_plan)])
@@ -214,6 +221,18 @@ def gs_bind_field(ctx, field: int, ptr: int, pitch: int) -> None:
 
 def gs_upload(ctx, field: int, host: np.ndarray) -> None:
     _check(_lib.gs_upload(ctx, field, _f32_ptr(host), host.size), ctx)
+
+
+def gs_upload_u8(ctx, field: int, host: np.ndarray) -> None:
+    host = np.ascontiguousarray(host, dtype=np.uint8)
+    _check(_lib.gs_upload_u8(ctx, field, host.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), host.size), ctx)
+
+
+def gs_set_fdtd_media(ctx, table) -> None:
+    """table: rows of (eps_r, sigma, mu_r, sigma_m); empty for vacuum."""
+    rows = list(table)
+    arr = (gs_medium * max(1, len(rows)))(*[gs_medium(*map(float, r)) for r in rows])
+    _check(_lib.gs_set_fdtd_media(ctx, arr, len(rows)), ctx)
 
 
 def gs_read_field(ctx, field: int, out: np.ndarray) -> np.ndarray:

@@ -60,12 +60,15 @@ struct gs_ctx {
     gs_fdtd_params fp{};
     float scale = 1.0f;
     gs_plan plan{};
-    void* ptr[11] = {};
-    int64_t pitch[11] = {};
+    void* ptr[12] = {};
+    int64_t pitch[12] = {};
     int parity = 0;
     int64_t time = 0;
     long long* d_counter = nullptr;
     unsigned long long* d_loop = nullptr;  // trips left of the device loop
+    std::vector<gs_medium> media;           // FDTD media table (empty: vacuum)
+    std::vector<float2> h_med;              // coefficients as uploaded
+    float2* d_med = nullptr;                // [256] (da, db) | [256] (ca, cb)
     float* staging = nullptr;
     size_t staging_bytes = 0;
     // Launch descriptors, valid while descs_ok: thermal [0]=depth 1,
@@ -127,7 +130,7 @@ bool field_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows) {
         *rows = 1;
         return true;
     }
-    if (id >= GS_FIELD_EX && id <= GS_FIELD_HZ) {
+    if ((id >= GS_FIELD_EX && id <= GS_FIELD_HZ) || id == GS_FIELD_MAT) {
         *width = c->nx + 1;
         *rows = (c->nx + 1) * (c->nx + 1);
         return true;
@@ -283,7 +286,31 @@ gs_status require_fields(gs_ctx* c) {
         for (int f = GS_FIELD_EY; f <= GS_FIELD_HZ; ++f)
             if (c->pitch[f] != c->pitch[GS_FIELD_EX])
                 return fail(c, GS_ERR_STATE, "all six FDTD components must have the same pitch");
+        if (!c->media.empty()) {
+            if (!c->ptr[GS_FIELD_MAT]) return fail(c, GS_ERR_STATE, "a media table is set: bind GS_FIELD_MAT");
+            if (c->pitch[GS_FIELD_MAT] != c->pitch[GS_FIELD_EX])
+                return fail(c, GS_ERR_STATE, "GS_FIELD_MAT must have the components' pitch (in elements)");
+        }
     }
+    return GS_OK;
+}
+
+// Coefficients of the media table at the current courant number, all 256
+// ids (vacuum past the table), uploaded to the context's device table.
+gs_status upload_media(gs_ctx* c) {
+    const double s = c->fp.courant;
+    c->h_med.assign(2 * GS_MAX_MEDIA, make_float2(1.0f, (float)s));
+    for (size_t m = 0; m < c->media.size(); ++m) {
+        const gs_medium& r = c->media[m];
+        const double ae = (double)r.sigma * s / (2.0 * r.eps_r);
+        const double ah = (double)r.sigma_m * s / (2.0 * r.mu_r);
+        c->h_med[m] = make_float2((float)((1.0 - ah) / (1.0 + ah)), (float)((s / r.mu_r) / (1.0 + ah)));
+        c->h_med[GS_MAX_MEDIA + m] = make_float2((float)((1.0 - ae) / (1.0 + ae)), (float)((s / r.eps_r) / (1.0 + ae)));
+    }
+    if (!c->d_med) GS_CUDA(c, cudaMalloc(&c->d_med, 2 * GS_MAX_MEDIA * sizeof(float2)));
+    GS_CUDA(c, cudaMemcpyAsync(c->d_med, c->h_med.data(), 2 * GS_MAX_MEDIA * sizeof(float2), cudaMemcpyHostToDevice,
+                               c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
     return GS_OK;
 }
 
@@ -344,6 +371,16 @@ gs_status ensure_descs(gs_ctx* c) {
         a.delay = c->fp.src_delay;
         a.width = c->fp.src_width;
         a.counter = c->d_counter;
+        a.mat = nullptr;
+        a.med = nullptr;
+        if (!c->media.empty()) {
+            if (c->plan.kernel != GS_KERNEL_COLUMN)
+                return fail(c, GS_ERR_UNSUPPORTED, "FDTD media run on the COLUMN kernels only");
+            gs_status ms = upload_media(c);
+            if (ms != GS_OK) return ms;
+            a.mat = static_cast<const unsigned char*>(c->ptr[GS_FIELD_MAT]);
+            a.med = c->d_med;
+        }
         cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, c->plan.kernel, &c->desc[0][0]);
         if (e == cudaSuccess) e = fdtd_desc(c->dt, true, a, c->plan.block_x, c->plan.kernel, &c->desc[0][1]);
         if (e != cudaSuccess) return cuda_fail(c, e, "FDTD kernel set-up");
@@ -729,6 +766,7 @@ gs_status gs_destroy(gs_ctx* c) {
     destroy_graphs(c);
     if (c->d_counter) cudaFree(c->d_counter);
     if (c->d_loop) cudaFree(c->d_loop);
+    if (c->d_med) cudaFree(c->d_med);
     if (c->staging) cudaFree(c->staging);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -768,6 +806,38 @@ gs_status gs_set_fdtd_params(gs_ctx* c, const gs_fdtd_params* p) {
     return GS_OK;
 }
 
+gs_status gs_set_fdtd_media(gs_ctx* c, const gs_medium* table, int32_t n) {
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (c->kind != GS_FDTD3D) return fail(c, GS_ERR_INVALID_ARG, "not an FDTD context");
+    if (n < 0 || n > GS_MAX_MEDIA) return fail(c, GS_ERR_INVALID_ARG, "media table: 0 <= n <= 256 rows");
+    if (n > 0 && !table) return fail(c, GS_ERR_INVALID_ARG, "NULL media table");
+    for (int32_t m = 0; m < n; ++m) {
+        const gs_medium& r = table[m];
+        if (!finite_all(&r.eps_r, 4)) return fail(c, GS_ERR_NUMERIC, "media row " + std::to_string(m) + ": non-finite");
+        if (!(r.eps_r > 0.f) || !(r.mu_r > 0.f) || r.sigma < 0.f || r.sigma_m < 0.f)
+            return fail(c, GS_ERR_INVALID_ARG,
+                        "media row " + std::to_string(m) + ": need eps_r > 0, mu_r > 0, sigma >= 0, sigma_m >= 0");
+    }
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->media.assign(table, table + n);
+    invalidate(c);
+    return GS_OK;
+}
+
+gs_status gs_upload_u8(gs_ctx* c, gs_field id, const uint8_t* host, int64_t n) {
+    if (!c || !host) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    int64_t width, rows;
+    if (id != GS_FIELD_MAT || !field_shape(c, id, &width, &rows))
+        return fail(c, GS_ERR_INVALID_ARG, "gs_upload_u8 takes GS_FIELD_MAT of an FDTD context");
+    if (!c->ptr[id]) return fail(c, GS_ERR_STATE, "field is not bound");
+    if (n != width * rows)
+        return fail(c, GS_ERR_INVALID_ARG, "n must equal the dense element count " + std::to_string(width * rows));
+    GS_CUDA(c, cudaMemcpy2DAsync(c->ptr[id], c->pitch[id], host, width, width, rows, cudaMemcpyHostToDevice,
+                                 c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GS_OK;
+}
+
 gs_status gs_set_plan(gs_ctx* c, const gs_plan* plan) {
     if (!c || !plan) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
     gs_plan p = *plan;
@@ -788,7 +858,7 @@ gs_status gs_bind_field(gs_ctx* c, gs_field id, void* ptr, int64_t pitch) {
     if (!c) return GS_ERR_INVALID_ARG;
     const int f = resolve(c, id);
     int64_t width, rows;
-    if (f < 0 || f > GS_FIELD_X || f == GS_FIELD_T || !field_shape(c, f, &width, &rows))
+    if (f < 0 || f > GS_FIELD_MAT || f == GS_FIELD_T || !field_shape(c, f, &width, &rows))
         return fail(c, GS_ERR_INVALID_ARG, "field id not valid for this context kind");
     if (ptr) {
         if (reinterpret_cast<uintptr_t>(ptr) % 16)

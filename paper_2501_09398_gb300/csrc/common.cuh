@@ -88,6 +88,24 @@ __device__ __forceinline__ void load_vecw(const ST* __restrict__ p, float (&v)[W
     }
 }
 
+// W consecutive uint8 ids (W = 4 or 8: a 4- or 8-byte access).
+template <int W>
+__device__ __forceinline__ void load_ids(const unsigned char* __restrict__ p, unsigned (&id)[W]) {
+    static_assert(W == 4 || W == 8, "4 or 8 ids");
+    if constexpr (W == 4) {
+        const unsigned raw = __ldg(reinterpret_cast<const unsigned*>(p));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) id[i] = (raw >> (8 * i)) & 0xffu;
+    } else {
+        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            id[i] = (raw.x >> (8 * i)) & 0xffu;
+            id[4 + i] = (raw.y >> (8 * i)) & 0xffu;
+        }
+    }
+}
+
 template <typename ST, int W>
 __device__ __forceinline__ void store_vecw(ST* p, const float (&v)[W], int n_valid) {
     if (n_valid >= W) {
@@ -152,6 +170,11 @@ struct FdtdArgs {
     int si, sj, sk;
     float amp, delay, width;
     long long* counter;   // device step counter (E kernel, source owner)
+    // Media (NULL mat: vacuum): uint8 material ids at the components' own
+    // element offsets, and the coefficient table: med[m] = (da, db) of the
+    // H update, med[256 + m] = (ca, cb) of the E update, for all 256 ids.
+    const unsigned char* mat;
+    const float2* med;
 };
 
 struct SkeletonArgs {

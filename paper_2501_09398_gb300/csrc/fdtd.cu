@@ -30,6 +30,14 @@ __device__ __forceinline__ float curl_sub(float f, float s, float a, float b, fl
 __device__ __forceinline__ float curl_add(float f, float s, float a, float b, float c, float d) {
     return __fmaf_rn(s, __fsub_rn(__fsub_rn(a, b), __fsub_rn(c, d)), f);
 }
+// Media forms: da*f - db*curl and ca*f + cb*curl.  With a vacuum row
+// (da = ca = 1, db = cb = s) they round exactly like curl_sub / curl_add.
+__device__ __forceinline__ float curl_sub_m(float f, float2 m, float a, float b, float c, float d) {
+    return __fmaf_rn(-m.y, __fsub_rn(__fsub_rn(a, b), __fsub_rn(c, d)), __fmul_rn(m.x, f));
+}
+__device__ __forceinline__ float curl_add_m(float f, float2 m, float a, float b, float c, float d) {
+    return __fmaf_rn(m.y, __fsub_rn(__fsub_rn(a, b), __fsub_rn(c, d)), __fmul_rn(m.x, f));
+}
 
 template <typename ST>
 __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
@@ -202,10 +210,21 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
 // issues all of its loads at once (own components, the k+1 / j+1 (H) or
 // k-1 / j-1 (E) neighbour vectors, and the i-edge scalars of lanes 31 / 0).
 // Block (32, by, bz); neighbour vectors are re-read through L1/L2.
-template <typename ST>
-__global__ void __launch_bounds__(256) fdtd_h_column_kernel(const FdtdArgs a) {
+// MAT: lossy media; the thread also loads its vector of material ids with
+// the fields and takes each cell's coefficients from the block's copy of
+// the 256-row table in shared memory (staged once per block: through L1 the
+// streaming field loads evict it and every lookup would wait on L2).
+template <typename ST, bool MAT>
+__global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_column_kernel(const FdtdArgs a) {
     constexpr int V = Vec<ST>::N;
     pdl_wait_then_trigger();
+    __shared__ float2 s_med[MAT ? 256 : 1];
+    if constexpr (MAT) {
+        const int nt = 32 * blockDim.y * blockDim.z;
+        for (int t = threadIdx.x + 32 * (threadIdx.y + blockDim.y * threadIdx.z); t < 256; t += nt)
+            s_med[t] = __ldg(a.med + t);
+        __syncthreads();
+    }
     const int N = a.N, M = N + 1;
     const int lane = threadIdx.x;
     const int i0 = (blockIdx.x * 32 + lane) * V;
@@ -227,7 +246,11 @@ __global__ void __launch_bounds__(256) fdtd_h_column_kernel(const FdtdArgs a) {
         hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f;
     }
     float ez_r = 0.f, ey_r = 0.f;
+    unsigned id[V];  // material ids (MAT), loaded with the fields
+#pragma unroll
+    for (int e = 0; e < V; ++e) id[e] = 0;
     if (act) {
+        if constexpr (MAT) load_ids<V>(a.mat + o, id);
         load_vec(Ex + o, exk);
         load_vec(Ey + o, eyk);
         load_vec(Ez + o, ez);
@@ -252,14 +275,27 @@ __global__ void __launch_bounds__(256) fdtd_h_column_kernel(const FdtdArgs a) {
     if (!act) return;
     const float ez_last = (lane == 31) ? ez_r : ez_n;
     const float ey_last = (lane == 31) ? ey_r : ey_n;
+    if constexpr (MAT) {
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-        const int i = i0 + e;
-        const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
-        const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
-        if (j < N && k < N) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
-        if (i < N && k < N) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
-        if (i < N && j < N) hz[e] = curl_sub(hz[e], s, ey_ip, eyk[e], exj1[e], exk[e]);
+        for (int e = 0; e < V; ++e) {
+            const int i = i0 + e;
+            const float2 m = s_med[id[e]];
+            const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
+            const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
+            if (j < N && k < N) hx[e] = curl_sub_m(hx[e], m, ezj1[e], ez[e], eyk1[e], eyk[e]);
+            if (i < N && k < N) hy[e] = curl_sub_m(hy[e], m, exk1[e], exk[e], ez_ip, ez[e]);
+            if (i < N && j < N) hz[e] = curl_sub_m(hz[e], m, ey_ip, eyk[e], exj1[e], exk[e]);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int i = i0 + e;
+            const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
+            const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
+            if (j < N && k < N) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
+            if (i < N && k < N) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
+            if (i < N && j < N) hz[e] = curl_sub(hz[e], s, ey_ip, eyk[e], exj1[e], exk[e]);
+        }
     }
     const int nv = M - i0;
     store_vec(Hx + o, hx, nv);
@@ -267,10 +303,17 @@ __global__ void __launch_bounds__(256) fdtd_h_column_kernel(const FdtdArgs a) {
     store_vec(Hz + o, hz, nv);
 }
 
-template <typename ST>
-__global__ void __launch_bounds__(256) fdtd_e_column_kernel(const FdtdArgs a) {
+template <typename ST, bool MAT>
+__global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_column_kernel(const FdtdArgs a) {
     constexpr int V = Vec<ST>::N;
     pdl_wait_then_trigger();
+    __shared__ float2 s_med[MAT ? 256 : 1];
+    if constexpr (MAT) {
+        const int nt = 32 * blockDim.y * blockDim.z;
+        for (int t = threadIdx.x + 32 * (threadIdx.y + blockDim.y * threadIdx.z); t < 256; t += nt)
+            s_med[t] = __ldg(a.med + 256 + t);
+        __syncthreads();
+    }
     const int N = a.N, M = N + 1;
     const int lane = threadIdx.x;
     const int i0 = (blockIdx.x * 32 + lane) * V;
@@ -292,7 +335,11 @@ __global__ void __launch_bounds__(256) fdtd_e_column_kernel(const FdtdArgs a) {
         ex[e] = 0.f; ey[e] = 0.f; ez[e] = 0.f;
     }
     float hz_l = 0.f, hy_l = 0.f;
+    unsigned id[V];  // material ids (MAT), loaded with the fields
+#pragma unroll
+    for (int e = 0; e < V; ++e) id[e] = 0;
     if (act) {
+        if constexpr (MAT) load_ids<V>(a.mat + o, id);
         load_vec(Hx + o, hx);
         load_vec(Hy + o, hy);
         load_vec(Hz + o, hz);
@@ -319,15 +366,29 @@ __global__ void __launch_bounds__(256) fdtd_e_column_kernel(const FdtdArgs a) {
     const float hy_first = (lane == 0) ? hy_l : hy_p;
     const bool j_int = (j >= 1 && j <= N - 1);
     const bool k_int = (k >= 1 && k <= N - 1);
+    if constexpr (MAT) {
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-        const int i = i0 + e;
-        const bool i_int = (i >= 1 && i <= N - 1);
-        const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
-        const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
-        if (i < N && j_int && k_int) ex[e] = curl_add(ex[e], s, hz[e], hzj_1[e], hy[e], hyk_1[e]);
-        if (j < N && i_int && k_int) ey[e] = curl_add(ey[e], s, hx[e], hxk_1[e], hz[e], hz_im);
-        if (k < N && i_int && j_int) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
+        for (int e = 0; e < V; ++e) {
+            const int i = i0 + e;
+            const bool i_int = (i >= 1 && i <= N - 1);
+            const float2 m = s_med[id[e]];
+            const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
+            const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
+            if (i < N && j_int && k_int) ex[e] = curl_add_m(ex[e], m, hz[e], hzj_1[e], hy[e], hyk_1[e]);
+            if (j < N && i_int && k_int) ey[e] = curl_add_m(ey[e], m, hx[e], hxk_1[e], hz[e], hz_im);
+            if (k < N && i_int && j_int) ez[e] = curl_add_m(ez[e], m, hy[e], hy_im, hx[e], hxj_1[e]);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int i = i0 + e;
+            const bool i_int = (i >= 1 && i <= N - 1);
+            const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
+            const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
+            if (i < N && j_int && k_int) ex[e] = curl_add(ex[e], s, hz[e], hzj_1[e], hy[e], hyk_1[e]);
+            if (j < N && i_int && k_int) ey[e] = curl_add(ey[e], s, hx[e], hxk_1[e], hz[e], hz_im);
+            if (k < N && i_int && j_int) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
+        }
     }
     if (j == a.sj && k == a.sk && a.si >= i0 && a.si < i0 + V) {
         const long long n = *a.counter;
@@ -345,25 +406,27 @@ __global__ void __launch_bounds__(256) fdtd_e_column_kernel(const FdtdArgs a) {
     store_vec(Ez + o, ez, nv);
 }
 
+namespace {
+
+template <typename ST>
+const void* fdtd_func(bool e_half, bool col, bool mat) {
+    if (!col) return e_half ? (const void*)fdtd_e_kernel<ST> : (const void*)fdtd_h_kernel<ST>;
+    if (mat) return e_half ? (const void*)fdtd_e_column_kernel<ST, true> : (const void*)fdtd_h_column_kernel<ST, true>;
+    return e_half ? (const void*)fdtd_e_column_kernel<ST, false> : (const void*)fdtd_h_column_kernel<ST, false>;
+}
+
+}  // namespace
+
 cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out) {
     const int V = (dt == GS_F32) ? 4 : 8;
     const int M = a.N + 1;
     const bool col = (variant == GS_KERNEL_COLUMN);
+    const bool mat = (a.mat != nullptr);
+    if (mat && !col) return cudaErrorNotSupported;  // media: column kernels only
     switch (dt) {
-        case GS_F32:
-            out->func = col ? (e_half ? (const void*)fdtd_e_column_kernel<float> : (const void*)fdtd_h_column_kernel<float>)
-                            : (e_half ? (const void*)fdtd_e_kernel<float> : (const void*)fdtd_h_kernel<float>);
-            break;
-        case GS_BF16:
-            out->func = col ? (e_half ? (const void*)fdtd_e_column_kernel<__nv_bfloat16>
-                                      : (const void*)fdtd_h_column_kernel<__nv_bfloat16>)
-                            : (e_half ? (const void*)fdtd_e_kernel<__nv_bfloat16>
-                                      : (const void*)fdtd_h_kernel<__nv_bfloat16>);
-            break;
-        case GS_F16:
-            out->func = col ? (e_half ? (const void*)fdtd_e_column_kernel<__half> : (const void*)fdtd_h_column_kernel<__half>)
-                            : (e_half ? (const void*)fdtd_e_kernel<__half> : (const void*)fdtd_h_kernel<__half>);
-            break;
+        case GS_F32: out->func = fdtd_func<float>(e_half, col, mat); break;
+        case GS_BF16: out->func = fdtd_func<__nv_bfloat16>(e_half, col, mat); break;
+        case GS_F16: out->func = fdtd_func<__half>(e_half, col, mat); break;
         default: return cudaErrorInvalidValue;
     }
     if (col) {

@@ -8,8 +8,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (GS_BF16, GS_F16, GS_F32, GS_FIELD_P, GS_FIELD_T0, GS_FIELD_T1, FDTD_FIELDS, gs_bind_field,
-               gs_multi_bind_field, gs_required_pitch)
+from . import (GS_BF16, GS_F16, GS_F32, GS_FIELD_MAT, GS_FIELD_P, GS_FIELD_T0, GS_FIELD_T1, FDTD_FIELDS,
+               gs_bind_field, gs_multi_bind_field, gs_required_pitch)
 
 _TORCH = {GS_F32: torch.float32, GS_BF16: torch.bfloat16, GS_F16: torch.float16}
 
@@ -44,18 +44,23 @@ class HeatFields:
 
 
 class FdtdFields:
-    """Six (N+1)^3 Yee components with a common pitch."""
+    """Six (N+1)^3 Yee components with a common pitch and, with media=True,
+    the uint8 material map (same pitch in elements)."""
 
-    def __init__(self, ctx, N: int, dtype: int = GS_F32, device="cuda", pitch: int = 0):
+    def __init__(self, ctx, N: int, dtype: int = GS_F32, device="cuda", pitch: int = 0, media: bool = False):
         self.pitch = pitch or gs_required_pitch(dtype, N + 1)
         self.N, self.dtype = N, dtype
         self.f = [_alloc((N + 1) * (N + 1), self.pitch, dtype, device) for _ in range(6)]
         for fid, t in zip(FDTD_FIELDS, self.f):
             gs_bind_field(ctx, fid, t.data_ptr(), self.pitch)
+        self.mat = None
+        if media:
+            self.mat = torch.zeros((N + 1) * (N + 1) * self.pitch, dtype=torch.uint8, device=device)
+            gs_bind_field(ctx, GS_FIELD_MAT, self.mat.data_ptr(), self.pitch)
         _ready(device)
 
     def bytes(self) -> int:
-        return sum(t.numel() * t.element_size() for t in self.f)
+        return sum(t.numel() * t.element_size() for t in self.f + ([self.mat] if self.mat is not None else []))
 
 
 class MultiFields:

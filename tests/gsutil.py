@@ -76,10 +76,14 @@ def rel_l2(a, ref):
 FDTD_NAMES = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
 
 
-def fdtd_setup(N, dtype="f32", plan=None, src=None, courant=0.5):
+def fdtd_setup(N, dtype="f32", plan=None, src=None, courant=0.5, media=None):
+    """media: None, or (mat, table) as gs_inputs.fdtd_media returns."""
     g = gs()
     ctx = g.gs_create(g.GS_FDTD3D, N, N, N, g.DTYPES[dtype], g.GS_BC_PEC, stream_handle())
-    fields = g.FdtdFields(ctx, N, g.DTYPES[dtype])
+    fields = g.FdtdFields(ctx, N, g.DTYPES[dtype], media=media is not None)
+    if media is not None:
+        g.gs_set_fdtd_media(ctx, media[1])
+        g.gs_upload_u8(ctx, g.GS_FIELD_MAT, media[0])
     if src is not None:
         g.gs_set_fdtd_params(ctx, courant=courant, src_on=1, src=src)
     else:
