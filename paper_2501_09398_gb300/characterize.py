@@ -11,6 +11,9 @@ For each workload size (1e3, 1e6, 1e7 elements, the paper's "threads"):
   fitted to Eq. 6 (T_E = a/S + b);
 * the batch size minimising Eq. 1 over the divisors of I_k, and the relaxed
   optimum sqrt(a / k_c);
+* device memory of an uploaded executable graph of S nodes (the drop in
+  free memory across one build; the paper notes it grows linearly in S,
+  Sec. IV-A);
 * speed-up of graph batches of 100 over per-step launches for I = 1, 2, 3,
   5, 10, 100 batches, graph creation included (the paper's convention,
   Sec. IV-B).
@@ -58,16 +61,21 @@ def _timed(ctx, stream, n_iters, S):
 
 
 def characterize(n, stream, reps=10):
+    import torch
+
     ctx, keep = _ctx(n, stream.cuda_stream)
     try:
         gs_step(ctx, 200, 0)  # warm-up (module load, clocks)
         gs_sync(ctx)
-        create = {}
+        create, graph_mem = {}, {}
         for S in CREATE_S:
             ts = []
             for _ in range(reps):
                 gs_graph_destroy(ctx)
+                torch.cuda.synchronize()
+                free0 = torch.cuda.mem_get_info()[0]
                 gs_graph_build(ctx, S)
+                graph_mem[S] = free0 - torch.cuda.mem_get_info()[0]
                 ts.append(gs_get_stats(ctx)["last_build_seconds"])
             create[S] = ts
         divs = [d for d in range(1, 2501) if I_K % d == 0]
@@ -104,6 +112,7 @@ def characterize(n, stream, reps=10):
         return dict(n=n, model=model, S_star_divisor=best_S, S_star_relaxed=math.sqrt(max(model["a"], 0) / model["k_c"]),
                     S_best_measured=min(meas, key=meas.get),
                     create_mean_s={S: statistics.mean(v) for S, v in create.items()},
+                    graph_device_bytes=graph_mem,
                     exec_mean_s={S: statistics.mean(v) for S, v in execute.items()},
                     speedup_S100=speed)
     finally:
@@ -129,7 +138,8 @@ def main():
         print(f"n={r['n']:>9}  k_c={m['k_c']:.3e} b_c={m['b_c']:.3e} MAE={m['mae_create']:.2e}  "
               f"a={m['a']:.3e} b={m['b']:.3e} MAE={m['mae_exec']:.2e}  S*={r['S_star_divisor']} "
               f"(relaxed {r['S_star_relaxed']:.0f}, measured {r['S_best_measured']})  "
-              + " ".join(f"I={I}:{v['speedup']:.2f}" for I, v in r["speedup_S100"].items()))
+              + " ".join(f"I={I}:{v['speedup']:.2f}" for I, v in r["speedup_S100"].items())
+              + "  graph MiB: " + " ".join(f"S={S}:{b / 2**20:.1f}" for S, b in r["graph_device_bytes"].items()))
 
 
 if __name__ == "__main__":
