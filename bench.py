@@ -39,7 +39,7 @@ import gs_inputs  # noqa: E402
 # The per-step baseline always uses plain launches (use_pdl forced off).
 WORKLOADS = {
     "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=1,
-                             plan=dict(kernel=4, rows=4, use_pdl=1)),
+                             plan=dict(kernel=4, rows=4)),
     "heat2d-512": dict(kind="heat2d", nx=512, ny=512, nz=1, iters=1000, S=100, depth=1,
                        plan=dict(kernel=4, rows=4)),
     "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1,

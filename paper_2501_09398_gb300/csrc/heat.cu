@@ -380,97 +380,137 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
 }
 
 // Cells per thread of the COLUMN kernel: a full 16-byte vector in 2D; in 3D
-// (every plane of the column in registers) a half vector, which halves the
-// register arrays and doubles the threads in flight.
+// (every plane of the column in registers) four cells, a 16-byte f32 or an
+// 8-byte bf16/f16 access, which keeps the three register arrays of a column
+// of eight planes within the 128 registers that two blocks of 256 threads
+// per SM leave each thread.
 template <typename ST>
 constexpr int column_width(bool is3d) {
-    return is3d ? Vec<ST>::N / 2 : Vec<ST>::N;
+    return is3d ? 4 : Vec<ST>::N;
 }
 
 // --------------------------------------------------------------- column --
 //
-// Depth 1 without a march: each thread owns one 16-byte vector along x at
-// one y and keeps every plane of its column (nz <= NZM) in registers, so
-// one round of independent loads (rows y-1, y, y+1 of every plane, the P
-// row, and the x-edge scalars of lanes 0 and 31) feeds the whole update.
-// x-neighbours come from warp shuffles, y- and z-neighbours from registers;
-// no shared memory and no barrier.  Vertical reuse between the rows of a
-// block goes through L1 (read-only path).  Block (32, rows).
-template <typename ST, int BC, int NZM, int W>
-__device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int by) {
-    constexpr int V = W;  // cells per thread (a 16- or 8-byte access)
+// Depth 1 without a march: each thread owns W cells along x at one y and
+// keeps every plane of its column (nz <= NZM) in registers, so one round of
+// independent loads (the P row, then rows y-1, y, y+1 of every plane and the
+// x-edge scalars of lanes 0 and 31) feeds the whole update.  x-neighbours
+// come from warp shuffles, y- and z-neighbours from registers; no shared
+// memory and no barrier.  Vertical reuse between the rows of a block goes
+// through L1 (read-only path).  Block (32, rows).
+//
+// Every load uses coordinates clamped into the grid, so every thread reads
+// valid memory (threads past the grid's edge only skip their stores) and no
+// register needs a zero fill.  Under the clamp boundary the clamped address
+// IS the boundary value (a missing neighbour reads the cell itself), so the
+// update needs no per-cell select, except at a ragged row end (a partial
+// last vector).  The Dirichlet-0 boundary selects zeros by coordinate.
+// EXACT (nz == NZM) makes every z-boundary a compile-time choice.  FAST is
+// the warp-uniform common case (every vector of the warp inside the row, the
+// warp's row inside the grid): no per-cell edge checks, full-vector stores.
+// The kernel is latency- and issue-bound when L2-resident, so instruction
+// count and load order matter: the P row first (measured 9-12 % faster in
+// 2D), one predicated edge load per plane serving both lanes 0 and 31.
+template <typename ST, int BC, int NZM, int W, bool EXACT, bool FAST>
+__device__ __forceinline__ void heat_column_body(const HeatArgs& a, int x0, int y, bool full_x, bool inner_x) {
     const int lane = threadIdx.x;
-    const int x0 = (bx * 32 + lane) * V;
-    const int y = by * blockDim.y + threadIdx.y;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const bool act = (x0 < nx) && (y < ny);
-    const bool fast_x = __all_sync(0xffffffffu, x0 > 0 && x0 + V < nx);
+    const int nx = a.nx, ny = a.ny;
+    const int nz = EXACT ? NZM : a.nz;
+    const bool act = FAST || ((x0 < nx) && (y < ny));
     const long long pitch = a.pitch, plane = a.plane;
-    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
-    const ST* base = Tin + (long long)min(y, ny - 1) * pitch + x0;
+    const int xc = FAST ? x0 : min(x0, (nx - 1) / W * W);  // last vector's start when past the row
+    const int yc = FAST ? y : min(y, ny - 1);
+    const long long dn = (yc > 0) ? -pitch : 0;       // row above, clamped
+    const long long ds = (yc + 1 < ny) ? pitch : 0;   // row below, clamped
+    // lane 0 reads its west scalar, lane 31 its east scalar, both clamped
+    const int dedge = (lane == 0) ? ((xc > 0) ? -1 : 0) : min(W, nx - 1 - xc);
+    const ST* __restrict__ rc = static_cast<const ST*>(a.Tin) + (long long)yc * pitch + xc;
 
-    float c[NZM][V], n[NZM][V], so[NZM][V], p[V];
-    float wl[NZM], er[NZM];
+    float c[NZM][W], n[NZM][W], so[NZM][W], p[W], edge[NZM];
+    load_vecw<ST, W>(static_cast<const ST*>(a.P) + (long long)yc * a.p_pitch + xc, p);
 #pragma unroll
     for (int z = 0; z < NZM; ++z) {
-        wl[z] = 0.f;
-        er[z] = 0.f;
-#pragma unroll
-        for (int i = 0; i < V; ++i) { c[z][i] = 0.f; n[z][i] = 0.f; so[z][i] = 0.f; }
+        // planes past nz (general kernel only) re-read the last plane and
+        // are never updated: a branch-free load keeps the register arrays
+        // from spilling
+        const ST* q = rc + (EXACT ? z : min(z, nz - 1)) * plane;
+        load_vecw<ST, W>(q, c[z]);
+        load_vecw<ST, W>(q + dn, n[z]);
+        load_vecw<ST, W>(q + ds, so[z]);
+        edge[z] = 0.f;
+        if (lane == 0 || lane == 31) edge[z] = load_scalar(q + dedge);
     }
-#pragma unroll
-    for (int i = 0; i < V; ++i) p[i] = 0.f;
-    if (act) {
-#pragma unroll
-        for (int z = 0; z < NZM; ++z) {
-            if (z < nz) {
-                const ST* q = base + z * plane;
-                load_vecw<ST, V>(q, c[z]);
-                if (y > 0) load_vecw<ST, V>(q - pitch, n[z]);
-                if (y + 1 < ny) load_vecw<ST, V>(q + pitch, so[z]);
-                if (lane == 0 && x0 > 0) wl[z] = load_scalar(q - 1);
-                if (lane == 31 && x0 + V < nx) er[z] = load_scalar(q + V);
-            }
-        }
-        load_vecw<ST, V>(static_cast<const ST*>(a.P) + (long long)y * a.p_pitch + x0, p);
-    }
+
+    ST* out_row = static_cast<ST*>(a.Tout) + (long long)y * pitch + x0;
 #pragma unroll
     for (int z = 0; z < NZM; ++z) {
-        if (z < nz) {  // warp-uniform
-            float w0 = __shfl_up_sync(0xffffffffu, c[z][V - 1], 1);
-            float eV = __shfl_down_sync(0xffffffffu, c[z][0], 1);
-            if (lane == 0) w0 = wl[z];
-            if (lane == 31) eV = er[z];
-            if (!act) continue;
-            float out[V];
+        if (!EXACT && z >= nz) break;  // warp-uniform
+        float w0 = __shfl_up_sync(0xffffffffu, c[z][W - 1], 1);
+        float eW = __shfl_down_sync(0xffffffffu, c[z][0], 1);
+        if (lane == 0) w0 = edge[z];
+        if (lane == 31) eW = edge[z];
+        if (!act) continue;
+        float out[W];
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const float t = c[z][i];
-                float w = (i == 0) ? w0 : c[z][i - 1];
-                float e = (i == V - 1) ? eV : c[z][i + 1];
-                if (!fast_x) {
-                    if (x0 + i == 0) w = bnd<BC>(t);
-                    if (x0 + i + 1 >= nx) e = bnd<BC>(t);
-                }
-                const float nv = (y > 0) ? n[z][i] : bnd<BC>(t);
-                const float sv = (y + 1 < ny) ? so[z][i] : bnd<BC>(t);
-                float d = 0.f, u = 0.f;
-                if (NZM > 1) {
-                    d = (z > 0) ? c[z > 0 ? z - 1 : 0][i] : bnd<BC>(t);
-                    u = (z + 1 < nz) ? c[z + 1 < NZM ? z + 1 : z][i] : bnd<BC>(t);
-                }
-                out[i] = heat_cell<(NZM > 1)>(t, nv, sv, w, e, d, u, (z == 0) ? p[i] : 0.0f, a.c);
+        for (int i = 0; i < W; ++i) {
+            const float t = c[z][i];
+            float w = (i == 0) ? w0 : c[z][i - 1];
+            float e = (i == W - 1) ? eW : c[z][i + 1];
+            float nv = n[z][i], sv = so[z][i];
+            float d = 0.f, u = 0.f;
+            if (NZM > 1) {
+                d = (z > 0) ? c[z > 0 ? z - 1 : 0][i] : bnd<BC>(t);
+                u = (z + 1 < NZM) ? c[z + 1 < NZM ? z + 1 : z][i] : bnd<BC>(t);
+                if (!EXACT) u = (z + 1 < nz) ? u : bnd<BC>(t);
             }
-            store_vecw<ST, V>(static_cast<ST*>(a.Tout) + (long long)z * plane + (long long)y * pitch + x0, out,
-                      fast_x ? V : nx - x0);
+            if (BC == GS_BC_CLAMP) {
+                if (!FAST && !full_x && x0 + i + 1 >= nx) e = t;
+            } else {
+                if (!inner_x) {
+                    if (x0 + i == 0) w = 0.f;
+                    if (x0 + i + 1 >= nx) e = 0.f;
+                }
+                if (y == 0) nv = 0.f;
+                if (y + 1 >= ny) sv = 0.f;
+            }
+            out[i] = heat_cell<(NZM > 1)>(t, nv, sv, w, e, d, u, (z == 0) ? p[i] : 0.0f, a.c);
         }
+        store_vecw<ST, W>(out_row + z * plane, out, (FAST || full_x) ? W : nx - x0);
     }
 }
 
+// The COLUMN tile (bx, by): the FAST body for full warps inside the grid,
+// the general body for the warps at a ragged row end or past the last row.
+template <typename ST, int BC, int NZM, int W, bool EXACT>
+__device__ __forceinline__ void heat_column_dispatch(const HeatArgs& a, int bx, int by) {
+    const int x0 = (bx * 32 + threadIdx.x) * W;
+    const int y = by * blockDim.y + threadIdx.y;
+    // every vector of the warp lies inside the row (no ragged end, no lane past it)
+    const bool full_x = __all_sync(0xffffffffu, x0 + W <= a.nx);
+    // ... and none touches the row's first or last cell (Dirichlet-0 only)
+    const bool inner_x = __all_sync(0xffffffffu, x0 > 0 && x0 + W < a.nx);
+    if (full_x && y < a.ny) heat_column_body<ST, BC, NZM, W, EXACT, true>(a, x0, y, full_x, inner_x);
+    else heat_column_body<ST, BC, NZM, W, EXACT, false>(a, x0, y, full_x, inner_x);
+}
+
+// The COLUMN tile of a 2D depth-1 step (the multi-instance kernel's COLUMN
+// work item).
 template <typename ST, int BC, int NZM, int W>
-__global__ void __launch_bounds__(256) heat_column_kernel(const HeatArgs a) {
+__device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int by) {
+    static_assert(NZM == 1, "multi-instance grids are 2D");
+    heat_column_dispatch<ST, BC, 1, W, true>(a, bx, by);
+}
+
+// At most 256 threads per block and two blocks per SM: 128 registers a
+// thread, which the 3D column (three arrays of eight planes x four cells)
+// needs without spilling, and one wave of blocks at 512 x 512 x 8.  EXACT
+// kernels serve nz == NZM (2D, and 3D stacks of 2, 4 or 8 planes); the
+// general one (NZM = 8), every other nz <= 8 (separate kernels: one holding
+// both paths spills).
+template <typename ST, int BC, int NZM, int W, bool EXACT>
+__global__ void __launch_bounds__(256, 2) heat_column_kernel(const HeatArgs a) {
     pdl_wait_then_trigger();
-    heat_column_tile<ST, BC, NZM, W>(a, blockIdx.x, blockIdx.y);
+    heat_column_dispatch<ST, BC, NZM, W, EXACT>(a, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------- column, rows in shared memory --
@@ -791,10 +831,17 @@ const void* pick_wave(int depth) {
 }
 
 template <typename ST, int BC>
-const void* pick(bool is3d, int depth, int variant) {
-    if (variant == GS_KERNEL_COLUMN && depth == 1)
-        return is3d ? (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, column_width<ST>(true)>
-                    : (const void*)heat_column_kernel<ST, BC, 1, column_width<ST>(false)>;
+const void* pick(bool is3d, int depth, int variant, int nz) {
+    if (variant == GS_KERNEL_COLUMN && depth == 1) {
+        constexpr int W3 = column_width<ST>(true);
+        if (!is3d) return (const void*)heat_column_kernel<ST, BC, 1, column_width<ST>(false), true>;
+        switch (nz) {
+            case 2: return (const void*)heat_column_kernel<ST, BC, 2, W3, true>;
+            case 4: return (const void*)heat_column_kernel<ST, BC, 4, W3, true>;
+            case kColumnMaxNz: return (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, true>;
+            default: return (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, false>;
+        }
+    }
     if (variant == GS_KERNEL_COLUMN_SMEM && depth == 1)
         return is3d ? (const void*)heat_scol_kernel<ST, BC, kColumnMaxNz>
                     : (const void*)heat_scol_kernel<ST, BC, 1>;
@@ -808,9 +855,9 @@ const void* pick(bool is3d, int depth, int variant) {
 }
 
 template <typename ST>
-const void* pick_bc(gs_bc bc, bool is3d, int depth, int variant) {
-    return bc == GS_BC_CLAMP ? pick<ST, GS_BC_CLAMP>(is3d, depth, variant)
-                             : pick<ST, GS_BC_DIRICHLET0>(is3d, depth, variant);
+const void* pick_bc(gs_bc bc, bool is3d, int depth, int variant, int nz) {
+    return bc == GS_BC_CLAMP ? pick<ST, GS_BC_CLAMP>(is3d, depth, variant, nz)
+                             : pick<ST, GS_BC_DIRICHLET0>(is3d, depth, variant, nz);
 }
 
 int vec_elems(gs_dtype dt) { return dt == GS_F32 ? 4 : 8; }
@@ -822,9 +869,9 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
     const bool is3d = (kind == GS_HEAT3D);
     const void* f = nullptr;
     switch (dt) {
-        case GS_F32: f = pick_bc<float>(bc, is3d, depth, variant); break;
-        case GS_BF16: f = pick_bc<__nv_bfloat16>(bc, is3d, depth, variant); break;
-        case GS_F16: f = pick_bc<__half>(bc, is3d, depth, variant); break;
+        case GS_F32: f = pick_bc<float>(bc, is3d, depth, variant, a.nz); break;
+        case GS_BF16: f = pick_bc<__nv_bfloat16>(bc, is3d, depth, variant, a.nz); break;
+        case GS_F16: f = pick_bc<__half>(bc, is3d, depth, variant, a.nz); break;
     }
     if (!f) return cudaErrorInvalidValue;
     out->func = f;
