@@ -671,7 +671,8 @@ def main():
         # 2D 4096^2: HBM roofline of the depth-1 kernel, and the wavefront
         # depth-4 kernel's throughput
         for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(loop=True), "device_loop"),
-                              ("fdtd-256", {}, "column"), ("fdtd-media-256", {}, "column"),
+                              ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
+                              ("fdtd-media-256", {}, "column"),
                               ("heat2d-4096", {}, "depth1"),
                               ("heat2d-4096", dict(depth=4, kernel=2, rows=64, block_x=256), "wave4")):
             ww = WORKLOADS[nm]

@@ -214,23 +214,49 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
 // the fields and takes each cell's coefficients from the block's copy of
 // the 256-row table in shared memory (staged once per block: through L1 the
 // streaming field loads evict it and every lookup would wait on L2).
-template <typename ST, bool MAT>
-__global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_column_kernel(const FdtdArgs a) {
-    constexpr int V = Vec<ST>::N;
-    pdl_wait_then_trigger();
-    __shared__ float2 s_med[MAT ? 256 : 1];
-    if constexpr (MAT) {
-        const int nt = 32 * blockDim.y * blockDim.z;
-        for (int t = threadIdx.x + 32 * (threadIdx.y + blockDim.y * threadIdx.z); t < 256; t += nt)
-            s_med[t] = __ldg(a.med + t);
-        __syncthreads();
+//
+// Two bodies.  FAST serves the warps whose vectors all lie in [0, N) and
+// whose (j, k) has every neighbour the update reads (H: j, k < N; E:
+// 1 <= j, k <= N-1): all loads unconditional, no zero-filled registers, no
+// per-cell predicates (E only keeps the i = 0 wall cell of lane 0).  The
+// general body serves the rest with per-cell predicates.  ALN grids (N a
+// multiple of the 32 V cells of a warp) cover only i in [0, N): the i = N
+// column, where only Hx has an update, is an extra scalar cell of lane 31
+// (without it every (j, k) would need a second, one-cell warp).
+
+// Ez[si, sj, sk] += source(n) and the step counter: the one thread that owns
+// the source cell (lane 31's extra cell i = N in ALN grids) does both.
+template <typename ST, int V, bool ALN>
+__device__ __forceinline__ void fdtd_source(const FdtdArgs& a, int lane, int i0, int j, int k, long long o,
+                                            float (&ez)[V], bool* extra_src) {
+    *extra_src = false;
+    if (j != a.sj || k != a.sk) return;
+    const bool in_vec = (a.si >= i0 && a.si < i0 + V);
+    const bool in_extra = ALN && lane == 31 && a.si == i0 + V;
+    if (!in_vec && !in_extra) return;
+    const long long n = *a.counter;
+    if (a.src_on) {
+        const float u = __fdiv_rn(__fsub_rn((float)n, a.delay), a.width);
+        const float g = __fmul_rn(a.amp, expf(-u * u));
+        if (in_vec) {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (i0 + e == a.si) ez[e] = __fadd_rn(ez[e], g);
+        } else {
+            ST* Ez = static_cast<ST*>(a.f[EZ]);
+            Ez[o + V] = from_f32<ST>(__fadd_rn(to_f32(Ez[o + V]), g));
+            *extra_src = true;
+        }
     }
+    *a.counter = n + 1;
+}
+
+template <typename ST, bool MAT, bool FAST, bool EXTRA>
+__device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const float2* s_med, int lane, int i0, int j,
+                                                   int k) {
+    constexpr int V = Vec<ST>::N;
     const int N = a.N, M = N + 1;
-    const int lane = threadIdx.x;
-    const int i0 = (blockIdx.x * 32 + lane) * V;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    const bool act = (i0 < M) && (j < M) && (k < M);
+    const bool act = FAST || ((i0 < M) && (j < M) && (k < M));
     const ST* Ex = static_cast<const ST*>(a.f[EX]);
     const ST* Ey = static_cast<const ST*>(a.f[EY]);
     const ST* Ez = static_cast<const ST*>(a.f[EZ]);
@@ -240,34 +266,60 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_
     const float s = a.s;
     const long long o = act ? (long long)k * a.plane + (long long)j * a.pitch + i0 : 0;
     float exk[V], eyk[V], ez[V], exk1[V], eyk1[V], ezj1[V], exj1[V], hx[V], hy[V], hz[V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-        exk[e] = 0.f; eyk[e] = 0.f; ez[e] = 0.f; exk1[e] = 0.f; eyk1[e] = 0.f; ezj1[e] = 0.f; exj1[e] = 0.f;
-        hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f;
-    }
-    float ez_r = 0.f, ey_r = 0.f;
     unsigned id[V];  // material ids (MAT), loaded with the fields
-#pragma unroll
-    for (int e = 0; e < V; ++e) id[e] = 0;
-    if (act) {
+    float ez_r = 0.f, ey_r = 0.f;
+    // lane 31's extra cell i = N (Hx only): Ez at j+1, Ey at k+1, Hx, id
+    float ezj1_x = 0.f, eyk1_x = 0.f, hx_x = 0.f;
+    unsigned id_x = 0;
+    if constexpr (FAST) {
         if constexpr (MAT) load_ids<V>(a.mat + o, id);
         load_vec(Ex + o, exk);
         load_vec(Ey + o, eyk);
         load_vec(Ez + o, ez);
-        if (k + 1 < M) {
-            load_vec(Ex + o + a.plane, exk1);
-            load_vec(Ey + o + a.plane, eyk1);
-        }
-        if (j + 1 < M) {
-            load_vec(Ez + o + a.pitch, ezj1);
-            load_vec(Ex + o + a.pitch, exj1);
-        }
+        load_vec(Ex + o + a.plane, exk1);
+        load_vec(Ey + o + a.plane, eyk1);
+        load_vec(Ez + o + a.pitch, ezj1);
+        load_vec(Ex + o + a.pitch, exj1);
         load_vec_rw(Hx + o, hx);
         load_vec_rw(Hy + o, hy);
         load_vec_rw(Hz + o, hz);
-        if (lane == 31 && i0 + V < M) {
+        if (lane == 31) {  // i0 + V <= N: in range
             ez_r = load_scalar(Ez + o + V);
             ey_r = load_scalar(Ey + o + V);
+            if constexpr (EXTRA) {
+                ezj1_x = load_scalar(Ez + o + a.pitch + V);
+                eyk1_x = load_scalar(Ey + o + a.plane + V);
+                hx_x = to_f32(Hx[o + V]);
+                if constexpr (MAT) id_x = __ldg(a.mat + o + V);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            exk[e] = 0.f; eyk[e] = 0.f; ez[e] = 0.f; exk1[e] = 0.f; eyk1[e] = 0.f; ezj1[e] = 0.f; exj1[e] = 0.f;
+            hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f;
+            id[e] = 0;
+        }
+        if (act) {
+            if constexpr (MAT) load_ids<V>(a.mat + o, id);
+            load_vec(Ex + o, exk);
+            load_vec(Ey + o, eyk);
+            load_vec(Ez + o, ez);
+            if (k + 1 < M) {
+                load_vec(Ex + o + a.plane, exk1);
+                load_vec(Ey + o + a.plane, eyk1);
+            }
+            if (j + 1 < M) {
+                load_vec(Ez + o + a.pitch, ezj1);
+                load_vec(Ex + o + a.pitch, exj1);
+            }
+            load_vec_rw(Hx + o, hx);
+            load_vec_rw(Hy + o, hy);
+            load_vec_rw(Hz + o, hz);
+            if (lane == 31 && i0 + V < M) {
+                ez_r = load_scalar(Ez + o + V);
+                ey_r = load_scalar(Ey + o + V);
+            }
         }
     }
     const float ez_n = __shfl_down_sync(0xffffffffu, ez[0], 1);
@@ -275,51 +327,44 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_
     if (!act) return;
     const float ez_last = (lane == 31) ? ez_r : ez_n;
     const float ey_last = (lane == 31) ? ey_r : ey_n;
-    if constexpr (MAT) {
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int i = i0 + e;
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
+        const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
+        const bool ux = FAST || (j < N && k < N);
+        const bool uy = FAST || (i < N && k < N);
+        const bool uz = FAST || (i < N && j < N);
+        if constexpr (MAT) {
             const float2 m = s_med[id[e]];
-            const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
-            const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
-            if (j < N && k < N) hx[e] = curl_sub_m(hx[e], m, ezj1[e], ez[e], eyk1[e], eyk[e]);
-            if (i < N && k < N) hy[e] = curl_sub_m(hy[e], m, exk1[e], exk[e], ez_ip, ez[e]);
-            if (i < N && j < N) hz[e] = curl_sub_m(hz[e], m, ey_ip, eyk[e], exj1[e], exk[e]);
-        }
-    } else {
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int i = i0 + e;
-            const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
-            const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
-            if (j < N && k < N) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
-            if (i < N && k < N) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
-            if (i < N && j < N) hz[e] = curl_sub(hz[e], s, ey_ip, eyk[e], exj1[e], exk[e]);
+            if (ux) hx[e] = curl_sub_m(hx[e], m, ezj1[e], ez[e], eyk1[e], eyk[e]);
+            if (uy) hy[e] = curl_sub_m(hy[e], m, exk1[e], exk[e], ez_ip, ez[e]);
+            if (uz) hz[e] = curl_sub_m(hz[e], m, ey_ip, eyk[e], exj1[e], exk[e]);
+        } else {
+            if (ux) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
+            if (uy) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
+            if (uz) hz[e] = curl_sub(hz[e], s, ey_ip, eyk[e], exj1[e], exk[e]);
         }
     }
-    const int nv = M - i0;
+    const int nv = FAST ? V : M - i0;
     store_vec(Hx + o, hx, nv);
     store_vec(Hy + o, hy, nv);
     store_vec(Hz + o, hz, nv);
+    if constexpr (EXTRA) {
+        if (lane == 31) {
+            if constexpr (MAT) hx_x = curl_sub_m(hx_x, s_med[id_x], ezj1_x, ez_r, eyk1_x, ey_r);
+            else hx_x = curl_sub(hx_x, s, ezj1_x, ez_r, eyk1_x, ey_r);
+            Hx[o + V] = from_f32<ST>(hx_x);
+        }
+    }
 }
 
-template <typename ST, bool MAT>
-__global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_column_kernel(const FdtdArgs a) {
+template <typename ST, bool MAT, bool FAST, bool ALN>
+__device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const float2* s_med, int lane, int i0, int j,
+                                                   int k) {
     constexpr int V = Vec<ST>::N;
-    pdl_wait_then_trigger();
-    __shared__ float2 s_med[MAT ? 256 : 1];
-    if constexpr (MAT) {
-        const int nt = 32 * blockDim.y * blockDim.z;
-        for (int t = threadIdx.x + 32 * (threadIdx.y + blockDim.y * threadIdx.z); t < 256; t += nt)
-            s_med[t] = __ldg(a.med + 256 + t);
-        __syncthreads();
-    }
     const int N = a.N, M = N + 1;
-    const int lane = threadIdx.x;
-    const int i0 = (blockIdx.x * 32 + lane) * V;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    const bool act = (i0 < M) && (j < M) && (k < M);
+    const bool act = FAST || ((i0 < M) && (j < M) && (k < M));
     ST* Ex = static_cast<ST*>(a.f[EX]);
     ST* Ey = static_cast<ST*>(a.f[EY]);
     ST* Ez = static_cast<ST*>(a.f[EZ]);
@@ -329,34 +374,52 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_
     const float s = a.s;
     const long long o = act ? (long long)k * a.plane + (long long)j * a.pitch + i0 : 0;
     float hx[V], hy[V], hz[V], hxk_1[V], hyk_1[V], hzj_1[V], hxj_1[V], ex[V], ey[V], ez[V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-        hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f; hxk_1[e] = 0.f; hyk_1[e] = 0.f; hzj_1[e] = 0.f; hxj_1[e] = 0.f;
-        ex[e] = 0.f; ey[e] = 0.f; ez[e] = 0.f;
-    }
-    float hz_l = 0.f, hy_l = 0.f;
     unsigned id[V];  // material ids (MAT), loaded with the fields
-#pragma unroll
-    for (int e = 0; e < V; ++e) id[e] = 0;
-    if (act) {
+    float hz_l = 0.f, hy_l = 0.f;
+    if constexpr (FAST) {
         if constexpr (MAT) load_ids<V>(a.mat + o, id);
         load_vec(Hx + o, hx);
         load_vec(Hy + o, hy);
         load_vec(Hz + o, hz);
-        if (k >= 1) {
-            load_vec(Hx + o - a.plane, hxk_1);
-            load_vec(Hy + o - a.plane, hyk_1);
-        }
-        if (j >= 1) {
-            load_vec(Hz + o - a.pitch, hzj_1);
-            load_vec(Hx + o - a.pitch, hxj_1);
-        }
+        load_vec(Hx + o - a.plane, hxk_1);
+        load_vec(Hy + o - a.plane, hyk_1);
+        load_vec(Hz + o - a.pitch, hzj_1);
+        load_vec(Hx + o - a.pitch, hxj_1);
         load_vec_rw(Ex + o, ex);
         load_vec_rw(Ey + o, ey);
         load_vec_rw(Ez + o, ez);
-        if (lane == 0 && i0 >= 1) {
-            hz_l = load_scalar(Hz + o - 1);
-            hy_l = load_scalar(Hy + o - 1);
+        if (lane == 0) {  // the i = 0 cell's west value is never used: clamp the address
+            const int dw = (i0 > 0) ? -1 : 0;
+            hz_l = load_scalar(Hz + o + dw);
+            hy_l = load_scalar(Hy + o + dw);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f; hxk_1[e] = 0.f; hyk_1[e] = 0.f; hzj_1[e] = 0.f; hxj_1[e] = 0.f;
+            ex[e] = 0.f; ey[e] = 0.f; ez[e] = 0.f;
+            id[e] = 0;
+        }
+        if (act) {
+            if constexpr (MAT) load_ids<V>(a.mat + o, id);
+            load_vec(Hx + o, hx);
+            load_vec(Hy + o, hy);
+            load_vec(Hz + o, hz);
+            if (k >= 1) {
+                load_vec(Hx + o - a.plane, hxk_1);
+                load_vec(Hy + o - a.plane, hyk_1);
+            }
+            if (j >= 1) {
+                load_vec(Hz + o - a.pitch, hzj_1);
+                load_vec(Hx + o - a.pitch, hxj_1);
+            }
+            load_vec_rw(Ex + o, ex);
+            load_vec_rw(Ey + o, ey);
+            load_vec_rw(Ez + o, ez);
+            if (lane == 0 && i0 >= 1) {
+                hz_l = load_scalar(Hz + o - 1);
+                hy_l = load_scalar(Hy + o - 1);
+            }
         }
     }
     const float hz_p = __shfl_up_sync(0xffffffffu, hz[V - 1], 1);
@@ -364,55 +427,94 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_
     if (!act) return;
     const float hz_first = (lane == 0) ? hz_l : hz_p;
     const float hy_first = (lane == 0) ? hy_l : hy_p;
-    const bool j_int = (j >= 1 && j <= N - 1);
-    const bool k_int = (k >= 1 && k <= N - 1);
-    if constexpr (MAT) {
+    const bool j_int = FAST || (j >= 1 && j <= N - 1);
+    const bool k_int = FAST || (k >= 1 && k <= N - 1);
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int i = i0 + e;
-            const bool i_int = (i >= 1 && i <= N - 1);
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        // FAST: every i < N; only the i = 0 wall cell (lane 0 of the first warp) is not interior
+        const bool i_int = FAST ? (e > 0 || i0 > 0) : (i >= 1 && i <= N - 1);
+        const bool ux = FAST || (i < N && j_int && k_int);
+        const bool uy = i_int && (FAST || (j < N && k_int));
+        const bool uz = i_int && (FAST || (k < N && j_int));
+        const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
+        const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
+        if constexpr (MAT) {
             const float2 m = s_med[id[e]];
-            const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
-            const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
-            if (i < N && j_int && k_int) ex[e] = curl_add_m(ex[e], m, hz[e], hzj_1[e], hy[e], hyk_1[e]);
-            if (j < N && i_int && k_int) ey[e] = curl_add_m(ey[e], m, hx[e], hxk_1[e], hz[e], hz_im);
-            if (k < N && i_int && j_int) ez[e] = curl_add_m(ez[e], m, hy[e], hy_im, hx[e], hxj_1[e]);
-        }
-    } else {
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int i = i0 + e;
-            const bool i_int = (i >= 1 && i <= N - 1);
-            const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
-            const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
-            if (i < N && j_int && k_int) ex[e] = curl_add(ex[e], s, hz[e], hzj_1[e], hy[e], hyk_1[e]);
-            if (j < N && i_int && k_int) ey[e] = curl_add(ey[e], s, hx[e], hxk_1[e], hz[e], hz_im);
-            if (k < N && i_int && j_int) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
+            if (ux) ex[e] = curl_add_m(ex[e], m, hz[e], hzj_1[e], hy[e], hyk_1[e]);
+            if (uy) ey[e] = curl_add_m(ey[e], m, hx[e], hxk_1[e], hz[e], hz_im);
+            if (uz) ez[e] = curl_add_m(ez[e], m, hy[e], hy_im, hx[e], hxj_1[e]);
+        } else {
+            if (ux) ex[e] = curl_add(ex[e], s, hz[e], hzj_1[e], hy[e], hyk_1[e]);
+            if (uy) ey[e] = curl_add(ey[e], s, hx[e], hxk_1[e], hz[e], hz_im);
+            if (uz) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
         }
     }
-    if (j == a.sj && k == a.sk && a.si >= i0 && a.si < i0 + V) {
-        const long long n = *a.counter;
-        if (a.src_on) {
-            const float u = __fdiv_rn(__fsub_rn((float)n, a.delay), a.width);
-#pragma unroll
-            for (int e = 0; e < V; ++e)
-                if (i0 + e == a.si) ez[e] = __fadd_rn(ez[e], __fmul_rn(a.amp, expf(-u * u)));
-        }
-        *a.counter = n + 1;
-    }
-    const int nv = M - i0;
+    bool extra_src;
+    fdtd_source<ST, V, ALN>(a, lane, i0, j, k, o, ez, &extra_src);
+    const int nv = FAST ? V : M - i0;
     store_vec(Ex + o, ex, nv);
     store_vec(Ey + o, ey, nv);
     store_vec(Ez + o, ez, nv);
 }
 
+// Stage the media table (rows `base` .. base+255) in shared memory.
+template <bool MAT>
+__device__ __forceinline__ void stage_media(const FdtdArgs& a, float2* s_med, int base) {
+    if constexpr (MAT) {
+        const int nt = 32 * blockDim.y * blockDim.z;
+        for (int t = threadIdx.x + 32 * (threadIdx.y + blockDim.y * threadIdx.z); t < 256; t += nt)
+            s_med[t] = __ldg(a.med + base + t);
+        __syncthreads();
+    }
+}
+
+template <typename ST, bool MAT, bool ALN>
+__global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_column_kernel(const FdtdArgs a) {
+    constexpr int V = Vec<ST>::N;
+    pdl_wait_then_trigger();
+    __shared__ float2 s_med[MAT ? 256 : 1];
+    stage_media<MAT>(a, s_med, 0);
+    const int N = a.N;
+    const int lane = threadIdx.x;
+    const int i0 = (blockIdx.x * 32 + lane) * V;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
+    if (in_x && j < N && k < N) fdtd_h_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);
+    else fdtd_h_column_body<ST, MAT, false, false>(a, s_med, lane, i0, j, k);
+}
+
+template <typename ST, bool MAT, bool ALN>
+__global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_column_kernel(const FdtdArgs a) {
+    constexpr int V = Vec<ST>::N;
+    pdl_wait_then_trigger();
+    __shared__ float2 s_med[MAT ? 256 : 1];
+    stage_media<MAT>(a, s_med, 256);
+    const int N = a.N;
+    const int lane = threadIdx.x;
+    const int i0 = (blockIdx.x * 32 + lane) * V;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
+    if (in_x && j >= 1 && j <= N - 1 && k >= 1 && k <= N - 1)
+        fdtd_e_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);
+    else
+        fdtd_e_column_body<ST, MAT, false, ALN>(a, s_med, lane, i0, j, k);
+}
+
 namespace {
 
+template <typename ST, bool MAT>
+const void* fdtd_column_func(bool e_half, bool aln) {
+    if (aln) return e_half ? (const void*)fdtd_e_column_kernel<ST, MAT, true> : (const void*)fdtd_h_column_kernel<ST, MAT, true>;
+    return e_half ? (const void*)fdtd_e_column_kernel<ST, MAT, false> : (const void*)fdtd_h_column_kernel<ST, MAT, false>;
+}
+
 template <typename ST>
-const void* fdtd_func(bool e_half, bool col, bool mat) {
+const void* fdtd_func(bool e_half, bool col, bool mat, bool aln) {
     if (!col) return e_half ? (const void*)fdtd_e_kernel<ST> : (const void*)fdtd_h_kernel<ST>;
-    if (mat) return e_half ? (const void*)fdtd_e_column_kernel<ST, true> : (const void*)fdtd_h_column_kernel<ST, true>;
-    return e_half ? (const void*)fdtd_e_column_kernel<ST, false> : (const void*)fdtd_h_column_kernel<ST, false>;
+    return mat ? fdtd_column_func<ST, true>(e_half, aln) : fdtd_column_func<ST, false>(e_half, aln);
 }
 
 }  // namespace
@@ -423,10 +525,12 @@ cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, 
     const bool col = (variant == GS_KERNEL_COLUMN);
     const bool mat = (a.mat != nullptr);
     if (mat && !col) return cudaErrorNotSupported;  // media: column kernels only
+    // ALN: the warps tile i in [0, N) exactly; lane 31 takes the i = N column
+    const bool aln = col && (a.N % (32 * V) == 0);
     switch (dt) {
-        case GS_F32: out->func = fdtd_func<float>(e_half, col, mat); break;
-        case GS_BF16: out->func = fdtd_func<__nv_bfloat16>(e_half, col, mat); break;
-        case GS_F16: out->func = fdtd_func<__half>(e_half, col, mat); break;
+        case GS_F32: out->func = fdtd_func<float>(e_half, col, mat, aln); break;
+        case GS_BF16: out->func = fdtd_func<__nv_bfloat16>(e_half, col, mat, aln); break;
+        case GS_F16: out->func = fdtd_func<__half>(e_half, col, mat, aln); break;
         default: return cudaErrorInvalidValue;
     }
     if (col) {
@@ -434,7 +538,8 @@ cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, 
         const int by = std::max(1, std::min(a.kc, 8));
         const int bz = std::max(1, 8 / by);
         out->block = dim3(32, by, bz);
-        out->grid = dim3((M + 32 * V - 1) / (32 * V), (M + by - 1) / by, (M + bz - 1) / bz);
+        const int span = aln ? a.N : M;
+        out->grid = dim3((span + 32 * V - 1) / (32 * V), (M + by - 1) / by, (M + bz - 1) / bz);
     } else {
         const int by = std::max(1, 256 / block_x);
         out->block = dim3(block_x, by, 1);
