@@ -71,6 +71,18 @@ def fdtd_random_e(N: int, seed: int = DEFAULT_SEED):
     return out
 
 
+def fdtd_random_all(N: int, seed: int = DEFAULT_SEED):
+    """Random values in every entry of all six components (float32,
+    (N+1)^3 each, [k][j][i]), the PEC walls and the unused entries included.
+
+    Not a physical state: a stress input for the arithmetic at the walls
+    (entries the update never writes keep their values, and H next to a wall
+    then sees non-zero tangential E)."""
+    rng = np.random.default_rng(seed)
+    m = N + 1
+    return {name: rng.standard_normal((m, m, m)).astype(np.float32) for name in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")}
+
+
 def fdtd_media(N: int, n_mat: int = 4, n_boxes: int = 8, lossy: bool = True, seed: int = DEFAULT_SEED,
                swap_symmetric: bool = False):
     """A material map (uint8, (N+1)^3, [k][j][i]) and its table of

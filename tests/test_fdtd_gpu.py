@@ -169,3 +169,25 @@ def test_config2_full_size(fdtd_config2_ref):
     err = rel_l2(fdtd_concat(got), fdtd_concat(ref))
     print(f"config2 f32 rel L2 {err:.3e}")
     assert err <= FDTD_RL2
+
+
+@pytest.mark.parametrize("N,src", [(128, (128, 64, 64)), (128, (64, 0, 64)), (37, (37, 20, 20))])
+def test_wall_column_and_wall_source(oracle, N, src):
+    # N = 128: the warps tile i in [0, N) exactly and lane 31 updates the
+    # i = N column (Hx) as an extra cell; from random values in every entry
+    # (walls included) Hx there changes every step.  A source on the i = N
+    # wall or on the j = 0 wall exercises the extra-cell and boundary-row
+    # source paths and the step counter.  N = 37 is the ragged layout.
+    n = 12
+    init = gs_inputs.fdtd_random_all(N, seed=N)
+    ref = _oracle_run(oracle, N, n, src=src, init=init)
+    got = _gpu_run(N, n, 5, src=src, init=init)
+    assert rel_l2(fdtd_concat(got), fdtd_concat(ref)) <= FDTD_RL2
+    wall = got["Hx"][:, :, N].astype(np.float64)
+    ref_wall = ref["Hx"][:, :, N]
+    assert np.linalg.norm(wall - ref_wall) <= FDTD_RL2 * np.linalg.norm(ref_wall)
+    assert np.linalg.norm(ref_wall - init["Hx"][:, :, N]) > 0.1 * np.linalg.norm(ref_wall)
+    si, sj, sk = src
+    assert abs(float(got["Ez"][sk, sj, si]) - ref["Ez"][sk, sj, si]) <= 1e-5 * (1.0 + abs(ref["Ez"][sk, sj, si]))
+    per_step = _gpu_run(N, n, 0, src=src, init=init)
+    assert all(np.array_equal(got[k], per_step[k]) for k in FDTD_NAMES)

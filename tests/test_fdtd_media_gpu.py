@@ -72,6 +72,21 @@ def test_random_field_media_parity(oracle):
     assert rel_l2(fdtd_concat(got), fdtd_concat(ref)) <= FDTD_RL2
 
 
+def test_media_aligned_grid_parity(oracle):
+    # N = 128: the aligned layout (lane 31 takes the i = N column) with the
+    # media coefficients, from random values in every entry, source on the
+    # i = N wall
+    N, n = 128, 10
+    media = gs_inputs.fdtd_media(N, n_mat=6, n_boxes=12, seed=5)
+    init = gs_inputs.fdtd_random_all(N, seed=6)
+    src = (N, 40, 70)
+    ref = _ref(oracle, N, n, media, src=src, init=init)
+    got = _gpu(N, n, 4, media=media, src=src, init=init)
+    assert rel_l2(fdtd_concat(got), fdtd_concat(ref)) <= FDTD_RL2
+    wall = got["Hx"][:, :, N].astype(np.float64)
+    assert np.linalg.norm(wall - ref["Hx"][:, :, N]) <= FDTD_RL2 * np.linalg.norm(ref["Hx"][:, :, N])
+
+
 def test_media_graphs_bit_identical():
     N, n = 21, 45
     media = gs_inputs.fdtd_media(N, n_mat=4, seed=9)
