@@ -31,7 +31,8 @@ def _coeffs(nz):
 # shapes span several blocks and ragged tails in x (vector width 4 or 8 and
 # 32-lane warps), y (rows per block) and z (planes per block)
 SHAPES_2D = [(130, 17), (37, 29), (5, 1), (1, 9), (4, 4), (257, 66), (1, 1)]
-SHAPES_3D = [(33, 21, 5), (19, 7, 3), (130, 9, 17), (8, 8, 1), (3, 2, 2)]
+SHAPES_3D = [(33, 21, 5), (19, 7, 3), (130, 9, 17), (8, 8, 1), (3, 2, 2),
+             (67, 13, 4), (45, 10, 8), (140, 6, 2)]  # compile-time plane counts of the column kernel
 
 
 @pytest.mark.parametrize("shape", SHAPES_2D)
