@@ -674,7 +674,7 @@ def main():
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-media-256", {}, "column"),
                               ("heat2d-4096", {}, "depth1"),
-                              ("heat2d-4096", dict(depth=4, kernel=2, rows=64, block_x=256), "wave4")):
+                              ("heat2d-4096", dict(depth=4, kernel=2, rows=32, block_x=128), "wave4")):
             ww = WORKLOADS[nm]
             mm = measure_workload(nm, ww, argparse.Namespace(**{**base, **over}), flush, with_e2e=False)
             c = cells_of(ww) * ww["iters"]

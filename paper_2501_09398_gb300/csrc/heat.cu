@@ -26,6 +26,49 @@ __device__ __forceinline__ float heat_cell(float t, float n, float s, float w, f
     return __fmaf_rn(c.k, acc, t);
 }
 
+// heat_cell for two adjacent cells with Blackwell's packed FP32 pair
+// operations (add/sub/fma .rn.f32x2): each half is rounded exactly as the
+// scalar operation of heat_cell, in the same order, so the results are the
+// same bits.  The x-neighbour sums w+e arrive already rounded (scalar adds:
+// the shifted neighbours are not register pairs).
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <bool IS3D>
+__device__ __forceinline__ void heat_cell_x2(const float* t, const float* n, const float* s, const float* xs,
+                                             const float* d, const float* u, const float* p, const HeatCoef& c,
+                                             float* out) {
+    const unsigned long long T = f2_pack(t[0], t[1]);
+    const unsigned long long M2 = f2_pack(-2.0f, -2.0f);
+    unsigned long long acc = f2_pack(p[0], p[1]);
+    acc = f2_fma(f2_pack(c.cy, c.cy), f2_fma(M2, T, f2_add(f2_pack(n[0], n[1]), f2_pack(s[0], s[1]))), acc);
+    acc = f2_fma(f2_pack(c.cx, c.cx), f2_fma(M2, T, f2_pack(xs[0], xs[1])), acc);
+    acc = f2_fma(f2_pack(c.cz, c.cz), f2_sub(f2_pack(c.t_amb, c.t_amb), T), acc);
+    if (IS3D) acc = f2_fma(f2_pack(c.cz2, c.cz2), f2_fma(M2, T, f2_add(f2_pack(d[0], d[1]), f2_pack(u[0], u[1]))), acc);
+    f2_unpack(f2_fma(f2_pack(c.k, c.k), acc, T), out[0], out[1]);
+}
+
 // 16-byte shared-memory row segments (V is 4 or 8 floats).
 template <int V>
 __device__ __forceinline__ void sm_put(float* p, const float (&v)[V]) {
@@ -640,7 +683,10 @@ __global__ void __launch_bounds__(256) heat_scol_kernel(const HeatArgs a) {
 // (requires T <= V).  In 3D the block holds all nz planes (one warp row per
 // plane) and exchanges each level's newest row through a double-buffered
 // shared-memory row, with one barrier per march step.  A block marches
-// R + 2T level-0 rows to produce R output rows.
+// R + 2T level-0 rows to produce R output rows.  The kernel is bound by
+// instruction issue: rows and tiles away from the grid's edges (a
+// warp-uniform test) update with no boundary selects and packed f32x2
+// arithmetic.
 //
 // Launch: 3D: block (32, nz), grid (x tiles, ceil(ny/R)).
 //         2D: block (32, WB) with WB independent warps stacked in y,
@@ -665,6 +711,9 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
     const bool ld_ok = (x0 >= 0) && (x0 < nx);   // vector lies (at least partly) in the grid
     const bool st_lane = (lane >= 1) && (lane <= 30) && (x0 < nx);
     const int rowlen = 32 * V;
+    // the block's 32 vectors lie inside the row, away from both x edges
+    // (every cell has both x-neighbours in the grid)
+    const bool x_fast = (xs >= 1) && (xs + 32 * V < nx);
 
     const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
     ST* __restrict__ Tout = static_cast<ST*>(a.Tout);
@@ -744,22 +793,40 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
                 if (tz + 1 < nz) sm_get<V>(lv + (size_t)(tz + 1) * rowlen, uv);
             }
             float out[V];
+            if (x_fast && q >= 1 && q + 1 < ny) {  // warp-uniform: no boundary within reach
+                float xs[V], dd[V], uu[V], pp[V];
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const int x = x0 + i;
-                const float t = c[i];
-                float w = (i == 0) ? w0 : c[i - 1];
-                float e = (i == V - 1) ? eV : c[i + 1];
-                if (x == 0) w = bnd<BC>(t);
-                if (x + 1 >= nx) e = bnd<BC>(t);
-                const float n = (q == 0) ? bnd<BC>(t) : win[s - 1][0][i];
-                const float so = (q + 1 >= ny) ? bnd<BC>(t) : win[s - 1][2][i];
-                float d = 0.f, u = 0.f;
-                if (IS3D) {
-                    d = (tz > 0) ? dv[i] : bnd<BC>(t);
-                    u = (tz + 1 < nz) ? uv[i] : bnd<BC>(t);
+                for (int i = 0; i < V; ++i) {
+                    xs[i] = __fadd_rn((i == 0) ? w0 : c[i - 1], (i == V - 1) ? eV : c[i + 1]);
+                    dd[i] = uu[i] = 0.f;
+                    if (IS3D) {
+                        dd[i] = (tz > 0) ? dv[i] : bnd<BC>(c[i]);
+                        uu[i] = (tz + 1 < nz) ? uv[i] : bnd<BC>(c[i]);
+                    }
+                    pp[i] = has_p ? pr[s][i] : 0.0f;
                 }
-                out[i] = heat_cell<IS3D>(t, n, so, w, e, d, u, has_p ? pr[s][i] : 0.0f, a.c);
+#pragma unroll
+                for (int i = 0; i < V; i += 2)
+                    heat_cell_x2<IS3D>(&c[i], &win[s - 1][0][i], &win[s - 1][2][i], &xs[i], &dd[i], &uu[i], &pp[i],
+                                       a.c, &out[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const int x = x0 + i;
+                    const float t = c[i];
+                    float w = (i == 0) ? w0 : c[i - 1];
+                    float e = (i == V - 1) ? eV : c[i + 1];
+                    if (x == 0) w = bnd<BC>(t);
+                    if (x + 1 >= nx) e = bnd<BC>(t);
+                    const float n = (q == 0) ? bnd<BC>(t) : win[s - 1][0][i];
+                    const float so = (q + 1 >= ny) ? bnd<BC>(t) : win[s - 1][2][i];
+                    float d = 0.f, u = 0.f;
+                    if (IS3D) {
+                        d = (tz > 0) ? dv[i] : bnd<BC>(t);
+                        u = (tz + 1 < nz) ? uv[i] : bnd<BC>(t);
+                    }
+                    out[i] = heat_cell<IS3D>(t, n, so, w, e, d, u, has_p ? pr[s][i] : 0.0f, a.c);
+                }
             }
             if (s < T) {
 #pragma unroll
