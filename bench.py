@@ -368,7 +368,7 @@ class MultiRunner:
         self.m = g.gs_multi_create(self.sides, self.sides, g.GS_F32, g.GS_BC_CLAMP, self.stream.cuda_stream)
         self.ctx = None
         self.fields = g.MultiFields(self.m, self.sides, self.sides)
-        mp = {k: v for k, v in plan_extra.items() if k in ("block_x", "rows", "use_pdl", "kernel")}
+        mp = {k: v for k, v in plan_extra.items() if k in ("block_x", "rows", "use_pdl", "kernel", "traverse")}
         if mp:
             g.gs_multi_set_plan(self.m, **mp)
         self.inputs = gs_inputs.instance_fields(self.sides)
@@ -516,6 +516,8 @@ def measure_workload(name, w, args, flush, with_e2e=True):
         g_plan["kernel"] = args.kernel
     if getattr(args, "loop", False):
         g_plan["graph_loop"] = 1
+    if getattr(args, "traverse", 0):
+        g_plan["traverse"] = args.traverse
     S = args.batch or w["S"]
     depth = args.depth or w["depth"]
     run = (MultiRunner if w["kind"] == "multi" else Runner)(w, S, depth, g_plan)
@@ -584,6 +586,8 @@ def main():
     ap.add_argument("--kernel", type=int, default=0, help="thermal kernel variant (gs_kernel; 0 = auto)")
     ap.add_argument("--loop", action="store_true",
                     help="run the batches as one device-side loop (conditional while node) per step")
+    ap.add_argument("--traverse", type=int, default=0,
+                    help="block order of consecutive launches (gs_traverse: 0 auto, 1 forward, 2 alternate)")
     ap.add_argument("--no-extras", action="store_true", help="skip the 2D 512^2 / 4096^2 side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     args = ap.parse_args()
@@ -666,7 +670,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras and args.workload == DEFAULT:
         extra = {}
         base = {**vars(args), "batch": 0, "depth": 0, "block_x": 0, "rows": 0, "tile_x": 0, "tile_y": 0,
-                "pdl": False, "kernel": 0, "loop": False, "steps": 20}
+                "pdl": False, "kernel": 0, "loop": False, "traverse": 0, "steps": 20}
         # 2D 512^2: graph-batched vs per-step launch of the same depth-1 kernel
         # 2D 4096^2: HBM roofline of the depth-1 kernel, and the wavefront
         # depth-4 kernel's throughput

@@ -34,6 +34,7 @@ GS_HEAT2D, GS_HEAT3D, GS_FDTD3D, GS_SKELETON = range(4)
 GS_F32, GS_BF16, GS_F16 = range(3)
 GS_BC_CLAMP, GS_BC_DIRICHLET0, GS_BC_PEC = range(3)
 GS_KERNEL_AUTO, GS_KERNEL_MARCH, GS_KERNEL_WAVE, GS_KERNEL_TILE, GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM = range(6)
+GS_TRAVERSE_AUTO, GS_TRAVERSE_FORWARD, GS_TRAVERSE_ALTERNATE = range(3)
 (GS_FIELD_T0, GS_FIELD_T1, GS_FIELD_P, GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY,
  GS_FIELD_HZ, GS_FIELD_T, GS_FIELD_X, GS_FIELD_MAT) = range(12)
 GS_MAX_MEDIA = 256
@@ -65,11 +66,11 @@ class gs_medium(ctypes.Structure):
 
 class gs_plan(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "tile_x", "tile_y", "temporal_depth", "use_pdl",
-                                              "device_launch", "kernel", "graph_loop")]
+                                              "device_launch", "kernel", "graph_loop", "traverse")]
 
 
 class gs_multi_plan(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "blocks", "use_pdl", "kernel")]
+    _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "blocks", "use_pdl", "kernel", "traverse")]
 
 
 class gs_tune_candidate(ctypes.Structure):
@@ -204,8 +205,8 @@ def gs_set_scale(ctx, c: float) -> None:
 
 
 def gs_set_plan(ctx, block_x=0, rows=0, tile_x=0, tile_y=0, temporal_depth=0, use_pdl=0, device_launch=0,
-                kernel=0, graph_loop=0) -> None:
-    p = gs_plan(block_x, rows, tile_x, tile_y, temporal_depth, use_pdl, device_launch, kernel, graph_loop)
+                kernel=0, graph_loop=0, traverse=0) -> None:
+    p = gs_plan(block_x, rows, tile_x, tile_y, temporal_depth, use_pdl, device_launch, kernel, graph_loop, traverse)
     _check(_lib.gs_set_plan(ctx, ctypes.byref(p)), ctx)
 
 
@@ -503,8 +504,8 @@ def gs_multi_set_heat_coeffs(m, k=0.5, cx=0.1, cy=0.1, cz=0.01, cz2=0.05, t_amb=
     _mcheck(_lib.gs_multi_set_heat_coeffs(m, ctypes.byref(c)), m)
 
 
-def gs_multi_set_plan(m, block_x=0, rows=0, blocks=0, use_pdl=0, kernel=0) -> None:
-    p = gs_multi_plan(block_x, rows, blocks, use_pdl, kernel)
+def gs_multi_set_plan(m, block_x=0, rows=0, blocks=0, use_pdl=0, kernel=0, traverse=0) -> None:
+    p = gs_multi_plan(block_x, rows, blocks, use_pdl, kernel, traverse)
     _mcheck(_lib.gs_multi_set_plan(m, ctypes.byref(p)), m)
 
 

@@ -202,6 +202,8 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     if (p->tile_y == 0) p->tile_y = d.tile_y;
     if (p->temporal_depth == 0) p->temporal_depth = 1;
     if (p->graph_loop != 0 && p->graph_loop != 1) return fail(c, GS_ERR_INVALID_ARG, "plan.graph_loop must be 0 or 1");
+    if (p->traverse < GS_TRAVERSE_AUTO || p->traverse > GS_TRAVERSE_ALTERNATE)
+        return fail(c, GS_ERR_INVALID_ARG, "plan.traverse must be a gs_traverse value");
     if (p->graph_loop && p->device_launch)
         return fail(c, GS_ERR_UNSUPPORTED, "a device-launch graph cannot hold the conditional node of plan.graph_loop");
     if (p->block_x < 32 || p->block_x > 1024 || p->block_x % 32)
@@ -339,9 +341,14 @@ gs_status ensure_descs(gs_ctx* c) {
         a.tile_y = c->plan.tile_y;
         a.c = HeatCoef{c->hc.k, c->hc.cx, c->hc.cy, c->hc.cz, c->hc.cz2, c->hc.t_amb};
         const int t = c->plan.temporal_depth;
+        // one step reads T and P and writes T
+        const double step_bytes =
+            (double)ctx_elem_bytes(c) * ((double)a.pitch * c->ny * c->nz * 2 + (double)a.p_pitch * c->ny);
+        const bool alt = traverse_alternates(c->plan.traverse, step_bytes);
         for (int par = 0; par < 2; ++par) {
             a.Tin = c->ptr[par ? GS_FIELD_T1 : GS_FIELD_T0];
             a.Tout = c->ptr[par ? GS_FIELD_T0 : GS_FIELD_T1];
+            a.rev = (alt && par == 1) ? 1 : 0;
             // single-step launches (depth 1, and the peeled n mod t steps)
             const int v1 = (c->plan.kernel == GS_KERNEL_WAVE || c->plan.kernel == GS_KERNEL_COLUMN ||
                             c->plan.kernel == GS_KERNEL_COLUMN_SMEM)
@@ -381,7 +388,12 @@ gs_status ensure_descs(gs_ctx* c) {
             a.mat = static_cast<const unsigned char*>(c->ptr[GS_FIELD_MAT]);
             a.med = c->d_med;
         }
+        // one half-step reads all six components (and the ids), writes three
+        const double step_bytes = (double)ctx_elem_bytes(c) * 6.0 * (double)a.plane * (double)(c->nx + 1) +
+                                  (a.mat ? (double)a.plane * (double)(c->nx + 1) : 0.0);
+        a.rev = 0;
         cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, c->plan.kernel, &c->desc[0][0]);
+        a.rev = traverse_alternates(c->plan.traverse, step_bytes) ? 1 : 0;
         if (e == cudaSuccess) e = fdtd_desc(c->dt, true, a, c->plan.block_x, c->plan.kernel, &c->desc[0][1]);
         if (e != cudaSuccess) return cuda_fail(c, e, "FDTD kernel set-up");
     }
@@ -670,6 +682,19 @@ int device_sm_count() {
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
+}
+
+size_t device_l2_bytes() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev) != cudaSuccess) return 0;
+    return n > 0 ? (size_t)n : 0;
+}
+
+bool traverse_alternates(int mode, double step_bytes) {
+    if (mode == GS_TRAVERSE_FORWARD) return false;
+    if (mode == GS_TRAVERSE_ALTERNATE) return true;
+    return step_bytes > 0.5 * (double)device_l2_bytes();
 }
 }  // namespace gs
 

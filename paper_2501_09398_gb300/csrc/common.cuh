@@ -140,6 +140,14 @@ __device__ __forceinline__ void pdl_wait_then_trigger() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The launch's block index, walked last to first when `rev` is set: with
+// consecutive launches alternating, a step starts on the blocks the previous
+// step ran last, whose rows are still in L2 (gs_traverse).
+__device__ __forceinline__ uint3 block_index(int rev) {
+    if (!rev) return blockIdx;
+    return make_uint3(gridDim.x - 1 - blockIdx.x, gridDim.y - 1 - blockIdx.y, gridDim.z - 1 - blockIdx.z);
+}
+
 // ---------------------------------------------------------- kernel args --
 
 struct HeatCoef {
@@ -156,6 +164,7 @@ struct HeatArgs {
     long long plane;     // elements per z plane (pitch * ny)
     long long p_pitch;   // elements per row of P
     int tile_x, tile_y;  // output tile (temporal kernels)
+    int rev;             // walk the blocks last to first (block_index)
     HeatCoef c;
 };
 
@@ -175,6 +184,7 @@ struct FdtdArgs {
     // H update, med[256 + m] = (ca, cb) of the E update, for all 256 ids.
     const unsigned char* mat;
     const float2* med;
+    int rev;              // walk the blocks last to first (block_index)
 };
 
 struct SkeletonArgs {
@@ -200,6 +210,7 @@ struct MultiArgs {
     int total_items;
     int rows;
     int parity;  // 0: read T0, write T1; 1: the reverse
+    int rev;     // take the work items last to first
     HeatCoef c;
 };
 
@@ -245,6 +256,10 @@ cudaError_t convert_from_storage(gs_dtype dt, const void* src, float* dst, long 
 cudaError_t skeleton_desc(gs_dtype dt, const SkeletonArgs& a, int block_x, LaunchDesc* out);
 
 int device_sm_count();
+size_t device_l2_bytes();
+// Whether consecutive launches alternate their block order (gs_traverse):
+// `mode` as given, AUTO deciding on the bytes one step touches.
+bool traverse_alternates(int mode, double step_bytes);
 
 // Accessors of a context for the other translation units.
 void ctx_field(const gs_ctx* c, int id, void** ptr, int64_t* pitch);  // NULL / 0 if unbound

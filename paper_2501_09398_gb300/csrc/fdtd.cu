@@ -45,9 +45,10 @@ __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
     pdl_wait_then_trigger();
     const int N = a.N, M = N + 1;
     const int lane = threadIdx.x & 31;
-    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = blockIdx.z * a.kc;
+    const uint3 blk = block_index(a.rev);
+    const int i0 = (blk.x * blockDim.x + threadIdx.x) * V;
+    const int j = blk.y * blockDim.y + threadIdx.y;
+    const int k0 = blk.z * a.kc;
     const int k1 = min(k0 + a.kc, M);
     const bool act = (i0 < M) && (j < M);
     const int nv = M - i0;  // valid elements in this vector (if act)
@@ -121,9 +122,10 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
     pdl_wait_then_trigger();
     const int N = a.N, M = N + 1;
     const int lane = threadIdx.x & 31;
-    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = blockIdx.z * a.kc;
+    const uint3 blk = block_index(a.rev);
+    const int i0 = (blk.x * blockDim.x + threadIdx.x) * V;
+    const int j = blk.y * blockDim.y + threadIdx.y;
+    const int k0 = blk.z * a.kc;
     const int k1 = min(k0 + a.kc, M);
     const bool act = (i0 < M) && (j < M);
     const int nv = M - i0;
@@ -477,9 +479,10 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_
     stage_media<MAT>(a, s_med, 0);
     const int N = a.N;
     const int lane = threadIdx.x;
-    const int i0 = (blockIdx.x * 32 + lane) * V;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const uint3 blk = block_index(a.rev);
+    const int i0 = (blk.x * 32 + lane) * V;
+    const int j = blk.y * blockDim.y + threadIdx.y;
+    const int k = blk.z * blockDim.z + threadIdx.z;
     const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
     if (in_x && j < N && k < N) fdtd_h_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);
     else fdtd_h_column_body<ST, MAT, false, false>(a, s_med, lane, i0, j, k);
@@ -493,9 +496,10 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_
     stage_media<MAT>(a, s_med, 256);
     const int N = a.N;
     const int lane = threadIdx.x;
-    const int i0 = (blockIdx.x * 32 + lane) * V;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const uint3 blk = block_index(a.rev);
+    const int i0 = (blk.x * 32 + lane) * V;
+    const int j = blk.y * blockDim.y + threadIdx.y;
+    const int k = blk.z * blockDim.z + threadIdx.z;
     const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
     if (in_x && j >= 1 && j <= N - 1 && k >= 1 && k <= N - 1)
         fdtd_e_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);

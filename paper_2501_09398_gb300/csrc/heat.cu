@@ -278,7 +278,8 @@ template <typename ST, int BC, bool IS3D>
 __global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
     extern __shared__ float zsm[];  // [2][ZB+2][BX*V] (3D only)
     pdl_wait_then_trigger();
-    heat_march_tile<ST, BC, IS3D>(a, blockIdx.x, blockIdx.y, blockIdx.z, zsm);
+    const uint3 b = block_index(a.rev);
+    heat_march_tile<ST, BC, IS3D>(a, b.x, b.y, b.z, zsm);
 }
 
 template <typename ST, int BC, int NZM, int W = Vec<ST>::N>
@@ -296,7 +297,8 @@ __global__ void __launch_bounds__(512) heat_multi_kernel(const MultiArgs m) {
     pdl_wait_then_trigger();
     const int V = Vec<ST>::N;
     const int span = (COL ? 32 : blockDim.x) * V;
-    for (int w = blockIdx.x; w < m.total_items; w += gridDim.x) {
+    for (int w0 = blockIdx.x; w0 < m.total_items; w0 += gridDim.x) {
+        const int w = m.rev ? m.total_items - 1 - w0 : w0;
         // binary search: last instance whose first item <= w
         int lo = 0, hi = m.n_inst - 1;
         while (lo < hi) {
@@ -349,8 +351,9 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
     float* bufA = tsm;
     float* bufB = tsm + vol;
     float* ptile = tsm + 2 * vol;
-    const int gx0 = blockIdx.x * a.tile_x - D;  // global x of local ix = 0
-    const int gy0 = blockIdx.y * a.tile_y - D;
+    const uint3 blk = block_index(a.rev);
+    const int gx0 = blk.x * a.tile_x - D;  // global x of local ix = 0
+    const int gy0 = blk.y * a.tile_y - D;
     const int nx = a.nx, ny = a.ny;
     const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
     ST* __restrict__ Tout = static_cast<ST*>(a.Tout);
@@ -553,7 +556,8 @@ __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int 
 template <typename ST, int BC, int NZM, int W, bool EXACT>
 __global__ void __launch_bounds__(256, 2) heat_column_kernel(const HeatArgs a) {
     pdl_wait_then_trigger();
-    heat_column_dispatch<ST, BC, NZM, W, EXACT>(a, blockIdx.x, blockIdx.y);
+    const uint3 b = block_index(a.rev);
+    heat_column_dispatch<ST, BC, NZM, W, EXACT>(a, b.x, b.y);
 }
 
 // ------------------------------------------- column, rows in shared memory --
@@ -570,8 +574,9 @@ __global__ void __launch_bounds__(256) heat_scol_kernel(const HeatArgs a) {
     extern __shared__ float ssm[];
     pdl_wait_then_trigger();
     const int lane = threadIdx.x, ty = threadIdx.y, BY = blockDim.y;
-    const int x0 = (blockIdx.x * 32 + lane) * V;
-    const int y0 = blockIdx.y * BY;
+    const uint3 blk = block_index(a.rev);
+    const int x0 = (blk.x * 32 + lane) * V;
+    const int y0 = blk.y * BY;
     const int y = y0 + ty;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const bool xin = x0 < nx;
@@ -702,11 +707,12 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
     const int nx = a.nx, ny = a.ny;
     const int R = a.rows;
     const int stride = 30 * V;
-    const int xs = blockIdx.x * stride - V;       // global x of lane 0, element 0
+    const uint3 blk = block_index(a.rev);
+    const int xs = (int)blk.x * stride - V;      // global x of lane 0, element 0
     const int x0 = xs + lane * V;                 // this lane's first cell
     const int tz = IS3D ? (int)threadIdx.y : 0;
     const int nz = IS3D ? a.nz : 1;
-    const int y0 = IS3D ? (int)blockIdx.y * R : ((int)blockIdx.y * (int)blockDim.y + (int)threadIdx.y) * R;
+    const int y0 = IS3D ? (int)blk.y * R : ((int)blk.y * (int)blockDim.y + (int)threadIdx.y) * R;
     const bool has_p = !IS3D || tz == 0;
     const bool ld_ok = (x0 >= 0) && (x0 < nx);   // vector lies (at least partly) in the grid
     const bool st_lane = (lane >= 1) && (lane <= 30) && (x0 < nx);

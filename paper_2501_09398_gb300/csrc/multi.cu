@@ -90,6 +90,7 @@ gs_status ensure_table(gs_multi* m) {
     const int span = (col ? 32 : m->plan.block_x) * vec_elems(m->dt);
     std::vector<MultiInstance> host(n);
     int item = 0;
+    double step_bytes = 0.0;  // one step reads T and P and writes T of every instance
     for (int k = 0; k < n; ++k) {
         const int i = order[k];
         void* t0;
@@ -115,7 +116,9 @@ gs_status ensure_table(gs_multi* m) {
         d.first_item = item;
         d.n_items = ntx * nty;
         item += d.n_items;
+        step_bytes += (double)ctx_elem_bytes(m->inst[i]) * ((double)pt0 * d.ny * 2 + (double)pp * d.ny);
     }
+    const bool alt = traverse_alternates(m->plan.traverse, step_bytes);
     if (!m->d_desc) GS_MCUDA(m, cudaMalloc(&m->d_desc, sizeof(MultiInstance) * n));
     GS_MCUDA(m, cudaMemcpyAsync(m->d_desc, host.data(), sizeof(MultiInstance) * n, cudaMemcpyHostToDevice,
                                 m->stream));
@@ -137,6 +140,7 @@ gs_status ensure_table(gs_multi* m) {
         a.total_items = item;
         a.rows = m->plan.rows;
         a.parity = par;
+        a.rev = (alt && par == 1) ? 1 : 0;
         a.c = HeatCoef{m->hc.k, m->hc.cx, m->hc.cy, m->hc.cz, m->hc.cz2, m->hc.t_amb};
         LaunchDesc& d = m->desc[par];
         d.func = f;
@@ -292,11 +296,14 @@ gs_status gs_multi_set_plan(gs_multi* m, const gs_multi_plan* p) {
         return mfail(m, GS_ERR_INVALID_ARG, "COLUMN tiles take rows <= 8");
     if (q.rows < 1 || q.blocks < 0 || (q.use_pdl != 0 && q.use_pdl != 1))
         return mfail(m, GS_ERR_INVALID_ARG, "rows >= 1, blocks >= 0, use_pdl in {0, 1}");
+    if (q.traverse < GS_TRAVERSE_AUTO || q.traverse > GS_TRAVERSE_ALTERNATE)
+        return mfail(m, GS_ERR_INVALID_ARG, "traverse must be a gs_traverse value");
     gs_plan sp{};
     sp.block_x = q.block_x;
     sp.rows = q.rows;
     sp.temporal_depth = 1;
     sp.use_pdl = q.use_pdl;
+    sp.traverse = q.traverse;
     sp.kernel = GS_KERNEL_MARCH;
     for (size_t i = 0; i < m->inst.size(); ++i) {
         gs_status st = gs_set_plan(m->inst[i], &sp);
