@@ -116,6 +116,7 @@ def candidates(w):
         if w["kind"] == "heat2d" or w["nz"] <= 16:
             shapes += [dict(block_x=64, rows=4, temporal_depth=t, kernel=W) for t in (2, 4)]
             shapes.append(dict(block_x=64, rows=16, temporal_depth=4, kernel=W))
+            shapes += [dict(block_x=128, rows=32, temporal_depth=t, kernel=W) for t in (2, 4)]
     if default_plan(w) not in shapes:
         shapes.append(default_plan(w))
     return [(dict(p), S) for p in shapes for S in S_LIST]
