@@ -40,6 +40,9 @@ import gs_inputs  # noqa: E402
 WORKLOADS = {
     "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=1,
                              plan=dict(kernel=4, rows=4)),
+    # a deep stack (nz > 8): the column kernel in 8-plane chunks
+    "heat3d-256": dict(kind="heat3d", nx=256, ny=256, nz=256, iters=200, S=100, depth=1,
+                       plan=dict(kernel=4, rows=4)),
     "heat2d-512": dict(kind="heat2d", nx=512, ny=512, nz=1, iters=1000, S=100, depth=1,
                        plan=dict(kernel=4, rows=4)),
     "heat2d-4096": dict(kind="heat2d", nx=4096, ny=4096, nz=1, iters=200, S=100, depth=1,
@@ -675,6 +678,7 @@ def main():
         # 2D 4096^2: HBM roofline of the depth-1 kernel, and the wavefront
         # depth-4 kernel's throughput
         for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(loop=True), "device_loop"),
+                              ("heat3d-256", {}, "column"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-media-256", {}, "column"),
                               ("heat2d-4096", {}, "depth1"),

@@ -173,23 +173,18 @@ gs_plan default_plan(const gs_ctx* c) {
         p.rows = 4;  // COLUMN: j rows per block (k planes per block for MARCH)
         p.temporal_depth = 1;
         p.kernel = GS_KERNEL_COLUMN;
-    } else if (c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz) {
-        // the column kernel (measured fastest at depth 1 for 2D and thin
-        // stacks); rows = warps per block stacked in y
+    } else {
+        // the column kernel (measured fastest at depth 1 for 2D, thin stacks
+        // and, in 8-plane chunks, deep stacks); rows = warps per block
+        // stacked in y
         const bool small = c->nx * c->ny * c->nz <= (1 << 22);
+        const bool deep = c->kind == GS_HEAT3D && c->nz > kColumnMaxNz;
         p.block_x = 64;
-        p.rows = small ? 4 : 8;
+        p.rows = (small || deep) ? 4 : 8;
         p.tile_x = c->kind == GS_HEAT2D ? 64 : 32;
         p.tile_y = 32;
         p.temporal_depth = 1;
         p.kernel = GS_KERNEL_COLUMN;
-    } else {
-        p.block_x = 32;
-        p.rows = 16;
-        p.tile_x = 32;
-        p.tile_y = 32;
-        p.temporal_depth = 1;
-        p.kernel = GS_KERNEL_MARCH;
     }
     return p;
 }
@@ -240,18 +235,16 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
             return fail(c, GS_ERR_INVALID_ARG, "FDTD kernels: GS_KERNEL_COLUMN or GS_KERNEL_MARCH");
     }
     const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
-    const bool column_ok = (c->kind == GS_HEAT2D) || (c->nz <= kColumnMaxNz);
     if (is_heat(c) && p->kernel == GS_KERNEL_AUTO)
-        p->kernel = (t == 1) ? (column_ok ? GS_KERNEL_COLUMN : GS_KERNEL_MARCH)
-                             : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
+        p->kernel = (t == 1) ? GS_KERNEL_COLUMN : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
     if (p->kernel == GS_KERNEL_MARCH && t != 1)
         return fail(c, GS_ERR_INVALID_ARG, "the MARCH kernel runs depth 1 only");
     if (p->kernel == GS_KERNEL_TILE && t == 1)
         return fail(c, GS_ERR_INVALID_ARG, "the TILE kernel runs depth 2 or 4 only");
     const bool colv = (p->kernel == GS_KERNEL_COLUMN || p->kernel == GS_KERNEL_COLUMN_SMEM);
     if (colv && t != 1) return fail(c, GS_ERR_INVALID_ARG, "the COLUMN kernels run depth 1 only");
-    if (colv && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
-        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernels need nz <= 8");
+    if (p->kernel == GS_KERNEL_COLUMN_SMEM && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
+        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN_SMEM kernel needs nz <= 8");
     if (p->kernel == GS_KERNEL_WAVE && !wave_ok)
         return fail(c, GS_ERR_UNSUPPORTED, "the WAVE kernel needs nz <= 16 (all planes in one block)");
     if (p->kernel == GS_KERNEL_WAVE && heat_wave_smem(c->kind == GS_HEAT3D ? (int)c->nz : 0, t, vec_elems(c->dt)) > 227 * 1024)

@@ -457,11 +457,14 @@ constexpr int column_width(bool is3d) {
 // The kernel is latency- and issue-bound when L2-resident, so instruction
 // count and load order matter: the P row first (measured 9-12 % faster in
 // 2D), one predicated edge load per plane serving both lanes 0 and 31.
-template <typename ST, int BC, int NZM, int W, bool EXACT, bool FAST>
-__device__ __forceinline__ void heat_column_body(const HeatArgs& a, int x0, int y, bool full_x, bool inner_x) {
+template <typename ST, int BC, int NZM, int W, bool EXACT, bool FAST, bool DEEP>
+__device__ __forceinline__ void heat_column_body(const HeatArgs& a, int x0, int y, int z0, bool full_x,
+                                                 bool inner_x) {
     const int lane = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
-    const int nz = EXACT ? NZM : a.nz;
+    // planes this thread updates: z0 .. z0 + nz - 1 (DEEP: one chunk of a
+    // deeper stack, else the whole stack from z0 = 0)
+    const int nz = EXACT ? NZM : (DEEP ? min(NZM, a.nz - z0) : a.nz);
     const bool act = FAST || ((x0 < nx) && (y < ny));
     const long long pitch = a.pitch, plane = a.plane;
     const int xc = FAST ? x0 : min(x0, (nx - 1) / W * W);  // last vector's start when past the row
@@ -479,12 +482,20 @@ __device__ __forceinline__ void heat_column_body(const HeatArgs& a, int x0, int 
         // planes past nz (general kernel only) re-read the last plane and
         // are never updated: a branch-free load keeps the register arrays
         // from spilling
-        const ST* q = rc + (EXACT ? z : min(z, nz - 1)) * plane;
+        const ST* q = rc + (long long)(z0 + (EXACT ? z : min(z, nz - 1))) * plane;
         load_vecw<ST, W>(q, c[z]);
         load_vecw<ST, W>(q + dn, n[z]);
         load_vecw<ST, W>(q + ds, so[z]);
         edge[z] = 0.f;
         if (lane == 0 || lane == 31) edge[z] = load_scalar(q + dedge);
+    }
+    // DEEP: the planes just below and above the chunk, at clamped plane
+    // indices (at the stack's bottom / top that is the chunk's own edge
+    // plane: the clamp boundary's value)
+    float cd[W], cu[W];
+    if constexpr (DEEP) {
+        load_vecw<ST, W>(rc + (long long)max(z0 - 1, 0) * plane, cd);
+        load_vecw<ST, W>(rc + (long long)min(z0 + nz, a.nz - 1) * plane, cu);
     }
 
     ST* out_row = static_cast<ST*>(a.Tout) + (long long)y * pitch + x0;
@@ -505,9 +516,15 @@ __device__ __forceinline__ void heat_column_body(const HeatArgs& a, int x0, int 
             float nv = n[z][i], sv = so[z][i];
             float d = 0.f, u = 0.f;
             if (NZM > 1) {
-                d = (z > 0) ? c[z > 0 ? z - 1 : 0][i] : bnd<BC>(t);
-                u = (z + 1 < NZM) ? c[z + 1 < NZM ? z + 1 : z][i] : bnd<BC>(t);
-                if (!EXACT) u = (z + 1 < nz) ? u : bnd<BC>(t);
+                const float below = DEEP ? cd[i] : bnd<BC>(t);
+                const float above = DEEP ? cu[i] : bnd<BC>(t);
+                d = (z > 0) ? c[z > 0 ? z - 1 : 0][i] : below;
+                u = (z + 1 < NZM) ? c[z + 1 < NZM ? z + 1 : z][i] : above;
+                if (!EXACT) u = (z + 1 < nz) ? u : above;
+                if (DEEP && BC == GS_BC_DIRICHLET0) {
+                    if (z0 + z == 0) d = 0.f;
+                    if (z0 + z + 1 >= a.nz) u = 0.f;
+                }
             }
             if (BC == GS_BC_CLAMP) {
                 if (!FAST && !full_x && x0 + i + 1 >= nx) e = t;
@@ -519,24 +536,25 @@ __device__ __forceinline__ void heat_column_body(const HeatArgs& a, int x0, int 
                 if (y == 0) nv = 0.f;
                 if (y + 1 >= ny) sv = 0.f;
             }
-            out[i] = heat_cell<(NZM > 1)>(t, nv, sv, w, e, d, u, (z == 0) ? p[i] : 0.0f, a.c);
+            out[i] = heat_cell<(NZM > 1)>(t, nv, sv, w, e, d, u, (z == 0 && (!DEEP || z0 == 0)) ? p[i] : 0.0f, a.c);
         }
-        store_vecw<ST, W>(out_row + z * plane, out, (FAST || full_x) ? W : nx - x0);
+        store_vecw<ST, W>(out_row + (long long)(z0 + z) * plane, out, (FAST || full_x) ? W : nx - x0);
     }
 }
 
 // The COLUMN tile (bx, by): the FAST body for full warps inside the grid,
 // the general body for the warps at a ragged row end or past the last row.
-template <typename ST, int BC, int NZM, int W, bool EXACT>
-__device__ __forceinline__ void heat_column_dispatch(const HeatArgs& a, int bx, int by) {
+template <typename ST, int BC, int NZM, int W, bool EXACT, bool DEEP = false>
+__device__ __forceinline__ void heat_column_dispatch(const HeatArgs& a, int bx, int by, int bz = 0) {
     const int x0 = (bx * 32 + threadIdx.x) * W;
     const int y = by * blockDim.y + threadIdx.y;
+    const int z0 = DEEP ? bz * NZM : 0;
     // every vector of the warp lies inside the row (no ragged end, no lane past it)
     const bool full_x = __all_sync(0xffffffffu, x0 + W <= a.nx);
     // ... and none touches the row's first or last cell (Dirichlet-0 only)
     const bool inner_x = __all_sync(0xffffffffu, x0 > 0 && x0 + W < a.nx);
-    if (full_x && y < a.ny) heat_column_body<ST, BC, NZM, W, EXACT, true>(a, x0, y, full_x, inner_x);
-    else heat_column_body<ST, BC, NZM, W, EXACT, false>(a, x0, y, full_x, inner_x);
+    if (full_x && y < a.ny) heat_column_body<ST, BC, NZM, W, EXACT, true, DEEP>(a, x0, y, z0, full_x, inner_x);
+    else heat_column_body<ST, BC, NZM, W, EXACT, false, DEEP>(a, x0, y, z0, full_x, inner_x);
 }
 
 // The COLUMN tile of a 2D depth-1 step (the multi-instance kernel's COLUMN
@@ -552,12 +570,14 @@ __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int 
 // needs without spilling, and one wave of blocks at 512 x 512 x 8.  EXACT
 // kernels serve nz == NZM (2D, and 3D stacks of 2, 4 or 8 planes); the
 // general one (NZM = 8), every other nz <= 8 (separate kernels: one holding
-// both paths spills).
-template <typename ST, int BC, int NZM, int W, bool EXACT>
+// both paths spills).  DEEP kernels serve nz > 8: blockIdx.z picks a chunk
+// of 8 planes, which the thread updates with the planes just below and
+// above it as halos (EXACT when 8 divides nz).
+template <typename ST, int BC, int NZM, int W, bool EXACT, bool DEEP>
 __global__ void __launch_bounds__(256, 2) heat_column_kernel(const HeatArgs a) {
     pdl_wait_then_trigger();
     const uint3 b = block_index(a.rev);
-    heat_column_dispatch<ST, BC, NZM, W, EXACT>(a, b.x, b.y);
+    heat_column_dispatch<ST, BC, NZM, W, EXACT, DEEP>(a, b.x, b.y, b.z);
 }
 
 // ------------------------------------------- column, rows in shared memory --
@@ -907,12 +927,15 @@ template <typename ST, int BC>
 const void* pick(bool is3d, int depth, int variant, int nz) {
     if (variant == GS_KERNEL_COLUMN && depth == 1) {
         constexpr int W3 = column_width<ST>(true);
-        if (!is3d) return (const void*)heat_column_kernel<ST, BC, 1, column_width<ST>(false), true>;
+        if (!is3d) return (const void*)heat_column_kernel<ST, BC, 1, column_width<ST>(false), true, false>;
+        if (nz > kColumnMaxNz)
+            return nz % kColumnMaxNz == 0 ? (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, true, true>
+                                          : (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, false, true>;
         switch (nz) {
-            case 2: return (const void*)heat_column_kernel<ST, BC, 2, W3, true>;
-            case 4: return (const void*)heat_column_kernel<ST, BC, 4, W3, true>;
-            case kColumnMaxNz: return (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, true>;
-            default: return (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, false>;
+            case 2: return (const void*)heat_column_kernel<ST, BC, 2, W3, true, false>;
+            case 4: return (const void*)heat_column_kernel<ST, BC, 4, W3, true, false>;
+            case kColumnMaxNz: return (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, true, false>;
+            default: return (const void*)heat_column_kernel<ST, BC, kColumnMaxNz, W3, false, false>;
         }
     }
     if (variant == GS_KERNEL_COLUMN_SMEM && depth == 1)
@@ -956,11 +979,11 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
                          is3d ? (a.nz + zb - 1) / zb : 1);
         out->smem = is3d ? (size_t)2 * (zb + 2) * block_x * V * sizeof(float) : 0;
     } else if (variant == GS_KERNEL_COLUMN) {
-        if (is3d && a.nz > kColumnMaxNz) return cudaErrorInvalidValue;
         const int by = std::max(1, std::min(a.rows, 8));
         const int cw = (dt == GS_F32) ? column_width<float>(is3d) : column_width<__half>(is3d);
+        const int chunks = (is3d && a.nz > kColumnMaxNz) ? (a.nz + kColumnMaxNz - 1) / kColumnMaxNz : 1;
         out->block = dim3(32, by, 1);
-        out->grid = dim3((a.nx + 32 * cw - 1) / (32 * cw), (a.ny + by - 1) / by, 1);
+        out->grid = dim3((a.nx + 32 * cw - 1) / (32 * cw), (a.ny + by - 1) / by, chunks);
         out->smem = 0;
     } else if (variant == GS_KERNEL_COLUMN_SMEM) {
         if (is3d && a.nz > kColumnMaxNz) return cudaErrorInvalidValue;

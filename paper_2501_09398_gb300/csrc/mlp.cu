@@ -673,8 +673,7 @@ gs_status gs_features(const gs_workload* w, const gs_tune_candidate* c, int32_t 
         // kernel variant, with AUTO resolved as the context resolves it
         int k = p.kernel;
         if (k == GS_KERNEL_AUTO) {
-            const bool thin = w->kind != GS_HEAT3D || w->nz <= kColumnMaxNz;
-            k = (p.temporal_depth == 1) ? (thin ? GS_KERNEL_COLUMN : GS_KERNEL_MARCH)
+            k = (p.temporal_depth == 1) ? GS_KERNEL_COLUMN
                                         : ((w->kind == GS_HEAT2D || w->nz <= kWaveMaxNz) ? GS_KERNEL_WAVE
                                                                                           : GS_KERNEL_TILE);
         }

@@ -32,7 +32,8 @@ def _coeffs(nz):
 # 32-lane warps), y (rows per block) and z (planes per block)
 SHAPES_2D = [(130, 17), (37, 29), (5, 1), (1, 9), (4, 4), (257, 66), (1, 1)]
 SHAPES_3D = [(33, 21, 5), (19, 7, 3), (130, 9, 17), (8, 8, 1), (3, 2, 2),
-             (67, 13, 4), (45, 10, 8), (140, 6, 2)]  # compile-time plane counts of the column kernel
+             (67, 13, 4), (45, 10, 8), (140, 6, 2),  # compile-time plane counts of the column kernel
+             (70, 11, 24), (36, 9, 19)]  # the column kernel in 8-plane chunks
 
 
 @pytest.mark.parametrize("shape", SHAPES_2D)
@@ -57,9 +58,7 @@ def test_heat3d_parity_small(oracle, shape, bc):
     ref = oracle.heat_run(T0, P, 40, oracle.HEAT_COEFFS_3D, bc)
     import paper_2501_09398_gb300 as g
 
-    plans = [None, dict(block_x=64, rows=2)]
-    if nz <= 8:
-        plans.append(dict(kernel=g.GS_KERNEL_COLUMN, rows=3))
+    plans = [None, dict(block_x=64, rows=2), dict(kernel=g.GS_KERNEL_COLUMN, rows=3)]
     for plan in plans:
         got = heat_gpu(T0, P, 40, S=0, bc=bc, plan=plan)
         assert np.max(np.abs(got - ref)) <= HEAT_RTOL * np.max(np.abs(ref))
@@ -101,11 +100,11 @@ def test_temporal_blocking_bit_identical(shape, depth):
         plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_WAVE, rows=rows, block_x=bx)
         assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"wave rows={rows} bx={bx}"
         assert np.array_equal(heat_gpu(T0, P, n, S=6, plan=plan), base), f"wave graph rows={rows} bx={bx}"
-    if depth == 1:  # column kernel: every plane of a column in registers (nz <= 8)
+    if depth == 1:  # column kernels: every plane of a column (of an 8-plane chunk when nz > 8) in registers
         for rows, kern in ((1, g.GS_KERNEL_COLUMN), (4, g.GS_KERNEL_COLUMN), (8, g.GS_KERNEL_COLUMN),
                            (1, g.GS_KERNEL_COLUMN_SMEM), (3, g.GS_KERNEL_COLUMN_SMEM), (8, g.GS_KERNEL_COLUMN_SMEM)):
             plan = dict(kernel=kern, rows=rows)
-            if nz > 8:
+            if nz > 8 and kern == g.GS_KERNEL_COLUMN_SMEM:
                 with pytest.raises(g.GsError):
                     heat_gpu(T0, P, n, S=0, plan=plan)
                 continue

@@ -78,7 +78,7 @@ def test_feature_layout(g):
     deep = dict(kind=g.GS_HEAT3D, dtype=g.GS_F32, nx=64, ny=64, nz=16, n_iters=100)
     thin = dict(deep, nz=8)
     one = (dict(block_x=32, rows=16, temporal_depth=1), 10)
-    assert list(g.gs_features(deep, [one])[0][16:]) == [0, 0]  # AUTO -> MARCH above 8 planes
+    assert list(g.gs_features(deep, [one])[0][16:]) == [1, 0]  # AUTO -> COLUMN (8-plane chunks) above 8 planes
     assert list(g.gs_features(thin, [one])[0][16:]) == [1, 0]
     smem = (dict(block_x=64, rows=4, temporal_depth=1, kernel=g.GS_KERNEL_COLUMN_SMEM), 10)
     march = (dict(block_x=64, rows=4, temporal_depth=1, kernel=g.GS_KERNEL_MARCH), 10)
