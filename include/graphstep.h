@@ -130,15 +130,20 @@ typedef struct gs_medium {
  *          per plane in 3D).
  *   TILE   depth 2 or 4: overlapped shared-memory tile of tile_x x tile_y
  *          columns (all nz planes) with a t-wide halo.
- *   COLUMN depth 1 only: each thread owns one vector of cells at one y with
+ *   COLUMN depth 1: each thread owns one vector of cells at one y with
  *          every plane of its column in registers (no march, no shared
  *          memory); stacks of more than 8 planes in chunks of 8 (the planes
  *          just below and above a chunk loaded as halos); `rows` (<= 8) warps
- *          per block stacked in y.
+ *          per block stacked in y.  Depth 2 or 4, 2D only: each thread owns
+ *          one vector of cells in 4 rows (2 for bf16/f16), loads those rows
+ *          and 2t halo rows at once and advances t levels in registers
+ *          (lanes 0 and 31 of a warp are halo lanes); block_x/32 warps per
+ *          block stacked in y.
  *   COLUMN_SMEM  as COLUMN, but each thread loads only its own row of every
  *          plane; rows y-1 / y+1 come from shared memory after one barrier
  *          (fewer registers and L2 requests).
- *   AUTO   depth 1: COLUMN; depth > 1: WAVE for 2D and nz <= 16, else TILE. */
+ *   AUTO   depth 1 and 2D: COLUMN; 3D at depth > 1: WAVE for nz <= 16, else
+ *          TILE. */
 typedef enum gs_kernel {
     GS_KERNEL_AUTO = 0,
     GS_KERNEL_MARCH = 1,

@@ -869,6 +869,111 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
     }
 }
 
+// ------------------------------------------------- column, depth T (2D) ----
+//
+// Temporal blocking without a march, for 2D grids: each thread owns V cells
+// along x and R consecutive output rows.  It issues all of its loads at once
+// (rows y0-T .. y0+R+T-1 of T and the P rows y0-T+1 .. y0+R+T-2, at clamped
+// coordinates) and advances T levels in registers: level k updates array
+// rows k .. R+2T-1-k in place, each from level k-1's rows above and below.
+// x-neighbours come from shuffles; a warp edge loses one cell of validity per
+// level, so lanes 0 and 31 are halo lanes (T <= V) and a warp stores lanes
+// 1..30 (tiles of 30 V cells, overlapping by a vector on each side, as the
+// wavefront kernel's).  Rows outside the grid are computed but only feed rows
+// whose neighbour there is replaced by the boundary value.  Blocks away from
+// every grid edge (warp-uniform) update without boundary selects in packed
+// f32x2 arithmetic.  Block (32, BY): BY warps stacked in y.
+template <typename ST, int BC, int T, int R>
+__global__ void __launch_bounds__(256) heat_column_t_kernel(const HeatArgs a) {
+    constexpr int V = Vec<ST>::N;
+    constexpr int NR = R + 2 * T;
+    static_assert(T >= 1 && T <= V, "halo lane must cover T cells");
+    pdl_wait_then_trigger();
+    const uint3 blk = block_index(a.rev);
+    const int lane = threadIdx.x;
+    const int nx = a.nx, ny = a.ny;
+    const int xs = (int)blk.x * 30 * V - V;  // global x of lane 0, element 0
+    const int x0 = xs + lane * V;            // this lane's first cell
+    const int y0 = ((int)blk.y * (int)blockDim.y + (int)threadIdx.y) * R;
+    const int xc = min(max(x0, 0), (nx - 1) / V * V);  // a vector inside the row
+    const long long pitch = a.pitch;
+    const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
+    const ST* __restrict__ P = static_cast<const ST*>(a.P);
+
+    float row[NR][V], pr[NR - 2][V];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int yk = min(max(y0 - T + k, 0), ny - 1);
+        load_vec(Tin + (long long)yk * pitch + xc, row[k]);
+    }
+#pragma unroll
+    for (int k = 1; k < NR - 1; ++k) {
+        const int yk = min(max(y0 - T + k, 0), ny - 1);
+        load_vec(P + (long long)yk * a.p_pitch + xc, pr[k - 1]);
+    }
+    // the block's 32 vectors lie away from both x edges, and no row it
+    // updates is the grid's first or last
+    const bool fast = (xs >= 1) && (xs + 32 * V < nx) && (y0 >= T) && (y0 + R + T <= ny);
+
+#pragma unroll
+    for (int k = 1; k <= T; ++k) {
+        float prev[V];  // level k-1 value of the row above the one being updated
+#pragma unroll
+        for (int i = 0; i < V; ++i) prev[i] = row[k - 1][i];
+#pragma unroll
+        for (int j = k; j <= NR - 1 - k; ++j) {
+            const int yg = y0 - T + j;
+            const float(&c)[V] = row[j];
+            const float w0 = __shfl_up_sync(0xffffffffu, c[V - 1], 1);
+            const float eV = __shfl_down_sync(0xffffffffu, c[0], 1);
+            float out[V];
+            if (fast) {
+                float xsum[V], zero[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    xsum[i] = __fadd_rn((i == 0) ? w0 : c[i - 1], (i == V - 1) ? eV : c[i + 1]);
+                    zero[i] = 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < V; i += 2)
+                    heat_cell_x2<false>(&c[i], &prev[i], &row[j + 1][i], &xsum[i], &zero[i], &zero[i], &pr[j - 1][i],
+                                        a.c, &out[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const int x = x0 + i;
+                    const float t = c[i];
+                    float w = (i == 0) ? w0 : c[i - 1];
+                    float e = (i == V - 1) ? eV : c[i + 1];
+                    if (x == 0) w = bnd<BC>(t);
+                    if (x + 1 >= nx) e = bnd<BC>(t);
+                    const float n = (yg == 0) ? bnd<BC>(t) : prev[i];
+                    const float so = (yg + 1 >= ny) ? bnd<BC>(t) : row[j + 1][i];
+                    out[i] = heat_cell<false>(t, n, so, w, e, 0.f, 0.f, pr[j - 1][i], a.c);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                prev[i] = row[j][i];
+                row[j][i] = out[i];
+            }
+        }
+    }
+    if (lane >= 1 && lane <= 30 && x0 < nx) {
+#pragma unroll
+        for (int j = T; j < T + R; ++j) {
+            const int yg = y0 - T + j;
+            if (yg < ny) store_vec(static_cast<ST*>(a.Tout) + (long long)yg * pitch + x0, row[j], nx - x0);
+        }
+    }
+}
+
+// Output rows per thread of the depth-T column kernel (register budget).
+template <typename ST>
+constexpr int column_t_rows() {
+    return Vec<ST>::N == 4 ? 4 : 2;
+}
+
 // ------------------------------------------------------------- factory ----
 
 namespace {
@@ -941,6 +1046,11 @@ const void* pick(bool is3d, int depth, int variant, int nz) {
     if (variant == GS_KERNEL_COLUMN_SMEM && depth == 1)
         return is3d ? (const void*)heat_scol_kernel<ST, BC, kColumnMaxNz>
                     : (const void*)heat_scol_kernel<ST, BC, 1>;
+    if (variant == GS_KERNEL_COLUMN && depth > 1 && !is3d) {
+        if (depth == 2) return (const void*)heat_column_t_kernel<ST, BC, 2, column_t_rows<ST>()>;
+        if (depth == 4) return (const void*)heat_column_t_kernel<ST, BC, 4, column_t_rows<ST>()>;
+        return nullptr;
+    }
     if (variant == GS_KERNEL_WAVE)
         return is3d ? pick_wave<ST, BC, true>(depth) : pick_wave<ST, BC, false>(depth);
     if (variant == GS_KERNEL_MARCH && depth == 1)
@@ -978,6 +1088,13 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
         out->grid = dim3((a.nx + block_x * V - 1) / (block_x * V), (a.ny + a.rows - 1) / a.rows,
                          is3d ? (a.nz + zb - 1) / zb : 1);
         out->smem = is3d ? (size_t)2 * (zb + 2) * block_x * V * sizeof(float) : 0;
+    } else if (variant == GS_KERNEL_COLUMN && depth > 1) {
+        if (is3d) return cudaErrorInvalidValue;
+        const int bw = std::max(1, std::min(block_x / 32, 8));  // warps stacked in y
+        const int rt = (dt == GS_F32) ? column_t_rows<float>() : column_t_rows<__half>();
+        out->block = dim3(32, bw, 1);
+        out->grid = dim3((a.nx + 30 * V - 1) / (30 * V), (a.ny + rt * bw - 1) / (rt * bw), 1);
+        out->smem = 0;
     } else if (variant == GS_KERNEL_COLUMN) {
         const int by = std::max(1, std::min(a.rows, 8));
         const int cw = (dt == GS_F32) ? column_width<float>(is3d) : column_width<__half>(is3d);

@@ -673,9 +673,9 @@ gs_status gs_features(const gs_workload* w, const gs_tune_candidate* c, int32_t 
         // kernel variant, with AUTO resolved as the context resolves it
         int k = p.kernel;
         if (k == GS_KERNEL_AUTO) {
-            k = (p.temporal_depth == 1) ? GS_KERNEL_COLUMN
-                                        : ((w->kind == GS_HEAT2D || w->nz <= kWaveMaxNz) ? GS_KERNEL_WAVE
-                                                                                          : GS_KERNEL_TILE);
+            k = (p.temporal_depth == 1 || w->kind == GS_HEAT2D)
+                    ? GS_KERNEL_COLUMN
+                    : (w->nz <= kWaveMaxNz ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
         }
         f[16] = (k == GS_KERNEL_COLUMN || k == GS_KERNEL_COLUMN_SMEM);
         f[17] = (k == GS_KERNEL_COLUMN_SMEM);

@@ -86,7 +86,8 @@ def test_graph_batches_bit_identical_to_per_step(nz):
             assert np.array_equal(heat_gpu(T0, P, n, S=S, plan=plan), base), f"S={S} {plan}"
 
 
-@pytest.mark.parametrize("shape", [(96, 64, 1), (77, 45, 1), (300, 37, 1), (40, 33, 8), (21, 19, 3), (250, 20, 16)])
+@pytest.mark.parametrize("shape", [(96, 64, 1), (77, 45, 1), (300, 37, 1), (40, 33, 8), (21, 19, 3), (250, 20, 16),
+                                   (500, 130, 1), (3, 2, 1)])
 @pytest.mark.parametrize("depth", [1, 2, 4])
 def test_temporal_blocking_bit_identical(shape, depth):
     import paper_2501_09398_gb300 as g
@@ -110,6 +111,17 @@ def test_temporal_blocking_bit_identical(shape, depth):
                 continue
             assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"column {kern} rows={rows}"
             assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column {kern} graph rows={rows}"
+    if depth > 1:  # column kernel at depth 2 / 4: no march, levels in registers (2D only)
+        for bx in (32, 64, 256):
+            plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_COLUMN, block_x=bx)
+            if nz > 1:
+                with pytest.raises(g.GsError):
+                    heat_gpu(T0, P, n, S=0, plan=plan)
+                continue
+            assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"column depth={depth} bx={bx}"
+            assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column graph depth={depth} bx={bx}"
+            assert np.array_equal(heat_gpu(T0, P, n, S=0, bc=1, plan=plan), heat_gpu(T0, P, n, S=0, bc=1)), \
+                f"column dirichlet depth={depth} bx={bx}"
     if depth > 1:  # overlapped shared-memory tiles
         for tile in ((32, 32), (16, 8), (13, 7)):
             plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_TILE, tile_x=tile[0], tile_y=tile[1])

@@ -67,9 +67,9 @@ def test_feature_layout(g):
     f = g.gs_features(w, [(dict(block_x=64, rows=4, temporal_depth=1), 100),
                           (dict(block_x=128, rows=32, temporal_depth=4), 0)])
     # the last two inputs flag the kernel variant: AUTO resolves to COLUMN
-    # at depth 1 in 2D and to the wavefront kernel at depth 4
+    # in 2D, at depth 1 and at depth 4
     expect0 = [9, 8, 0, 1, 0, 0, 1, math.log2(1000), 1, 0, 0, math.log2(100), 0, 6, 2, 1, 1, 0]
-    expect1 = [9, 8, 0, 1, 0, 0, 1, math.log2(1000), 1, 0, 0, 0, 1, 7, 5, 4, 0, 0]
+    expect1 = [9, 8, 0, 1, 0, 0, 1, math.log2(1000), 1, 0, 0, 0, 1, 7, 5, 4, 1, 0]
     np.testing.assert_allclose(f[0], expect0, rtol=1e-6)
     np.testing.assert_allclose(f[1], expect1, rtol=1e-6)
     w3 = dict(kind=g.GS_FDTD3D, dtype=g.GS_BF16, nx=128, ny=128, nz=128, n_iters=5000)
@@ -84,5 +84,7 @@ def test_feature_layout(g):
     march = (dict(block_x=64, rows=4, temporal_depth=1, kernel=g.GS_KERNEL_MARCH), 10)
     assert list(g.gs_features(thin, [smem])[0][16:]) == [1, 1]
     assert list(g.gs_features(thin, [march])[0][16:]) == [0, 0]
+    wave = (dict(block_x=64, rows=4, temporal_depth=2), 10)
+    assert list(g.gs_features(thin, [wave])[0][16:]) == [0, 0]  # AUTO at depth 2 in 3D -> WAVE
     with pytest.raises(g.GsError):
         g.gs_features(w, [(dict(block_x=0, rows=4, temporal_depth=1), 10)])
