@@ -12,9 +12,13 @@ oracle on the same workload instead (the only comparison program there is:
 the paper ships no code).
 
 Other workloads (``--workload``): heat2d-512 (2D 512^2, 1000 iterations),
-heat2d-4096 (2D 4096^2, 200 iterations), fdtd-128 (Yee 128^3, 5000
-iterations).  Multi-GPU (torchrun): independent replicas, one per rank, no
-collective on the data path ("scaling": "weak").
+heat2d-4096 (2D 4096^2, 200 iterations), heat3d-256 (a deep stack, 256^3,
+200 iterations), fdtd-128 (Yee 128^3, 5000 iterations), fdtd-256 and
+fdtd-media-256 (256^3 cavities, vacuum and lossy objects, 500 iterations),
+multi-64 (64 uneven 2D grids, 2000 iterations).  The default run adds a
+line's "extra" measurements of several of these (and of temporal depths).
+Multi-GPU (torchrun): independent replicas, one per rank, no collective on
+the data path ("scaling": "weak").
 """
 from __future__ import annotations
 
@@ -681,7 +685,9 @@ def main():
                               ("heat3d-256", {}, "column"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-media-256", {}, "column"),
+                              ("heat2d-512", dict(depth=4, kernel=4, block_x=256), "column4"),
                               ("heat2d-4096", {}, "depth1"),
+                              ("heat2d-4096", dict(depth=2, kernel=4, block_x=64), "column2"),
                               ("heat2d-4096", dict(depth=4, kernel=2, rows=32, block_x=128), "wave4")):
             ww = WORKLOADS[nm]
             mm = measure_workload(nm, ww, argparse.Namespace(**{**base, **over}), flush, with_e2e=False)

@@ -118,6 +118,8 @@ def candidates(w):
             shapes += [dict(block_x=64, rows=4, temporal_depth=t, kernel=W) for t in (2, 4)]
             shapes.append(dict(block_x=64, rows=16, temporal_depth=4, kernel=W))
             shapes += [dict(block_x=128, rows=32, temporal_depth=t, kernel=W) for t in (2, 4)]
+        if w["kind"] == "heat2d":  # the column kernel's levels in registers
+            shapes += [dict(block_x=64, rows=4, temporal_depth=t, kernel=C) for t in (2, 4)]
     if default_plan(w) not in shapes:
         shapes.append(default_plan(w))
     return [(dict(p), S) for p in shapes for S in S_LIST]

@@ -5,11 +5,11 @@ packaged GB300 sweep (150 workloads) and picks (launch plan, batch size,
 temporal depth) for 200 held-out workloads without running them; its
 regret against each workload's swept optimum is compared with a fixed
 S = 100 and with the paper's analytic picker (Eqs. 2 and 6 fitted per
-workload at the default plan).  The analytic picker needs the workload's
-own build and run times at six batch sizes: free, it is slightly ahead (the
-default plan is the best plan for most workloads, leaving only S to pick);
-with the least calibration it needs charged (one build and one launch per
-batch size) it is far behind."""
+workload at the default plan, depth 1: it cannot choose a plan or a
+temporal depth).  The analytic picker also needs the workload's own build
+and run times at six batch sizes; it is reported with that calibration free
+and with the least of it charged (one build and one launch per batch
+size)."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -41,8 +41,12 @@ def test_learned_picker_within_5pct_and_beats_analytic():
     assert s["learned"]["mean"] <= 0.05
     assert s["learned"]["mean"] < 0.5 * s["fixed_S100"]["mean"]
     assert s["learned"]["p95"] < 0.5 * s["fixed_S100"]["p95"]
-    # the analytic model needs measurements of each new workload; charged
-    # for them it loses to the pick that needs none
+    # the analytic model picks S at the default plan (depth 1) and cannot
+    # choose a plan or temporal depth: its misses are large where another
+    # wins, so even with its calibration free the learned picks halve its
+    # mean and its tail
+    assert s["learned"]["mean"] < 0.5 * s["analytic"]["mean"]
+    assert s["learned"]["p95"] < 0.5 * s["analytic"]["p95"]
+    # and it needs measurements of each new workload: charged for them it
+    # loses by far to the pick that needs none
     assert s["learned"]["mean"] < 0.1 * s["analytic_with_calibration"]["mean"]
-    # free calibration: within two percentage points of the analytic picker
-    assert s["learned"]["mean"] < s["analytic"]["mean"] + 0.02
