@@ -56,7 +56,8 @@ WORKLOADS = {
     "fdtd-256": dict(kind="fdtd", N=256, iters=500, S=100, depth=1, plan=dict(kernel=4, rows=2)),
     "fdtd-media-256": dict(kind="fdtd", N=256, iters=500, S=100, depth=1, plan=dict(kernel=4, rows=2),
                            media=dict(n_mat=8, n_boxes=24, seed=0)),
-    "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=1, plan={}),
+    # fused launches of temporal depth 2 (COLUMN tiles): 1.55x depth 1
+    "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=2, plan=dict(kernel=4, rows=2)),
 }
 DEFAULT = "heat3d-512x512x8"
 METRIC = "cell-updates/s (graph-batched)"
@@ -376,6 +377,9 @@ class MultiRunner:
         self.ctx = None
         self.fields = g.MultiFields(self.m, self.sides, self.sides)
         mp = {k: v for k, v in plan_extra.items() if k in ("block_x", "rows", "use_pdl", "kernel", "traverse")}
+        if depth > 1:
+            mp["temporal_depth"] = depth
+            self.depth = depth
         if mp:
             g.gs_multi_set_plan(self.m, **mp)
         self.inputs = gs_inputs.instance_fields(self.sides)
@@ -395,7 +399,7 @@ class MultiRunner:
             g.gs_multi_step(self.m, self.w["iters"], S, g.GS_MULTI_FUSED)
 
     def one_launch(self):
-        self.g.gs_multi_step(self.m, 1, 0, self.g.GS_MULTI_FUSED)
+        self.g.gs_multi_step(self.m, self.depth, 0, self.g.GS_MULTI_FUSED)
 
     def read(self):
         g = self.g
@@ -403,7 +407,8 @@ class MultiRunner:
                 enumerate(self.inputs)]
 
     def launches_per_step(self, S):
-        return self.w["iters"] if S > 0 else self.w["iters"] * len(self.sides)
+        it, t = self.w["iters"], self.depth
+        return (it // t + it % t) if S > 0 else it * len(self.sides)
 
     def graph_build(self, S):
         self.step(S)  # first use captures the graphs
@@ -685,6 +690,7 @@ def main():
                               ("heat3d-256", {}, "column"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-media-256", {}, "column"),
+                              ("multi-64", {}, "column2"),
                               ("heat2d-512", dict(depth=4, kernel=4, block_x=256), "column4"),
                               ("heat2d-4096", {}, "depth1"),
                               ("heat2d-4096", dict(depth=2, kernel=4, block_x=64), "column2"),

@@ -545,6 +545,11 @@ typedef struct gs_multi_plan {
                         threads, one row per warp row) */
     int32_t traverse; /* gs_traverse (0: AUTO, on the batch's total bytes); the
                          reversed launches take the work items last to first */
+    int32_t temporal_depth; /* 1 (0: default), 2 or 4 with GS_KERNEL_COLUMN:
+                               each fused launch advances every instance that
+                               many steps (the depth-t COLUMN tile); n mod t
+                               steps run as depth-1 launches.  Results are
+                               bit-identical to depth 1. */
 } gs_multi_plan;
 
 /* Create a batch of n instances, instance i of size nx[i] x ny[i] (each in

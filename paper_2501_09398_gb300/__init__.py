@@ -70,7 +70,8 @@ class gs_plan(ctypes.Structure):
 
 
 class gs_multi_plan(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "blocks", "use_pdl", "kernel", "traverse")]
+    _fields_ = [(n, ctypes.c_int32) for n in ("block_x", "rows", "blocks", "use_pdl", "kernel", "traverse",
+                                              "temporal_depth")]
 
 
 class gs_tune_candidate(ctypes.Structure):
@@ -504,8 +505,8 @@ def gs_multi_set_heat_coeffs(m, k=0.5, cx=0.1, cy=0.1, cz=0.01, cz2=0.05, t_amb=
     _mcheck(_lib.gs_multi_set_heat_coeffs(m, ctypes.byref(c)), m)
 
 
-def gs_multi_set_plan(m, block_x=0, rows=0, blocks=0, use_pdl=0, kernel=0, traverse=0) -> None:
-    p = gs_multi_plan(block_x, rows, blocks, use_pdl, kernel, traverse)
+def gs_multi_set_plan(m, block_x=0, rows=0, blocks=0, use_pdl=0, kernel=0, traverse=0, temporal_depth=0) -> None:
+    p = gs_multi_plan(block_x, rows, blocks, use_pdl, kernel, traverse, temporal_depth)
     _mcheck(_lib.gs_multi_set_plan(m, ctypes.byref(p)), m)
 
 

@@ -243,8 +243,12 @@ size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth);
 size_t heat_wave_smem(int nz3d, int depth, int vec);
 size_t heat_scol_smem(int nzm, int rows, int vec);
 // heat_multi_kernel for (dt, bc) with MARCH tiles (blockDim.x threads x
-// `rows` rows) or COLUMN tiles (32 x `rows` threads, one row per warp row).
-const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant);
+// `rows` rows) or COLUMN tiles (32 x `rows` threads, one row per warp row),
+// the latter also at temporal depth 2 or 4 (NULL for other combinations).
+const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant, int depth = 1);
+// Cells along x and rows along y of one work item of that kernel.
+int heat_multi_span(gs_dtype dt, int variant, int depth, int block_x);
+int heat_multi_item_rows(gs_dtype dt, int variant, int depth, int rows);
 // FDTD H (e_half false) or E kernel; variant GS_KERNEL_COLUMN (no march,
 // block (32, kc, 8/kc)) or GS_KERNEL_MARCH (block_x threads marching kc planes).
 cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out);

@@ -284,6 +284,14 @@ __global__ void __launch_bounds__(512) heat_step_kernel(const HeatArgs a) {
 
 template <typename ST, int BC, int NZM, int W = Vec<ST>::N>
 __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int by);
+template <typename ST, int BC, int T, int R>
+__device__ __forceinline__ void heat_column_t_tile(const HeatArgs& a, int bx, int by);
+
+// Output rows per thread of the depth-T column kernel (register budget).
+template <typename ST>
+__host__ __device__ constexpr int column_t_rows() {
+    return Vec<ST>::N == 4 ? 4 : 2;
+}
 
 // ------------------------------------------------- multi-instance (2D) ----
 //
@@ -292,11 +300,15 @@ __device__ __forceinline__ void heat_column_tile(const HeatArgs& a, int bx, int 
 // first; block b takes items b, b + gridDim.x, ...  The descriptor table
 // (per instance: both buffers, P, sizes, pitches, first work item) lives in
 // device memory; `parity` selects which buffer is read.
-template <typename ST, int BC, bool COL>
+// KIND: 0 MARCH tiles (blockDim.x threads marching `rows` rows), 1 COLUMN
+// tiles (32 x blockDim.y threads, one row per warp row), 2 or 4: COLUMN
+// tiles of that temporal depth (30 stored vectors x column_t_rows() rows per
+// warp row; the launch advances every instance that many steps).
+template <typename ST, int BC, int KIND>
 __global__ void __launch_bounds__(512) heat_multi_kernel(const MultiArgs m) {
     pdl_wait_then_trigger();
     const int V = Vec<ST>::N;
-    const int span = (COL ? 32 : blockDim.x) * V;
+    const int span = (KIND == 0 ? (int)blockDim.x * V : KIND == 1 ? 32 * V : 30 * V);
     for (int w0 = blockIdx.x; w0 < m.total_items; w0 += gridDim.x) {
         const int w = m.rev ? m.total_items - 1 - w0 : w0;
         // binary search: last instance whose first item <= w
@@ -321,8 +333,9 @@ __global__ void __launch_bounds__(512) heat_multi_kernel(const MultiArgs m) {
         a.c = m.c;
         const int ntx = (d.nx + span - 1) / span;
         const int item = w - d.first_item;
-        if (COL) heat_column_tile<ST, BC, 1>(a, item % ntx, item / ntx);
-        else heat_march_tile<ST, BC, false>(a, item % ntx, item / ntx, 0, nullptr);
+        if constexpr (KIND == 0) heat_march_tile<ST, BC, false>(a, item % ntx, item / ntx, 0, nullptr);
+        else if constexpr (KIND == 1) heat_column_tile<ST, BC, 1>(a, item % ntx, item / ntx);
+        else heat_column_t_tile<ST, BC, KIND, column_t_rows<ST>()>(a, item % ntx, item / ntx);
     }
 }
 
@@ -884,17 +897,15 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
 // every grid edge (warp-uniform) update without boundary selects in packed
 // f32x2 arithmetic.  Block (32, BY): BY warps stacked in y.
 template <typename ST, int BC, int T, int R>
-__global__ void __launch_bounds__(256) heat_column_t_kernel(const HeatArgs a) {
+__device__ __forceinline__ void heat_column_t_tile(const HeatArgs& a, int bx, int by) {
     constexpr int V = Vec<ST>::N;
     constexpr int NR = R + 2 * T;
     static_assert(T >= 1 && T <= V, "halo lane must cover T cells");
-    pdl_wait_then_trigger();
-    const uint3 blk = block_index(a.rev);
     const int lane = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
-    const int xs = (int)blk.x * 30 * V - V;  // global x of lane 0, element 0
-    const int x0 = xs + lane * V;            // this lane's first cell
-    const int y0 = ((int)blk.y * (int)blockDim.y + (int)threadIdx.y) * R;
+    const int xs = bx * 30 * V - V;  // global x of lane 0, element 0
+    const int x0 = xs + lane * V;    // this lane's first cell
+    const int y0 = (by * (int)blockDim.y + (int)threadIdx.y) * R;
     const int xc = min(max(x0, 0), (nx - 1) / V * V);  // a vector inside the row
     const long long pitch = a.pitch;
     const ST* __restrict__ Tin = static_cast<const ST*>(a.Tin);
@@ -968,32 +979,52 @@ __global__ void __launch_bounds__(256) heat_column_t_kernel(const HeatArgs a) {
     }
 }
 
-// Output rows per thread of the depth-T column kernel (register budget).
-template <typename ST>
-constexpr int column_t_rows() {
-    return Vec<ST>::N == 4 ? 4 : 2;
+template <typename ST, int BC, int T, int R>
+__global__ void __launch_bounds__(256) heat_column_t_kernel(const HeatArgs a) {
+    pdl_wait_then_trigger();
+    const uint3 blk = block_index(a.rev);
+    heat_column_t_tile<ST, BC, T, R>(a, (int)blk.x, (int)blk.y);
 }
+
 
 // ------------------------------------------------------------- factory ----
 
 namespace {
-template <bool COL>
+template <int KIND>
 const void* multi_func(gs_dtype dt, gs_bc bc) {
     const bool cl = (bc == GS_BC_CLAMP);
     switch (dt) {
-        case GS_F32: return cl ? (const void*)heat_multi_kernel<float, GS_BC_CLAMP, COL>
-                               : (const void*)heat_multi_kernel<float, GS_BC_DIRICHLET0, COL>;
-        case GS_BF16: return cl ? (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_CLAMP, COL>
-                                : (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_DIRICHLET0, COL>;
-        case GS_F16: return cl ? (const void*)heat_multi_kernel<__half, GS_BC_CLAMP, COL>
-                               : (const void*)heat_multi_kernel<__half, GS_BC_DIRICHLET0, COL>;
+        case GS_F32: return cl ? (const void*)heat_multi_kernel<float, GS_BC_CLAMP, KIND>
+                               : (const void*)heat_multi_kernel<float, GS_BC_DIRICHLET0, KIND>;
+        case GS_BF16: return cl ? (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_CLAMP, KIND>
+                                : (const void*)heat_multi_kernel<__nv_bfloat16, GS_BC_DIRICHLET0, KIND>;
+        case GS_F16: return cl ? (const void*)heat_multi_kernel<__half, GS_BC_CLAMP, KIND>
+                               : (const void*)heat_multi_kernel<__half, GS_BC_DIRICHLET0, KIND>;
     }
     return nullptr;
 }
 }  // namespace
 
-const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant) {
-    return variant == GS_KERNEL_COLUMN ? multi_func<true>(dt, bc) : multi_func<false>(dt, bc);
+const void* heat_multi_func(gs_dtype dt, gs_bc bc, int variant, int depth) {
+    if (variant != GS_KERNEL_COLUMN) return depth == 1 ? multi_func<0>(dt, bc) : nullptr;
+    switch (depth) {
+        case 1: return multi_func<1>(dt, bc);
+        case 2: return multi_func<2>(dt, bc);
+        case 4: return multi_func<4>(dt, bc);
+    }
+    return nullptr;
+}
+
+int heat_multi_span(gs_dtype dt, int variant, int depth, int block_x) {
+    const int V = (dt == GS_F32) ? 4 : 8;
+    if (variant != GS_KERNEL_COLUMN) return block_x * V;
+    return depth > 1 ? 30 * V : 32 * V;
+}
+
+int heat_multi_item_rows(gs_dtype dt, int variant, int depth, int rows) {
+    if (variant == GS_KERNEL_COLUMN && depth > 1)
+        return rows * ((dt == GS_F32) ? column_t_rows<float>() : column_t_rows<__half>());
+    return rows;
 }
 
 size_t heat_scol_smem(int nzm, int rows, int vec) { return (size_t)(rows + 2) * nzm * 32 * vec * sizeof(float); }

@@ -30,10 +30,10 @@ struct gs_multi {
     gs_heat_coeffs hc{0.5f, 0.1f, 0.1f, 0.01f, 0.05f, 80.0f};
     gs_multi_plan plan{};
     int parity = 0;
-    MultiInstance* d_desc = nullptr;  // device descriptor table
-    int total_items = 0;
+    MultiInstance* d_desc = nullptr;    // device descriptor table (depth-1 items)
+    MultiInstance* d_desc_t = nullptr;  // the same for the depth-t items
     bool table_ok = false;
-    LaunchDesc desc[2];
+    LaunchDesc desc[2], desc_t[2];
     std::map<std::pair<int64_t, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
     gs_stats stats{};
     std::string err;
@@ -77,17 +77,18 @@ void invalidate(gs_multi* m) {
 
 int vec_elems(gs_dtype dt) { return dt == GS_F32 ? 4 : 8; }
 
-// Build the descriptor table (largest instances first) and the two launch
-// descriptors (one per buffer parity).
-gs_status ensure_table(gs_multi* m) {
-    if (m->table_ok) return GS_OK;
+// Build one descriptor table (largest instances first) for work items of
+// kernel `variant` at temporal depth `depth`, and its two launch descriptors
+// (one per buffer parity).
+gs_status build_table(gs_multi* m, int variant, int depth, MultiInstance** d_table, LaunchDesc (&desc)[2]) {
     const int n = (int)m->inst.size();
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return m->nx[a] * m->ny[a] > m->nx[b] * m->ny[b]; });
-    const bool col = (m->plan.kernel == GS_KERNEL_COLUMN);
-    const int span = (col ? 32 : m->plan.block_x) * vec_elems(m->dt);
+    const bool col = (variant == GS_KERNEL_COLUMN);
+    const int span = heat_multi_span(m->dt, variant, depth, m->plan.block_x);
+    const int item_rows = heat_multi_item_rows(m->dt, variant, depth, m->plan.rows);
     std::vector<MultiInstance> host(n);
     int item = 0;
     double step_bytes = 0.0;  // one step reads T and P and writes T of every instance
@@ -112,19 +113,19 @@ gs_status ensure_table(gs_multi* m) {
         d.nx = (int)m->nx[i];
         d.ny = (int)m->ny[i];
         const int ntx = (d.nx + span - 1) / span;
-        const int nty = (d.ny + m->plan.rows - 1) / m->plan.rows;
+        const int nty = (d.ny + item_rows - 1) / item_rows;
         d.first_item = item;
         d.n_items = ntx * nty;
         item += d.n_items;
         step_bytes += (double)ctx_elem_bytes(m->inst[i]) * ((double)pt0 * d.ny * 2 + (double)pp * d.ny);
     }
     const bool alt = traverse_alternates(m->plan.traverse, step_bytes);
-    if (!m->d_desc) GS_MCUDA(m, cudaMalloc(&m->d_desc, sizeof(MultiInstance) * n));
-    GS_MCUDA(m, cudaMemcpyAsync(m->d_desc, host.data(), sizeof(MultiInstance) * n, cudaMemcpyHostToDevice,
+    if (!*d_table) GS_MCUDA(m, cudaMalloc(d_table, sizeof(MultiInstance) * n));
+    GS_MCUDA(m, cudaMemcpyAsync(*d_table, host.data(), sizeof(MultiInstance) * n, cudaMemcpyHostToDevice,
                                 m->stream));
     GS_MCUDA(m, cudaStreamSynchronize(m->stream));
-    m->total_items = item;
-    const void* f = heat_multi_func(m->dt, m->bc, m->plan.kernel);
+    const void* f = heat_multi_func(m->dt, m->bc, variant, depth);
+    if (!f) return mfail(m, GS_ERR_UNSUPPORTED, "no instance-batch kernel for this plan");
     const dim3 block = col ? dim3(32, m->plan.rows, 1) : dim3(m->plan.block_x, 1, 1);
     int blocks = m->plan.blocks;
     if (blocks <= 0) {
@@ -135,26 +136,38 @@ gs_status ensure_table(gs_multi* m) {
     blocks = std::max(1, std::min(blocks, item));
     for (int par = 0; par < 2; ++par) {
         MultiArgs a{};
-        a.desc = m->d_desc;
+        a.desc = *d_table;
         a.n_inst = n;
         a.total_items = item;
         a.rows = m->plan.rows;
         a.parity = par;
         a.rev = (alt && par == 1) ? 1 : 0;
         a.c = HeatCoef{m->hc.k, m->hc.cx, m->hc.cy, m->hc.cz, m->hc.cz2, m->hc.t_amb};
-        LaunchDesc& d = m->desc[par];
+        LaunchDesc& d = desc[par];
         d.func = f;
         d.grid = dim3(blocks, 1, 1);
         d.block = block;
         d.smem = 0;
         d.set_args(a);
     }
+    return GS_OK;
+}
+
+// The depth-1 table and, for a temporally blocked plan, the depth-t one.
+gs_status ensure_table(gs_multi* m) {
+    if (m->table_ok) return GS_OK;
+    gs_status st = build_table(m, m->plan.kernel, 1, &m->d_desc, m->desc);
+    if (st != GS_OK) return st;
+    if (m->plan.temporal_depth > 1) {
+        st = build_table(m, m->plan.kernel, m->plan.temporal_depth, &m->d_desc_t, m->desc_t);
+        if (st != GS_OK) return st;
+    }
     m->table_ok = true;
     return GS_OK;
 }
 
-cudaError_t launch_fused(gs_multi* m, int parity) {
-    LaunchDesc& d = m->desc[parity];
+cudaError_t launch_fused(gs_multi* m, int parity, bool temporal) {
+    LaunchDesc& d = temporal ? m->desc_t[parity] : m->desc[parity];
     void* args[1] = {d.arg_ptr()};
     if (!m->plan.use_pdl) return cudaLaunchKernel(d.func, d.grid, d.block, args, d.smem, m->stream);
     cudaLaunchConfig_t cfg{};
@@ -170,7 +183,29 @@ cudaError_t launch_fused(gs_multi* m, int parity) {
     return cudaLaunchKernelExC(&cfg, d.func, args);
 }
 
-// Record S fused launches from parity p into a graph by stream capture.
+// The fused launches of n iterations from parity p: n / t depth-t launches,
+// then n % t depth-1 launches; each flips the parity.  Returns the launches
+// issued in *count and the final parity in *p_out.
+cudaError_t launch_iterations(gs_multi* m, int64_t n, int p, int64_t* count, int* p_out) {
+    const int t = m->plan.temporal_depth;
+    const int64_t q = (t > 1) ? n / t : 0;
+    const int64_t r = n - q * t;
+    cudaError_t err = cudaSuccess;
+    for (int64_t i = 0; i < q && err == cudaSuccess; ++i, p ^= 1) err = launch_fused(m, p, true);
+    for (int64_t i = 0; i < r && err == cudaSuccess; ++i, p ^= 1) err = launch_fused(m, p, false);
+    *count = q + r;
+    *p_out = p;
+    return err;
+}
+
+int64_t launches_for(const gs_multi* m, int64_t n) {
+    const int t = m->plan.temporal_depth;
+    const int64_t q = (t > 1) ? n / t : 0;
+    return q + (n - q * t);
+}
+
+// Record the launches of S iterations from parity p into a graph by stream
+// capture.
 gs_status capture_graph(gs_multi* m, int64_t S, int p, cudaGraphExec_t* out) {
     auto key = std::make_pair(S, p);
     auto it = m->graphs.find(key);
@@ -179,8 +214,9 @@ gs_status capture_graph(gs_multi* m, int64_t S, int p, cudaGraphExec_t* out) {
         return GS_OK;
     }
     GS_MCUDA(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = cudaSuccess;
-    for (int64_t i = 0; i < S && err == cudaSuccess; ++i) err = launch_fused(m, (p + (int)(i & 1)) & 1);
+    int64_t count = 0;
+    int p_end = p;
+    cudaError_t err = launch_iterations(m, S, p, &count, &p_end);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(m->stream, &g);
     if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -230,6 +266,7 @@ gs_status gs_multi_create(gs_multi** out, int32_t n, const int64_t* nx, const in
     m->plan.block_x = 64;
     m->plan.rows = 8;
     m->plan.kernel = GS_KERNEL_MARCH;
+    m->plan.temporal_depth = 1;
     cudaError_t e = cudaSuccess;
     if (stream) {
         m->stream = static_cast<cudaStream_t>(stream);
@@ -262,6 +299,7 @@ gs_status gs_multi_destroy(gs_multi* m) {
     drop_graphs(m);
     for (gs_ctx* c : m->inst) gs_destroy(c);
     if (m->d_desc) cudaFree(m->d_desc);
+    if (m->d_desc_t) cudaFree(m->d_desc_t);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
     return GS_OK;
@@ -298,6 +336,11 @@ gs_status gs_multi_set_plan(gs_multi* m, const gs_multi_plan* p) {
         return mfail(m, GS_ERR_INVALID_ARG, "rows >= 1, blocks >= 0, use_pdl in {0, 1}");
     if (q.traverse < GS_TRAVERSE_AUTO || q.traverse > GS_TRAVERSE_ALTERNATE)
         return mfail(m, GS_ERR_INVALID_ARG, "traverse must be a gs_traverse value");
+    if (q.temporal_depth == 0) q.temporal_depth = 1;
+    if (q.temporal_depth != 1 && q.temporal_depth != 2 && q.temporal_depth != 4)
+        return mfail(m, GS_ERR_INVALID_ARG, "temporal_depth must be 1, 2 or 4");
+    if (q.temporal_depth > 1 && q.kernel != GS_KERNEL_COLUMN)
+        return mfail(m, GS_ERR_INVALID_ARG, "temporal_depth > 1 runs COLUMN tiles only");
     gs_plan sp{};
     sp.block_x = q.block_x;
     sp.rows = q.rows;
@@ -359,11 +402,11 @@ gs_status gs_multi_step(gs_multi* m, int64_t n_iters, int64_t batch_size, gs_mul
     gs_status st = ensure_table(m);
     if (st != GS_OK) return st;
     if (batch_size == 0) {
-        for (int64_t k = 0; k < n_iters; ++k) {
-            GS_MCUDA(m, launch_fused(m, m->parity));
-            m->parity ^= 1;
-        }
-        m->stats.kernel_launches += n_iters;
+        int64_t count = 0;
+        int p_end = m->parity;
+        GS_MCUDA(m, launch_iterations(m, n_iters, m->parity, &count, &p_end));
+        m->parity = p_end;
+        m->stats.kernel_launches += count;
     } else {
         const int64_t nb = n_iters / batch_size, r = n_iters % batch_size;
         for (int64_t b = 0; b < nb; ++b) {
@@ -372,7 +415,7 @@ gs_status gs_multi_step(gs_multi* m, int64_t n_iters, int64_t batch_size, gs_mul
             if (st != GS_OK) return st;
             GS_MCUDA(m, cudaGraphLaunch(ex, m->stream));
             m->stats.graph_launches += 1;
-            m->parity ^= (int)(batch_size & 1);
+            m->parity ^= (int)(launches_for(m, batch_size) & 1);
         }
         if (r) {
             cudaGraphExec_t ex;
@@ -380,7 +423,7 @@ gs_status gs_multi_step(gs_multi* m, int64_t n_iters, int64_t batch_size, gs_mul
             if (st != GS_OK) return st;
             GS_MCUDA(m, cudaGraphLaunch(ex, m->stream));
             m->stats.graph_launches += 1;
-            m->parity ^= (int)(r & 1);
+            m->parity ^= (int)(launches_for(m, r) & 1);
         }
     }
     // keep each instance context's view of the current buffer in step

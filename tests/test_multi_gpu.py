@@ -62,6 +62,41 @@ def test_small_batch_all_modes_bit_identical(oracle):
             assert st["graph_launches"] == n // S + (1 if n % S else 0)
 
 
+@pytest.mark.parametrize("depth", [2, 4])
+def test_temporal_depth_bit_identical(depth):
+    # each fused launch advances every instance `depth` steps with the
+    # temporally blocked COLUMN tile; n mod depth steps run at depth 1
+    import paper_2501_09398_gb300 as g
+
+    dims = [(130, 17), (5, 9), (64, 64), (200, 3), (1, 1), (77, 120), (300, 41)]
+    fields_np = [gs_inputs.heat_fields(w, h, 1, seed=350 + i) for i, (w, h) in enumerate(dims)]
+    n = 23
+    base, _ = _run(None, fields_np, n, 0, g.GS_MULTI_SEPARATE, dims=dims)
+    for S, plan in ((0, dict(rows=4)), (7, dict(rows=2)), (8, dict(rows=8, blocks=5)), (23, dict(rows=1)),
+                    (5, dict(rows=4, traverse=g.GS_TRAVERSE_ALTERNATE))):
+        plan = dict(plan, kernel=g.GS_KERNEL_COLUMN, temporal_depth=depth)
+        got, st = _run(None, fields_np, n, S, g.GS_MULTI_FUSED, plan=plan, dims=dims)
+        assert all(np.array_equal(a, b) for a, b in zip(got, base)), (S, plan)
+        if S == 0:
+            assert st["kernel_launches"] == n // depth + n % depth
+
+
+def test_temporal_depth_plan_errors():
+    import torch
+
+    import paper_2501_09398_gb300 as g
+
+    m = g.gs_multi_create([16, 8], [16, 8], g.GS_F32, g.GS_BC_CLAMP, torch.cuda.Stream().cuda_stream)
+    try:
+        with pytest.raises(g.GsError):
+            g.gs_multi_set_plan(m, kernel=g.GS_KERNEL_MARCH, temporal_depth=2)
+        with pytest.raises(g.GsError):
+            g.gs_multi_set_plan(m, kernel=g.GS_KERNEL_COLUMN, temporal_depth=3)
+        g.gs_multi_set_plan(m, kernel=g.GS_KERNEL_COLUMN, temporal_depth=4)
+    finally:
+        g.gs_multi_destroy(m)
+
+
 def test_unbound_instance_is_a_state_error():
     import torch
 
