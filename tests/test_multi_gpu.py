@@ -124,6 +124,10 @@ def test_config3_batch(oracle):
     fused, _ = _run(sides, fields_np, n, 100, g.GS_MULTI_FUSED)
     sep, _ = _run(sides, fields_np, n, 0, g.GS_MULTI_SEPARATE)
     assert all(np.array_equal(a, b) for a, b in zip(fused, sep))
+    # the bench's plan: fused launches of temporal depth 2, COLUMN tiles of 2 rows
+    fused2, _ = _run(sides, fields_np, n, 100, g.GS_MULTI_FUSED,
+                     plan=dict(kernel=g.GS_KERNEL_COLUMN, rows=2, temporal_depth=2))
+    assert all(np.array_equal(a, b) for a, b in zip(fused2, sep))
     order = np.argsort(sides)
     for i in list(order[:6]) + [order[-1]]:
         T, P = fields_np[i]
