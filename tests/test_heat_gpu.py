@@ -175,6 +175,9 @@ def test_config0_full_size(oracle):
     print(f"config0 max rel err {err:.3e}")
     assert err <= HEAT_RTOL
     assert np.array_equal(heat_gpu(T0, P, 1000, S=0), got)
+    # the column kernel at temporal depth 2 and 4 (AUTO in 2D)
+    for depth in (2, 4):
+        assert np.array_equal(heat_gpu(T0, P, 1000, S=100, plan=dict(temporal_depth=depth, block_x=256)), got)
 
 
 def test_config1_full_size(oracle):
@@ -201,6 +204,8 @@ def test_large_2d_sampled(oracle):
     # and the grid's own corner, where the clamp boundary is inside the window
     sub = oracle.heat_run(T0[-w:, -w:], P[-w:, -w:], n, oracle.HEAT_COEFFS_2D)
     assert max_rel(got[-w + n:, -w + n:], sub[n:, n:]) <= HEAT_RTOL
+    # the bench's temporally blocked plan (column kernel, depth 2) gives the same bits
+    assert np.array_equal(heat_gpu(T0, P, 40, S=20, plan=dict(temporal_depth=2, block_x=64)), got)
 
 
 def test_zero_iterations_and_state_errors():
