@@ -192,6 +192,20 @@ def test_config1_full_size(oracle):
         assert np.array_equal(heat_gpu(T0, P, 1000, S=100, plan=dict(temporal_depth=depth)), got)
 
 
+def test_deep_stack_full_size(oracle):
+    # 256^3: the column kernel in 8-plane chunks (the default above 8 planes)
+    # against the oracle, and bit for bit against the MARCH kernel
+    import paper_2501_09398_gb300 as g
+
+    T0, P = gs_inputs.heat_fields(256, 256, 256, seed=0)
+    n = 12
+    got = heat_gpu(T0, P, n, S=5)
+    ref = oracle.heat_run(T0, P, n, oracle.HEAT_COEFFS_3D)
+    assert max_rel(got, ref) <= HEAT_RTOL
+    march = heat_gpu(T0, P, n, S=0, plan=dict(kernel=g.GS_KERNEL_MARCH, block_x=64, rows=8))
+    assert np.array_equal(march, got)
+
+
 def test_large_2d_sampled(oracle):
     # 4096^2 at the bench's launch shape: the oracle checks a 40-step run on
     # a 160x160 window whose dependence cone (radius 40) stays inside it.
