@@ -88,6 +88,23 @@ __device__ __forceinline__ void load_vecw(const ST* __restrict__ p, float (&v)[W
     }
 }
 
+// W elements per access through the coherent path (for in-place updates).
+template <typename ST, int W>
+__device__ __forceinline__ void load_vecw_rw(const ST* p, float (&v)[W]) {
+    static_assert(W * sizeof(ST) == 8 || W * sizeof(ST) == 16, "8- or 16-byte access");
+    if constexpr (W * sizeof(ST) == 16) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(p);
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
+    } else {
+        const uint2 raw = *reinterpret_cast<const uint2*>(p);
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
+    }
+}
+
 // W consecutive uint8 ids (W = 4 or 8: a 4- or 8-byte access).
 template <int W>
 __device__ __forceinline__ void load_ids(const unsigned char* __restrict__ p, unsigned (&id)[W]) {

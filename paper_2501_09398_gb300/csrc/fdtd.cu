@@ -22,6 +22,9 @@ namespace gs {
 
 enum { EX = 0, EY = 1, EZ = 2, HX = 3, HY = 4, HZ = 5 };
 
+// Cells along i per thread of the column kernels, in every storage type.
+constexpr int kFdtdColumnCells = 4;
+
 // f -/+ s*((a - b) - (c - d)) with every rounding spelled out, so that both
 // kernel variants produce the same bits.
 __device__ __forceinline__ float curl_sub(float f, float s, float a, float b, float c, float d) {
@@ -208,7 +211,9 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
 
 // ------------------------------------------------------------- column ----
 //
-// No march: each thread owns one 16-byte vector along i at one (j, k) and
+// No march: each thread owns four cells along i (a 16-byte f32 or an 8-byte
+// bf16/f16 access, so that a warp spans 128 cells in every storage type and
+// N = 128, 256 take the aligned layout below) at one (j, k) and
 // issues all of its loads at once (own components, the k+1 / j+1 (H) or
 // k-1 / j-1 (E) neighbour vectors, and the i-edge scalars of lanes 31 / 0).
 // Block (32, by, bz); neighbour vectors are re-read through L1/L2.
@@ -256,7 +261,7 @@ __device__ __forceinline__ void fdtd_source(const FdtdArgs& a, int lane, int i0,
 template <typename ST, bool MAT, bool FAST, bool EXTRA>
 __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const float2* s_med, int lane, int i0, int j,
                                                    int k) {
-    constexpr int V = Vec<ST>::N;
+    constexpr int V = kFdtdColumnCells;
     const int N = a.N, M = N + 1;
     const bool act = FAST || ((i0 < M) && (j < M) && (k < M));
     const ST* Ex = static_cast<const ST*>(a.f[EX]);
@@ -275,16 +280,16 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
     unsigned id_x = 0;
     if constexpr (FAST) {
         if constexpr (MAT) load_ids<V>(a.mat + o, id);
-        load_vec(Ex + o, exk);
-        load_vec(Ey + o, eyk);
-        load_vec(Ez + o, ez);
-        load_vec(Ex + o + a.plane, exk1);
-        load_vec(Ey + o + a.plane, eyk1);
-        load_vec(Ez + o + a.pitch, ezj1);
-        load_vec(Ex + o + a.pitch, exj1);
-        load_vec_rw(Hx + o, hx);
-        load_vec_rw(Hy + o, hy);
-        load_vec_rw(Hz + o, hz);
+        load_vecw<ST, V>(Ex + o, exk);
+        load_vecw<ST, V>(Ey + o, eyk);
+        load_vecw<ST, V>(Ez + o, ez);
+        load_vecw<ST, V>(Ex + o + a.plane, exk1);
+        load_vecw<ST, V>(Ey + o + a.plane, eyk1);
+        load_vecw<ST, V>(Ez + o + a.pitch, ezj1);
+        load_vecw<ST, V>(Ex + o + a.pitch, exj1);
+        load_vecw_rw<ST, V>(Hx + o, hx);
+        load_vecw_rw<ST, V>(Hy + o, hy);
+        load_vecw_rw<ST, V>(Hz + o, hz);
         if (lane == 31) {  // i0 + V <= N: in range
             ez_r = load_scalar(Ez + o + V);
             ey_r = load_scalar(Ey + o + V);
@@ -304,20 +309,20 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
         }
         if (act) {
             if constexpr (MAT) load_ids<V>(a.mat + o, id);
-            load_vec(Ex + o, exk);
-            load_vec(Ey + o, eyk);
-            load_vec(Ez + o, ez);
+            load_vecw<ST, V>(Ex + o, exk);
+            load_vecw<ST, V>(Ey + o, eyk);
+            load_vecw<ST, V>(Ez + o, ez);
             if (k + 1 < M) {
-                load_vec(Ex + o + a.plane, exk1);
-                load_vec(Ey + o + a.plane, eyk1);
+                load_vecw<ST, V>(Ex + o + a.plane, exk1);
+                load_vecw<ST, V>(Ey + o + a.plane, eyk1);
             }
             if (j + 1 < M) {
-                load_vec(Ez + o + a.pitch, ezj1);
-                load_vec(Ex + o + a.pitch, exj1);
+                load_vecw<ST, V>(Ez + o + a.pitch, ezj1);
+                load_vecw<ST, V>(Ex + o + a.pitch, exj1);
             }
-            load_vec_rw(Hx + o, hx);
-            load_vec_rw(Hy + o, hy);
-            load_vec_rw(Hz + o, hz);
+            load_vecw_rw<ST, V>(Hx + o, hx);
+            load_vecw_rw<ST, V>(Hy + o, hy);
+            load_vecw_rw<ST, V>(Hz + o, hz);
             if (lane == 31 && i0 + V < M) {
                 ez_r = load_scalar(Ez + o + V);
                 ey_r = load_scalar(Ey + o + V);
@@ -349,9 +354,9 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
         }
     }
     const int nv = FAST ? V : M - i0;
-    store_vec(Hx + o, hx, nv);
-    store_vec(Hy + o, hy, nv);
-    store_vec(Hz + o, hz, nv);
+    store_vecw<ST, V>(Hx + o, hx, nv);
+    store_vecw<ST, V>(Hy + o, hy, nv);
+    store_vecw<ST, V>(Hz + o, hz, nv);
     if constexpr (EXTRA) {
         if (lane == 31) {
             if constexpr (MAT) hx_x = curl_sub_m(hx_x, s_med[id_x], ezj1_x, ez_r, eyk1_x, ey_r);
@@ -364,7 +369,7 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
 template <typename ST, bool MAT, bool FAST, bool ALN>
 __device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const float2* s_med, int lane, int i0, int j,
                                                    int k) {
-    constexpr int V = Vec<ST>::N;
+    constexpr int V = kFdtdColumnCells;
     const int N = a.N, M = N + 1;
     const bool act = FAST || ((i0 < M) && (j < M) && (k < M));
     ST* Ex = static_cast<ST*>(a.f[EX]);
@@ -380,16 +385,16 @@ __device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const floa
     float hz_l = 0.f, hy_l = 0.f;
     if constexpr (FAST) {
         if constexpr (MAT) load_ids<V>(a.mat + o, id);
-        load_vec(Hx + o, hx);
-        load_vec(Hy + o, hy);
-        load_vec(Hz + o, hz);
-        load_vec(Hx + o - a.plane, hxk_1);
-        load_vec(Hy + o - a.plane, hyk_1);
-        load_vec(Hz + o - a.pitch, hzj_1);
-        load_vec(Hx + o - a.pitch, hxj_1);
-        load_vec_rw(Ex + o, ex);
-        load_vec_rw(Ey + o, ey);
-        load_vec_rw(Ez + o, ez);
+        load_vecw<ST, V>(Hx + o, hx);
+        load_vecw<ST, V>(Hy + o, hy);
+        load_vecw<ST, V>(Hz + o, hz);
+        load_vecw<ST, V>(Hx + o - a.plane, hxk_1);
+        load_vecw<ST, V>(Hy + o - a.plane, hyk_1);
+        load_vecw<ST, V>(Hz + o - a.pitch, hzj_1);
+        load_vecw<ST, V>(Hx + o - a.pitch, hxj_1);
+        load_vecw_rw<ST, V>(Ex + o, ex);
+        load_vecw_rw<ST, V>(Ey + o, ey);
+        load_vecw_rw<ST, V>(Ez + o, ez);
         if (lane == 0) {  // the i = 0 cell's west value is never used: clamp the address
             const int dw = (i0 > 0) ? -1 : 0;
             hz_l = load_scalar(Hz + o + dw);
@@ -404,20 +409,20 @@ __device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const floa
         }
         if (act) {
             if constexpr (MAT) load_ids<V>(a.mat + o, id);
-            load_vec(Hx + o, hx);
-            load_vec(Hy + o, hy);
-            load_vec(Hz + o, hz);
+            load_vecw<ST, V>(Hx + o, hx);
+            load_vecw<ST, V>(Hy + o, hy);
+            load_vecw<ST, V>(Hz + o, hz);
             if (k >= 1) {
-                load_vec(Hx + o - a.plane, hxk_1);
-                load_vec(Hy + o - a.plane, hyk_1);
+                load_vecw<ST, V>(Hx + o - a.plane, hxk_1);
+                load_vecw<ST, V>(Hy + o - a.plane, hyk_1);
             }
             if (j >= 1) {
-                load_vec(Hz + o - a.pitch, hzj_1);
-                load_vec(Hx + o - a.pitch, hxj_1);
+                load_vecw<ST, V>(Hz + o - a.pitch, hzj_1);
+                load_vecw<ST, V>(Hx + o - a.pitch, hxj_1);
             }
-            load_vec_rw(Ex + o, ex);
-            load_vec_rw(Ey + o, ey);
-            load_vec_rw(Ez + o, ez);
+            load_vecw_rw<ST, V>(Ex + o, ex);
+            load_vecw_rw<ST, V>(Ey + o, ey);
+            load_vecw_rw<ST, V>(Ez + o, ez);
             if (lane == 0 && i0 >= 1) {
                 hz_l = load_scalar(Hz + o - 1);
                 hy_l = load_scalar(Hy + o - 1);
@@ -455,9 +460,9 @@ __device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const floa
     bool extra_src;
     fdtd_source<ST, V, ALN>(a, lane, i0, j, k, o, ez, &extra_src);
     const int nv = FAST ? V : M - i0;
-    store_vec(Ex + o, ex, nv);
-    store_vec(Ey + o, ey, nv);
-    store_vec(Ez + o, ez, nv);
+    store_vecw<ST, V>(Ex + o, ex, nv);
+    store_vecw<ST, V>(Ey + o, ey, nv);
+    store_vecw<ST, V>(Ez + o, ez, nv);
 }
 
 // Stage the media table (rows `base` .. base+255) in shared memory.
@@ -473,7 +478,7 @@ __device__ __forceinline__ void stage_media(const FdtdArgs& a, float2* s_med, in
 
 template <typename ST, bool MAT, bool ALN>
 __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_column_kernel(const FdtdArgs a) {
-    constexpr int V = Vec<ST>::N;
+    constexpr int V = kFdtdColumnCells;
     pdl_wait_then_trigger();
     __shared__ float2 s_med[MAT ? 256 : 1];
     stage_media<MAT>(a, s_med, 0);
@@ -490,7 +495,7 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_
 
 template <typename ST, bool MAT, bool ALN>
 __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_column_kernel(const FdtdArgs a) {
-    constexpr int V = Vec<ST>::N;
+    constexpr int V = kFdtdColumnCells;
     pdl_wait_then_trigger();
     __shared__ float2 s_med[MAT ? 256 : 1];
     stage_media<MAT>(a, s_med, 256);
@@ -524,9 +529,9 @@ const void* fdtd_func(bool e_half, bool col, bool mat, bool aln) {
 }  // namespace
 
 cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out) {
-    const int V = (dt == GS_F32) ? 4 : 8;
-    const int M = a.N + 1;
     const bool col = (variant == GS_KERNEL_COLUMN);
+    const int V = col ? kFdtdColumnCells : ((dt == GS_F32) ? 4 : 8);
+    const int M = a.N + 1;
     const bool mat = (a.mat != nullptr);
     if (mat && !col) return cudaErrorNotSupported;  // media: column kernels only
     // ALN: the warps tile i in [0, N) exactly; lane 31 takes the i = N column
