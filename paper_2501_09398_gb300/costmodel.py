@@ -12,7 +12,7 @@ learned model:
    S in {per-step, 1, 10, 50, 100, 500, 1000}.
 3. ``sweep``: times every candidate on the GPU with ``gs_autotune`` (graph
    build time T_C and milliseconds per iteration); the swept table is both
-   the training data and the judge.
+   the training data and the yardstick of every pick's regret.
 4. ``train``: fits an ensemble of MLPs (``gs_mlp_*``: the library's CUDA
    forward, backward and Adam kernels; different seeds) to log(ms per
    iteration of the whole run), total = T_C + I_k * ms_per_iter; the pick
