@@ -33,3 +33,20 @@ def test_analytic_and_fixed_pickers_run_on_the_sweep(cm):
         ra = cm.regret(w, tab, cm.pick_analytic(w, tab))
         rf = cm.regret(w, tab, cm.pick_fixed(w, tab))
         assert ra >= 0 and rf >= 0
+
+
+def test_calibration_cost_of_the_analytic_picker(cm):
+    # the analytic picker must time every batch size it fits Eqs. 2/6 to:
+    # at least one build and one launch each, i.e. the sum over the default
+    # plan's swept rows of T_C + S * t_iter; charging it can only add regret
+    _, held = cm.load_tables()
+    for w, tab in held[:40]:
+        dp = cm.default_plan(w)
+        rows = [r for r in tab if r["plan"] == dp and r["S"] > 0 and r["status"] == 0]
+        assert len(rows) >= 2
+        expect = sum(r["build_seconds"] * 1e3 + r["S"] * r["ms_per_iter"] for r in rows)
+        assert math.isclose(cm.calibration_ms(w, tab), expect, rel_tol=1e-12)
+        assert cm.calibration_ms(w, tab) > 0
+        # the iterations alone exceed 1 + 10 + 50 + 100 + 500 + 1000 of the fastest plan's
+        fastest = min(r["ms_per_iter"] for r in tab if r["status"] == 0 and math.isfinite(r["ms_per_iter"]))
+        assert cm.calibration_ms(w, tab) >= 1661 * fastest * (1 - 1e-9)
