@@ -78,13 +78,18 @@ def multi_sides(w):
 
 
 def kernel_sha():
-    """First 16 hex digits of sha256 over the thermal kernel sources."""
+    """First 16 hex digits of sha256 over the thermal kernel sources with
+    their comments removed (so an edit of a comment keeps a capture valid)."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for f in ("heat.cu", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2501_09398_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2501_09398_gb300", "csrc", f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(src.encode())
     return h.hexdigest()[:16]
 
 
