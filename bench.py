@@ -79,7 +79,8 @@ def multi_sides(w):
 
 def kernel_sha():
     """First 16 hex digits of sha256 over the thermal kernel sources with
-    their comments removed (so an edit of a comment keeps a capture valid)."""
+    their comments and blank lines removed (so an edit of a comment keeps a
+    capture valid)."""
     import hashlib
     import re
 
@@ -89,6 +90,7 @@ def kernel_sha():
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
+        src = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
         h.update(src.encode())
     return h.hexdigest()[:16]
 

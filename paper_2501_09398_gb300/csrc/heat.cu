@@ -1,7 +1,9 @@
 // Thermal stencil kernels: 2D 5-point and 3D 7-point explicit updates (the
 // roles of Rodinia Hotspot / Hotspot3D in the paper's Sec. III-C), one step
-// per launch (depth 1) or t steps per launch on an overlapped shared-memory
-// tile (temporal blocking, depth 2 or 4).
+// per launch (depth 1: COLUMN, COLUMN_SMEM, MARCH) or t steps per launch
+// (temporal blocking, depth 2 or 4: COLUMN in 2D and WAVE with the levels in
+// registers, TILE on an overlapped shared-memory tile), and the persistent
+// kernel of an instance batch.
 //
 // Update (per cell, FP32):
 //   T' = T + k*(P + cy*(N+S-2T) + cx*(E+W-2T) + cz*(t_amb-T) [+ cz2*(U+D-2T)])
