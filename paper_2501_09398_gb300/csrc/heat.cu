@@ -28,6 +28,15 @@ __device__ __forceinline__ float heat_cell(float t, float n, float s, float w, f
     return __fmaf_rn(c.k, acc, t);
 }
 
+// A level computed inside a temporally blocked launch, rounded to the
+// storage type exactly as a depth-1 launch's store rounds it (identity for
+// f32), so that a depth-t launch equals t depth-1 launches in every storage
+// type.
+template <typename ST>
+__device__ __forceinline__ float as_stored(float v) {
+    return to_f32(from_f32<ST>(v));
+}
+
 // heat_cell for two adjacent cells with Blackwell's packed FP32 pair
 // operations (add/sub/fma .rn.f32x2): each half is rounded exactly as the
 // scalar operation of heat_cell, in the same order, so the results are the
@@ -419,7 +428,7 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
                 u = (iz + 1 < nz) ? bufA[l + area] : bnd<BC>(t);
             }
             const float p = (!IS3D || iz == 0) ? ptile[iy * IX + ix] : 0.0f;
-            bufB[l] = heat_cell<IS3D>(t, n, so, w, e, d, u, p, a.c);
+            bufB[l] = as_stored<ST>(heat_cell<IS3D>(t, n, so, w, e, d, u, p, a.c));
         }
         __syncthreads();
         float* sw = bufA;
@@ -874,7 +883,7 @@ __global__ void __launch_bounds__(512) heat_wave_kernel(const HeatArgs a) {
                 for (int i = 0; i < V; ++i) {
                     win[s][0][i] = win[s][1][i];
                     win[s][1][i] = win[s][2][i];
-                    win[s][2][i] = out[i];
+                    win[s][2][i] = out[i] = as_stored<ST>(out[i]);
                 }
                 if (IS3D) sm_put<V>(wbuf + ((size_t)s * nz + tz) * rowlen, out);
             } else if (st_lane && q >= y0 && q < y0 + R && q < ny) {
@@ -968,7 +977,7 @@ __device__ __forceinline__ void heat_column_t_tile(const HeatArgs& a, int bx, in
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 prev[i] = row[j][i];
-                row[j][i] = out[i];
+                row[j][i] = as_stored<ST>(out[i]);
             }
         }
     }

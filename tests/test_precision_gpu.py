@@ -130,3 +130,53 @@ def test_config2_reduced_precision(fdtd_config2_ref, dtype):
     bound = 2.0 * math.sqrt(n) * UNIT_ROUNDOFF[dtype]
     print(f"config2 {dtype} rel L2 {err:.3e} (bound {bound:.3e})")
     assert err <= bound
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("shape", [(300, 37, 1), (130, 45, 8), (60, 20, 17)])
+def test_temporal_blocking_rounds_every_level(dtype, shape):
+    # a depth-t launch rounds each level it computes to the storage type, as
+    # t depth-1 launches store (and so round) every step: same bits
+    import paper_2501_09398_gb300 as g
+
+    nx, ny, nz = shape
+    T0, P = gs_inputs.heat_fields(nx, ny, nz, seed=41)
+    n = 9  # peels n mod t steps at depth 1
+    base = heat_gpu(T0, P, n, S=0, dtype=dtype, plan=dict(kernel=g.GS_KERNEL_MARCH, block_x=32, rows=5))
+    plans = [dict(kernel=g.GS_KERNEL_TILE, tile_x=16, tile_y=8)]
+    if nz <= 16:
+        plans.append(dict(kernel=g.GS_KERNEL_WAVE, rows=3, block_x=64))
+    if nz == 1:
+        plans.append(dict(kernel=g.GS_KERNEL_COLUMN, block_x=64))
+    for depth in (2, 4):
+        for plan in plans:
+            got = heat_gpu(T0, P, n, S=4, dtype=dtype, plan=dict(plan, temporal_depth=depth))
+            assert np.array_equal(got, base), (depth, plan)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_instance_batch_temporal_depth_reduced_precision(dtype):
+    import paper_2501_09398_gb300 as g
+    from gsutil import stream_handle
+
+    dims = [(130, 17), (300, 41), (64, 64), (5, 9)]
+    fields_np = [gs_inputs.heat_fields(w, h, 1, seed=60 + i) for i, (w, h) in enumerate(dims)]
+    dt = g.DTYPES[dtype]
+    out = []
+    for plan in (None, dict(kernel=g.GS_KERNEL_COLUMN, rows=2, temporal_depth=2),
+                 dict(kernel=g.GS_KERNEL_COLUMN, rows=4, temporal_depth=4)):
+        m = g.gs_multi_create([d[0] for d in dims], [d[1] for d in dims], dt, g.GS_BC_CLAMP, stream_handle())
+        bufs = g.MultiFields(m, [d[0] for d in dims], [d[1] for d in dims], dt)
+        try:
+            if plan:
+                g.gs_multi_set_plan(m, **plan)
+            for i, (T, P) in enumerate(fields_np):
+                g.gs_multi_upload(m, i, g.GS_FIELD_T, T)
+                g.gs_multi_upload(m, i, g.GS_FIELD_P, P)
+            g.gs_multi_step(m, 11, 5, g.GS_MULTI_FUSED)
+            out.append([g.gs_multi_read_field(m, i, g.GS_FIELD_T, np.empty_like(T)) for i, (T, _) in enumerate(fields_np)])
+        finally:
+            g.gs_multi_destroy(m)
+            del bufs
+    for o in out[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(o, out[0]))
