@@ -25,9 +25,12 @@ Parity pins: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms (heat eigenmode decay, uniform relaxation, Yee energy
 invariance, Yee cavity dispersion, the cavity-mode recurrence in a uniform
 lossy medium), invariants (the permittivity-weighted Yee energy in a
-lossless heterogeneous medium) and a brute-force matrix restatement.  The source-driven FDTD field has no closed form; it is pinned
-through the source value, the mirror/swap symmetries and the same scheme's
-source-free pins.
+lossless heterogeneous medium) and a brute-force matrix restatement.  The
+source-driven FDTD field has no closed form; it is pinned through the source
+value, the mirror/swap symmetries, the same scheme's source-free pins and,
+step by step, the discrete energy budget of the soft source
+(W^{n+1} - W^n = g(n) (Ez^{n+1} + Ez^n) at the source); its 5000-step field
+values themselves stay parity unpinned.
 """
 from __future__ import annotations
 

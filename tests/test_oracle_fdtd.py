@@ -14,6 +14,13 @@
 * With the source at the cavity centre the driven field keeps the cavity's
   mirror and x<->y swap symmetries (E a vector, H a pseudovector).
 * Courant number above 1/sqrt(3) is unstable; 0.5 is not.
+* Driven cavity, energy budget: with the soft source added to Ez[src] after
+  the E update of step n (E^{n+1} = E~^{n+1} + g(n) e_src), the adjoint
+  relation of the two curls gives exactly
+  W^{n+1} - W^n = g(n) (Ez^{n+1}[src] + Ez^n[src])
+  at every step, so the source-driven run (which has no closed form) is
+  pinned step by step: a wrong source time, place, amplitude or sign, or a
+  slip in any curl term, breaks it.
 """
 import math
 
@@ -250,3 +257,24 @@ def test_media_swap_symmetry(oracle):
     g = oracle.fdtd_zero_fields(N)
     oracle.fdtd_run(g, N, 90, src=(c, c, c))
     assert np.max(np.abs(g["Ez"] - Ez)) > 1e-3 * scale
+
+
+def test_driven_energy_budget(oracle):
+    N, s_c, amp, delay, width = 14, 0.5, 0.7, 30.0, 10.0
+    src = (7, 6, 8)
+    si, sj, sk = src
+    f = oracle.fdtd_zero_fields(N)
+    W, ez = [], []
+    K = 90
+    for n in range(K + 1):
+        e_n = {c: f[c].copy() for c in ("Ex", "Ey", "Ez")}
+        h_before = {c: f[c].copy() for c in ("Hx", "Hy", "Hz")}
+        oracle.fdtd_run(f, N, 1, courant=s_c, n0=n, src=src, amp=amp, delay=delay, width=width)
+        W.append(sum(float(np.sum(e_n[c] ** 2)) for c in e_n)
+                 + sum(float(np.sum(h_before[c] * f[c])) for c in h_before))
+        ez.append(float(e_n["Ez"][sk, sj, si]))
+    scale = max(abs(w) for w in W)
+    assert scale > 1.0  # the pulse has put energy in
+    for n in range(K):
+        g = amp * math.exp(-(((n - delay) / width) ** 2))
+        assert abs((W[n + 1] - W[n]) - g * (ez[n + 1] + ez[n])) <= 1e-12 * scale, n
