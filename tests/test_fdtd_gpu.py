@@ -191,3 +191,36 @@ def test_wall_column_and_wall_source(oracle, N, src):
     assert abs(float(got["Ez"][sk, sj, si]) - ref["Ez"][sk, sj, si]) <= 1e-5 * (1.0 + abs(ref["Ez"][sk, sj, si]))
     per_step = _gpu_run(N, n, 0, src=src, init=init)
     assert all(np.array_equal(got[k], per_step[k]) for k in FDTD_NAMES)
+
+
+def test_driven_energy_budget_on_gpu():
+    # the soft source's exact discrete energy budget on the GPU's own FP32
+    # fields, one step at a time: W^{n+1} - W^n = g(n) (Ez^{n+1} + Ez^n)[src]
+    import paper_2501_09398_gb300 as g
+
+    N, amp, delay, width = 24, 0.8, 20.0, 8.0
+    si, sj, sk = src = (12, 11, 13)
+    ctx, fields = fdtd_setup(N)
+    E, H = ("Ex", "Ey", "Ez"), ("Hx", "Hy", "Hz")
+    try:
+        g.gs_set_fdtd_params(ctx, courant=0.5, src_on=1, src=src, amp=amp, delay=delay, width=width)
+        fdtd_upload(ctx, N, {})
+        g.gs_set_time(ctx, 0)
+        hist = [fdtd_read(ctx, N)]
+        for _ in range(46):
+            g.gs_step(ctx, 1, 0)
+            hist.append(fdtd_read(ctx, N))
+    finally:
+        g.gs_destroy(ctx)
+        del fields
+    h = [{c: np.zeros_like(hist[0][c], dtype=np.float64) for c in H}] + [
+        {c: f[c].astype(np.float64) for c in H} for f in hist[1:]]  # h[n] = H^{n-1/2}
+    e = [{c: f[c].astype(np.float64) for c in E} for f in hist]
+    W = [sum(float(np.sum(e[n][c] ** 2)) for c in E) + sum(float(np.sum(h[n][c] * h[n + 1][c])) for c in H)
+         for n in range(45)]
+    scale = max(abs(w) for w in W)
+    assert scale > 1.0
+    for n in range(44):
+        gn = amp * math.exp(-(((n - delay) / width) ** 2))
+        budget = gn * (float(e[n + 1]["Ez"][sk, sj, si]) + float(e[n]["Ez"][sk, sj, si]))
+        assert abs((W[n + 1] - W[n]) - budget) <= 2e-6 * scale, n
