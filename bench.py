@@ -16,7 +16,9 @@ heat2d-4096 (2D 4096^2, 200 iterations), heat3d-256 (a deep stack, 256^3,
 200 iterations), fdtd-128 (Yee 128^3, 5000 iterations), fdtd-256 and
 fdtd-media-256 (256^3 cavities, vacuum and lossy objects, 500 iterations),
 multi-64 (64 uneven 2D grids, 2000 iterations).  The default run adds a
-line's "extra" measurements of several of these (and of temporal depths).
+line's "extra" measurements of several of these (and of temporal depths),
+and the batch-size sweep S = 1 ... 1000 of the 2D 512^2 and 3D 512x512x8
+workloads at temporal depths 1, 2 and 4.
 Multi-GPU (torchrun): independent replicas, one per rank, no collective on
 the data path ("scaling": "weak").
 """
@@ -576,6 +578,40 @@ def measure_workload(name, w, args, flush, with_e2e=True):
                 launches=run.launches_per_step(S))
 
 
+SWEEP_S = (1, 10, 50, 100, 500, 1000)
+# (temporal depth, launch plan) per swept workload: depth 1 is the bench's
+# COLUMN plan; depths 2 and 4 are the cost model's temporal candidates (the
+# register COLUMN kernel in 2D, the shared-memory WAVE kernel in 3D)
+SWEEP_PLANS = {
+    "heat2d-512": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=4, block_x=64, rows=4)),
+                   (4, dict(kernel=4, block_x=64, rows=4))),
+    "heat3d-512x512x8": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=2, block_x=64, rows=4)),
+                         (4, dict(kernel=2, block_x=64, rows=4))),
+}
+
+
+def batch_sweep(w, plans, flush, steps=10, warmup=3):
+    """Cell-updates/s of one workload's whole run at every batch size of the
+    sweep (each graph built during the warm-up, outside the timing) beside
+    per-step launch of the same kernels, for each (temporal depth, plan)."""
+    units = cells_of(w) * w["iters"]
+    out = {}
+    for depth, plan in plans:
+        run = Runner(w, 0, depth, plan)
+        try:
+            row = {"plan": dict(plan),
+                   "per_step": units / (statistics.mean(timed_steps(run, 0, steps, warmup, flush)) * 1e-3)}
+            for S in SWEEP_S:
+                row[f"S={S}"] = units / (statistics.mean(timed_steps(run, S, steps, warmup, flush)) * 1e-3)
+        finally:
+            run.close()
+        best = max(SWEEP_S, key=lambda s: row[f"S={s}"])
+        row["best_S"] = best
+        row["best_vs_per_step"] = row[f"S={best}"] / row["per_step"]
+        out[f"depth{depth}"] = row
+    return out
+
+
 def error_vs_oracle(w, result, full_ref):
     if full_ref is None:
         return None
@@ -713,6 +749,15 @@ def main():
             extra[f"{nm}/{tag}"] = {"graph_value": gv, "per_step_value": pv, "graph_speedup": gv / pv,
                                     "S": mm["S"], "depth": mm["depth"], "in_step_GBps": bw,
                                     "hbm_frac": bw / peak, "paper_convention_ms": mm["paper_conv_ms"]}
+        # the batch-size sweep of the 2D 512^2 and 3D 512x512x8 workloads at
+        # temporal depths 1, 2 and 4; a failure here is recorded, not raised
+        sweeps = {}
+        for nm, plans in SWEEP_PLANS.items():
+            try:
+                sweeps[nm] = batch_sweep(WORKLOADS[nm], plans, flush)
+            except Exception as e:  # noqa: BLE001
+                sweeps[nm] = {"error": f"{type(e).__name__}: {e}"}
+        extra["batch_sweep"] = sweeps
         line["extra"] = extra
 
     if world > 1:
