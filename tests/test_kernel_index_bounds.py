@@ -1,12 +1,16 @@
-"""CPU re-trace of the index arithmetic of the COLUMN kernels (thermal depth
-1 in 2D, thin and chunked deep stacks; thermal depth 2 and 4 in 2D; the
-FDTD H and E kernels in the aligned and general layouts): for every thread
-of every block of the launch the library makes, every global load and store
-must lie inside its buffer and inside its row (the pitch), and the stores of
-a launch must cover every cell of the field exactly once.  The formulas
-restate the kernels' address computations (csrc/heat.cu, csrc/fdtd.cu) for
-ragged shapes, so that a change to either is checked here before it runs on
-a GPU."""
+"""CPU re-trace of the kernels' index arithmetic: the COLUMN kernels (thermal
+depth 1 in 2D, thin and chunked deep stacks; thermal depth 2 and 4 in 2D;
+the FDTD H and E kernels in the aligned and general layouts), the MARCH
+kernel (2D and 3D, with its shared-memory plane slab), the WAVE kernel
+(depths 1, 2 and 4, with its 3D level buffers), and the work items of the
+multi-instance kernel (host table, persistent loop, binary search, tile
+stores).  For every thread of every block of the launch the library makes,
+every global load and store must lie inside its buffer and inside its row
+(the pitch), every shared-memory access inside the launch's allocation, and
+the stores of a launch must cover every cell of the field exactly once.
+The formulas restate the kernels' address computations (csrc/heat.cu,
+csrc/fdtd.cu, csrc/multi.cu) for ragged shapes, so that a change to either
+is checked here before it runs on a GPU."""
 import numpy as np
 import pytest
 
@@ -41,6 +45,12 @@ def check_vec(lo_elem, n, row_start, pitch, size):
     assert np.all(lo_elem >= 0) and np.all(lo_elem + n <= size)
     col = lo_elem - row_start
     assert np.all(col >= 0) and np.all(col + n <= pitch)
+
+
+def every_block_stores(stored, bx, by, bz):
+    """No block of the launch is empty (the grid is not over-sized)."""
+    key = (bx * 65536 + by) * 65536 + bz
+    assert np.array_equal(np.unique(key[stored]), np.unique(key))
 
 
 # ------------------------------------------------------------- thermal ----
@@ -208,3 +218,216 @@ def test_fdtd_column_kernel_addresses(N, esize, rows):
     cells = np.zeros((M, M, pitch), dtype=bool)
     cells[:, :, :M] = True
     assert np.array_equal(owned.reshape(M, M, pitch) == 1, cells)
+
+
+# ---------------------------------------------------- MARCH and WAVE ----
+
+@pytest.mark.parametrize("nx,ny,nz", [(300, 37, 1), (77, 45, 1), (3, 2, 1), (513, 9, 1), (130, 17, 3),
+                                      (64, 10, 8), (90, 7, 16), (33, 5, 20), (5, 4, 2)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("block_x,rows", [(32, 4), (64, 1), (128, 7), (256, 16)])
+def test_march_kernel_addresses(nx, ny, nz, esize, block_x, rows):
+    # heat_march_tile: thread (tx, tz) owns V cells at x0 = (bx BX + tx) V of
+    # plane z = bz ZB + tz and marches rows y0 .. y1-1 of its block's tile
+    V = VEC[esize]
+    is3d = nz > 1
+    zb = min(min(nz, 16), max(1, 512 // block_x)) if is3d else 1
+    assert block_x * zb <= 512  # __launch_bounds__(512)
+    grid = (-(-nx // (block_x * V)), -(-ny // rows), -(-nz // zb) if is3d else 1)
+    pitch = pitch_of(nx, esize)
+    plane = pitch * ny
+    size = plane * nz
+    bx, by, bz, tx, tz, _ = threads(grid, (block_x, zb, 1))
+    x0 = (bx * block_x + tx) * V
+    z0 = bz * zb
+    z = z0 + tz
+    y0 = by * rows
+    y1 = np.minimum(y0 + rows, ny)
+    act = (x0 < nx) & (z < nz)
+    has_p = (z == 0) if is3d else np.ones_like(act)
+    dn = is3d & (tz == 0) & (z0 > 0) & (x0 < nx)
+    up = is3d & (tz == zb - 1) & (z0 + zb < nz) & (x0 < nx)
+    lane = tx & 31
+    covered = np.zeros(size, dtype=np.int64)
+    stored = np.zeros_like(act)
+    for k in range(-1, rows + 1):  # rows y0-1 .. y0+rows of the tile
+        y = y0 + k
+        inrow = (y >= 0) & (y < ny) & (y <= y1)
+        m = act & inrow
+        check_vec((z * plane + y * pitch + x0)[m], V, (z * plane + y * pitch)[m], pitch, size)
+        for halo, dz in ((dn, -1), (up, 1)):
+            mh = halo & (y >= y0) & (y < y1)
+            check_vec(((z + dz) * plane + y * pitch + x0)[mh], V, ((z + dz) * plane + y * pitch)[mh], pitch, size)
+        tile = (y >= y0) & (y < y1)
+        mp = act & has_p & tile
+        check_vec((y * pitch + x0)[mp], V, (y * pitch)[mp], pitch, ny * pitch)
+        for cond, off in (((lane == 0) & (x0 > 0), -1), ((lane == 31) & (x0 + V < nx), V)):
+            ms = act & tile & cond
+            check_vec((z * plane + y * pitch + x0 + off)[ms], 1, (z * plane + y * pitch)[ms], pitch, size)
+        # stores of row y
+        ms = act & tile
+        stored |= ms
+        nv = np.minimum(V, nx - x0)
+        check_vec((z * plane + y * pitch + x0)[ms], nv[ms], (z * plane + y * pitch)[ms], pitch, size)
+        for c in range(V):
+            mm = ms & (c < nv)
+            np.add.at(covered, (z * plane + y * pitch + x0)[mm] + c, 1)
+    if is3d:  # the shared slab [2][ZB+2][BX V]: rows tz, tz+1, tz+2, 0 and ZB+1
+        rowlen = block_x * V
+        for r in (tz, tz + 1, tz + 2, np.zeros_like(tz), np.full_like(tz, zb + 1)):
+            off = (zb + 2) * rowlen + r * rowlen + tx * V
+            assert np.all(off + V <= 2 * (zb + 2) * rowlen)
+    every_block_stores(stored, bx, by, bz)
+    cells = np.zeros((nz, ny, pitch), dtype=bool)
+    cells[:, :, :nx] = True
+    assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(300, 37, 1), (77, 45, 1), (3, 2, 1), (130, 17, 1), (500, 9, 1),
+                                      (131, 19, 3), (64, 10, 8), (250, 7, 16), (5, 5, 2)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("depth", [1, 2, 4])
+@pytest.mark.parametrize("block_x,rows", [(64, 4), (128, 32), (32, 1), (96, 7)])
+def test_wave_kernel_addresses(nx, ny, nz, esize, depth, block_x, rows):
+    # heat_wave_kernel: warps of 32 vectors at x0 = bx 30V - V + lane V
+    # (lanes 0 and 31 are halo lanes), marching level-0 rows y0-T ..
+    # y0+R+T-1 and storing level T's rows y0 .. y0+R-1 from lanes 1..30
+    V = VEC[esize]
+    is3d = nz > 1
+    stride = 30 * V
+    wb = nz if is3d else max(1, block_x // 32)
+    ry = rows if is3d else rows * wb
+    assert 32 * wb <= 512  # __launch_bounds__(512)
+    grid = (-(-nx // stride), -(-ny // ry), 1)
+    pitch = pitch_of(nx, esize)
+    plane = pitch * ny
+    size = plane * nz
+    bx, by, bz, lane, ty, _ = threads(grid, (32, wb, 1))
+    x0 = bx * stride - V + lane * V
+    zz = ty if is3d else np.zeros_like(ty)
+    y0 = by * rows if is3d else (by * wb + ty) * rows
+    has_p = (zz == 0) if is3d else np.ones_like(lane, dtype=bool)
+    ld_ok = (x0 >= 0) & (x0 < nx)
+    st_lane = (lane >= 1) & (lane <= 30) & (x0 < nx)
+    nsteps = rows + 2 * depth
+    covered = np.zeros(size, dtype=np.int64)
+    nv = np.minimum(V, nx - x0)
+    stored = np.zeros_like(ld_ok)
+    for j in range(nsteps):
+        r = y0 - depth + j
+        m = ld_ok & (r >= 0) & (r < ny)
+        check_vec((zz * plane + r * pitch + x0)[m], V, (zz * plane + r * pitch)[m], pitch, size)
+        mp = m & has_p
+        check_vec((r * pitch + x0)[mp], V, (r * pitch)[mp], pitch, ny * pitch)
+        q = r - depth  # the row level T computes at this march step
+        ms = st_lane & (q >= y0) & (q < y0 + rows) & (q < ny)
+        stored |= ms
+        check_vec((zz * plane + q * pitch + x0)[ms], nv[ms], (zz * plane + q * pitch)[ms], pitch, size)
+        for c in range(V):
+            mm = ms & (c < nv)
+            np.add.at(covered, (zz * plane + q * pitch + x0)[mm] + c, 1)
+    if is3d:  # [2][T][nz][32 V] floats: writes at level s < T, reads at s-1 of planes tz +- 1
+        rowlen = 32 * V
+        total = 2 * depth * nz * rowlen
+        assert total * 4 == 2 * depth * nz * 32 * V * 4 <= 227 * 1024
+        for buf in (0, 1):
+            for s in range(depth):
+                off = buf * depth * nz * rowlen + lane * V + (s * nz + zz) * rowlen
+                assert np.all(off >= 0) and np.all(off + V <= total)
+            for s in range(1, depth + 1):
+                base = buf * depth * nz * rowlen + lane * V + (s - 1) * nz * rowlen
+                for zn, ok in ((zz - 1, zz > 0), (zz + 1, zz + 1 < nz)):
+                    off = (base + zn * rowlen)[ok]
+                    assert np.all(off >= 0) and np.all(off + V <= total)
+    every_block_stores(stored, bx, by, bz)
+    cells = np.zeros((nz, ny, pitch), dtype=bool)
+    cells[:, :, :nx] = True
+    assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
+
+
+# ------------------------------------------------- instance batches ----
+
+# widths 125 and 250 need one more tile of 30 vectors than of 32 (f32, bf16)
+MULTI_DIMS = [(130, 17), (5, 9), (64, 64), (200, 3), (1, 1), (77, 120), (300, 41), (64, 64), (125, 13), (250, 6)]
+
+
+def multi_table(dims, esize, kind, block_x, rows):
+    """The descriptor table build_table makes: instances largest first
+    (stable), tiles of `span` cells by `item_rows` rows, first_item the
+    running sum of the items before."""
+    V = VEC[esize]
+    col = kind != 0
+    span = (30 * V if kind > 1 else 32 * V) if col else block_x * V
+    item_rows = rows * (4 if V == 4 else 2) if kind > 1 else rows
+    order = sorted(range(len(dims)), key=lambda i: -dims[i][0] * dims[i][1])  # sorted() is stable
+    table, item = [], 0
+    for i in order:
+        nx, ny = dims[i]
+        ntx, nty = -(-nx // span), -(-ny // item_rows)
+        table.append(dict(inst=i, nx=nx, ny=ny, first=item, n=ntx * nty, ntx=ntx))
+        item += ntx * nty
+    return table, item, span
+
+
+def tile_stores(kind, esize, nx, ny, tx_, ty_, block_x, rows):
+    """(x0, y, n_valid) of every store the tile (tx_, ty_) makes."""
+    V = VEC[esize]
+    out = []
+    if kind == 0:  # MARCH tile: block_x threads, rows y0 .. y1-1
+        for t in range(block_x):
+            x0 = (tx_ * block_x + t) * V
+            if x0 < nx:
+                out += [(x0, y, min(V, nx - x0)) for y in range(ty_ * rows, min(ty_ * rows + rows, ny))]
+    elif kind == 1:  # COLUMN tile, depth 1: (32, rows) threads, one row each
+        for ty in range(rows):
+            y = ty_ * rows + ty
+            for lane in range(32):
+                x0 = (tx_ * 32 + lane) * V
+                if x0 < nx and y < ny:
+                    out.append((x0, y, min(V, nx - x0)))
+    else:  # COLUMN tile of temporal depth `kind`: R rows per warp row, lanes 1..30 store
+        R = 4 if V == 4 else 2
+        for ty in range(rows):
+            y0 = (ty_ * rows + ty) * R
+            for lane in range(1, 31):
+                x0 = tx_ * 30 * V - V + lane * V
+                if x0 < nx:
+                    out += [(x0, y, min(V, nx - x0)) for y in range(y0, min(y0 + R, ny))]
+    return out
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 4])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("blocks", [1, 7, 608])
+@pytest.mark.parametrize("rev", [0, 1])
+@pytest.mark.parametrize("block_x,rows", [(64, 4), (32, 1), (128, 3)])
+def test_multi_items_cover_every_instance_once(kind, esize, blocks, rev, block_x, rows):
+    # heat_multi_kernel: block b takes items b, b + grid, ... (last to first
+    # on reversed launches), finds its instance by binary search on
+    # first_item, and runs tile (item mod ntx, item div ntx) of it
+    table, total, _ = multi_table(MULTI_DIMS, esize, kind, block_x, rows)
+    grid = max(1, min(blocks, total))
+    firsts = [d["first"] for d in table]
+    seen = np.zeros(total, dtype=np.int64)
+    cover = {d["inst"]: np.zeros((d["ny"], d["nx"]), dtype=np.int64) for d in table}
+    for b in range(grid):
+        for w0 in range(b, total, grid):
+            w = total - 1 - w0 if rev else w0
+            lo, hi = 0, len(table) - 1
+            while lo < hi:
+                mid = (lo + hi + 1) >> 1
+                if firsts[mid] <= w:
+                    lo = mid
+                else:
+                    hi = mid - 1
+            d = table[lo]
+            assert d["first"] <= w < d["first"] + d["n"], (w, lo)
+            seen[w] += 1
+            item = w - d["first"]
+            for x0, y, nv in tile_stores(kind, esize, d["nx"], d["ny"], item % d["ntx"], item // d["ntx"],
+                                         block_x, rows):
+                assert 0 <= x0 and x0 + nv <= d["nx"] and 0 <= y < d["ny"]
+                cover[d["inst"]][y, x0:x0 + nv] += 1
+    assert np.all(seen == 1)
+    for i, c in cover.items():
+        assert np.all(c == 1), i
