@@ -431,3 +431,115 @@ def test_multi_items_cover_every_instance_once(kind, esize, blocks, rev, block_x
     assert np.all(seen == 1)
     for i, c in cover.items():
         assert np.all(c == 1), i
+
+
+@pytest.mark.parametrize("N", [9, 16, 37, 64])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("block_x,kc", [(32, 1), (64, 4), (128, 16), (256, 3)])
+def test_fdtd_kmarch_kernel_addresses(N, esize, block_x, kc):
+    # fdtd_h/e_kernel: thread owns V cells along i at one j and marches
+    # planes k0 .. k1-1 (kc per block); block (block_x, 256 / block_x)
+    V = VEC[esize]
+    M = N + 1
+    pitch = pitch_of(M, esize)
+    plane = pitch * M
+    size = plane * M
+    by_ = max(1, 256 // block_x)
+    assert block_x * by_ <= 256  # __launch_bounds__(256)
+    grid = (-(-M // (block_x * V)), -(-M // by_), -(-M // kc))
+    bx, by, bz, tx, ty, _ = threads(grid, (block_x, by_, 1))
+    i0 = (bx * block_x + tx) * V
+    j = by * by_ + ty
+    k0 = bz * kc
+    lane = tx & 31
+    act = (i0 < M) & (j < M)
+    nv = np.minimum(V, M - i0)
+    row = j * pitch
+    owned = np.zeros(size, dtype=np.int64)
+    stored = np.zeros_like(act)
+    for dk in range(-1, kc + 1):
+        k = k0 + dk
+        o = k * plane + row + i0
+        base = k * plane + row
+        # H: own vectors at k (and k+1 / j+1 neighbours); E: own vectors at
+        # k (and k-1 plane before the march, j-1 neighbours)
+        mine = act & (k >= k0) & (k < np.minimum(k0 + kc, M))
+        check_vec(o[mine], V, base[mine], pitch, size)
+        mk1 = mine & (k + 1 < M)
+        check_vec((o + plane)[mk1], V, (base + plane)[mk1], pitch, size)
+        mj1 = mine & (j + 1 < M)
+        check_vec((o + pitch)[mj1], V, (base + pitch)[mj1], pitch, size)
+        mjm = mine & (j >= 1)
+        check_vec((o - pitch)[mjm], V, (base - pitch)[mjm], pitch, size)
+        mkm = act & (k == k0 - 1) & (k0 > 0)  # the E march's first k-1 plane
+        check_vec(o[mkm], V, base[mkm], pitch, size)
+        me = mine & (lane == 31) & (i0 + V < M)
+        check_vec((o + V)[me], 1, base[me], pitch, size)
+        mw = mine & (lane == 0) & (i0 >= 1)
+        check_vec((o - 1)[mw], 1, base[mw], pitch, size)
+        check_vec(o[mine], nv[mine], base[mine], pitch, size)  # stores
+        stored |= mine
+        for c in range(V):
+            m = mine & (c < nv)
+            np.add.at(owned, o[m] + c, 1)
+    every_block_stores(stored, bx, by, bz)
+    cells = np.zeros((M, M, pitch), dtype=bool)
+    cells[:, :, :M] = True
+    assert np.array_equal(owned.reshape(M, M, pitch) == 1, cells)
+
+
+def _column_owner_cells(N, rows):
+    """(i0, j, k, extra) of every active thread of a column E launch; extra
+    marks lane 31 of the aligned layout, which also owns cell i0 + V."""
+    V, M = 4, N + 1
+    aln = N % (32 * V) == 0
+    by_ = max(1, min(rows, 8))
+    bz_ = max(1, 8 // by_)
+    span = N if aln else M
+    grid = (-(-span // (32 * V)), -(-M // by_), -(-M // bz_))
+    bx, by, bz, lane, ty, tz = threads(grid, (32, by_, bz_))
+    i0 = (bx * 32 + lane) * V
+    j = by * by_ + ty
+    k = bz * bz_ + tz
+    act = (i0 < M) & (j < M) & (k < M)  # FAST threads are in range too
+    return i0[act], j[act], k[act], (aln & (lane == 31))[act], V
+
+
+def _kmarch_owner_cells(N, esize, block_x, kc):
+    """(i0, j, k, extra) of every (active thread, marched plane) of a
+    k-march E launch."""
+    V, M = VEC[esize], N + 1
+    by_ = max(1, 256 // block_x)
+    grid = (-(-M // (block_x * V)), -(-M // by_), -(-M // kc))
+    bx, by, bz, tx, ty, _ = threads(grid, (block_x, by_, 1))
+    i0 = (bx * block_x + tx) * V
+    j = by * by_ + ty
+    k0 = bz * kc
+    act = (i0 < M) & (j < M)
+    out = [], [], []
+    for dk in range(kc):
+        m = act & (k0 + dk < M)
+        out[0].append(i0[m])
+        out[1].append(j[m])
+        out[2].append((k0 + dk)[m])
+    i0, j, k = (np.concatenate(v) for v in out)
+    return i0, j, k, np.zeros_like(i0, dtype=bool), V
+
+
+@pytest.mark.parametrize("N", [9, 37, 128, 130])
+def test_fdtd_source_cell_has_one_owner(N):
+    # the thread that owns the source cell adds the pulse and advances the
+    # device step counter: exactly one thread of every E launch must own
+    # each cell (si, sj, sk) in [0, N]^3, walls and the aligned layout's
+    # i = N column included
+    pos = sorted({0, 1, N // 2, N - 1, N})
+    shapes = [_column_owner_cells(N, rows) for rows in (1, 2, 8)]
+    shapes += [_kmarch_owner_cells(N, e, bx, kc) for e, bx, kc in ((4, 32, 1), (4, 128, 16), (2, 64, 4))]
+    for n_shape, (i0, j, k, extra, V) in enumerate(shapes):
+        for sj in pos:
+            for sk in (0, N // 2, N):
+                at = (j == sj) & (k == sk)
+                a0, ex = i0[at], extra[at]
+                for si in pos:
+                    owners = np.sum(((si >= a0) & (si < a0 + V)) | (ex & (si == a0 + V)))
+                    assert owners == 1, (n_shape, si, sj, sk)
