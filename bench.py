@@ -256,10 +256,18 @@ def oracle_sample(w, budget_s=10.0):
 
 
 def config_of(name, w, S, depth, world):
-    """The bench line's config (same keys on both arms)."""
+    """The bench line's config (same keys on both arms), with the seeds of
+    its synthetic inputs."""
+    if w["kind"] == "multi":
+        seed = "sides: seed 0; instance k fields: seed 1000 + k"
+    elif w["kind"] == "fdtd":
+        seed = "fields start at 0 (source-driven); media: seed %d" % w["media"]["seed"] if w.get("media") else \
+            "none: fields start at 0 (source-driven)"
+    else:
+        seed = 0
     return {"workload": name, "iterations_per_step": w["iters"], "batch_size_S": S, "temporal_depth": depth,
             "parallelism": f"replicas x{world}" if world > 1 else "single",
-            "l2": "flushed between steps (256 MiB write)"}
+            "l2": "flushed between steps (256 MiB write)", "seed": seed}
 
 
 def aggregate(step_ms, units_per_step, group=None):
