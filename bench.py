@@ -620,6 +620,52 @@ def batch_sweep(w, plans, flush, steps=10, warmup=3):
     return out
 
 
+def multi_streams_per_step(w, flush, reps=5, warmup=2):
+    """The instance batch's per-step baseline with one stream per instance:
+    a context per grid (default plan) on its own stream, each stepped by
+    plain per-step launches, issued instance after instance; the GPU may
+    overlap the streams.  Device time from an event on the launching stream
+    (every instance stream waits on it) to one recorded after the launching
+    stream has waited on every instance stream."""
+    import torch
+
+    import paper_2501_09398_gb300 as g
+
+    sides = multi_sides(w)
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in sides]
+    ctxs, keep = [], []
+    try:
+        for s, st, (T, P) in zip(sides, streams, gs_inputs.instance_fields(sides)):
+            c = g.gs_create(g.GS_HEAT2D, s, s, 1, g.GS_F32, g.GS_BC_CLAMP, st.cuda_stream)
+            ctxs.append(c)
+            keep.append(g.HeatFields(c, s, s, 1))
+            g.gs_upload(c, g.GS_FIELD_T, T)
+            g.gs_upload(c, g.GS_FIELD_P, P)
+        torch.cuda.synchronize()
+        times = []
+        for r in range(warmup + reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            for st in streams:
+                st.wait_stream(main)
+            for c in ctxs:
+                g.gs_step(c, w["iters"], 0)
+            for st in streams:
+                main.wait_stream(st)
+            b.record(main)
+            torch.cuda.synchronize()
+            if r >= warmup:
+                times.append(a.elapsed_time(b))
+    finally:
+        for c in ctxs:
+            g.gs_destroy(c)
+    ms = statistics.mean(times)
+    return {"value": cells_of(w) * w["iters"] / (ms * 1e-3), "ms": ms, "ms_std": statistics.pstdev(times),
+            "streams": len(streams), "launches": len(sides) * w["iters"], "plan": "each context's default (COLUMN)"}
+
+
 def error_vs_oracle(w, result, full_ref):
     if full_ref is None:
         return None
@@ -766,6 +812,17 @@ def main():
             except Exception as e:  # noqa: BLE001
                 sweeps[nm] = {"error": f"{type(e).__name__}: {e}"}
         extra["batch_sweep"] = sweeps
+        # the instance batch's per-step baseline on 64 streams (the one-stream
+        # baseline is multi-64/column2's per_step_value)
+        try:
+            ms = multi_streams_per_step(WORKLOADS["multi-64"], flush)
+            one = extra.get("multi-64/column2", {})
+            if one:
+                ms["vs_one_stream_per_step"] = ms["value"] / one["per_step_value"]
+                ms["fused_graph_speedup"] = one["graph_value"] / ms["value"]
+            extra["multi-64/per_step_64_streams"] = ms
+        except Exception as e:  # noqa: BLE001
+            extra["multi-64/per_step_64_streams"] = {"error": f"{type(e).__name__}: {e}"}
         line["extra"] = extra
 
     if world > 1:
