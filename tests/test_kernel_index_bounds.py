@@ -1,6 +1,7 @@
 """CPU re-trace of the kernels' index arithmetic: the COLUMN kernels (thermal
 depth 1 in 2D, thin and chunked deep stacks; thermal depth 2 and 4 in 2D;
-the FDTD H and E kernels in the aligned and general layouts), the MARCH
+the FDTD H and E kernels in the aligned and general layouts), COLUMN_SMEM
+(its shared slab of neighbour rows), the FDTD k-march kernels, the MARCH
 kernel (2D and 3D, with its shared-memory plane slab), the WAVE kernel
 (depths 1, 2 and 4, with its 3D level buffers), and the work items of the
 multi-instance kernel (host table, persistent loop, binary search, tile
@@ -543,3 +544,69 @@ def test_fdtd_source_cell_has_one_owner(N):
                 for si in pos:
                     owners = np.sum(((si >= a0) & (si < a0 + V)) | (ex & (si == a0 + V)))
                     assert owners == 1, (n_shape, si, sj, sk)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(130, 17, 1), (37, 29, 1), (5, 1, 1), (257, 66, 1), (33, 21, 5),
+                                      (67, 13, 4), (45, 10, 8), (3, 2, 2), (512, 16, 8), (9, 3, 1)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("rows", [1, 2, 3, 8])
+def test_scol_kernel_addresses(nx, ny, nz, esize, rows):
+    # heat_scol_kernel (COLUMN_SMEM): thread (lane, ty) loads its own row of
+    # every plane; rows y-1 and y+1 come from a shared slab of BY + 2 rows
+    # (row 0 and BY + 1 are the block's halo rows, loaded by the first and
+    # last thread rows).  With one thread row per block the same thread
+    # loads both halo rows, each under its own condition.
+    V = VEC[esize]
+    is3d = nz > 1
+    nzm = 8 if is3d else 1
+    BY = max(1, min(rows, 8))
+    grid = (-(-nx // (32 * V)), -(-ny // BY), 1)
+    pitch = pitch_of(nx, esize)
+    plane = pitch * ny
+    size = plane * nz
+    slabf = 32 * V
+    smem = (BY + 2) * nzm * slabf  # floats (heat_scol_smem)
+    bx, by, bz, lane, ty, _ = threads(grid, (32, BY, 1))
+    x0 = (bx * 32 + lane) * V
+    y0 = by * BY
+    y = y0 + ty
+    xin = x0 < nx
+    act = xin & (y < ny)
+    row_ld = np.minimum(y, ny - 1)
+    written = set()
+    covered = np.zeros(size, dtype=np.int64)
+    blk = (bx * 65536 + by)
+    for z in range(min(nz, nzm)):
+        q = z * plane + row_ld * pitch + x0
+        check_vec(q[act], V, (z * plane + row_ld * pitch)[act], pitch, size)
+        m = act & (lane == 0) & (x0 > 0)
+        check_vec((q - 1)[m], 1, (z * plane + row_ld * pitch)[m], pitch, size)
+        m = act & (lane == 31) & (x0 + V < nx)
+        check_vec((q + V)[m], 1, (z * plane + row_ld * pitch)[m], pitch, size)
+        for side in (0, 1):
+            want = ((ty == 0) & (y0 > 0)) if side == 0 else ((ty == BY - 1) & (y0 + BY < ny))
+            m = xin & want
+            hy = y0 - 1 if side == 0 else y0 + BY
+            hr = 0 if side == 0 else BY + 1
+            check_vec((z * plane + hy * pitch + x0)[m], V, (z * plane + hy * pitch)[m], pitch, size)
+            off = (hr * nzm + z) * slabf + lane * V
+            assert np.all(off[m] + V <= smem)
+            written.update(zip(blk[m].tolist(), (off[m]).tolist()))
+        off = ((ty + 1) * nzm + z) * slabf + lane * V
+        assert np.all(off[act] + V <= smem)
+        written.update(zip(blk[act].tolist(), off[act].tolist()))
+    for z in range(min(nz, nzm)):  # after the barrier: rows y-1 and y+1 from the slab
+        for cond, r in ((act & (y > 0), ty), (act & (y + 1 < ny), ty + 2)):
+            off = (r * nzm + z) * slabf + lane * V
+            for key in zip(blk[cond].tolist(), off[cond].tolist()):
+                assert key in written, key
+        nv = np.minimum(V, nx - x0)
+        s0 = z * plane + y * pitch + x0
+        check_vec(s0[act], nv[act], (z * plane + y * pitch)[act], pitch, size)
+        for c in range(V):
+            mm = act & (c < nv)
+            np.add.at(covered, s0[mm] + c, 1)
+    check_vec((y * pitch + x0)[act], V, (y * pitch)[act], pitch, ny * pitch)  # the P row
+    cells = np.zeros((nz, ny, pitch), dtype=bool)
+    cells[:, :, :nx] = True
+    assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
