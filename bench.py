@@ -64,6 +64,7 @@ WORKLOADS = {
 DEFAULT = "heat3d-512x512x8"
 METRIC = "cell-updates/s (graph-batched)"
 FLUSH_BYTES = 256 << 20
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, vendor figure (context beside the measured copy peak)
 
 
 def _peaks():
@@ -678,6 +679,46 @@ def error_vs_oracle(w, result, full_ref):
     return {"max_rel": float(np.max(np.abs(result.astype(np.float64) - full_ref) / np.abs(full_ref)))}
 
 
+def bench_line(args, w, m, clk, world):
+    """The contract's JSON line (without cpu_baseline and extras) from one
+    workload's measurements `m` (measure_workload) and clock record `clk`."""
+    cells = cells_of(w)
+    value, total_ms, _ = aggregate(m["graph_ms"], cells * w["iters"])
+    ms_per_step = total_ms / args.steps
+    per_step_value = cells * w["iters"] / (statistics.mean(m["per_step_ms"]) * 1e-3)
+    peak, peak_kind = _peaks()
+    bytes_launch = algo_bytes_per_launch(w, m["depth"])
+    # average launch duration inside the timed region: CUDA events around
+    # each graph-batched step on the launching stream, divided by the
+    # kernel launches in it (so inter-node gaps are charged to the kernel)
+    launch_ms = ms_per_step / m["launches"]
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    isolated = bytes_launch / (m["kern_ms"] * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(args.workload, w, m["S"], m["depth"], world),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic(args.workload), "peak_kind": peak_kind,
+                     "launch_ms_in_step": launch_ms,
+                     "bytes_per_launch": bytes_launch, "isolated_launch_ms": m["kern_ms"],
+                     "isolated_GBps": isolated, "nominal_GBps": NOMINAL_HBM_GBS,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
+        "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
+                            "graph_speedup": (value / world) / per_step_value},
+        "paper_convention": {"ms_build_plus_run": m["paper_conv_ms"], "build_s": m["build_s"]},
+        "gpu_launches": m["launches"] * args.steps,
+        "clocks": clk,
+    }
+    if m["e2e"] is not None:
+        dt, h2d, d2h = m["e2e"]
+        line["e2e"] = {"value": cells * w["iters"] / dt, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -734,39 +775,7 @@ def main():
         import torch.distributed as dist
 
         dist.barrier()
-    cells = cells_of(w)
-    value, total_ms, _ = aggregate(m["graph_ms"], cells * w["iters"])
-    ms_per_step = total_ms / args.steps
-    per_step_value = cells * w["iters"] / (statistics.mean(m["per_step_ms"]) * 1e-3)
-    peak, peak_kind = _peaks()
-    bytes_launch = algo_bytes_per_launch(w, m["depth"])
-    # average launch duration inside the timed region: CUDA events around
-    # each graph-batched step on the launching stream, divided by the
-    # kernel launches in it (so inter-node gaps are charged to the kernel)
-    launch_ms = ms_per_step / m["launches"]
-    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
-    isolated = bytes_launch / (m["kern_ms"] * 1e-3) / 1e9
-
-    line = {
-        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_of(args.workload, w, m["S"], m["depth"], world),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(args.workload), "peak_kind": peak_kind,
-                     "launch_ms_in_step": launch_ms,
-                     "bytes_per_launch": bytes_launch, "isolated_launch_ms": m["kern_ms"],
-                     "isolated_GBps": isolated},
-        "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
-                            "graph_speedup": (value / world) / per_step_value},
-        "paper_convention": {"ms_build_plus_run": m["paper_conv_ms"], "build_s": m["build_s"]},
-        "gpu_launches": m["launches"] * args.steps,
-        "clocks": clk,
-    }
-    if m["e2e"] is not None:
-        dt, h2d, d2h = m["e2e"]
-        line["e2e"] = {"value": cells * w["iters"] / dt, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h}
+    line = bench_line(args, w, m, clk, world)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sample, threads, full = oracle_sample(w)
@@ -778,6 +787,7 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_extras and args.workload == DEFAULT:
         extra = {}
+        peak = line["roofline"]["peak"]
         base = {**vars(args), "batch": 0, "depth": 0, "block_x": 0, "rows": 0, "tile_x": 0, "tile_y": 0,
                 "pdl": False, "kernel": 0, "loop": False, "traverse": 0, "steps": 20}
         # 2D 512^2: graph-batched vs per-step launch of the same depth-1 kernel

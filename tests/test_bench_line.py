@@ -1,0 +1,69 @@
+"""The bench line on CPU: bench_line() assembles the contract's JSON line
+from one workload's measurements, here fake ones with round numbers, so
+that every key and every derived figure is checked without a GPU."""
+import argparse
+import json
+import math
+
+import pytest
+
+import bench
+
+
+def _fake(w, launches):
+    return dict(S=100, depth=1, graph_ms=[3.0, 3.2, 3.1, 2.9], per_step_ms=[6.0, 6.2, 6.1, 5.9], kern_ms=0.0025,
+                e2e=(0.004, 9_437_184, 8_388_608), paper_conv_ms=30.0, build_s=0.01, launches=launches)
+
+
+@pytest.mark.parametrize("workload", sorted(bench.WORKLOADS))
+def test_bench_line_keys_and_arithmetic(workload):
+    w = bench.WORKLOADS[workload]
+    args = argparse.Namespace(steps=4, warmup=3, workload=workload)
+    launches = 2 * w["iters"] if w["kind"] == "fdtd" else w["iters"]
+    m = _fake(w, launches)
+    clk = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    line = bench.bench_line(args, w, m, clk, 1)
+    json.dumps(line)  # serialisable
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
+        assert k in line, k
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in line["roofline"], k
+    for k in ("h2d_bytes_per_step", "d2h_bytes_per_step", "value", "unit"):
+        assert k in line["e2e"], k
+    assert line["config"]["workload"] == workload and "seed" in line["config"]
+    units = bench.cells_of(w) * w["iters"]
+    total_ms = sum(m["graph_ms"])
+    assert math.isclose(line["value"], units * 4 / (total_ms * 1e-3), rel_tol=1e-12)
+    assert math.isclose(line["ms_per_step"], total_ms / 4, rel_tol=1e-12)
+    launch_ms = total_ms / 4 / launches
+    achieved = bench.algo_bytes_per_launch(w, 1) / (launch_ms * 1e-3) / 1e9
+    rf = line["roofline"]
+    assert math.isclose(rf["achieved"], achieved, rel_tol=1e-12)
+    assert math.isclose(rf["frac"], achieved / rf["peak"], rel_tol=1e-12)
+    assert math.isclose(rf["frac_of_nominal"], achieved / bench.NOMINAL_HBM_GBS, rel_tol=1e-12)
+    assert rf["traffic"] is None or isinstance(rf["traffic"], int)
+    assert math.isclose(line["e2e"]["value"], units / 0.004, rel_tol=1e-12)
+    assert line["gpu_launches"] == launches * 4
+    assert math.isclose(line["per_step_launch"]["graph_speedup"], line["value"] / (units / 6.05e-3), rel_tol=1e-12)
+
+
+def test_profiles_hold_the_default_workloads_traffic_line():
+    # roofline.traffic comes from a committed ncu summary's line
+    # "bench-traffic: workload=W kernel=K sha256=H bytes=B"; the bench takes it
+    # only while H is the hash of the current kernel sources
+    import glob
+    import os
+    import re
+
+    found = []
+    for path in glob.glob(os.path.join(bench.ROOT, "profiles", "*.md")):
+        with open(path) as f:
+            found += re.findall(r"^bench-traffic: workload=(\S+) kernel=\S+ sha256=(\w{16}) bytes=(\d+)$", f.read(),
+                                flags=re.M)
+    mine = [f for f in found if f[0] == bench.DEFAULT]
+    assert mine, "no bench-traffic line for the default workload under profiles/"
+    rec = bench.recorded_traffic(bench.DEFAULT)
+    assert rec is None or rec in [int(b) for _, _, b in mine]
+    if rec is not None:  # no gross re-reads (an L2-resident workload reads less than its algorithmic bytes)
+        assert 0 < rec <= 1.5 * bench.algo_bytes_per_launch(bench.WORKLOADS[bench.DEFAULT], 1)
