@@ -256,6 +256,20 @@ def oracle_sample(w, budget_s=10.0):
     return cells_of(w) * n / dt, f"thermal {shape}, first {n} of {w['iters']} iterations", threads, full
 
 
+def oracle_single_thread(w, budget_s=5.0):
+    """The oracle's throughput on one host thread (a shorter bounded sample
+    of the same workload), beside its all-cores figure."""
+    import oracle
+
+    every = oracle.num_threads()
+    try:
+        oracle.set_num_threads(1)
+        v, sample, threads, _ = oracle_sample(w, budget_s=budget_s)
+    finally:
+        oracle.set_num_threads(every)
+    return {"value": v, "unit": "cell-updates/s", "cores": threads, "sample": sample}
+
+
 def config_of(name, w, S, depth, world):
     """The bench line's config (same keys on both arms), with the seeds of
     its synthetic inputs."""
@@ -781,6 +795,7 @@ def main():
         v, sample, threads, full = oracle_sample(w)
         line["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                                 "sample": sample}
+        line["cpu_baseline"]["single_thread"] = oracle_single_thread(w)
         err = error_vs_oracle(w, m["result"], full)
         if err is not None:
             line["error_vs_oracle"] = err

@@ -92,6 +92,8 @@ def _load():
             lib.or_fdtd_source.restype = ctypes.c_double
             lib.or_num_threads.argtypes = []
             lib.or_num_threads.restype = ctypes.c_int
+            lib.or_set_num_threads.argtypes = [ctypes.c_int]
+            lib.or_set_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -104,6 +106,12 @@ def _dptr(a: np.ndarray):
 def num_threads() -> int:
     """Threads the oracle's loops run on (OpenMP; 1 without it)."""
     return int(_load().or_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Threads of the oracle's later loops in the calling thread; returns the
+    count now in effect."""
+    return int(_load().or_set_num_threads(int(n)))
 
 
 def heat_run(T0, P, n_steps: int, coeffs: dict, bc: int = BC_CLAMP) -> np.ndarray:

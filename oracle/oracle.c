@@ -336,3 +336,16 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* Set the OpenMP thread count of the calling thread's later loops (n >= 1);
+   returns the count now in effect (1 when built without OpenMP). */
+int or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n >= 1 ? n : 1);
+#else
+    (void)n;
+#endif
+    return or_num_threads();
+}

@@ -67,3 +67,12 @@ def test_profiles_hold_the_default_workloads_traffic_line():
     assert rec is None or rec in [int(b) for _, _, b in mine]
     if rec is not None:  # no gross re-reads (an L2-resident workload reads less than its algorithmic bytes)
         assert 0 < rec <= 1.5 * bench.algo_bytes_per_launch(bench.WORKLOADS[bench.DEFAULT], 1)
+
+
+def test_oracle_single_thread_figure_restores_the_thread_count():
+    import oracle
+
+    every = oracle.num_threads()
+    r = bench.oracle_single_thread(bench.WORKLOADS["heat2d-512"], budget_s=0.05)
+    assert r["cores"] == 1 and r["value"] > 0 and "first" in r["sample"]
+    assert oracle.num_threads() == every
