@@ -29,8 +29,12 @@ lossless heterogeneous medium) and a brute-force matrix restatement.  The
 source-driven FDTD field has no closed form; it is pinned through the source
 value, the mirror/swap symmetries, the same scheme's source-free pins and,
 step by step, the discrete energy budget of the soft source
-(W^{n+1} - W^n = g(n) (Ez^{n+1} + Ez^n) at the source); its 5000-step field
-values themselves stay parity unpinned.
+(W^{n+1} - W^n = g(n) (Ez^{n+1} + Ez^n) at the source; in a lossy medium
+with the Joule terms and the source cell's (eps + s sigma / 2) factor); its
+5000-step field values themselves stay parity unpinned.
+``tests/test_oracle_mutations.py`` plants plausible mistakes in a copy of
+``oracle.c`` (selected with the GS_ORACLE_SRC environment variable) and
+checks that a pin fails for each.
 """
 from __future__ import annotations
 
@@ -42,8 +46,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# GS_ORACLE_SRC names another copy of oracle.c, built beside it: the oracle's
+# mutation test plants a mistake in such a copy and checks that a pin fails.
+_SRC = os.environ.get("GS_ORACLE_SRC") or os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(_SRC)), "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 

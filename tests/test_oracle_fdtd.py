@@ -278,3 +278,46 @@ def test_driven_energy_budget(oracle):
     for n in range(K):
         g = amp * math.exp(-(((n - delay) / width) ** 2))
         assert abs((W[n + 1] - W[n]) - g * (ez[n + 1] + ez[n])) <= 1e-12 * scale, n
+
+
+def test_driven_media_energy_budget(oracle):
+    # The soft source in a lossy dielectric cell, added after the E update.
+    # With W^n = sum eps |E^n|^2 + sum mu H^{n-1/2} . H^{n+1/2}, the lossy
+    # update and the adjoint curls give, exactly,
+    #   W^{n+1} - W^n = -(s/2) [sum sigma (E^{n+1}+E^n)^2
+    #                           + sum sigma_m H^{n+1/2}(H^{n+3/2} + 2H^{n+1/2} + H^{n-1/2})]
+    #                   + (eps + s sigma / 2)[src] g(n) (Ez^{n+1} + Ez^n)[src]
+    # (the source's pre-update value enters the conduction average).  The
+    # sigma term at the source tells the order of source and E update apart:
+    # in vacuum the two orders agree up to rounding.
+    N, s, amp, delay, width = 10, 0.5, 0.7, 12.0, 4.0
+    mat, table = gs_inputs.fdtd_media(N, n_mat=4, n_boxes=10, lossy=True, seed=11)
+    eps, sig, mu, sigm = (_per_location(mat, table, q) for q in range(4))
+    inner = np.argwhere(sig[1:N, 1:N, 1:N] > 0) + 1  # interior Ez unknowns in a lossy cell
+    sk, sj, si = (int(v) for v in inner[len(inner) // 2])
+    assert sig[sk, sj, si] > 0 and eps[sk, sj, si] > 1
+    E, H = ("Ex", "Ey", "Ez"), ("Hx", "Hy", "Hz")
+    f = oracle.fdtd_zero_fields(N)
+    e_hist = [{c: f[c].copy() for c in E}]
+    h_hist = [{c: f[c].copy() for c in H}]
+    K = 50
+    for n in range(K + 1):
+        oracle.fdtd_run(f, N, 1, courant=s, n0=n, src=(si, sj, sk), amp=amp, delay=delay, width=width,
+                        media=(mat, table))
+        e_hist.append({c: f[c].copy() for c in E})
+        h_hist.append({c: f[c].copy() for c in H})
+
+    def W(n):
+        return (sum(float(np.sum(eps * e_hist[n][c] ** 2)) for c in E)
+                + sum(float(np.sum(mu * h_hist[n][c] * h_hist[n + 1][c])) for c in H))
+
+    scale = max(abs(W(n)) for n in range(K + 1))
+    assert scale > 1e-2  # the pulse has put energy in
+    src_w = eps[sk, sj, si] + 0.5 * s * sig[sk, sj, si]
+    for n in range(K - 1):
+        joule = (sum(float(np.sum(sig * (e_hist[n + 1][c] + e_hist[n][c]) ** 2)) for c in E)
+                 + sum(float(np.sum(sigm * h_hist[n + 1][c] * (h_hist[n + 2][c] + 2 * h_hist[n + 1][c]
+                                                                + h_hist[n][c]))) for c in H))
+        g = amp * math.exp(-(((n - delay) / width) ** 2))
+        ez = e_hist[n + 1]["Ez"][sk, sj, si] + e_hist[n]["Ez"][sk, sj, si]
+        assert abs((W(n + 1) - W(n)) + 0.5 * s * joule - src_w * g * ez) <= 1e-12 * scale, n
