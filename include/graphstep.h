@@ -532,7 +532,9 @@ typedef enum gs_multi_mode {
                               graph by stream capture */
     GS_MULTI_SEPARATE = 1  /* baseline: each instance stepped by its own
                               launches (per-step, or its own graphs), one
-                              instance after another on the stream */
+                              instance after another on the stream; the
+                              instance contexts run the depth-1 MARCH kernel
+                              with the batch plan's block_x and rows */
 } gs_multi_mode;
 
 typedef struct gs_multi_plan {
