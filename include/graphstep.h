@@ -444,7 +444,7 @@ gs_status gs_model_calibrate(gs_ctx *ctx, int64_t n_iters, const int64_t *S_list
  * plan and temporal depth — the automatic characterisation and batch-size
  * selection the paper leaves as future work (Sec. VI).
  * Network: GS_MLP_INPUTS -> GS_MLP_HIDDEN -> GS_MLP_HIDDEN -> 1, ReLU, one
- * flat FP32 parameter array: W1[32][16] | b1[32] | W2[32][32] | b2[32] |
+ * flat FP32 parameter array: W1[32][18] | b1[32] | W2[32][32] | b2[32] |
  * W3[32] | b3.  Inputs are standardised inside the kernels with a stored
  * per-feature mean and 1/std.  Loss: mean squared error.  Training: Adam
  * (0.9, 0.999, 1e-8), minibatches in row order; one epoch is replayed as a
@@ -514,6 +514,49 @@ gs_status gs_mlp_argmin(gs_mlp *m, const float *X, int64_t n_rows, int64_t *best
  * for CUDA failures, gs_last_error(NULL) for bad arguments. */
 gs_status gs_mlp_argmin_ensemble(gs_mlp *const *models, int32_t k, const float *X, int64_t n_rows,
                                  int64_t *best_row, float *best_pred);
+
+/* ------------------------------- choosing the plan and the batch size -- */
+
+/* Would gs_set_plan accept `plan` on a context of workload w (kind, dtype,
+ * nx, ny, nz; n_iters is not read)?  The same checks, on the host, without a
+ * context or a GPU.  resolved (may be NULL) receives the plan with defaults
+ * filled in and GS_KERNEL_AUTO resolved.  Errors: as gs_set_plan
+ * (GS_ERR_INVALID_ARG, GS_ERR_UNSUPPORTED), and GS_ERR_INVALID_ARG for a
+ * workload gs_create would refuse; message in gs_last_error(NULL). */
+gs_status gs_plan_check(const gs_workload *w, const gs_plan *plan, gs_plan *resolved);
+
+/* The candidate (launch plan, batch size) pairs the pickers choose from for
+ * a thermal or FDTD workload: each of the workload's candidate plans (the
+ * library's default plan among them) with batch size 0 (per-step launches)
+ * and the paper's swept graph batch sizes 1, 10, 50, 100, 500, 1000
+ * (Sec. IV), plan after plan.  Plans carry block_x, rows, temporal_depth
+ * and kernel; their other fields are 0.  Some plans may not fit the grid
+ * (see gs_plan_check).  out == NULL (capacity 0) only counts: *n_out gets
+ * the number.  Host only.  Errors: GS_ERR_INVALID_ARG (bad workload kind,
+ * or capacity below the count, with *n_out set). */
+gs_status gs_candidates(const gs_workload *w, gs_tune_candidate *out, int32_t capacity, int32_t *n_out);
+
+/* The learned choice (the automatic batch-size selection the paper leaves
+ * to future work, Sec. VI, widened to the launch plan and temporal depth):
+ * among the workload's candidates that fit its grid, the one the ensemble
+ * models[0..k-1] predicts fastest for a run of w->n_iters iterations
+ * (gs_features, then gs_mlp_argmin_ensemble); nothing of the workload runs.
+ * *pred_ms_per_iter (may be NULL) gets the predicted milliseconds per
+ * iteration with graph creation amortised over the run.  Synchronous (on
+ * models[0]'s stream).  Errors: GS_ERR_INVALID_ARG, GS_ERR_UNSUPPORTED (no
+ * candidate fits), GS_ERR_NUMERIC (no finite prediction), GS_ERR_CUDA /
+ * GS_ERR_OOM (message in gs_mlp_last_error(models[0])). */
+gs_status gs_pick(gs_mlp *const *models, int32_t k, const gs_workload *w, gs_tune_candidate *best,
+                  float *pred_ms_per_iter);
+
+/* The paper's choice (Sec. III-B): on ctx at its current plan, measure graph
+ * creation and execution for the batch sizes 1, 10, 50, 100, 500, 1000 that
+ * do not exceed n_iters (gs_model_calibrate: reps timed runs of n_iters
+ * iterations each, fields restored), fit Eqs. 2 and 6, and take the batch
+ * size minimising Eq. 1 (gs_model_pick).  *model_out (may be NULL) gets the
+ * fit.  Synchronous; runs the workload.  Errors: GS_ERR_INVALID_ARG
+ * (n_iters < 10, reps < 1), and those of gs_model_calibrate. */
+gs_status gs_pick_analytic(gs_ctx *ctx, int64_t n_iters, int32_t reps, int64_t *batch_out, gs_model *model_out);
 
 /* ------------------------------------------------ uneven instance batch -- */
 

@@ -472,6 +472,58 @@ def gs_mlp_argmin_ensemble(models, X_dev_ptr: int, n_rows: int):
     return idx.value, val.value
 
 
+# ------------------------------------- choosing the plan and batch size --
+_sig("gs_plan_check", [ctypes.POINTER(gs_workload), ctypes.POINTER(gs_plan), ctypes.POINTER(gs_plan)])
+_sig("gs_candidates", [ctypes.POINTER(gs_workload), ctypes.POINTER(gs_tune_candidate), _i32, ctypes.POINTER(_i32)])
+_sig("gs_pick", [ctypes.POINTER(_vp), _i32, ctypes.POINTER(gs_workload), ctypes.POINTER(gs_tune_candidate), _fp])
+_sig("gs_pick_analytic", [_vp, _i64, _i32, ctypes.POINTER(_i64), ctypes.POINTER(gs_model)])
+
+_SHAPE = ("block_x", "rows", "temporal_depth", "kernel")  # the plan fields a candidate sets
+
+
+def _workload(workload: dict):
+    return gs_workload(*[int(workload.get(k, 1) if k == "n_iters" else workload[k]) for k, _ in gs_workload._fields_])
+
+
+def gs_plan_check(workload: dict, plan: dict) -> dict:
+    """The plan as gs_set_plan would apply it on a context of the workload
+    (kind, dtype, nx, ny, nz), defaults filled in; GsError if refused."""
+    p = gs_plan(*[int(plan.get(f, 0)) for f, _ in gs_plan._fields_])
+    out = gs_plan()
+    _check(_lib.gs_plan_check(ctypes.byref(_workload(workload)), ctypes.byref(p), ctypes.byref(out)))
+    return {n: getattr(out, n) for n, _ in gs_plan._fields_}
+
+
+def gs_candidates(workload: dict):
+    """The (plan dict of block_x, rows, temporal_depth, kernel; S) pairs the
+    pickers choose from, plan after plan."""
+    w = _workload(workload)
+    n = _i32()
+    _check(_lib.gs_candidates(ctypes.byref(w), None, 0, ctypes.byref(n)))
+    arr = (gs_tune_candidate * n.value)()
+    _check(_lib.gs_candidates(ctypes.byref(w), arr, n.value, ctypes.byref(n)))
+    return [({f: getattr(c.plan, f) for f in _SHAPE}, c.batch_size) for c in arr]
+
+
+def gs_pick(models, workload: dict):
+    """The learned choice for a run of workload["n_iters"] iterations:
+    (plan dict, S, predicted ms per iteration)."""
+    arr = (_vp * len(models))(*models)
+    best = gs_tune_candidate()
+    pred = ctypes.c_float()
+    _lcheck(_lib.gs_pick(arr, len(models), ctypes.byref(_workload(workload)), ctypes.byref(best),
+                         ctypes.byref(pred)), models[0] if models else None)
+    return {f: getattr(best.plan, f) for f in _SHAPE}, best.batch_size, pred.value
+
+
+def gs_pick_analytic(ctx, n_iters: int, reps: int = 2):
+    """The paper's choice on a context at its current plan: (S, fitted model)."""
+    S = _i64()
+    m = gs_model()
+    _check(_lib.gs_pick_analytic(ctx, int(n_iters), int(reps), ctypes.byref(S), ctypes.byref(m)), ctx)
+    return S.value, _model_dict(m)
+
+
 # ----------------------------------------------------- instance batches --
 GS_MULTI_FUSED, GS_MULTI_SEPARATE = range(2)
 

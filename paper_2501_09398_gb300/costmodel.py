@@ -36,12 +36,11 @@ import time
 import numpy as np
 
 from . import (GS_BC_CLAMP, GS_BC_PEC, GS_F32, GS_FDTD3D, GS_FIELD_P, GS_FIELD_T, GS_HEAT2D, GS_HEAT3D,
-               GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM, GS_KERNEL_MARCH, GS_KERNEL_WAVE, FDTD_FIELDS, FdtdFields, HeatFields, gs_autotune, gs_create,
-               gs_destroy, gs_features, gs_model_fit, gs_model_pick, gs_mlp_argmin_ensemble, gs_mlp_create,
+               GS_KERNEL_COLUMN, FDTD_FIELDS, FdtdFields, HeatFields, gs_autotune, gs_create,
+               gs_candidates, gs_destroy, gs_features, gs_model_fit, gs_model_pick, gs_mlp_argmin_ensemble, gs_mlp_create,
                gs_mlp_destroy, gs_mlp_fit_normalization, gs_mlp_loss_grad, gs_mlp_train, gs_set_fdtd_params,
                gs_upload)
 
-S_LIST = (0, 1, 10, 50, 100, 500, 1000)
 KINDS = ("heat2d", "heat3d", "fdtd")
 KIND_ID = {"heat2d": GS_HEAT2D, "heat3d": GS_HEAT3D, "fdtd": GS_FDTD3D}
 
@@ -99,30 +98,9 @@ def default_plan(w):
 
 
 def candidates(w):
-    """(plan, S) pairs for a workload; every plan field explicit."""
-    C, CS, M, W = GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM, GS_KERNEL_MARCH, GS_KERNEL_WAVE
-    shapes = []
-    if w["kind"] == "fdtd":
-        for rows in (1, 2, 4, 8):
-            shapes.append(dict(block_x=64, rows=rows, temporal_depth=1, kernel=C))
-        shapes += [dict(block_x=64, rows=4, temporal_depth=1, kernel=M),
-                   dict(block_x=32, rows=16, temporal_depth=1, kernel=M)]
-    else:
-        thin = w["kind"] == "heat2d" or w["nz"] <= 8
-        shapes += [dict(block_x=64, rows=r, temporal_depth=1, kernel=C) for r in (2, 4, 8)]
-        if thin:
-            shapes += [dict(block_x=64, rows=r, temporal_depth=1, kernel=CS) for r in (4, 8)]
-        shapes += [dict(block_x=32, rows=4, temporal_depth=1, kernel=M), dict(block_x=64, rows=8, temporal_depth=1, kernel=M),
-                   dict(block_x=32, rows=16, temporal_depth=1, kernel=M)]
-        if w["kind"] == "heat2d" or w["nz"] <= 16:
-            shapes += [dict(block_x=64, rows=4, temporal_depth=t, kernel=W) for t in (2, 4)]
-            shapes.append(dict(block_x=64, rows=16, temporal_depth=4, kernel=W))
-            shapes += [dict(block_x=128, rows=32, temporal_depth=t, kernel=W) for t in (2, 4)]
-        if w["kind"] == "heat2d":  # the column kernel's levels in registers
-            shapes += [dict(block_x=64, rows=4, temporal_depth=t, kernel=C) for t in (2, 4)]
-    if default_plan(w) not in shapes:
-        shapes.append(default_plan(w))
-    return [(dict(p), S) for p in shapes for S in S_LIST]
+    """(plan, S) pairs for a workload, plan after plan, as the library lists
+    them (gs_candidates): block_x, rows, temporal_depth and kernel explicit."""
+    return gs_candidates(_fw(w))
 
 
 def _context(w, stream):

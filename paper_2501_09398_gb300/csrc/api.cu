@@ -695,6 +695,32 @@ bool traverse_alternates(int mode, double step_bytes) {
 
 // ------------------------------------------------------------- C ABI -----
 
+namespace {
+
+// The grid checks of gs_create: nullptr if (kind, sizes, storage, bc) make a
+// valid context, else why not.
+const char* grid_error(gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc) {
+    if (kind != GS_HEAT2D && kind != GS_HEAT3D && kind != GS_FDTD3D && kind != GS_SKELETON) return "unknown kind";
+    if (kind == GS_SKELETON && (ny != 1 || nz != 1 || nx < 1 || nx >= (int64_t(1) << 31)))
+        return "GS_SKELETON needs ny == nz == 1 and 1 <= nx < 2^31";
+    if (storage != GS_F32 && storage != GS_BF16 && storage != GS_F16) return "unknown storage dtype";
+    const int64_t lim = int64_t(1) << 20;
+    if (kind != GS_SKELETON && (nx < 1 || ny < 1 || nz < 1 || nx > lim || ny > lim || nz > lim))
+        return "grid sizes must be in [1, 2^20]";
+    if (kind == GS_HEAT2D && nz != 1) return "GS_HEAT2D needs nz == 1";
+    if (kind == GS_FDTD3D && (nx != ny || ny != nz)) return "GS_FDTD3D needs a cubic grid (nx == ny == nz)";
+    const int64_t w = (kind == GS_FDTD3D) ? nx + 1 : nx;
+    const int64_t rows = (kind == GS_FDTD3D) ? (nx + 1) * (nx + 1) : ny * nz;
+    if (kind != GS_SKELETON && (double)(w + 8) * (double)rows >= 2147483647.0)
+        return "field too large (needs >= 2^31 elements)";
+    if (kind == GS_FDTD3D && bc != GS_BC_PEC) return "GS_FDTD3D needs GS_BC_PEC";
+    if ((kind == GS_HEAT2D || kind == GS_HEAT3D) && bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0)
+        return "thermal kinds need GS_BC_CLAMP or GS_BC_DIRICHLET0";
+    return nullptr;
+}
+
+}  // namespace
+
 extern "C" {
 
 int gs_version(void) { return 100; }
@@ -727,25 +753,7 @@ gs_status gs_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t 
                     void* stream) {
     if (!out) return fail(nullptr, GS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (kind != GS_HEAT2D && kind != GS_HEAT3D && kind != GS_FDTD3D && kind != GS_SKELETON)
-        return fail(nullptr, GS_ERR_INVALID_ARG, "unknown kind");
-    if (kind == GS_SKELETON && (ny != 1 || nz != 1 || nx < 1 || nx >= (int64_t(1) << 31)))
-        return fail(nullptr, GS_ERR_INVALID_ARG, "GS_SKELETON needs ny == nz == 1 and 1 <= nx < 2^31");
-    if (storage != GS_F32 && storage != GS_BF16 && storage != GS_F16)
-        return fail(nullptr, GS_ERR_INVALID_ARG, "unknown storage dtype");
-    const int64_t lim = int64_t(1) << 20;
-    if (kind != GS_SKELETON && (nx < 1 || ny < 1 || nz < 1 || nx > lim || ny > lim || nz > lim))
-        return fail(nullptr, GS_ERR_INVALID_ARG, "grid sizes must be in [1, 2^20]");
-    if (kind == GS_HEAT2D && nz != 1) return fail(nullptr, GS_ERR_INVALID_ARG, "GS_HEAT2D needs nz == 1");
-    if (kind == GS_FDTD3D && (nx != ny || ny != nz))
-        return fail(nullptr, GS_ERR_INVALID_ARG, "GS_FDTD3D needs a cubic grid (nx == ny == nz)");
-    const int64_t w = (kind == GS_FDTD3D) ? nx + 1 : nx;
-    const int64_t rows = (kind == GS_FDTD3D) ? (nx + 1) * (nx + 1) : ny * nz;
-    if (kind != GS_SKELETON && (double)(w + 8) * (double)rows >= 2147483647.0)
-        return fail(nullptr, GS_ERR_INVALID_ARG, "field too large (needs >= 2^31 elements)");
-    if (kind == GS_FDTD3D && bc != GS_BC_PEC) return fail(nullptr, GS_ERR_INVALID_ARG, "GS_FDTD3D needs GS_BC_PEC");
-    if ((kind == GS_HEAT2D || kind == GS_HEAT3D) && bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0)
-        return fail(nullptr, GS_ERR_INVALID_ARG, "thermal kinds need GS_BC_CLAMP or GS_BC_DIRICHLET0");
+    if (const char* why = grid_error(kind, nx, ny, nz, storage, bc)) return fail(nullptr, GS_ERR_INVALID_ARG, why);
 
     gs_ctx* c = new (std::nothrow) gs_ctx();
     if (!c) return fail(nullptr, GS_ERR_OOM, "host allocation failed");
@@ -865,6 +873,26 @@ gs_status gs_set_plan(gs_ctx* c, const gs_plan* plan) {
     if (st != GS_OK) return st;
     c->plan = p;
     invalidate(c);
+    return GS_OK;
+}
+
+gs_status gs_plan_check(const gs_workload* w, const gs_plan* plan, gs_plan* resolved) {
+    if (!w || !plan) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_plan_check: NULL argument");
+    const gs_kind kind = static_cast<gs_kind>(w->kind);
+    const gs_bc bc = (kind == GS_FDTD3D) ? GS_BC_PEC : GS_BC_CLAMP;  // no plan rule depends on the thermal bc
+    if (const char* why = grid_error(kind, w->nx, w->ny, w->nz, static_cast<gs_dtype>(w->dtype), bc))
+        return fail(nullptr, GS_ERR_INVALID_ARG, std::string("gs_plan_check: ") + why);
+    gs_ctx c;  // the grid only: no stream, fields or device memory
+    c.kind = kind;
+    c.nx = w->nx;
+    c.ny = w->ny;
+    c.nz = w->nz;
+    c.dt = static_cast<gs_dtype>(w->dtype);
+    c.bc = bc;
+    gs_plan p = *plan;
+    const gs_status st = validate_plan(&c, &p);
+    if (st != GS_OK) return fail(nullptr, st, "gs_plan_check: " + c.err);
+    if (resolved) *resolved = p;
     return GS_OK;
 }
 

@@ -1,7 +1,7 @@
-// Learned cost model: a 16-32-32-1 ReLU MLP predicting log(ms per
+// Learned cost model: an 18-32-32-1 ReLU MLP predicting log(ms per
 // iteration) of a (workload, candidate) pair, trained and evaluated by the
 // kernels in this file.  Parameters are one flat FP32 array:
-//   W1[32][16] | b1[32] | W2[32][32] | b2[32] | W3[32] | b3      (1633 floats)
+//   W1[32][18] | b1[32] | W2[32][32] | b2[32] | W3[32] | b3      (1697 floats)
 // Inputs are standardised inside the kernels: xh = (x - mean) * inv_std.
 // Loss: L = (1/N) sum_r (pred_r - y_r)^2 over the N rows of a batch.
 // Training: Adam (beta1 0.9, beta2 0.999, eps 1e-8); one epoch of
@@ -455,7 +455,7 @@ gs_status gs_mlp_destroy(gs_mlp* m) {
 const char* gs_mlp_last_error(const gs_mlp* m) { return m ? m->err.c_str() : ""; }
 
 gs_status gs_mlp_set_params(gs_mlp* m, const float* host, int64_t n) {
-    if (!m || !host || n != NP) return mlp_fail(m, GS_ERR_INVALID_ARG, "gs_mlp_set_params: need 1633 floats");
+    if (!m || !host || n != NP) return mlp_fail(m, GS_ERR_INVALID_ARG, "gs_mlp_set_params: need GS_MLP_PARAMS (1697) floats");
     GS_MLPC(m, cudaMemcpyAsync(m->params, host, NP * sizeof(float), cudaMemcpyHostToDevice, m->stream));
     GS_MLPC(m, cudaMemsetAsync(m->m, 0, NP * sizeof(float), m->stream));
     GS_MLPC(m, cudaMemsetAsync(m->v, 0, NP * sizeof(float), m->stream));
@@ -465,7 +465,7 @@ gs_status gs_mlp_set_params(gs_mlp* m, const float* host, int64_t n) {
 }
 
 gs_status gs_mlp_get_params(gs_mlp* m, float* host, int64_t n) {
-    if (!m || !host || n != NP) return mlp_fail(m, GS_ERR_INVALID_ARG, "gs_mlp_get_params: need 1633 floats");
+    if (!m || !host || n != NP) return mlp_fail(m, GS_ERR_INVALID_ARG, "gs_mlp_get_params: need GS_MLP_PARAMS (1697) floats");
     GS_MLPC(m, cudaMemcpyAsync(host, m->params, NP * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
     GS_MLPC(m, cudaStreamSynchronize(m->stream));
     return GS_OK;
@@ -680,6 +680,134 @@ gs_status gs_features(const gs_workload* w, const gs_tune_candidate* c, int32_t 
         f[16] = (k == GS_KERNEL_COLUMN || k == GS_KERNEL_COLUMN_SMEM);
         f[17] = (k == GS_KERNEL_COLUMN_SMEM);
     }
+    return GS_OK;
+}
+
+// ------------------------------------------------ choosing a candidate --
+
+}  // extern "C"
+
+namespace {
+
+// Batch sizes of the candidate set: per-step launch (0) and the graph batch
+// sizes the paper sweeps (Sec. IV).
+constexpr int64_t kPickBatchSizes[] = {0, 1, 10, 50, 100, 500, 1000};
+
+gs_plan plan_of(int32_t block_x, int32_t rows, int32_t depth, int32_t kernel) {
+    gs_plan p{};
+    p.block_x = block_x;
+    p.rows = rows;
+    p.temporal_depth = depth;
+    p.kernel = kernel;
+    return p;
+}
+
+bool same_shape(const gs_plan& a, const gs_plan& b) {
+    return a.block_x == b.block_x && a.rows == b.rows && a.temporal_depth == b.temporal_depth && a.kernel == b.kernel;
+}
+
+// The launch plans the pickers (and the cost model's sweep) consider for a
+// workload, in sweep order.  FDTD: COLUMN with 1, 2, 4, 8 rows and two
+// k-march shapes.  Thermal: COLUMN with 2, 4, 8 rows; COLUMN_SMEM (2D and
+// stacks of at most 8 planes); three MARCH shapes; WAVE at depth 2 and 4
+// (2D and stacks of at most 16 planes); COLUMN at depth 2 and 4 (2D).  The
+// library's default plan is included.
+std::vector<gs_plan> candidate_plans(const gs_workload& w) {
+    const int C = GS_KERNEL_COLUMN, CS = GS_KERNEL_COLUMN_SMEM, M = GS_KERNEL_MARCH, W = GS_KERNEL_WAVE;
+    std::vector<gs_plan> v;
+    gs_plan dflt;
+    if (w.kind == GS_FDTD3D) {
+        for (int32_t r : {1, 2, 4, 8}) v.push_back(plan_of(64, r, 1, C));
+        v.push_back(plan_of(64, 4, 1, M));
+        v.push_back(plan_of(32, 16, 1, M));
+        dflt = plan_of(64, 4, 1, C);
+    } else {
+        const bool is2d = w.kind == GS_HEAT2D;
+        for (int32_t r : {2, 4, 8}) v.push_back(plan_of(64, r, 1, C));
+        if (is2d || w.nz <= 8)
+            for (int32_t r : {4, 8}) v.push_back(plan_of(64, r, 1, CS));
+        v.push_back(plan_of(32, 4, 1, M));
+        v.push_back(plan_of(64, 8, 1, M));
+        v.push_back(plan_of(32, 16, 1, M));
+        if (is2d || w.nz <= 16) {
+            for (int32_t t : {2, 4}) v.push_back(plan_of(64, 4, t, W));
+            v.push_back(plan_of(64, 16, 4, W));
+            for (int32_t t : {2, 4}) v.push_back(plan_of(128, 32, t, W));
+        }
+        if (is2d)
+            for (int32_t t : {2, 4}) v.push_back(plan_of(64, 4, t, C));
+        const bool small = w.nx * w.ny * w.nz <= (int64_t(1) << 22);
+        const bool deep = w.kind == GS_HEAT3D && w.nz > 8;
+        dflt = plan_of(64, (small || deep) ? 4 : 8, 1, C);
+    }
+    bool have = false;
+    for (const gs_plan& p : v) have = have || same_shape(p, dflt);
+    if (!have) v.push_back(dflt);
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_candidates(const gs_workload* w, gs_tune_candidate* out, int32_t capacity, int32_t* n_out) {
+    if (!w || !n_out || capacity < 0 || (capacity > 0 && !out))
+        return global_fail(GS_ERR_INVALID_ARG, "gs_candidates: bad arguments");
+    if (w->kind != GS_HEAT2D && w->kind != GS_HEAT3D && w->kind != GS_FDTD3D)
+        return global_fail(GS_ERR_INVALID_ARG, "gs_candidates: kind must be GS_HEAT2D, GS_HEAT3D or GS_FDTD3D");
+    const std::vector<gs_plan> plans = candidate_plans(*w);
+    const int32_t nS = (int32_t)(sizeof(kPickBatchSizes) / sizeof(kPickBatchSizes[0]));
+    const int32_t n = (int32_t)plans.size() * nS;
+    *n_out = n;
+    if (!out) return GS_OK;
+    if (capacity < n) return global_fail(GS_ERR_INVALID_ARG, "gs_candidates: capacity below the candidate count");
+    int32_t i = 0;
+    for (const gs_plan& p : plans)
+        for (int32_t k = 0; k < nS; ++k) {
+            out[i].plan = p;
+            out[i].batch_size = kPickBatchSizes[k];
+            ++i;
+        }
+    return GS_OK;
+}
+
+gs_status gs_pick(gs_mlp* const* models, int32_t k, const gs_workload* w, gs_tune_candidate* best,
+                  float* pred_ms_per_iter) {
+    if (!models || k < 1 || !w || !best) return global_fail(GS_ERR_INVALID_ARG, "gs_pick: bad arguments");
+    for (int32_t i = 0; i < k; ++i)
+        if (!models[i]) return global_fail(GS_ERR_INVALID_ARG, "gs_pick: NULL model");
+    int32_t n = 0;
+    gs_status st = gs_candidates(w, nullptr, 0, &n);
+    if (st != GS_OK) return st;
+    std::vector<gs_tune_candidate> all((size_t)n);
+    st = gs_candidates(w, all.data(), n, &n);
+    if (st != GS_OK) return st;
+    // the candidates this grid can run (the checks gs_set_plan applies); the
+    // refusals are expected, so the thread's last error message is kept
+    const std::string saved = gs_last_error(nullptr);
+    std::vector<gs_tune_candidate> ok;
+    for (const gs_tune_candidate& c : all)
+        if (gs_plan_check(w, &c.plan, nullptr) == GS_OK) ok.push_back(c);
+    global_fail(GS_OK, saved);
+    if (ok.empty()) return global_fail(GS_ERR_UNSUPPORTED, "gs_pick: no candidate plan fits this grid");
+    std::vector<float> X(ok.size() * (size_t)NI);
+    st = gs_features(w, ok.data(), (int32_t)ok.size(), X.data());
+    if (st != GS_OK) return st;
+    gs_mlp* m0 = models[0];
+    float* dX = nullptr;
+    GS_MLPC(m0, cudaMalloc(&dX, X.size() * sizeof(float)));
+    // on the first model's stream, where the ensemble argmin runs
+    cudaError_t e = cudaMemcpyAsync(dX, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, m0->stream);
+    int64_t row = -1;
+    float pred = 0.f;
+    if (e == cudaSuccess) st = gs_mlp_argmin_ensemble(models, k, dX, (int64_t)ok.size(), &row, &pred);
+    const cudaError_t ef = cudaFree(dX);
+    if (e != cudaSuccess) return mlp_cuda(m0, e, "gs_pick: feature upload");
+    if (st != GS_OK) return st;
+    if (ef != cudaSuccess) return mlp_cuda(m0, ef, "gs_pick: free");
+    if (row < 0 || row >= (int64_t)ok.size()) return mlp_fail(m0, GS_ERR_NUMERIC, "gs_pick: no finite prediction");
+    *best = ok[(size_t)row];
+    if (pred_ms_per_iter) *pred_ms_per_iter = std::exp(pred);
     return GS_OK;
 }
 

@@ -118,4 +118,20 @@ gs_status gs_model_calibrate(gs_ctx* ctx, int64_t n_iters, const int64_t* S_list
     return GS_OK;
 }
 
+gs_status gs_pick_analytic(gs_ctx* ctx, int64_t n_iters, int32_t reps, int64_t* batch_out, gs_model* model_out) {
+    if (!ctx || n_iters < 10 || reps < 1 || !batch_out)
+        return ctx_fail(ctx, GS_ERR_INVALID_ARG, "gs_pick_analytic: need n_iters >= 10, reps >= 1 and batch_out");
+    // the graph batch sizes of the paper's sweep (Sec. IV) that fit in the run
+    std::vector<int64_t> S;
+    for (int64_t s : {1, 10, 50, 100, 500, 1000})
+        if (s <= n_iters) S.push_back(s);
+    gs_model m;
+    gs_status st = gs_model_calibrate(ctx, n_iters, S.data(), (int32_t)S.size(), reps, &m);
+    if (st != GS_OK) return st;
+    st = gs_model_pick(&m, S.data(), (int32_t)S.size(), batch_out, nullptr);
+    if (st != GS_OK) return ctx_fail(ctx, st, gs_last_error(nullptr));
+    if (model_out) *model_out = m;
+    return GS_OK;
+}
+
 }  // extern "C"
