@@ -681,6 +681,42 @@ def multi_streams_per_step(w, flush, reps=5, warmup=2):
             "streams": len(streams), "launches": len(sides) * w["iters"], "plan": "each context's default (COLUMN)"}
 
 
+def fdtd_precision(N=128, iters=5000, S=100):
+    """Relative L2 error (six components concatenated) of the driven 128^3
+    cavity after 5000 steps against the FP64 oracle, for each storage type,
+    with the bar the arithmetic gives for bf16/f16 storage (two roundings per
+    step, unbiased: 2 sqrt(n) u)."""
+    import math
+
+    import torch
+
+    import oracle
+    import paper_2501_09398_gb300 as g
+
+    src = (N // 2, N // 2, N // 2)
+    ref = oracle.fdtd_run(oracle.fdtd_zero_fields(N), N, iters, src=src)
+    refv = np.concatenate([ref[c].ravel() for c in oracle.FDTD_COMPONENTS])
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {"workload": f"FDTD {N}^3 driven cavity, {iters} steps, S = {S}"}
+    for name, dt, u in (("f32", g.GS_F32, 2.0 ** -24), ("bf16", g.GS_BF16, 2.0 ** -8), ("f16", g.GS_F16, 2.0 ** -11)):
+        ctx = g.gs_create(g.GS_FDTD3D, N, N, N, dt, g.GS_BC_PEC, stream)
+        fields = g.FdtdFields(ctx, N, dt)
+        try:
+            g.gs_set_fdtd_params(ctx, courant=0.5, src_on=1, src=src)
+            z = np.zeros((N + 1,) * 3, dtype=np.float32)
+            for fid in g.FDTD_FIELDS:
+                g.gs_upload(ctx, fid, z)
+            g.gs_step(ctx, iters, S)
+            got = np.concatenate([g.gs_read_field(ctx, fid, np.empty((N + 1,) * 3, dtype=np.float32))
+                                  .astype(np.float64).ravel() for fid in g.FDTD_FIELDS])
+        finally:
+            g.gs_destroy(ctx)
+            del fields
+        err = float(np.linalg.norm(got - refv) / np.linalg.norm(refv))
+        out[name] = {"rel_l2": err, "bar": 1e-4 if name == "f32" else 2.0 * math.sqrt(iters) * u}
+    return out
+
+
 def error_vs_oracle(w, result, full_ref):
     if full_ref is None:
         return None
@@ -799,6 +835,12 @@ def main():
         err = error_vs_oracle(w, m["result"], full)
         if err is not None:
             line["error_vs_oracle"] = err
+        if not args.no_extras and args.workload == DEFAULT:
+            # the storage types' errors on the FDTD workload (one FP64 oracle run)
+            try:
+                line["fdtd_precision"] = fdtd_precision()
+            except Exception as e:  # noqa: BLE001
+                line["fdtd_precision"] = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0 and world == 1 and not args.no_extras and args.workload == DEFAULT:
         extra = {}
