@@ -168,8 +168,10 @@ typedef enum gs_traverse { GS_TRAVERSE_AUTO = 0, GS_TRAVERSE_FORWARD = 1, GS_TRA
 /* Launch plan.  Zero fields select defaults.
  *   block_x        threads along x per block (multiple of 32; <= 512 thermal,
  *                  <= 256 FDTD)
- *   rows           rows each block (or warp) marches along y; FDTD: k planes
- *                  per block
+ *   rows           MARCH / WAVE: rows each block (or warp) marches along y;
+ *                  COLUMN at depth 1: warps per block stacked in y (more
+ *                  than 8 act as 8; at depth 2/4 block_x/32 warps); FDTD
+ *                  COLUMN: j rows per block; FDTD MARCH: k planes per block
  *   tile_x, tile_y output tile of the TILE kernel
  *   temporal_depth thermal steps fused in one launch: 1, 2 or 4; a depth-t
  *                  launch is bit-identical to t depth-1 launches
@@ -186,9 +188,9 @@ typedef struct gs_plan {
     int32_t temporal_depth;
     int32_t use_pdl;
     int32_t device_launch;
-    int32_t kernel; /* gs_kernel; FDTD: COLUMN (default: one vector per thread,
-                       block 32 x rows x 8/rows) or MARCH (block_x threads
-                       marching `rows` k planes) */
+    int32_t kernel; /* gs_kernel; FDTD: COLUMN (default: four cells along i
+                       per thread, block 32 x rows x 8/rows) or MARCH
+                       (block_x threads marching `rows` k planes) */
     int32_t graph_loop; /* 0: the floor(n/S) batches are floor(n/S) graph
                            launches (Listing 3).  1: one launch of a graph
                            whose conditional while node repeats the batch on
