@@ -1,7 +1,8 @@
 """The Python binding and the C header agree on the ABI: every struct the
 binding declares with ctypes has the size, field offsets and field sizes
-the C compiler gives the header's struct, and every GS_ constant the binding defines has the
-header's value.  A small C program built with gcc against
+the C compiler gives the header's struct, every GS_ constant the binding
+defines has the header's value, and every prototype's parameters and return
+have the ABI classes of the binding's argtypes and restype.  A small C program built with gcc against
 include/graphstep.h prints the header's side; no GPU and no library call is
 involved."""
 import ctypes
@@ -74,3 +75,57 @@ def test_constants_match_the_header(header_side):
     assert len(consts) >= 40
     for name, v in consts.items():
         assert v == table[("const", name)], name
+
+
+def _c_class(decl: str):
+    """ABI class of a C parameter or return type: 'ptr', 'i32' (int, int32_t
+    and the gs_ enums), 'i64' (int64_t, uint64_t), 'f32', 'f64', or None
+    for void."""
+    if "*" in decl:
+        return "ptr"
+    words = [w for w in decl.replace("const", " ").split()]
+    t = words[0] if words else "void"
+    if t == "void":
+        return None
+    if t in ("int", "int32_t") or (t.startswith("gs_") and t not in ("gs_ctx", "gs_multi", "gs_mlp")):
+        return "i32"
+    if t in ("int64_t", "uint64_t"):
+        return "i64"
+    return {"float": "f32", "double": "f64"}[t]
+
+
+def _py_class(t):
+    if t is None:
+        return None
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    if t is ctypes.c_float:
+        return "f32"
+    if t is ctypes.c_double:
+        return "f64"
+    return {4: "i32", 8: "i64"}[ctypes.sizeof(t)]
+
+
+def test_function_signatures_match_the_header(g):
+    # every prototype the header declares: the binding's argtypes have the
+    # same number of parameters and the same ABI class for each, and the
+    # restype the class of the return type (an int32 passed for an int64_t
+    # would leave the register's upper half undefined)
+    import re
+
+    with open(os.path.join(HEADER_DIR, "graphstep.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = re.sub(r"#[^\n]*", " ", src)
+    flat = " ".join(src.split())
+    protos = re.findall(r"([A-Za-z_][\w\s\*]*?)\b(gs_\w+)\s*\(([^()]*)\)\s*;", flat)
+    assert len(protos) >= 60
+    for ret, name, params in protos:
+        fn = getattr(g._lib, name)
+        assert fn.argtypes is not None, name
+        cparams = [] if params.strip() == "void" else [p.strip() for p in params.split(",")]
+        assert len(fn.argtypes) == len(cparams), name
+        for i, (p, t) in enumerate(zip(cparams, fn.argtypes)):
+            assert _py_class(t) == _c_class(p), (name, i, p, t)
+        assert _py_class(fn.restype) == _c_class(ret), (name, ret, fn.restype)
