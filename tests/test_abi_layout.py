@@ -2,9 +2,9 @@
 binding declares with ctypes has the size, field offsets and field sizes
 the C compiler gives the header's struct, every GS_ constant the binding
 defines has the header's value, and every prototype's parameters and return
-have the ABI classes of the binding's argtypes and restype.  A small C program built with gcc against
-include/graphstep.h prints the header's side; no GPU and no library call is
-involved."""
+have the ABI classes of the binding's argtypes and restype.  A small C
+program built with gcc against include/graphstep.h prints the header's
+side; no GPU and no library call is involved."""
 import ctypes
 import os
 import subprocess
