@@ -69,7 +69,11 @@ def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``liboracle.so`` (gcc, -O2, no FP contraction)."""
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
-    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    # GS_ORACLE_CFLAGS: extra compiler flags (the sanitizer test builds a copy
+    # with -fsanitize=address,undefined)
+    extra = os.environ.get("GS_ORACLE_CFLAGS", "").split()
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra, _SRC, "-o", _LIB_PATH + ".tmp",
+            "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
