@@ -547,7 +547,9 @@ gs_status gs_candidates(const gs_workload *w, gs_tune_candidate *out, int32_t ca
  * iteration with graph creation amortised over the run.  Synchronous (on
  * models[0]'s stream).  Errors: GS_ERR_INVALID_ARG, GS_ERR_UNSUPPORTED (no
  * candidate fits), GS_ERR_NUMERIC (no finite prediction), GS_ERR_CUDA /
- * GS_ERR_OOM (message in gs_mlp_last_error(models[0])). */
+ * GS_ERR_OOM (message in gs_mlp_last_error(models[0])).  The exhaustive
+ * fallback (and the yardstick of a pick's regret) is gs_autotune over the
+ * same gs_candidates on a context of the workload. */
 gs_status gs_pick(gs_mlp *const *models, int32_t k, const gs_workload *w, gs_tune_candidate *best,
                   float *pred_ms_per_iter);
 
