@@ -747,7 +747,9 @@ def bench_line(args, w, m, clk, world):
 
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "ms_per_step_std": statistics.pstdev(m["graph_ms"]) if len(m["graph_ms"]) > 1 else 0.0,
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(args.workload, w, m["S"], m["depth"], world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -757,6 +759,7 @@ def bench_line(args, w, m, clk, world):
                      "isolated_GBps": isolated, "nominal_GBps": NOMINAL_HBM_GBS,
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
+                            "ms_per_step_std": statistics.pstdev(m["per_step_ms"]) if len(m["per_step_ms"]) > 1 else 0.0,
                             "graph_speedup": (value / world) / per_step_value},
         "paper_convention": {"ms_build_plus_run": m["paper_conv_ms"], "build_s": m["build_s"]},
         "gpu_launches": m["launches"] * args.steps,

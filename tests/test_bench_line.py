@@ -45,6 +45,8 @@ def test_bench_line_keys_and_arithmetic(workload):
     assert rf["traffic"] is None or isinstance(rf["traffic"], int)
     assert math.isclose(line["e2e"]["value"], units / 0.004, rel_tol=1e-12)
     assert line["gpu_launches"] == launches * 4
+    assert math.isclose(line["ms_per_step_std"], 0.1118033988749895, rel_tol=1e-9)  # pstdev of 3.0, 3.2, 3.1, 2.9
+    assert math.isclose(line["per_step_launch"]["ms_per_step_std"], 0.1118033988749895, rel_tol=1e-9)
     assert math.isclose(line["per_step_launch"]["graph_speedup"], line["value"] / (units / 6.05e-3), rel_tol=1e-12)
 
 
