@@ -1,0 +1,93 @@
+"""gs_multi_step_noalloc refuses bad arguments before any CUDA call (CPU).
+
+Each case carries at least one invalid argument, so the call returns from
+its checks and never reaches the device: the pointers below are
+placeholders that nothing dereferences."""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def g():
+    import __graft_entry__
+
+    __graft_entry__._builder().build()
+    import paper_2501_09398_gb300
+
+    return paper_2501_09398_gb300
+
+
+FAKE = 0x10000  # 16-byte aligned, never dereferenced
+
+
+def _inst(g, **over):
+    d = dict(T0=FAKE, T1=FAKE + 0x1000, P=FAKE + 0x2000, nx=64, ny=32, pitch=64, p_pitch=64)
+    d.update(over)
+    return g.gs_instance(ctypes.c_void_p(d["T0"]), ctypes.c_void_p(d["T1"]), ctypes.c_void_p(d["P"]), d["nx"],
+                         d["ny"], d["pitch"], d["p_pitch"])
+
+
+def _call(g, insts, n=None, parity=0, n_iters=10, coeffs=None, storage=None, bc=None):
+    arr = (g.gs_instance * max(1, len(insts)))(*insts)
+    c = coeffs or g.gs_heat_coeffs(0.5, 0.1, 0.1, 0.01, 0.05, 80.0)
+    out = ctypes.c_int32(-1)
+    st = g._lib.gs_multi_step_noalloc(arr, len(insts) if n is None else n, parity, n_iters, ctypes.byref(c),
+                                      g.GS_F32 if storage is None else storage,
+                                      g.GS_BC_CLAMP if bc is None else bc, None, ctypes.byref(out))
+    return st, g.gs_last_error(None), out.value
+
+
+def test_instance_count_outside_the_table(g):
+    for n in (0, -1, g.GS_NOALLOC_MAX_INSTANCES + 1):
+        st, msg, out = _call(g, [_inst(g, nx=0)], n=n)  # nx = 0 too: invalid whatever is checked first
+        assert st == g.GS_ERR_INVALID_ARG and out == -1
+        assert "n_inst" in msg or "nx" in msg
+    st, msg, _ = _call(g, [_inst(g)], n=0)
+    assert st == g.GS_ERR_INVALID_ARG and str(g.GS_NOALLOC_MAX_INSTANCES) in msg
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(parity=2), "INVALID_ARG"),
+    (dict(n_iters=-1), "INVALID_ARG"),
+    (dict(storage=7), "INVALID_ARG"),
+    (dict(bc=2), "INVALID_ARG"),  # PEC is an FDTD boundary
+])
+def test_call_arguments(g, kw, status):
+    st, _, out = _call(g, [_inst(g, nx=0)], **kw)  # a bad instance as a backstop
+    assert st == getattr(g, "GS_ERR_" + status) and out == -1
+
+
+def test_non_finite_coefficient(g):
+    for k in ("k", "cx", "cz2", "t_amb"):
+        c = g.gs_heat_coeffs(0.5, 0.1, 0.1, 0.01, 0.05, 80.0)
+        setattr(c, k, float("nan"))
+        st, msg, _ = _call(g, [_inst(g, nx=0)], coeffs=c)
+        assert st == g.GS_ERR_NUMERIC, k
+
+
+@pytest.mark.parametrize("over,storage", [
+    (dict(T0=0), None),                  # NULL buffer
+    (dict(T1=FAKE + 4), None),           # misaligned
+    (dict(P=FAKE + 8), None),
+    (dict(nx=0), None),
+    (dict(ny=(1 << 20) + 1), None),
+    (dict(pitch=63), None),              # below nx
+    (dict(pitch=66), None),              # not a multiple of 16 bytes (f32: 4 elements)
+    (dict(nx=60, pitch=60, p_pitch=60), 1),   # bf16 rows need 8-element pitches
+    (dict(p_pitch=32), None),
+])
+def test_bad_instance_is_named(g, over, storage):
+    # the second instance is the bad one; the message names it
+    st, msg, out = _call(g, [_inst(g), _inst(g, **over)], storage=storage)
+    assert st == g.GS_ERR_INVALID_ARG and out == -1
+    assert "instance 1" in msg, msg
+
+
+def test_null_arguments(g):
+    c = g.gs_heat_coeffs(0.5, 0.1, 0.1, 0.01, 0.05, 80.0)
+    assert g._lib.gs_multi_step_noalloc(None, 1, 0, 1, ctypes.byref(c), g.GS_F32, g.GS_BC_CLAMP, None,
+                                        None) == g.GS_ERR_INVALID_ARG
+    arr = (g.gs_instance * 1)(_inst(g, nx=0))
+    assert g._lib.gs_multi_step_noalloc(arr, 1, 0, 1, None, g.GS_F32, g.GS_BC_CLAMP, None,
+                                        None) == g.GS_ERR_INVALID_ARG
