@@ -249,18 +249,24 @@ extern "C" {
 
 gs_status gs_multi_create(gs_multi** out, int32_t n, const int64_t* nx, const int64_t* ny, gs_dtype storage,
                           gs_bc bc, void* stream) {
-    if (!out || !nx || !ny || n < 1) return GS_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (storage != GS_F32 && storage != GS_BF16 && storage != GS_F16) return GS_ERR_INVALID_ARG;
-    if (bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0) return GS_ERR_INVALID_ARG;
+    if (out) *out = nullptr;
+    if (!out || !nx || !ny || n < 1)
+        return global_fail(GS_ERR_INVALID_ARG, "gs_multi_create: NULL argument or n < 1");
+    if (storage != GS_F32 && storage != GS_BF16 && storage != GS_F16)
+        return global_fail(GS_ERR_INVALID_ARG, "gs_multi_create: unknown storage dtype");
+    if (bc != GS_BC_CLAMP && bc != GS_BC_DIRICHLET0)
+        return global_fail(GS_ERR_INVALID_ARG, "gs_multi_create: bc must be clamp or Dirichlet-0");
     int64_t items = 0;
     for (int i = 0; i < n; ++i) {
-        if (nx[i] < 1 || ny[i] < 1 || nx[i] > (1 << 20) || ny[i] > (1 << 20)) return GS_ERR_INVALID_ARG;
+        if (nx[i] < 1 || ny[i] < 1 || nx[i] > (1 << 20) || ny[i] > (1 << 20))
+            return global_fail(GS_ERR_INVALID_ARG,
+                               "gs_multi_create: instance " + std::to_string(i) + ": sizes must be in [1, 2^20]");
         items += (nx[i] + 127) / 128 * ny[i];
     }
-    if (items >= (int64_t(1) << 31)) return GS_ERR_INVALID_ARG;
+    if (items >= (int64_t(1) << 31))
+        return global_fail(GS_ERR_INVALID_ARG, "gs_multi_create: more than 2^31 work items");
     gs_multi* m = new (std::nothrow) gs_multi();
-    if (!m) return GS_ERR_OOM;
+    if (!m) return global_fail(GS_ERR_OOM, "gs_multi_create: host allocation failed");
     m->dt = storage;
     m->bc = bc;
     m->plan.block_x = 64;
@@ -276,7 +282,7 @@ gs_status gs_multi_create(gs_multi** out, int32_t n, const int64_t* nx, const in
     }
     if (e != cudaSuccess) {
         gs_multi_destroy(m);
-        return GS_ERR_CUDA;
+        return global_fail(GS_ERR_CUDA, std::string("gs_multi_create: stream creation: ") + cudaGetErrorString(e));
     }
     for (int i = 0; i < n; ++i) {
         gs_ctx* c = nullptr;

@@ -1,4 +1,5 @@
-"""gs_multi_step_noalloc refuses bad arguments before any CUDA call (CPU).
+"""gs_multi_step_noalloc and gs_multi_create refuse bad arguments before any
+CUDA call (CPU).
 
 Each case carries at least one invalid argument, so the call returns from
 its checks and never reaches the device: the pointers below are
@@ -91,3 +92,26 @@ def test_null_arguments(g):
     arr = (g.gs_instance * 1)(_inst(g, nx=0))
     assert g._lib.gs_multi_step_noalloc(arr, 1, 0, 1, None, g.GS_F32, g.GS_BC_CLAMP, None,
                                         None) == g.GS_ERR_INVALID_ARG
+
+
+def test_multi_create_refusals_carry_a_message(g):
+    # gs_multi_create's argument checks run before any CUDA call; each
+    # refusal sets *out to NULL and leaves its reason in gs_last_error(NULL)
+    i64 = ctypes.c_int64
+    good = (i64 * 2)(64, 32)
+    cases = [
+        (2, (i64 * 2)(64, 0), g.GS_F32, g.GS_BC_CLAMP, "instance 1"),
+        (2, (i64 * 2)(64, 1 << 21), g.GS_F32, g.GS_BC_CLAMP, "instance 1"),
+        (2, good, 9, g.GS_BC_CLAMP, "dtype"),
+        (2, good, g.GS_F32, g.GS_BC_PEC, "bc"),
+        (0, good, g.GS_F32, g.GS_BC_CLAMP, "n < 1"),
+    ]
+    for n, ny, dt, bc, text in cases:
+        h = ctypes.c_void_p(123)
+        st = g._lib.gs_multi_create(ctypes.byref(h), n, good, ny, dt, bc, None)
+        assert st == g.GS_ERR_INVALID_ARG and h.value is None, text
+        assert text in g.gs_last_error(None), (text, g.gs_last_error(None))
+    h = ctypes.c_void_p(123)
+    assert g._lib.gs_multi_create(ctypes.byref(h), 2, None, good, g.GS_F32, g.GS_BC_CLAMP, None) \
+        == g.GS_ERR_INVALID_ARG
+    assert h.value is None
