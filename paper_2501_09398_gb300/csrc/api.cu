@@ -743,7 +743,7 @@ const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err.c_str() : g
 
 gs_status gs_required_pitch(gs_dtype dtype, int64_t width, int64_t* pitch_out) {
     if (!pitch_out || width < 1 || (dtype != GS_F32 && dtype != GS_BF16 && dtype != GS_F16))
-        return GS_ERR_INVALID_ARG;
+        return fail(nullptr, GS_ERR_INVALID_ARG, "gs_required_pitch: need width >= 1, a known dtype and pitch_out");
     const int64_t v = vec_elems(dtype);
     *pitch_out = (width + v - 1) / v * v;
     return GS_OK;
@@ -811,7 +811,7 @@ gs_status gs_set_heat_coeffs(gs_ctx* c, const gs_heat_coeffs* hc) {
 }
 
 gs_status gs_set_scale(gs_ctx* c, float scale) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     if (!is_skel(c)) return fail(c, GS_ERR_INVALID_ARG, "not a skeleton context");
     if (!std::isfinite(scale)) return fail(c, GS_ERR_NUMERIC, "non-finite scale");
     c->scale = scale;
@@ -835,7 +835,7 @@ gs_status gs_set_fdtd_params(gs_ctx* c, const gs_fdtd_params* p) {
 }
 
 gs_status gs_set_fdtd_media(gs_ctx* c, const gs_medium* table, int32_t n) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     if (c->kind != GS_FDTD3D) return fail(c, GS_ERR_INVALID_ARG, "not an FDTD context");
     if (n < 0 || n > GS_MAX_MEDIA) return fail(c, GS_ERR_INVALID_ARG, "media table: 0 <= n <= 256 rows");
     if (n > 0 && !table) return fail(c, GS_ERR_INVALID_ARG, "NULL media table");
@@ -897,13 +897,13 @@ gs_status gs_plan_check(const gs_workload* w, const gs_plan* plan, gs_plan* reso
 }
 
 gs_status gs_get_plan(const gs_ctx* c, gs_plan* out) {
-    if (!c || !out) return GS_ERR_INVALID_ARG;
+    if (!c || !out) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context or output pointer");
     *out = c->plan;
     return GS_OK;
 }
 
 gs_status gs_bind_field(gs_ctx* c, gs_field id, void* ptr, int64_t pitch) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     const int f = resolve(c, id);
     int64_t width, rows;
     if (f < 0 || f > GS_FIELD_MAT || f == GS_FIELD_T || !field_shape(c, f, &width, &rows))
@@ -972,7 +972,7 @@ gs_status gs_read_field(gs_ctx* c, gs_field id, float* host_out, int64_t n) {
 }
 
 gs_status gs_get_parity(const gs_ctx* c, int32_t* out) {
-    if (!c || !out) return GS_ERR_INVALID_ARG;
+    if (!c || !out) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context or output pointer");
     *out = c->parity;
     return GS_OK;
 }
@@ -996,13 +996,13 @@ gs_status gs_set_time(gs_ctx* c, int64_t n) {
 }
 
 gs_status gs_get_time(const gs_ctx* c, int64_t* out) {
-    if (!c || !out) return GS_ERR_INVALID_ARG;
+    if (!c || !out) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context or output pointer");
     *out = c->time;
     return GS_OK;
 }
 
 gs_status gs_step(gs_ctx* c, int64_t n_iters, int64_t batch_size) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     if (n_iters < 0 || batch_size < 0) return fail(c, GS_ERR_INVALID_ARG, "n_iters and batch_size must be >= 0");
     gs_status st = ensure_descs(c);
     if (st != GS_OK) return st;
@@ -1040,7 +1040,7 @@ gs_status gs_step(gs_ctx* c, int64_t n_iters, int64_t batch_size) {
 }
 
 gs_status gs_graph_build(gs_ctx* c, int64_t S) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     if (S < 1) return fail(c, GS_ERR_INVALID_ARG, "batch_size must be >= 1");
     gs_status st = ensure_descs(c);
     if (st != GS_OK) return st;
@@ -1080,7 +1080,7 @@ gs_status gs_graph_build(gs_ctx* c, int64_t S) {
 }
 
 gs_status gs_graph_launch(gs_ctx* c, int64_t n_launches) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     if (n_launches < 0) return fail(c, GS_ERR_INVALID_ARG, "n_launches must be >= 0");
     if (c->built_S == 0) return fail(c, GS_ERR_STATE, "no graph built (call gs_graph_build first)");
     gs_status st = run_batches(c, c->built_S, n_launches);
@@ -1091,21 +1091,21 @@ gs_status gs_graph_launch(gs_ctx* c, int64_t n_launches) {
 }
 
 gs_status gs_graph_destroy(gs_ctx* c) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     if (c->stream) cudaStreamSynchronize(c->stream);
     destroy_graphs(c);
     return GS_OK;
 }
 
 gs_status gs_sync(gs_ctx* c) {
-    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context");
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     GS_CUDA(c, cudaGetLastError());
     return GS_OK;
 }
 
 gs_status gs_get_stats(const gs_ctx* c, gs_stats* out) {
-    if (!c || !out) return GS_ERR_INVALID_ARG;
+    if (!c || !out) return fail(nullptr, GS_ERR_INVALID_ARG, "NULL context or output pointer");
     *out = c->stats;
     return GS_OK;
 }

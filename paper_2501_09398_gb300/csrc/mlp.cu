@@ -384,10 +384,10 @@ bool dev_ptr_ok(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 3
 extern "C" {
 
 gs_status gs_mlp_create(gs_mlp** out, uint64_t seed, void* stream) {
-    if (!out) return GS_ERR_INVALID_ARG;
+    if (!out) return global_fail(GS_ERR_INVALID_ARG, "gs_mlp_create: out is NULL");
     *out = nullptr;
     gs_mlp* m = new (std::nothrow) gs_mlp();
-    if (!m) return GS_ERR_OOM;
+    if (!m) return global_fail(GS_ERR_OOM, "gs_mlp_create: host allocation failed");
     cudaError_t e = cudaSuccess;
     if (stream) {
         m->stream = static_cast<cudaStream_t>(stream);

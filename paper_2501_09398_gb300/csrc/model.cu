@@ -68,7 +68,8 @@ gs_status gs_model_fit(const double* S, const double* t_create, const double* t_
 }
 
 gs_status gs_model_total(const gs_model* m, double S, double* total_out) {
-    if (!m || !total_out || !(S >= 1)) return GS_ERR_INVALID_ARG;
+    if (!m || !total_out || !(S >= 1))
+        return global_fail(GS_ERR_INVALID_ARG, "gs_model_total: need a model, an output and S >= 1");
     *total_out = m->k_c * S + m->b_c + m->a / S + m->b;
     return GS_OK;
 }

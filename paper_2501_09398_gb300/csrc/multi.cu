@@ -238,7 +238,7 @@ gs_status capture_graph(gs_multi* m, int64_t S, int p, cudaGraphExec_t* out) {
 }
 
 gs_status check_inst(gs_multi* m, int32_t i) {
-    if (!m) return GS_ERR_INVALID_ARG;
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
     if (i < 0 || i >= (int32_t)m->inst.size()) return mfail(m, GS_ERR_INVALID_ARG, "instance index out of range");
     return GS_OK;
 }
@@ -314,7 +314,8 @@ gs_status gs_multi_destroy(gs_multi* m) {
 const char* gs_multi_last_error(const gs_multi* m) { return m ? m->err.c_str() : ""; }
 
 gs_status gs_multi_set_heat_coeffs(gs_multi* m, const gs_heat_coeffs* c) {
-    if (!m || !c) return GS_ERR_INVALID_ARG;
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
+    if (!c) return mfail(m, GS_ERR_INVALID_ARG, "NULL argument");
     for (size_t i = 0; i < m->inst.size(); ++i) {
         gs_status st = gs_set_heat_coeffs(m->inst[i], c);
         if (st != GS_OK) return from_ctx(m, st, (int)i);
@@ -325,7 +326,8 @@ gs_status gs_multi_set_heat_coeffs(gs_multi* m, const gs_heat_coeffs* c) {
 }
 
 gs_status gs_multi_set_plan(gs_multi* m, const gs_multi_plan* p) {
-    if (!m || !p) return GS_ERR_INVALID_ARG;
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
+    if (!p) return mfail(m, GS_ERR_INVALID_ARG, "NULL argument");
     gs_multi_plan q = *p;
     // MARCH tiles measured faster here: a persistent loop over small column
     // tiles exposes one full load round trip per work item
@@ -386,13 +388,14 @@ gs_status gs_multi_read_field(gs_multi* m, int32_t i, gs_field id, float* host_o
 }
 
 gs_status gs_multi_get_parity(const gs_multi* m, int32_t* out) {
-    if (!m || !out) return GS_ERR_INVALID_ARG;
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
+    if (!out) return global_fail(GS_ERR_INVALID_ARG, "NULL output pointer");
     *out = m->parity;
     return GS_OK;
 }
 
 gs_status gs_multi_step(gs_multi* m, int64_t n_iters, int64_t batch_size, gs_multi_mode mode) {
-    if (!m) return GS_ERR_INVALID_ARG;
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
     if (n_iters < 0 || batch_size < 0) return mfail(m, GS_ERR_INVALID_ARG, "n_iters and batch_size must be >= 0");
     if (mode != GS_MULTI_FUSED && mode != GS_MULTI_SEPARATE) return mfail(m, GS_ERR_INVALID_ARG, "unknown mode");
     if (n_iters == 0) return GS_OK;
@@ -439,13 +442,14 @@ gs_status gs_multi_step(gs_multi* m, int64_t n_iters, int64_t batch_size, gs_mul
 }
 
 gs_status gs_multi_sync(gs_multi* m) {
-    if (!m) return GS_ERR_INVALID_ARG;
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
     GS_MCUDA(m, cudaStreamSynchronize(m->stream));
     return GS_OK;
 }
 
 gs_status gs_multi_get_stats(const gs_multi* m, gs_stats* out) {
-    if (!m || !out) return GS_ERR_INVALID_ARG;
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
+    if (!out) return global_fail(GS_ERR_INVALID_ARG, "NULL output pointer");
     *out = m->stats;
     for (gs_ctx* c : m->inst) {
         gs_stats s;

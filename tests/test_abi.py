@@ -90,3 +90,32 @@ def test_null_handles(lib):
     assert g.raw_call("gs_step", None, 1, 1) == g.GS_ERR_INVALID_ARG
     assert g.raw_call("gs_sync", None) == g.GS_ERR_INVALID_ARG
     assert g.raw_call("gs_graph_launch", None, 1) == g.GS_ERR_INVALID_ARG
+
+
+def test_null_handle_refusals_leave_a_message(lib):
+    # with no context to hold it, the reason goes to gs_last_error(NULL)
+    import paper_2501_09398_gb300 as g
+
+    out64 = ctypes.c_int64()
+    out32 = ctypes.c_int32()
+    cases = [
+        ("gs_step", (None, 1, 1)), ("gs_sync", (None,)), ("gs_graph_build", (None, 10)),
+        ("gs_graph_launch", (None, 1)), ("gs_graph_destroy", (None,)), ("gs_set_scale", (None, 1.0)),
+        ("gs_bind_field", (None, g.GS_FIELD_T0, None, 16)), ("gs_get_time", (None, ctypes.byref(out64))),
+        ("gs_get_parity", (None, ctypes.byref(out32))), ("gs_get_plan", (None, ctypes.byref(g.gs_plan()))),
+        ("gs_get_stats", (None, ctypes.byref(g.gs_stats()))), ("gs_set_fdtd_media", (None, None, 0)),
+        ("gs_required_pitch", (g.GS_F32, 0, ctypes.byref(out64))),
+        ("gs_multi_sync", (None,)), ("gs_multi_get_parity", (None, ctypes.byref(out32))),
+        ("gs_multi_get_stats", (None, ctypes.byref(g.gs_stats()))),
+        ("gs_multi_set_plan", (None, ctypes.byref(g.gs_multi_plan()))),
+        ("gs_multi_set_heat_coeffs", (None, None)),
+        ("gs_model_total", (None, 10.0, ctypes.byref(ctypes.c_double()))),
+    ]
+    h = ctypes.c_void_p()
+    for name, args in cases:
+        # a known message first (gs_create refusing an unknown kind), which
+        # the refusal under test must replace with its own
+        g.raw_call("gs_create", ctypes.byref(h), 7, 8, 8, 1, g.GS_F32, g.GS_BC_CLAMP, None)
+        assert g.gs_last_error(None) == "unknown kind"
+        assert g.raw_call(name, *args) == g.GS_ERR_INVALID_ARG, name
+        assert g.gs_last_error(None) not in ("", "unknown kind"), name
