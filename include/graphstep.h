@@ -226,7 +226,11 @@ const char *gs_status_string(gs_status s);
 
 /* Message of the last failed call on ctx ("" if none).  The pointer stays
  * valid until the next call on ctx.  ctx == NULL gives the message of the
- * last failed gs_create/gs_multi_create on this thread. */
+ * last call on this thread that failed with no context to hold it: a failed
+ * gs_create or gs_multi_create, a NULL handle, and the host-only calls
+ * (gs_required_pitch, gs_model_*, gs_features, gs_plan_check,
+ * gs_candidates, argument errors of gs_pick and gs_multi_step_noalloc).
+ * A successful call does not clear it. */
 const char *gs_last_error(const gs_ctx *ctx);
 
 /* Smallest valid row pitch (elements) for rows of `width` elements of
