@@ -791,8 +791,10 @@ def main():
                     help="run the batches as one device-side loop (conditional while node) per step")
     ap.add_argument("--traverse", type=int, default=0,
                     help="block order of consecutive launches (gs_traverse: 0 auto, 1 forward, 2 alternate)")
-    ap.add_argument("--no-extras", action="store_true", help="skip the 2D 512^2 / 4096^2 side measurements")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the side measurements of the default run (other workloads, the batch-size sweep, "
+                         "the 64-stream baseline, the FDTD storage-type errors)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle (timing and error checks)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
