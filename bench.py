@@ -98,20 +98,27 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per launch from the committed ncu summaries, if they were
-    taken on the current kernel sources (else None)."""
+def recorded_capture(workload):
+    """(DRAM bytes, cold-cache microseconds or None) per launch from the
+    committed ncu summaries, if they were taken on the current kernel
+    sources (else (None, None))."""
     import glob
     import re
 
     sha = kernel_sha()
-    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as f:
             for line in f:
-                m = re.match(r"bench-traffic: workload=(\S+) kernel=\S+ sha256=(\w+) bytes=(\d+)", line)
+                m = re.match(r"bench-traffic: workload=(\S+) kernel=\S+ sha256=(\w+) bytes=(\d+)(?: us=(\S+))?", line)
                 if m and m.group(1) == workload and m.group(2) == sha:
-                    return int(m.group(3))
-    return None
+                    return int(m.group(3)), (float(m.group(4)) if m.group(4) else None)
+    return None, None
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summaries, if they were
+    taken on the current kernel sources (else None)."""
+    return recorded_capture(workload)[0]
 
 
 def cells_of(w):
@@ -133,6 +140,73 @@ def algo_bytes_per_launch(w, depth, elem=4):
         return cells_of(w) * 3 * elem
     plane = w["nx"] * w["ny"]
     return cells_of(w) * 2 * elem + plane * elem
+
+
+def working_set_bytes(w, elem=4):
+    """Bytes one step touches: both thermal buffers and the power map; the
+    six FDTD components (and the material map); every instance's fields."""
+    if w["kind"] == "fdtd":
+        m = (w["N"] + 1) ** 3
+        return m * (6 * elem + (1 if w.get("media") else 0))
+    if w["kind"] == "multi":
+        return cells_of(w) * 3 * elem
+    return cells_of(w) * 2 * elem + w["nx"] * w["ny"] * elem
+
+
+def column_geometry(w, plan, depth):
+    """(blocks, threads per block) of the thermal COLUMN kernel's launch for
+    this workload and plan (the launch shapes of heat_desc), else None."""
+    if w["kind"] not in ("heat2d", "heat3d") or plan.get("kernel", 4) != 4:
+        return None
+    cdiv = lambda a, b: -(-a // b)  # noqa: E731
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    if depth > 1:
+        if w["kind"] == "heat3d":
+            return None
+        bw = max(1, min(plan.get("block_x", 64) // 32, 8))
+        return cdiv(nx, 30 * 4) * cdiv(ny, 4 * bw), 32 * bw
+    by = max(1, min(plan.get("rows", 4), 8))
+    cw = 4  # cells per thread in f32 (2D: one 16-byte vector; 3D: four cells)
+    chunks = cdiv(nz, 8) if nz > 8 else 1
+    return cdiv(nx, 32 * cw) * cdiv(ny, by) * chunks, 32 * by
+
+
+def graph_node_floor_us(blocks, threads, flush, nodes=100, launches=10):
+    """Per-node time of a graph of `nodes` skeleton-kernel nodes launched on
+    `blocks` blocks of `threads` threads, each thread scaling one 16-byte
+    vector in place (an L2-resident field): what one graph node of that
+    launch shape costs when its kernel does almost nothing."""
+    import torch
+
+    import paper_2501_09398_gb300 as g
+
+    n = blocks * threads * 4
+    st = torch.cuda.current_stream()
+    ctx = g.gs_create(g.GS_SKELETON, n, 1, 1, g.GS_F32, g.GS_BC_CLAMP, st.cuda_stream)
+    x = torch.ones(n, dtype=torch.float32, device="cuda")
+    try:
+        g.gs_bind_field(ctx, g.GS_FIELD_X, x.data_ptr(), n)
+        g.gs_set_plan(ctx, block_x=threads)
+        g.gs_step(ctx, nodes, nodes)  # builds the graph
+        times = []
+        for _ in range(5):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            g.gs_step(ctx, nodes * launches, nodes)
+            b.record(st)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+    finally:
+        g.gs_destroy(ctx)
+    return statistics.median(times) * 1e3 / (nodes * launches)
+
+
+def l2_bytes():
+    import torch
+
+    v = getattr(torch.cuda.get_device_properties(torch.cuda.current_device()), "L2_cache_size", 0)
+    return int(v) if v else 126 << 20
 
 
 # ------------------------------------------------------------ clocks ----
@@ -590,6 +664,11 @@ def measure_workload(name, w, args, flush, with_e2e=True):
             g.gs_graph_build(run.ctx, S)
         kern_ms = kernel_avg_ms(run, flush)
         e2e = e2e_steps(run, S, max(3, min(args.steps, 20))) if with_e2e else None
+        l2 = l2_bytes()
+        floor = None
+        geo = column_geometry(w, g_plan, depth)
+        if with_e2e and geo is not None and working_set_bytes(w) <= 0.5 * l2:
+            floor = graph_node_floor_us(geo[0], geo[1], flush)
         # result after one clean run, for the error check
         run.reset()
         run.step(S)
@@ -598,7 +677,7 @@ def measure_workload(name, w, args, flush, with_e2e=True):
         run.close()
     return dict(S=S, depth=depth, graph_ms=graph_ms, per_step_ms=per_step_ms, kern_ms=kern_ms, e2e=e2e,
                 paper_conv_ms=paper_conv_ms, build_s=build_s, result=result,
-                launches=run.launches_per_step(S))
+                launches=run.launches_per_step(S), l2_bytes=l2, node_floor_us=floor)
 
 
 SWEEP_S = (1, 10, 50, 100, 500, 1000)
@@ -731,7 +810,15 @@ def error_vs_oracle(w, result, full_ref):
 
 def bench_line(args, w, m, clk, world):
     """The contract's JSON line (without cpu_baseline and extras) from one
-    workload's measurements `m` (measure_workload) and clock record `clk`."""
+    workload's measurements `m` (measure_workload) and clock record `clk`.
+
+    roofline.bound says what limits the workload: "hbm" when one step touches
+    more than half of the L2 cache (the fields stream from DRAM every step),
+    else "l2/latency" (the fields stay in L2; a launch's time is its load
+    latency and the graph node's own cost, reported as per_node_us beside
+    graph_node_floor_us, a node of the same launch shape doing almost no
+    work).  achieved/frac are the in-step rate of algorithmic bytes against
+    the measured HBM copy peak either way."""
     cells = cells_of(w)
     value, total_ms, _ = aggregate(m["graph_ms"], cells * w["iters"])
     ms_per_step = total_ms / args.steps
@@ -744,6 +831,20 @@ def bench_line(args, w, m, clk, world):
     launch_ms = ms_per_step / m["launches"]
     achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
     isolated = bytes_launch / (m["kern_ms"] * 1e-3) / 1e9
+    ws = working_set_bytes(w)
+    l2 = m.get("l2_bytes") or (126 << 20)
+    bound = "hbm" if ws > 0.5 * l2 else "l2/latency"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(args.workload), "peak_kind": peak_kind,
+            "working_set_bytes": ws, "l2_bytes": l2,
+            "per_node_us": launch_ms * 1e3, "graph_node_floor_us": m.get("node_floor_us"),
+            "launch_ms_in_step": launch_ms,
+            "bytes_per_launch": bytes_launch, "isolated_launch_ms": m["kern_ms"],
+            "isolated_GBps": isolated, "nominal_GBps": NOMINAL_HBM_GBS,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    if bound != "hbm":
+        roof["note"] = ("working set in L2: frac compares the in-step rate of algorithmic bytes with the HBM copy "
+                        "peak and is no HBM roofline; the HBM roofline of the same kernel is hbm_roofline")
 
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
@@ -752,12 +853,7 @@ def bench_line(args, w, m, clk, world):
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(args.workload, w, m["S"], m["depth"], world),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(args.workload), "peak_kind": peak_kind,
-                     "launch_ms_in_step": launch_ms,
-                     "bytes_per_launch": bytes_launch, "isolated_launch_ms": m["kern_ms"],
-                     "isolated_GBps": isolated, "nominal_GBps": NOMINAL_HBM_GBS,
-                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
+        "roofline": roof,
         "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
                             "ms_per_step_std": statistics.pstdev(m["per_step_ms"]) if len(m["per_step_ms"]) > 1 else 0.0,
                             "graph_speedup": (value / world) / per_step_value},
@@ -770,6 +866,28 @@ def bench_line(args, w, m, clk, world):
         line["e2e"] = {"value": cells * w["iters"] / dt, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h}
     return line
+
+
+def hbm_roofline_of(name, w, mm):
+    """The HBM roofline figure of an HBM-bound workload's graph-batched run
+    (measure_workload's record `mm`): in-step rate of algorithmic bytes per
+    launch against the measured copy peak, with the cold-cache DRAM traffic
+    and launch time of the committed ncu capture of the same kernel sources
+    (None when the sources changed since)."""
+    peak, peak_kind = _peaks()
+    gms = statistics.mean(mm["graph_ms"])
+    bl = algo_bytes_per_launch(w, mm["depth"])
+    launch_ms = gms / mm["launches"]
+    achieved = bl / (launch_ms * 1e-3) / 1e9
+    traffic, cold_us = recorded_capture(name)
+    out = {"workload": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": bl,
+           "per_launch_us_in_step": launch_ms * 1e3, "depth": mm["depth"], "S": mm["S"],
+           "working_set_bytes": working_set_bytes(w)}
+    if cold_us:
+        out["cold_cache_us"] = cold_us
+        out["cold_cache_frac"] = bl / (cold_us * 1e-6) / 1e9 / peak
+    return out
 
 
 def main():
@@ -875,6 +993,10 @@ def main():
             extra[f"{nm}/{tag}"] = {"graph_value": gv, "per_step_value": pv, "graph_speedup": gv / pv,
                                     "S": mm["S"], "depth": mm["depth"], "in_step_GBps": bw,
                                     "hbm_frac": bw / peak, "paper_convention_ms": mm["paper_conv_ms"]}
+            if (nm, tag) == ("heat2d-4096", "depth1"):
+                # the HBM roofline of the default workload's kernel (COLUMN,
+                # depth 1) where the fields stream from DRAM every step
+                line["hbm_roofline"] = hbm_roofline_of(nm, ww, mm)
         # the batch-size sweep of the 2D 512^2 and 3D 512x512x8 workloads at
         # temporal depths 1, 2 and 4; a failure here is recorded, not raised
         sweeps = {}

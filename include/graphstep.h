@@ -649,6 +649,91 @@ gs_status gs_multi_sync(gs_multi *m);
 /* Counters summed over the fused kernel and every instance context. */
 gs_status gs_multi_get_stats(const gs_multi *m, gs_stats *out);
 
+/* ----------------------------------------------- slab decomposition -- */
+
+/* One grid split along its slowest axis into n_slabs sub-domains (slabs),
+ * each stepped by its own launches with halo rows exchanged between
+ * neighbours after every launch: the decomposition a grid too large for one
+ * GPU would take across several GPUs (one slab per GPU, the halo exchange a
+ * peer copy), run here with every slab on the current device.  The paper
+ * runs on one GPU and has no such decomposition; it extends the paper's
+ * iteration batches (Sec. III-A): a batch graph of S iterations holds every
+ * slab's kernel nodes and the halo copy nodes between them, so each slab's
+ * next kernel waits only on its own previous kernel and the copies into and
+ * out of its fields, and the slabs' kernels of one step can run at once.
+ *
+ * Split axis: y (rows) for GS_HEAT2D, z (planes) for GS_HEAT3D and GS_FDTD3D.
+ * Slab s owns a contiguous range of rows/planes (sizes differing by at most
+ * one, lower slabs the larger) and stores `halo` extra rows/planes on each
+ * side it shares with a neighbour.  Thermal: halo = the largest temporal
+ * depth the plans will use (a depth-t launch needs t halo rows, refreshed
+ * from the neighbour after each launch); every slab must own >= halo rows.
+ * FDTD: halo must be 1 (H's plane below a slab is refreshed after the H
+ * update, E's plane above after the E update); with N cells the N+1 array
+ * planes are partitioned, every slab owning >= 1.
+ * Results are bit-identical to an undivided context of the same grid, plan
+ * (depth, kernel) and coefficients, for every n_slabs, batch size, remainder
+ * and PDL setting.
+ * Memory: the slab set allocates and owns its fields (each slab's rows plus
+ * halos; the FDTD components of a slab in one allocation); the caller moves
+ * data with gs_slab_upload / gs_slab_read_field (dense host arrays of the
+ * whole grid). */
+typedef struct gs_slab gs_slab;
+
+/* Create a slab set.  kind, sizes, storage, bc, stream: as gs_create
+ * (stream NULL: the set creates its own); n_slabs in [1, 64]; halo as above.
+ * The FDTD source is off until gs_slab_set_fdtd_params.  Errors:
+ * GS_ERR_INVALID_ARG (sizes, a slab owning too few rows), GS_ERR_CUDA,
+ * GS_ERR_OOM; message in gs_last_error(NULL); *out NULL on failure. */
+gs_status gs_slab_create(gs_slab **out, gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc,
+                         int32_t n_slabs, int32_t halo, void *stream);
+
+/* Synchronise, free every slab's graphs, contexts and fields.  NULL is a no-op. */
+gs_status gs_slab_destroy(gs_slab *s);
+
+/* Message of the last failed call on s ("" if none). */
+const char *gs_slab_last_error(const gs_slab *s);
+
+/* The rows (2D) or planes (3D, FDTD arrays) slab k owns: [*first, *first + *count). */
+gs_status gs_slab_extent(const gs_slab *s, int32_t k, int64_t *first, int64_t *count);
+
+/* As gs_set_heat_coeffs / gs_set_fdtd_params (source cell in global
+ * coordinates; the slab that owns its plane applies it) / gs_set_plan for
+ * every slab.  gs_slab_set_plan: temporal_depth must not exceed the halo
+ * (GS_ERR_UNSUPPORTED), and graph_loop and device_launch are not provided
+ * for slab sets (GS_ERR_UNSUPPORTED); use_pdl applies to the per-step
+ * launches, while a batch graph's kernel nodes follow copy nodes, whose
+ * edges are full dependencies. */
+gs_status gs_slab_set_heat_coeffs(gs_slab *s, const gs_heat_coeffs *c);
+gs_status gs_slab_set_fdtd_params(gs_slab *s, const gs_fdtd_params *p);
+gs_status gs_slab_set_plan(gs_slab *s, const gs_plan *plan);
+
+/* Copy a dense float32 host array of the whole grid (as gs_upload for an
+ * undivided context: T/T0/T1 or P, or an FDTD component) into every slab's
+ * rows and halos.  GS_FIELD_T is the buffer holding the current state.
+ * Synchronous. */
+gs_status gs_slab_upload(gs_slab *s, gs_field id, const float *host, int64_t n);
+
+/* Gather the rows every slab owns into a dense float32 host array of the
+ * whole grid.  Synchronous. */
+gs_status gs_slab_read_field(gs_slab *s, gs_field id, float *host_out, int64_t n);
+
+/* Advance n_iters iterations: batch_size 0, per-step launches of every slab
+ * followed by the halo copies; batch_size S > 0, floor(n/S) launches of a
+ * cached batch graph and one remainder graph of n mod S iterations, as
+ * gs_step.  Asynchronous. */
+gs_status gs_slab_step(gs_slab *s, int64_t n_iters, int64_t batch_size);
+
+/* FDTD time index of the next step (written to every slab's counter). */
+gs_status gs_slab_set_time(gs_slab *s, int64_t n);
+
+gs_status gs_slab_sync(gs_slab *s);
+
+/* Counters of the set: graphs built and launched, kernel launches (per-step
+ * path, summed over slabs), iterations; last_build_nodes counts the kernel
+ * and copy nodes of the last batch graph. */
+gs_status gs_slab_get_stats(const gs_slab *s, gs_stats *out);
+
 /* -------------------------------------------- step without allocation -- */
 
 /* The paper has no counterpart to this entry point: it serves callers that
@@ -677,17 +762,27 @@ typedef struct gs_instance {
  * the current state of every instance (0: T0); *parity_out (may be NULL)
  * receives the parity after the call.  Same update and results, bit for bit,
  * as gs_multi_step in GS_MULTI_FUSED mode.  Asynchronous.
- * Set-up: the first call on a device resolves the table's device address
- * (cudaGetSymbolAddress) with that device current, so make the first call on
- * each device before relying on the call doing no set-up work.
+ * Buffers: T0 and T1 occupy ny*pitch elements each and P ny*p_pitch; no
+ * buffer may overlap another one, of the same instance or of another, except
+ * that P buffers may overlap other P buffers (they are only read).
+ * Set-up: the first call on a device (with a n_iters > 0) resolves the
+ * table's device address (cudaGetSymbolAddress), the SM count and the step
+ * kernel's occupancy with that device current, and loads the kernels; later
+ * calls in the same CUDA context reuse them (a new context on the device,
+ * e.g. after cudaDeviceReset, gets a new set-up on its first call).  Make
+ * that first call on each device before any stream capture and before
+ * relying on the call doing no set-up work.
+ * Each call writes the table with at most four small fill launches whose
+ * parameters carry the rows (nothing refers to the caller's memory after
+ * the call returns), then launches one step per iteration.
  * Sharing: every call writes the same table (stream-ordered on its own
  * stream) and the table keeps the last call's contents; calls that overlap
  * on the GPU (different streams, or host threads racing) race on it.
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  * Errors (message in gs_last_error(NULL)): GS_ERR_INVALID_ARG for n_inst
- * outside [1, GS_NOALLOC_MAX_INSTANCES], bad pointers, sizes or pitches, or
- * more than 2^31 work items; GS_ERR_NUMERIC for non-finite coefficients;
- * GS_ERR_CUDA if a CUDA call fails. */
+ * outside [1, GS_NOALLOC_MAX_INSTANCES], bad pointers, sizes or pitches,
+ * overlapping buffers, or more than 2^31 work items; GS_ERR_NUMERIC for
+ * non-finite coefficients; GS_ERR_CUDA if a CUDA call fails. */
 gs_status gs_multi_step_noalloc(const gs_instance *inst, int32_t n_inst, int32_t parity, int64_t n_iters,
                                 const gs_heat_coeffs *coeffs, gs_dtype storage, gs_bc bc, void *stream,
                                 int32_t *parity_out);

@@ -595,6 +595,97 @@ def gs_multi_get_stats(m) -> dict:
     return {n: getattr(s, n) for n, _ in gs_stats._fields_}
 
 
+# --------------------------------------------------- slab decomposition --
+_sig("gs_slab_create", [ctypes.POINTER(_vp), ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int, _i32, _i32,
+                        _vp])
+_sig("gs_slab_destroy", [_vp])
+_sig("gs_slab_last_error", [_vp], ctypes.c_char_p)
+_sig("gs_slab_extent", [_vp, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)])
+_sig("gs_slab_set_heat_coeffs", [_vp, ctypes.POINTER(gs_heat_coeffs)])
+_sig("gs_slab_set_fdtd_params", [_vp, ctypes.POINTER(gs_fdtd_params)])
+_sig("gs_slab_set_plan", [_vp, ctypes.POINTER(gs_plan)])
+_sig("gs_slab_upload", [_vp, ctypes.c_int, _fp, _i64])
+_sig("gs_slab_read_field", [_vp, ctypes.c_int, _fp, _i64])
+_sig("gs_slab_step", [_vp, _i64, _i64])
+_sig("gs_slab_set_time", [_vp, _i64])
+_sig("gs_slab_sync", [_vp])
+_sig("gs_slab_get_stats", [_vp, ctypes.POINTER(gs_stats)])
+
+
+def _scheck(st: int, s):
+    if st != GS_OK:
+        msg = _lib.gs_slab_last_error(s).decode(errors="replace") if s else ""
+        raise GsError(st, msg or _lib.gs_last_error(None).decode(errors="replace"))
+
+
+def gs_slab_create(kind: int, nx: int, ny: int, nz: int, n_slabs: int, halo: int = 1, dtype: int = GS_F32,
+                   bc: int = GS_BC_CLAMP, stream=None):
+    h = _vp()
+    st = _lib.gs_slab_create(ctypes.byref(h), kind, nx, ny, nz, dtype, bc, n_slabs, halo,
+                             _vp(stream) if stream else None)
+    if st != GS_OK:
+        raise GsError(st, _lib.gs_last_error(None).decode(errors="replace"))
+    return h
+
+
+def gs_slab_destroy(s) -> None:
+    _scheck(_lib.gs_slab_destroy(s), None)
+
+
+def gs_slab_last_error(s) -> str:
+    return _lib.gs_slab_last_error(s).decode(errors="replace")
+
+
+def gs_slab_extent(s, k: int):
+    """(first, count) of the rows/planes slab k owns."""
+    a, b = _i64(), _i64()
+    _scheck(_lib.gs_slab_extent(s, k, ctypes.byref(a), ctypes.byref(b)), None)
+    return a.value, b.value
+
+
+def gs_slab_set_heat_coeffs(s, k=0.5, cx=0.1, cy=0.1, cz=0.01, cz2=0.05, t_amb=80.0) -> None:
+    c = gs_heat_coeffs(k, cx, cy, cz, cz2, t_amb)
+    _scheck(_lib.gs_slab_set_heat_coeffs(s, ctypes.byref(c)), s)
+
+
+def gs_slab_set_fdtd_params(s, courant=0.5, src_on=0, src=(0, 0, 0), amp=1.0, delay=60.0, width=20.0) -> None:
+    p = gs_fdtd_params(courant, src_on, src[0], src[1], src[2], amp, delay, width)
+    _scheck(_lib.gs_slab_set_fdtd_params(s, ctypes.byref(p)), s)
+
+
+def gs_slab_set_plan(s, block_x=0, rows=0, tile_x=0, tile_y=0, temporal_depth=0, use_pdl=0, device_launch=0,
+                     kernel=0, graph_loop=0, traverse=0) -> None:
+    p = gs_plan(block_x, rows, tile_x, tile_y, temporal_depth, use_pdl, device_launch, kernel, graph_loop, traverse)
+    _scheck(_lib.gs_slab_set_plan(s, ctypes.byref(p)), s)
+
+
+def gs_slab_upload(s, field: int, host: np.ndarray) -> None:
+    _scheck(_lib.gs_slab_upload(s, field, _f32_ptr(host), host.size), s)
+
+
+def gs_slab_read_field(s, field: int, out: np.ndarray) -> np.ndarray:
+    _scheck(_lib.gs_slab_read_field(s, field, _f32_ptr(out), out.size), s)
+    return out
+
+
+def gs_slab_step(s, n_iters: int, batch_size: int) -> None:
+    _scheck(_lib.gs_slab_step(s, n_iters, batch_size), s)
+
+
+def gs_slab_set_time(s, n: int) -> None:
+    _scheck(_lib.gs_slab_set_time(s, n), s)
+
+
+def gs_slab_sync(s) -> None:
+    _scheck(_lib.gs_slab_sync(s), s)
+
+
+def gs_slab_get_stats(s) -> dict:
+    st = gs_stats()
+    _scheck(_lib.gs_slab_get_stats(s, ctypes.byref(st)), s)
+    return {n: getattr(st, n) for n, _ in gs_stats._fields_}
+
+
 # ------------------------------------------------- step without allocation --
 GS_NOALLOC_MAX_INSTANCES = 256
 

@@ -78,6 +78,7 @@ struct gs_ctx {
     std::map<std::pair<int64_t, int>, GraphEntry> graphs;
     std::map<std::pair<int64_t, int>, GraphEntry> loops;  // device-loop graphs
     int64_t built_S = 0;
+    int64_t rem_S = 0;  // size of the peeled remainder graphs kept from gs_step (0: none)
     gs_stats stats{};
     std::string err;
 };
@@ -132,7 +133,7 @@ bool field_shape(const gs_ctx* c, int id, int64_t* width, int64_t* rows) {
     }
     if ((id >= GS_FIELD_EX && id <= GS_FIELD_HZ) || id == GS_FIELD_MAT) {
         *width = c->nx + 1;
-        *rows = (c->nx + 1) * (c->nx + 1);
+        *rows = (c->nx + 1) * (c->nz + 1);  // nz == nx except in a slab set's sub-domains
         return true;
     }
     return false;
@@ -152,6 +153,27 @@ void destroy_graphs(gs_ctx* c) {
         m->clear();
     }
     c->built_S = 0;
+    c->rem_S = 0;
+}
+
+// gs_step keeps the remainder graphs (both parities) of one remainder size
+// only: a caller that varies n_iters would otherwise collect a graph of up to
+// S-1 nodes per remainder it ever met.  Graphs of the size being launched as
+// batches, or built by gs_graph_build, are left alone.
+void drop_remainder(gs_ctx* c, int64_t keep_S) {
+    const int64_t r = c->rem_S;
+    if (r == 0 || r == keep_S || r == c->built_S) return;
+    bool any = false;
+    for (int p = 0; p < 2; ++p) any |= c->graphs.count(std::make_pair(r, p)) > 0;
+    if (!any) return;
+    cudaStreamSynchronize(c->stream);  // no launch of these graphs may still be pending
+    for (int p = 0; p < 2; ++p) {
+        auto it = c->graphs.find(std::make_pair(r, p));
+        if (it == c->graphs.end()) continue;
+        cudaGraphExecDestroy(it->second.exec);
+        cudaGraphDestroy(it->second.graph);
+        c->graphs.erase(it);
+    }
 }
 
 void invalidate(gs_ctx* c) {
@@ -361,6 +383,7 @@ gs_status ensure_descs(gs_ctx* c) {
         FdtdArgs a{};
         for (int f = 0; f < 6; ++f) a.f[f] = c->ptr[GS_FIELD_EX + f];
         a.N = (int)c->nx;
+        a.Nk = (int)c->nz;
         a.kc = c->plan.rows;
         a.pitch = c->pitch[GS_FIELD_EX];
         a.plane = a.pitch * (c->nx + 1);
@@ -384,8 +407,8 @@ gs_status ensure_descs(gs_ctx* c) {
             a.med = c->d_med;
         }
         // one half-step reads all six components (and the ids), writes three
-        const double step_bytes = (double)ctx_elem_bytes(c) * 6.0 * (double)a.plane * (double)(c->nx + 1) +
-                                  (a.mat ? (double)a.plane * (double)(c->nx + 1) : 0.0);
+        const double step_bytes = (double)ctx_elem_bytes(c) * 6.0 * (double)a.plane * (double)(c->nz + 1) +
+                                  (a.mat ? (double)a.plane * (double)(c->nz + 1) : 0.0);
         a.rev = 0;
         cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, c->plan.kernel, &c->desc[0][0]);
         a.rev = traverse_alternates(c->plan.traverse, step_bytes) ? 1 : 0;
@@ -699,7 +722,8 @@ namespace {
 
 // The grid checks of gs_create: nullptr if (kind, sizes, storage, bc) make a
 // valid context, else why not.
-const char* grid_error(gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc) {
+const char* grid_error(gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc,
+                       bool fdtd_box = false) {
     if (kind != GS_HEAT2D && kind != GS_HEAT3D && kind != GS_FDTD3D && kind != GS_SKELETON) return "unknown kind";
     if (kind == GS_SKELETON && (ny != 1 || nz != 1 || nx < 1 || nx >= (int64_t(1) << 31)))
         return "GS_SKELETON needs ny == nz == 1 and 1 <= nx < 2^31";
@@ -708,9 +732,9 @@ const char* grid_error(gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtyp
     if (kind != GS_SKELETON && (nx < 1 || ny < 1 || nz < 1 || nx > lim || ny > lim || nz > lim))
         return "grid sizes must be in [1, 2^20]";
     if (kind == GS_HEAT2D && nz != 1) return "GS_HEAT2D needs nz == 1";
-    if (kind == GS_FDTD3D && (nx != ny || ny != nz)) return "GS_FDTD3D needs a cubic grid (nx == ny == nz)";
+    if (kind == GS_FDTD3D && (nx != ny || (ny != nz && !fdtd_box))) return "GS_FDTD3D needs a cubic grid (nx == ny == nz)";
     const int64_t w = (kind == GS_FDTD3D) ? nx + 1 : nx;
-    const int64_t rows = (kind == GS_FDTD3D) ? (nx + 1) * (nx + 1) : ny * nz;
+    const int64_t rows = (kind == GS_FDTD3D) ? (nx + 1) * (nz + 1) : ny * nz;
     if (kind != GS_SKELETON && (double)(w + 8) * (double)rows >= 2147483647.0)
         return "field too large (needs >= 2^31 elements)";
     if (kind == GS_FDTD3D && bc != GS_BC_PEC) return "GS_FDTD3D needs GS_BC_PEC";
@@ -751,9 +775,21 @@ gs_status gs_required_pitch(gs_dtype dtype, int64_t width, int64_t* pitch_out) {
 
 gs_status gs_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc,
                     void* stream) {
+    return gs::ctx_create(out, kind, nx, ny, nz, storage, bc, stream, false);
+}
+
+}  // extern "C"
+
+namespace gs {
+
+// gs_create, and (fdtd_box) FDTD contexts of N x N x Nk cells for the
+// sub-domains of a slab set.
+gs_status ctx_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc,
+                     void* stream, bool fdtd_box) {
     if (!out) return fail(nullptr, GS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (const char* why = grid_error(kind, nx, ny, nz, storage, bc)) return fail(nullptr, GS_ERR_INVALID_ARG, why);
+    if (const char* why = grid_error(kind, nx, ny, nz, storage, bc, fdtd_box))
+        return fail(nullptr, GS_ERR_INVALID_ARG, why);
 
     gs_ctx* c = new (std::nothrow) gs_ctx();
     if (!c) return fail(nullptr, GS_ERR_OOM, "host allocation failed");
@@ -787,6 +823,20 @@ gs_status gs_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t 
     *out = c;
     return GS_OK;
 }
+
+gs_status ctx_prepare(gs_ctx* c) { return ensure_descs(c); }
+
+void ctx_launch_list(gs_ctx* c, int64_t n, int p, std::vector<LaunchDesc*>* out) {
+    for_each_launch(c, n, p, [&](LaunchDesc& d) { out->push_back(&d); });
+}
+
+int ctx_flip(const gs_ctx* c, int64_t n) { return flip_of(c, n); }
+
+cudaError_t ctx_launch(gs_ctx* c, LaunchDesc& d) { return launch_one(c, d); }
+
+}  // namespace gs
+
+extern "C" {
 
 gs_status gs_destroy(gs_ctx* c) {
     if (!c) return GS_OK;
@@ -827,7 +877,7 @@ gs_status gs_set_fdtd_params(gs_ctx* c, const gs_fdtd_params* p) {
     if (p->src_width == 0.0f) return fail(c, GS_ERR_INVALID_ARG, "src_width must be non-zero");
     if (p->src_on != 0 && p->src_on != 1) return fail(c, GS_ERR_INVALID_ARG, "src_on must be 0 or 1");
     const int64_t N = c->nx;
-    if (p->src_i < 0 || p->src_j < 0 || p->src_k < 0 || p->src_i > N || p->src_j > N || p->src_k > N)
+    if (p->src_i < 0 || p->src_j < 0 || p->src_k < 0 || p->src_i > N || p->src_j > N || p->src_k > c->nz)
         return fail(c, GS_ERR_INVALID_ARG, "source cell outside the (N+1)^3 arrays");
     c->fp = *p;
     invalidate(c);
@@ -1030,6 +1080,10 @@ gs_status gs_step(gs_ctx* c, int64_t n_iters, int64_t batch_size) {
             if (st != GS_OK) return st;
         }
         if (r > 0) {
+            if (c->rem_S != r) {
+                drop_remainder(c, batch_size);
+                c->rem_S = r;
+            }
             st = launch_graphs(c, r, 1);
             if (st != GS_OK) return st;
         }

@@ -9,6 +9,7 @@
 
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "graphstep.h"
 
@@ -187,7 +188,8 @@ struct HeatArgs {
 
 struct FdtdArgs {
     void* f[6];           // Ex, Ey, Ez, Hx, Hy, Hz
-    int N;
+    int N;                // cells along i and j
+    int Nk;               // cells along k (N for a cube; a sub-domain of a slab set may differ)
     int kc;               // k planes per block
     long long pitch;      // elements per row (>= N+1)
     long long plane;      // pitch * (N+1)
@@ -290,6 +292,21 @@ bool ctx_is_heat(const gs_ctx* c);
 bool ctx_is_skel(const gs_ctx* c);
 cudaStream_t ctx_stream(const gs_ctx* c);
 gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg);  // records msg, returns s
+// gs_create; fdtd_box also admits FDTD grids of N x N x nz cells (nz != N),
+// the sub-domains of a slab set.
+gs_status ctx_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t nz, gs_dtype storage, gs_bc bc,
+                     void* stream, bool fdtd_box);
+// The context's launch descriptors, built if needed (GS_ERR_STATE for
+// unbound fields).
+gs_status ctx_prepare(gs_ctx* c);
+// The launches of n iterations starting at buffer parity p, in order
+// (thermal: n/t depth-t launches, then n mod t depth-1 launches; FDTD: H, E
+// per iteration); valid until the context's plan, fields or coefficients change.
+void ctx_launch_list(gs_ctx* c, int64_t n, int p, std::vector<LaunchDesc*>* out);
+// Buffer-parity flip of n iterations (thermal), 0 otherwise.
+int ctx_flip(const gs_ctx* c, int64_t n);
+// One launch on the context's stream (with the plan's PDL attribute).
+cudaError_t ctx_launch(gs_ctx* c, LaunchDesc& d);
 gs_status global_fail(gs_status s, const std::string& msg);  // message for gs_last_error(NULL)
 
 }  // namespace gs

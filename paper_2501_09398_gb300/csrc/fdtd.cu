@@ -6,8 +6,10 @@
 //                   tangential E on the walls is never written),
 //   Ez[src] += amp*exp(-((n - delay)/width)^2)  soft source after E at step n.
 // Staggering Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2) Hx(i,j+1/2,k+1/2)
-// Hy(i+1/2,j,k+1/2) Hz(i+1/2,j+1/2,k); each component is an (N+1)^3 array,
-// row pitch >= N+1, indexed [k][j][i].
+// Hy(i+1/2,j,k+1/2) Hz(i+1/2,j+1/2,k); each component is an (N+1)^2 x
+// (Nk+1) array (Nk = N for the cube; the sub-domains of a slab set have
+// their own Nk), row pitch >= N+1, indexed [k][j][i]; the walls k = 0 and
+// k = Nk are PEC like the others.
 //
 // Each thread owns one 16-byte vector along i at fixed j and marches a
 // chunk of kc planes in k, carrying the plane it needs from the previous
@@ -46,13 +48,13 @@ template <typename ST>
 __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
     constexpr int V = Vec<ST>::N;
     pdl_wait_then_trigger();
-    const int N = a.N, M = N + 1;
+    const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
     const int lane = threadIdx.x & 31;
     const uint3 blk = block_index(a.rev);
     const int i0 = (blk.x * blockDim.x + threadIdx.x) * V;
     const int j = blk.y * blockDim.y + threadIdx.y;
     const int k0 = blk.z * a.kc;
-    const int k1 = min(k0 + a.kc, M);
+    const int k1 = min(k0 + a.kc, Mk);
     const bool act = (i0 < M) && (j < M);
     const int nv = M - i0;  // valid elements in this vector (if act)
     const ST* Ex = static_cast<const ST*>(a.f[EX]);
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
         for (int e = 0; e < V; ++e) { exk1[e] = 0.f; eyk1[e] = 0.f; ez[e] = 0.f; ezj1[e] = 0.f; exj1[e] = 0.f; }
         float ez_r = 0.f, ey_r = 0.f;
         if (act) {
-            if (k + 1 < M) {
+            if (k + 1 < Mk) {
                 load_vec(Ex + o + a.plane, exk1);
                 load_vec(Ey + o + a.plane, eyk1);
             }
@@ -106,8 +108,8 @@ __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
                 const int i = i0 + e;
                 const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
                 const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
-                if (j < N && k < N) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
-                if (i < N && k < N) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
+                if (j < N && k < Nk) hx[e] = curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], eyk[e]);
+                if (i < N && k < Nk) hy[e] = curl_sub(hy[e], s, exk1[e], exk[e], ez_ip, ez[e]);
                 if (i < N && j < N) hz[e] = curl_sub(hz[e], s, ey_ip, eyk[e], exj1[e], exk[e]);
             }
             store_vec(Hx + o, hx, nv);
@@ -123,13 +125,13 @@ template <typename ST>
 __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
     constexpr int V = Vec<ST>::N;
     pdl_wait_then_trigger();
-    const int N = a.N, M = N + 1;
+    const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
     const int lane = threadIdx.x & 31;
     const uint3 blk = block_index(a.rev);
     const int i0 = (blk.x * blockDim.x + threadIdx.x) * V;
     const int j = blk.y * blockDim.y + threadIdx.y;
     const int k0 = blk.z * a.kc;
-    const int k1 = min(k0 + a.kc, M);
+    const int k1 = min(k0 + a.kc, Mk);
     const bool act = (i0 < M) && (j < M);
     const int nv = M - i0;
     ST* Ex = static_cast<ST*>(a.f[EX]);
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
     }
     for (int k = k0; k < k1; ++k) {
         const long long o = (long long)k * a.plane + rowj;
-        const bool k_int = (k >= 1 && k <= N - 1);
+        const bool k_int = (k >= 1 && k <= Nk - 1);
         float hx[V], hy[V], hz[V], hzj_1[V], hxj_1[V], ex[V], ey[V], ez[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) { hx[e] = 0.f; hy[e] = 0.f; hz[e] = 0.f; hzj_1[e] = 0.f; hxj_1[e] = 0.f; }
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
                 const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
                 if (i < N && j_int && k_int) ex[e] = curl_add(ex[e], s, hz[e], hzj_1[e], hy[e], hyk_1[e]);
                 if (j < N && i_int && k_int) ey[e] = curl_add(ey[e], s, hx[e], hxk_1[e], hz[e], hz_im);
-                if (k < N && i_int && j_int) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
+                if (k < Nk && i_int && j_int) ez[e] = curl_add(ez[e], s, hy[e], hy_im, hx[e], hxj_1[e]);
             }
             // The one thread that owns cell (si, sj, sk) keeps the device
             // step counter n and, if the source is on, adds it to Ez there.
@@ -223,8 +225,8 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
 // streaming field loads evict it and every lookup would wait on L2).
 //
 // Two bodies.  FAST serves the warps whose vectors all lie in [0, N) and
-// whose (j, k) has every neighbour the update reads (H: j, k < N; E:
-// 1 <= j, k <= N-1): all loads unconditional, no zero-filled registers, no
+// whose (j, k) has every neighbour the update reads (H: j < N, k < Nk; E:
+// 1 <= j <= N-1, 1 <= k <= Nk-1): all loads unconditional, no zero-filled registers, no
 // per-cell predicates (E only keeps the i = 0 wall cell of lane 0).  The
 // general body serves the rest with per-cell predicates.  ALN grids (N a
 // multiple of the 32 V cells of a warp) cover only i in [0, N): the i = N
@@ -262,8 +264,8 @@ template <typename ST, bool MAT, bool FAST, bool EXTRA>
 __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const float2* s_med, int lane, int i0, int j,
                                                    int k) {
     constexpr int V = kFdtdColumnCells;
-    const int N = a.N, M = N + 1;
-    const bool act = FAST || ((i0 < M) && (j < M) && (k < M));
+    const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
+    const bool act = FAST || ((i0 < M) && (j < M) && (k < Mk));
     const ST* Ex = static_cast<const ST*>(a.f[EX]);
     const ST* Ey = static_cast<const ST*>(a.f[EY]);
     const ST* Ez = static_cast<const ST*>(a.f[EZ]);
@@ -312,7 +314,7 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
             load_vecw<ST, V>(Ex + o, exk);
             load_vecw<ST, V>(Ey + o, eyk);
             load_vecw<ST, V>(Ez + o, ez);
-            if (k + 1 < M) {
+            if (k + 1 < Mk) {
                 load_vecw<ST, V>(Ex + o + a.plane, exk1);
                 load_vecw<ST, V>(Ey + o + a.plane, eyk1);
             }
@@ -339,8 +341,8 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
         const int i = i0 + e;
         const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
         const float ey_ip = (e + 1 < V) ? eyk[e + 1] : ey_last;
-        const bool ux = FAST || (j < N && k < N);
-        const bool uy = FAST || (i < N && k < N);
+        const bool ux = FAST || (j < N && k < Nk);
+        const bool uy = FAST || (i < N && k < Nk);
         const bool uz = FAST || (i < N && j < N);
         if constexpr (MAT) {
             const float2 m = s_med[id[e]];
@@ -370,8 +372,8 @@ template <typename ST, bool MAT, bool FAST, bool ALN>
 __device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const float2* s_med, int lane, int i0, int j,
                                                    int k) {
     constexpr int V = kFdtdColumnCells;
-    const int N = a.N, M = N + 1;
-    const bool act = FAST || ((i0 < M) && (j < M) && (k < M));
+    const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
+    const bool act = FAST || ((i0 < M) && (j < M) && (k < Mk));
     ST* Ex = static_cast<ST*>(a.f[EX]);
     ST* Ey = static_cast<ST*>(a.f[EY]);
     ST* Ez = static_cast<ST*>(a.f[EZ]);
@@ -435,7 +437,7 @@ __device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const floa
     const float hz_first = (lane == 0) ? hz_l : hz_p;
     const float hy_first = (lane == 0) ? hy_l : hy_p;
     const bool j_int = FAST || (j >= 1 && j <= N - 1);
-    const bool k_int = FAST || (k >= 1 && k <= N - 1);
+    const bool k_int = FAST || (k >= 1 && k <= Nk - 1);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const int i = i0 + e;
@@ -443,7 +445,7 @@ __device__ __forceinline__ void fdtd_e_column_body(const FdtdArgs& a, const floa
         const bool i_int = FAST ? (e > 0 || i0 > 0) : (i >= 1 && i <= N - 1);
         const bool ux = FAST || (i < N && j_int && k_int);
         const bool uy = i_int && (FAST || (j < N && k_int));
-        const bool uz = i_int && (FAST || (k < N && j_int));
+        const bool uz = i_int && (FAST || (k < Nk && j_int));
         const float hz_im = (e > 0) ? hz[e - 1] : hz_first;
         const float hy_im = (e > 0) ? hy[e - 1] : hy_first;
         if constexpr (MAT) {
@@ -489,7 +491,7 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_
     const int j = blk.y * blockDim.y + threadIdx.y;
     const int k = blk.z * blockDim.z + threadIdx.z;
     const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
-    if (in_x && j < N && k < N) fdtd_h_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);
+    if (in_x && j < N && k < a.Nk) fdtd_h_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);
     else fdtd_h_column_body<ST, MAT, false, false>(a, s_med, lane, i0, j, k);
 }
 
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_
     const int j = blk.y * blockDim.y + threadIdx.y;
     const int k = blk.z * blockDim.z + threadIdx.z;
     const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
-    if (in_x && j >= 1 && j <= N - 1 && k >= 1 && k <= N - 1)
+    if (in_x && j >= 1 && j <= N - 1 && k >= 1 && k <= a.Nk - 1)
         fdtd_e_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);
     else
         fdtd_e_column_body<ST, MAT, false, ALN>(a, s_med, lane, i0, j, k);
@@ -531,7 +533,7 @@ const void* fdtd_func(bool e_half, bool col, bool mat, bool aln) {
 cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out) {
     const bool col = (variant == GS_KERNEL_COLUMN);
     const int V = col ? kFdtdColumnCells : ((dt == GS_F32) ? 4 : 8);
-    const int M = a.N + 1;
+    const int M = a.N + 1, Mk = a.Nk + 1;
     const bool mat = (a.mat != nullptr);
     if (mat && !col) return cudaErrorNotSupported;  // media: column kernels only
     // ALN: the warps tile i in [0, N) exactly; lane 31 takes the i = N column
@@ -548,11 +550,11 @@ cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, 
         const int bz = std::max(1, 8 / by);
         out->block = dim3(32, by, bz);
         const int span = aln ? a.N : M;
-        out->grid = dim3((span + 32 * V - 1) / (32 * V), (M + by - 1) / by, (M + bz - 1) / bz);
+        out->grid = dim3((span + 32 * V - 1) / (32 * V), (M + by - 1) / by, (Mk + bz - 1) / bz);
     } else {
         const int by = std::max(1, 256 / block_x);
         out->block = dim3(block_x, by, 1);
-        out->grid = dim3((M + block_x * V - 1) / (block_x * V), (M + by - 1) / by, (M + a.kc - 1) / a.kc);
+        out->grid = dim3((M + block_x * V - 1) / (block_x * V), (M + by - 1) / by, (Mk + a.kc - 1) / a.kc);
     }
     out->smem = 0;
     out->set_args(a);

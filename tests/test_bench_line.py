@@ -43,11 +43,42 @@ def test_bench_line_keys_and_arithmetic(workload):
     assert math.isclose(rf["frac"], achieved / rf["peak"], rel_tol=1e-12)
     assert math.isclose(rf["frac_of_nominal"], achieved / bench.NOMINAL_HBM_GBS, rel_tol=1e-12)
     assert rf["traffic"] is None or isinstance(rf["traffic"], int)
+    # the bound follows the working set against the L2 size (fake: 126 MiB)
+    assert rf["bound"] == ("hbm" if bench.working_set_bytes(w) > 63 * 2 ** 20 else "l2/latency")
+    assert math.isclose(rf["per_node_us"], launch_ms * 1e3, rel_tol=1e-12)
     assert math.isclose(line["e2e"]["value"], units / 0.004, rel_tol=1e-12)
     assert line["gpu_launches"] == launches * 4
     assert math.isclose(line["ms_per_step_std"], 0.1118033988749895, rel_tol=1e-9)  # pstdev of 3.0, 3.2, 3.1, 2.9
     assert math.isclose(line["per_step_launch"]["ms_per_step_std"], 0.1118033988749895, rel_tol=1e-9)
     assert math.isclose(line["per_step_launch"]["graph_speedup"], line["value"] / (units / 6.05e-3), rel_tol=1e-12)
+
+
+def test_bounds_of_the_named_workloads():
+    # L2 126 MiB: the 3D 512x512x8 field (17 MiB) and FDTD 128^3 (53 MB) stay
+    # in L2; 2D 4096^2 (192 MiB), 256^3 and the 64-grid batch (141 MB) do not
+    half = 63 * 2 ** 20
+    ws = {k: bench.working_set_bytes(w) for k, w in bench.WORKLOADS.items()}
+    assert ws["heat3d-512x512x8"] < half and ws["fdtd-128"] < half and ws["heat2d-512"] < half
+    for k in ("heat2d-4096", "heat3d-256", "fdtd-256", "fdtd-media-256", "multi-64"):
+        assert ws[k] > half, k
+
+
+def test_hbm_roofline_of_arithmetic():
+    w = bench.WORKLOADS["heat2d-4096"]
+    mm = dict(S=100, depth=1, graph_ms=[5.2, 5.4], launches=200)
+    r = bench.hbm_roofline_of("heat2d-4096", w, mm)
+    bl = 4096 * 4096 * 12
+    assert r["bytes_per_launch"] == bl and r["bound"] == "hbm"
+    assert math.isclose(r["achieved"], bl / (5.3e-3 / 200) / 1e9, rel_tol=1e-12)
+    assert math.isclose(r["frac"], r["achieved"] / r["peak"], rel_tol=1e-12)
+    if r["traffic"] is not None and "cold_cache_us" in r:
+        assert math.isclose(r["cold_cache_frac"], bl / (r["cold_cache_us"] * 1e-6) / 1e9 / r["peak"], rel_tol=1e-12)
+
+
+def test_column_geometry_of_the_default_workload():
+    # 3D 512x512x8, COLUMN rows 4: 4 x 128 blocks of 32 x 4 threads
+    assert bench.column_geometry(bench.WORKLOADS["heat3d-512x512x8"], dict(kernel=4, rows=4), 1) == (512, 128)
+    assert bench.column_geometry(bench.WORKLOADS["fdtd-128"], dict(kernel=4), 1) is None
 
 
 def test_profiles_hold_the_default_workloads_traffic_line():
@@ -61,7 +92,7 @@ def test_profiles_hold_the_default_workloads_traffic_line():
     found = []
     for path in glob.glob(os.path.join(bench.ROOT, "profiles", "*.md")):
         with open(path) as f:
-            found += re.findall(r"^bench-traffic: workload=(\S+) kernel=\S+ sha256=(\w{16}) bytes=(\d+)$", f.read(),
+            found += re.findall(r"^bench-traffic: workload=(\S+) kernel=\S+ sha256=(\w{16}) bytes=(\d+)(?: us=\S+)?$", f.read(),
                                 flags=re.M)
     mine = [f for f in found if f[0] == bench.DEFAULT]
     assert mine, "no bench-traffic line for the default workload under profiles/"

@@ -86,6 +86,33 @@ def test_graph_batches_bit_identical_to_per_step(nz):
             assert np.array_equal(heat_gpu(T0, P, n, S=S, plan=plan), base), f"S={S} {plan}"
 
 
+def test_remainder_graphs_of_one_size_are_kept():
+    """gs_step keeps the peeled remainder graphs of the latest remainder size
+    only: returning to an earlier remainder builds its graph again, and the
+    results stay bit-identical to per-step launches."""
+    import paper_2501_09398_gb300 as g
+
+    T0, P = gs_inputs.heat_fields(97, 41, 1, seed=11)
+    calls = (37, 38, 37, 37)  # remainders 7, 8, 7, 7 of S = 10
+    base = heat_gpu(T0, P, sum(calls), S=0)
+    ctx, fields = heat_setup(97, 41)
+    try:
+        heat_upload(ctx, T0, P)
+        built = []
+        for n in calls:
+            g.gs_step(ctx, n, 10)
+            built.append(g.gs_get_stats(ctx)["graphs_built"])
+        got = heat_read(ctx, T0.shape)
+    finally:
+        g.gs_destroy(ctx)
+        del fields
+    assert np.array_equal(got, base)
+    # call 3 rebuilt a remainder graph of 7 (call 2 dropped the ones of 7);
+    # call 4 adds at most the remainder of 7 at the other buffer parity
+    assert built[2] > built[1]
+    assert built[3] - built[2] <= 1
+
+
 @pytest.mark.parametrize("shape", [(96, 64, 1), (77, 45, 1), (300, 37, 1), (40, 33, 8), (21, 19, 3), (250, 20, 16),
                                    (500, 130, 1), (3, 2, 1)])
 @pytest.mark.parametrize("depth", [1, 2, 4])

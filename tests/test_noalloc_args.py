@@ -19,11 +19,12 @@ def g():
     return paper_2501_09398_gb300
 
 
-FAKE = 0x10000  # 16-byte aligned, never dereferenced
+FAKE = 0x100000  # 16-byte aligned, never dereferenced
+GAP = 0x4000      # 16 KiB between placeholder buffers: an f32 64 x 32 field needs 8 KiB
 
 
-def _inst(g, **over):
-    d = dict(T0=FAKE, T1=FAKE + 0x1000, P=FAKE + 0x2000, nx=64, ny=32, pitch=64, p_pitch=64)
+def _inst(g, base=FAKE, **over):
+    d = dict(T0=base, T1=base + GAP, P=base + 2 * GAP, nx=64, ny=32, pitch=64, p_pitch=64)
     d.update(over)
     return g.gs_instance(ctypes.c_void_p(d["T0"]), ctypes.c_void_p(d["T1"]), ctypes.c_void_p(d["P"]), d["nx"],
                          d["ny"], d["pitch"], d["p_pitch"])
@@ -115,3 +116,32 @@ def test_multi_create_refusals_carry_a_message(g):
     assert g._lib.gs_multi_create(ctypes.byref(h), 2, None, good, g.GS_F32, g.GS_BC_CLAMP, None) \
         == g.GS_ERR_INVALID_ARG
     assert h.value is None
+
+
+def test_overlapping_buffers_are_refused(g):
+    # an instance whose T0 is its T1 would be updated in place while read
+    st, msg, out = _call(g, [_inst(g, T1=FAKE)])
+    assert st == g.GS_ERR_INVALID_ARG and out == -1
+    assert "instance 0" in msg and "overlap" in msg, msg
+    # instance 1's T1 starts inside instance 0's T0 (ny * pitch * 4 bytes long)
+    b1 = FAKE + 0x100000
+    st, msg, _ = _call(g, [_inst(g), _inst(g, base=b1, T1=FAKE + 0x1000)])
+    assert st == g.GS_ERR_INVALID_ARG and "instances 0 and 1" in msg, msg
+    # a power map that overlaps another instance's T buffer
+    st, msg, _ = _call(g, [_inst(g), _inst(g, base=b1, P=FAKE + GAP)])
+    assert st == g.GS_ERR_INVALID_ARG and "overlap" in msg, msg
+    # the last row's padding counts: T1 starting one element before T0's end
+    st, msg, _ = _call(g, [_inst(g, T1=FAKE + 32 * 64 * 4 - 4 * 4)])
+    assert st == g.GS_ERR_INVALID_ARG and "overlap" in msg, msg
+
+
+def test_shared_power_map_is_accepted(g):
+    # P buffers are only read, so instances may share one; n_iters = 0 runs
+    # every check and returns before any CUDA call
+    b1 = FAKE + 0x100000
+    st, msg, out = _call(g, [_inst(g), _inst(g, base=b1, P=FAKE + 2 * GAP)], parity=1, n_iters=0)
+    assert st == g.GS_OK, msg
+    assert out == 1
+    # adjacent (touching, not overlapping) buffers are fine too
+    st, msg, _ = _call(g, [_inst(g, T1=FAKE + 32 * 64 * 4)], n_iters=0)
+    assert st == g.GS_OK, msg
