@@ -44,8 +44,10 @@ import gs_inputs  # noqa: E402
 # autotuner can re-derive them).  kernel: 1 = MARCH, 2 = WAVE, 4 = COLUMN.
 # The per-step baseline always uses plain launches (use_pdl forced off).
 WORKLOADS = {
-    "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=1,
-                             plan=dict(kernel=4, rows=4)),
+    # temporal depth 2: the register COLUMN kernel advances two steps per
+    # launch (measured 6.95e11 against 6.73e11 cell-updates/s at depth 1)
+    "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=2,
+                             plan=dict(kernel=4, block_x=64)),
     # a deep stack (nz > 8): the column kernel in 8-plane chunks
     "heat3d-256": dict(kind="heat3d", nx=256, ny=256, nz=256, iters=200, S=100, depth=1,
                        plan=dict(kernel=4, rows=4)),
@@ -58,8 +60,10 @@ WORKLOADS = {
     "fdtd-256": dict(kind="fdtd", N=256, iters=500, S=100, depth=1, plan=dict(kernel=4, rows=2)),
     "fdtd-media-256": dict(kind="fdtd", N=256, iters=500, S=100, depth=1, plan=dict(kernel=4, rows=2),
                            media=dict(n_mat=8, n_boxes=24, seed=0)),
-    # fused launches of temporal depth 2 (COLUMN tiles): 1.55x depth 1
-    "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=2, plan=dict(kernel=4, rows=2)),
+    # the fused plan comes from gs_multi_autotune over the library's candidates
+    # at S = 100 (tune=True); plan/depth are the fallback when a flag overrides
+    "multi-64": dict(kind="multi", n=64, lo=64, hi=1024, iters=2000, S=100, depth=2, plan=dict(kernel=4, rows=2),
+                     tune=True),
 }
 DEFAULT = "heat3d-512x512x8"
 METRIC = "cell-updates/s (graph-batched)"
@@ -161,9 +165,12 @@ def column_geometry(w, plan, depth):
     cdiv = lambda a, b: -(-a // b)  # noqa: E731
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     if depth > 1:
-        if w["kind"] == "heat3d":
-            return None
         bw = max(1, min(plan.get("block_x", 64) // 32, 8))
+        if w["kind"] == "heat3d":  # one cell a lane, 32 - 2t stored; R rows a warp
+            if nz > 8:
+                return None
+            R = 4 if (depth == 2 and plan.get("rows", 0) != 2) else 2
+            return cdiv(nx, 32 - 2 * depth) * cdiv(ny, R * bw), 32 * bw
         return cdiv(nx, 30 * 4) * cdiv(ny, 4 * bw), 32 * bw
     by = max(1, min(plan.get("rows", 4), 8))
     cw = 4  # cells per thread in f32 (2D: one 16-byte vector; 3D: four cells)
@@ -471,7 +478,7 @@ class MultiRunner:
     """The uneven-instance batch: fused persistent kernel in captured graphs
     (S > 0) against 64 separate per-step launch loops (S = 0)."""
 
-    def __init__(self, w, S, depth, plan_extra):
+    def __init__(self, w, S, depth, plan_extra, tune=False):
         import torch
 
         import paper_2501_09398_gb300 as g
@@ -482,14 +489,24 @@ class MultiRunner:
         self.m = g.gs_multi_create(self.sides, self.sides, g.GS_F32, g.GS_BC_CLAMP, self.stream.cuda_stream)
         self.ctx = None
         self.fields = g.MultiFields(self.m, self.sides, self.sides)
+        self.inputs = gs_inputs.instance_fields(self.sides)
+        self.reset()
+        self.tuned = None
+        if tune:
+            # the fused plan the batch's tuner picks for a whole run at this S
+            cands = [(p, s) for p, s in g.gs_multi_candidates(self.m) if s == S]
+            res, best = g.gs_multi_autotune(self.m, w["iters"], cands, reps=2)
+            self.tuned = dict(res[best]["plan"])
+            self.tuned["candidates"] = len(cands)
+            g.gs_multi_set_plan(self.m, **{k: v for k, v in res[best]["plan"].items()})
+            self.depth = res[best]["plan"]["temporal_depth"]
+            return
         mp = {k: v for k, v in plan_extra.items() if k in ("block_x", "rows", "use_pdl", "kernel", "traverse")}
         if depth > 1:
             mp["temporal_depth"] = depth
             self.depth = depth
         if mp:
             g.gs_multi_set_plan(self.m, **mp)
-        self.inputs = gs_inputs.instance_fields(self.sides)
-        self.reset()
 
     def reset(self):
         g = self.g
@@ -638,7 +655,12 @@ def measure_workload(name, w, args, flush, with_e2e=True):
         g_plan["traverse"] = args.traverse
     S = args.batch or w["S"]
     depth = args.depth or w["depth"]
-    run = (MultiRunner if w["kind"] == "multi" else Runner)(w, S, depth, g_plan)
+    if w["kind"] == "multi":
+        overridden = args.depth or args.block_x or args.rows or getattr(args, "kernel", 0) or args.pdl
+        run = MultiRunner(w, S, depth, g_plan, tune=bool(w.get("tune")) and not overridden)
+        depth = run.depth
+    else:
+        run = Runner(w, S, depth, g_plan)
     try:
         g = run.g
         # paper convention (Sec. III-C): graph creation + execution of one run
@@ -677,18 +699,20 @@ def measure_workload(name, w, args, flush, with_e2e=True):
         run.close()
     return dict(S=S, depth=depth, graph_ms=graph_ms, per_step_ms=per_step_ms, kern_ms=kern_ms, e2e=e2e,
                 paper_conv_ms=paper_conv_ms, build_s=build_s, result=result,
-                launches=run.launches_per_step(S), l2_bytes=l2, node_floor_us=floor)
+                launches=run.launches_per_step(S), l2_bytes=l2, node_floor_us=floor,
+                tuned_plan=getattr(run, "tuned", None))
 
 
 SWEEP_S = (1, 10, 50, 100, 500, 1000)
 # (temporal depth, launch plan) per swept workload: depth 1 is the bench's
-# COLUMN plan; depths 2 and 4 are the cost model's temporal candidates (the
-# register COLUMN kernel in 2D, the shared-memory WAVE kernel in 3D)
+# COLUMN plan; depths 2 and 4 run the register COLUMN kernel (2D, and stacks
+# of up to eight planes); the 3D sweep also keeps the shared-memory WAVE
+# kernel at depth 2 for comparison
 SWEEP_PLANS = {
     "heat2d-512": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=4, block_x=64, rows=4)),
                    (4, dict(kernel=4, block_x=64, rows=4))),
-    "heat3d-512x512x8": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=2, block_x=64, rows=4)),
-                         (4, dict(kernel=2, block_x=64, rows=4))),
+    "heat3d-512x512x8": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=4, block_x=256)),
+                         (4, dict(kernel=4, block_x=256)), (2, dict(kernel=2, block_x=64, rows=4))),
 }
 
 
@@ -710,7 +734,8 @@ def batch_sweep(w, plans, flush, steps=10, warmup=3):
         best = max(SWEEP_S, key=lambda s: row[f"S={s}"])
         row["best_S"] = best
         row["best_vs_per_step"] = row[f"S={best}"] / row["per_step"]
-        out[f"depth{depth}"] = row
+        key = f"depth{depth}" if f"depth{depth}" not in out else f"depth{depth}/kernel{plan.get('kernel', 0)}"
+        out[key] = row
     return out
 
 
@@ -852,7 +877,8 @@ def bench_line(args, w, m, clk, world):
         "ms_per_step_std": statistics.pstdev(m["graph_ms"]) if len(m["graph_ms"]) > 1 else 0.0,
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_of(args.workload, w, m["S"], m["depth"], world),
+        "config": {**config_of(args.workload, w, m["S"], m["depth"], world),
+                   **({"tuned_plan": m["tuned_plan"]} if m.get("tuned_plan") else {})},
         "roofline": roof,
         "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
                             "ms_per_step_std": statistics.pstdev(m["per_step_ms"]) if len(m["per_step_ms"]) > 1 else 0.0,
@@ -977,7 +1003,7 @@ def main():
                               ("heat3d-256", {}, "column"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-media-256", {}, "column"),
-                              ("multi-64", {}, "column2"),
+                              ("multi-64", {}, "tuned"),
                               ("heat2d-512", dict(depth=4, kernel=4, block_x=256), "column4"),
                               ("heat2d-4096", {}, "depth1"),
                               ("heat2d-4096", dict(depth=2, kernel=4, block_x=64), "column2"),
@@ -993,6 +1019,8 @@ def main():
             extra[f"{nm}/{tag}"] = {"graph_value": gv, "per_step_value": pv, "graph_speedup": gv / pv,
                                     "S": mm["S"], "depth": mm["depth"], "in_step_GBps": bw,
                                     "hbm_frac": bw / peak, "paper_convention_ms": mm["paper_conv_ms"]}
+            if mm.get("tuned_plan"):
+                extra[f"{nm}/{tag}"]["tuned_plan"] = mm["tuned_plan"]
             if (nm, tag) == ("heat2d-4096", "depth1"):
                 # the HBM roofline of the default workload's kernel (COLUMN,
                 # depth 1) where the fields stream from DRAM every step
@@ -1007,10 +1035,10 @@ def main():
                 sweeps[nm] = {"error": f"{type(e).__name__}: {e}"}
         extra["batch_sweep"] = sweeps
         # the instance batch's per-step baseline on 64 streams (the one-stream
-        # baseline is multi-64/column2's per_step_value)
+        # baseline is multi-64/tuned's per_step_value)
         try:
             ms = multi_streams_per_step(WORKLOADS["multi-64"], flush)
-            one = extra.get("multi-64/column2", {})
+            one = extra.get("multi-64/tuned", {})
             if one:
                 ms["vs_one_stream_per_step"] = ms["value"] / one["per_step_value"]
                 ms["fused_graph_speedup"] = one["graph_value"] / ms["value"]

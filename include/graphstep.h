@@ -649,6 +649,48 @@ gs_status gs_multi_sync(gs_multi *m);
 /* Counters summed over the fused kernel and every instance context. */
 gs_status gs_multi_get_stats(const gs_multi *m, gs_stats *out);
 
+/* Autotuning an instance batch (the batch's counterpart of gs_autotune):
+ * candidates are (fused-kernel plan, batch size S) pairs; S = 0 times
+ * per-step fused launches. */
+typedef struct gs_multi_tune_candidate {
+    gs_multi_plan plan;  /* zero fields: defaults */
+    int64_t batch_size;
+} gs_multi_tune_candidate;
+
+typedef struct gs_multi_tune_result {
+    gs_multi_plan plan;       /* as applied (defaults filled in) */
+    int64_t batch_size;
+    double build_seconds;     /* T_C: host wall time of capturing, instantiating
+                                 and uploading the batch graphs (0 for S = 0) */
+    double exec_ms_per_iter;  /* best of `reps` timed runs, CUDA events */
+    double total_ms;          /* build_seconds*1e3 + T_E of one n_iters run */
+    int32_t status;           /* GS_OK, or why the candidate was skipped */
+    int32_t reserved;
+} gs_multi_tune_result;
+
+/* The candidates the batch's tuner sweeps: MARCH tiles (block_x 64, 128;
+ * rows 4, 8, 16), COLUMN tiles at depth 1 (rows 2, 4, 8), 2 (rows 1, 2, 4)
+ * and 4 (rows 1, 2), each with S = 0, 10, 100 and 1000, plan after plan.
+ * out == NULL (capacity 0) only counts.  Host only.  Errors:
+ * GS_ERR_INVALID_ARG (capacity below the count, *n_out set). */
+gs_status gs_multi_candidates(const gs_multi *m, gs_multi_tune_candidate *out, int32_t capacity, int32_t *n_out);
+
+/* Time every candidate on the batch's own bound fields, fused mode: set its
+ * plan, capture its batch graphs (timed: T_C), run n_iters iterations once
+ * to warm up, then `reps` timed runs; results[i] describes cands[i] and
+ * *best_index (may be NULL) the candidate with the smallest total_ms (the
+ * paper's T = T_C + T_E, Eq. 1, for a run of n_iters iterations).  Every
+ * instance's fields, the buffer parity and the plan are restored afterwards
+ * (the current buffers are snapshotted into temporary device memory).
+ * Synchronous.  Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE (unbound fields),
+ * GS_ERR_CUDA, GS_ERR_OOM (snapshot), GS_ERR_UNSUPPORTED if no candidate
+ * could run. */
+gs_status gs_multi_autotune(gs_multi *m, int64_t n_iters, int32_t reps, const gs_multi_tune_candidate *cands,
+                            int32_t n_cands, gs_multi_tune_result *results, int32_t *best_index);
+
+/* The plan in effect, defaults filled in. */
+gs_status gs_multi_get_plan(const gs_multi *m, gs_multi_plan *out);
+
 /* ----------------------------------------------- slab decomposition -- */
 
 /* One grid split along its slowest axis into n_slabs sub-domains (slabs),

@@ -686,6 +686,58 @@ def gs_slab_get_stats(s) -> dict:
     return {n: getattr(st, n) for n, _ in gs_stats._fields_}
 
 
+class gs_multi_tune_candidate(ctypes.Structure):
+    _fields_ = [("plan", gs_multi_plan), ("batch_size", ctypes.c_int64)]
+
+
+class gs_multi_tune_result(ctypes.Structure):
+    _fields_ = [("plan", gs_multi_plan), ("batch_size", ctypes.c_int64), ("build_seconds", ctypes.c_double),
+                ("exec_ms_per_iter", ctypes.c_double), ("total_ms", ctypes.c_double), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_sig("gs_multi_candidates", [_vp, ctypes.POINTER(gs_multi_tune_candidate), _i32, ctypes.POINTER(_i32)])
+_sig("gs_multi_autotune", [_vp, _i64, _i32, ctypes.POINTER(gs_multi_tune_candidate), _i32,
+                           ctypes.POINTER(gs_multi_tune_result), ctypes.POINTER(_i32)])
+_sig("gs_multi_get_plan", [_vp, ctypes.POINTER(gs_multi_plan)])
+
+
+def _mplan_dict(p) -> dict:
+    return {n: getattr(p, n) for n, _ in gs_multi_plan._fields_}
+
+
+def gs_multi_get_plan(m) -> dict:
+    p = gs_multi_plan()
+    _mcheck(_lib.gs_multi_get_plan(m, ctypes.byref(p)), m)
+    return _mplan_dict(p)
+
+
+def gs_multi_candidates(m):
+    """The (plan dict, S) pairs the batch's tuner sweeps."""
+    n = _i32()
+    _mcheck(_lib.gs_multi_candidates(m, None, 0, ctypes.byref(n)), m)
+    arr = (gs_multi_tune_candidate * n.value)()
+    _mcheck(_lib.gs_multi_candidates(m, arr, n.value, ctypes.byref(n)), m)
+    return [(_mplan_dict(c.plan), c.batch_size) for c in arr]
+
+
+def gs_multi_autotune(m, n_iters: int, candidates, reps: int = 3):
+    """candidates: list of (plan dict, batch_size).  Returns (results, best
+    index); each result a dict with the plan as applied, batch_size,
+    build_seconds, exec_ms_per_iter, total_ms and status."""
+    n = len(candidates)
+    arr = (gs_multi_tune_candidate * n)()
+    for i, (plan, S) in enumerate(candidates):
+        arr[i].plan = gs_multi_plan(*[int(plan.get(f, 0)) for f, _ in gs_multi_plan._fields_])
+        arr[i].batch_size = int(S)
+    res = (gs_multi_tune_result * n)()
+    best = _i32(-1)
+    _mcheck(_lib.gs_multi_autotune(m, n_iters, reps, arr, n, res, ctypes.byref(best)), m)
+    out = [dict(plan=_mplan_dict(r.plan), batch_size=r.batch_size, build_seconds=r.build_seconds,
+                exec_ms_per_iter=r.exec_ms_per_iter, total_ms=r.total_ms, status=r.status) for r in res]
+    return out, best.value
+
+
 # ------------------------------------------------- step without allocation --
 GS_NOALLOC_MAX_INSTANCES = 256
 

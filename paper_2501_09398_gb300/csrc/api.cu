@@ -258,15 +258,17 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     }
     const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
     if (is_heat(c) && p->kernel == GS_KERNEL_AUTO)
-        p->kernel = (t == 1 || c->kind == GS_HEAT2D) ? GS_KERNEL_COLUMN : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
+        p->kernel = (t == 1 || c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz)
+                        ? GS_KERNEL_COLUMN
+                        : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
     if (p->kernel == GS_KERNEL_MARCH && t != 1)
         return fail(c, GS_ERR_INVALID_ARG, "the MARCH kernel runs depth 1 only");
     if (p->kernel == GS_KERNEL_TILE && t == 1)
         return fail(c, GS_ERR_INVALID_ARG, "the TILE kernel runs depth 2 or 4 only");
     if (p->kernel == GS_KERNEL_COLUMN_SMEM && t != 1)
         return fail(c, GS_ERR_INVALID_ARG, "the COLUMN_SMEM kernel runs depth 1 only");
-    if (p->kernel == GS_KERNEL_COLUMN && t != 1 && c->kind != GS_HEAT2D)
-        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernel runs depth 2 or 4 in 2D only");
+    if (p->kernel == GS_KERNEL_COLUMN && t != 1 && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
+        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernel runs depth 2 or 4 in 2D and for nz <= 8 only");
     if (p->kernel == GS_KERNEL_COLUMN_SMEM && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
         return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN_SMEM kernel needs nz <= 8");
     if (p->kernel == GS_KERNEL_WAVE && !wave_ok)

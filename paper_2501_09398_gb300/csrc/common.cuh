@@ -72,12 +72,17 @@ __device__ __forceinline__ void store_vec(ST* p, const float (&v)[Vec<ST>::N], i
 template <typename ST>
 __device__ __forceinline__ float load_scalar(const ST* p) { return to_f32(__ldg(p)); }
 
-// W elements per access, W * sizeof(ST) = 8 or 16 bytes (read-only path).
+// W elements per access, W * sizeof(ST) = 4, 8 or 16 bytes (read-only path).
 template <typename ST, int W>
 __device__ __forceinline__ void load_vecw(const ST* __restrict__ p, float (&v)[W]) {
-    static_assert(W * sizeof(ST) == 8 || W * sizeof(ST) == 16, "8- or 16-byte access");
+    static_assert(W * sizeof(ST) == 4 || W * sizeof(ST) == 8 || W * sizeof(ST) == 16, "4-, 8- or 16-byte access");
     if constexpr (W * sizeof(ST) == 16) {
         const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
+    } else if constexpr (W * sizeof(ST) == 4) {
+        const unsigned raw = __ldg(reinterpret_cast<const unsigned*>(p));
         const ST* e = reinterpret_cast<const ST*>(&raw);
 #pragma unroll
         for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
@@ -133,6 +138,12 @@ __device__ __forceinline__ void store_vecw(ST* p, const float (&v)[W], int n_val
 #pragma unroll
             for (int i = 0; i < W; ++i) e[i] = from_f32<ST>(v[i]);
             *reinterpret_cast<uint4*>(p) = raw;
+        } else if constexpr (W * sizeof(ST) == 4) {
+            unsigned raw;
+            ST* e = reinterpret_cast<ST*>(&raw);
+#pragma unroll
+            for (int i = 0; i < W; ++i) e[i] = from_f32<ST>(v[i]);
+            *reinterpret_cast<unsigned*>(p) = raw;
         } else {
             uint2 raw;
             ST* e = reinterpret_cast<ST*>(&raw);

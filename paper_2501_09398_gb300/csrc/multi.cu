@@ -9,6 +9,8 @@
 // (or graph-batched) launches, instance after instance on the same stream.
 // Both give bit-identical results: the fused kernel runs the same tile code.
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <map>
 #include <new>
 #include <numeric>
@@ -438,6 +440,181 @@ gs_status gs_multi_step(gs_multi* m, int64_t n_iters, int64_t batch_size, gs_mul
     // keep each instance context's view of the current buffer in step
     for (gs_ctx* c : m->inst) gs_set_parity(c, m->parity);
     m->stats.iterations += n_iters;
+    return GS_OK;
+}
+
+gs_status gs_multi_get_plan(const gs_multi* m, gs_multi_plan* out) {
+    if (!m || !out) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch or output pointer");
+    *out = m->plan;
+    return GS_OK;
+}
+
+gs_status gs_multi_candidates(const gs_multi* m, gs_multi_tune_candidate* out, int32_t capacity, int32_t* n_out) {
+    if (!m || !n_out || capacity < 0 || (capacity > 0 && !out))
+        return global_fail(GS_ERR_INVALID_ARG, "gs_multi_candidates: NULL argument or negative capacity");
+    // (kernel, block_x, rows, depth) of each plan
+    static const int plans[][4] = {
+        {GS_KERNEL_MARCH, 64, 4, 1},  {GS_KERNEL_MARCH, 64, 8, 1},  {GS_KERNEL_MARCH, 64, 16, 1},
+        {GS_KERNEL_MARCH, 128, 4, 1}, {GS_KERNEL_MARCH, 128, 8, 1}, {GS_KERNEL_MARCH, 128, 16, 1},
+        {GS_KERNEL_COLUMN, 64, 2, 1}, {GS_KERNEL_COLUMN, 64, 4, 1}, {GS_KERNEL_COLUMN, 64, 8, 1},
+        {GS_KERNEL_COLUMN, 64, 1, 2}, {GS_KERNEL_COLUMN, 64, 2, 2}, {GS_KERNEL_COLUMN, 64, 4, 2},
+        {GS_KERNEL_COLUMN, 64, 1, 4}, {GS_KERNEL_COLUMN, 64, 2, 4}};
+    static const int64_t batches[] = {0, 10, 100, 1000};
+    const int32_t n = (int32_t)(sizeof(plans) / sizeof(plans[0]) * (sizeof(batches) / sizeof(batches[0])));
+    *n_out = n;
+    if (!out) return GS_OK;
+    if (capacity < n)
+        return global_fail(GS_ERR_INVALID_ARG, "gs_multi_candidates: capacity below the " + std::to_string(n) +
+                                                   " candidates");
+    int32_t i = 0;
+    for (const auto& pl : plans)
+        for (int64_t S : batches) {
+            gs_multi_tune_candidate& c = out[i++];
+            c = gs_multi_tune_candidate{};
+            c.plan.kernel = pl[0];
+            c.plan.block_x = pl[1];
+            c.plan.rows = pl[2];
+            c.plan.temporal_depth = pl[3];
+            c.batch_size = S;
+        }
+    return GS_OK;
+}
+
+namespace {
+
+// Capture every graph gs_multi_step(n, S, FUSED) uses from the current
+// parity: the batch graph (both parities when a batch flips it and more
+// than one batch runs) and the remainder graph.
+gs_status capture_for_run(gs_multi* m, int64_t n, int64_t S) {
+    gs_status st = ensure_table(m);
+    if (st != GS_OK) return st;
+    const int p = m->parity;
+    const int64_t nb = n / S, r = n % S;
+    const int fl = (int)(launches_for(m, S) & 1);
+    cudaGraphExec_t ex;
+    if (nb > 0) {
+        st = capture_graph(m, S, p, &ex);
+        if (st == GS_OK && fl && nb > 1) st = capture_graph(m, S, p ^ 1, &ex);
+        if (st != GS_OK) return st;
+    }
+    if (r > 0) return capture_graph(m, r, p ^ (fl & (int)(nb & 1)), &ex);
+    return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_multi_autotune(gs_multi* m, int64_t n_iters, int32_t reps, const gs_multi_tune_candidate* cands,
+                            int32_t n_cands, gs_multi_tune_result* results, int32_t* best_index) {
+    if (!m) return global_fail(GS_ERR_INVALID_ARG, "NULL instance batch");
+    if (!cands || !results || n_cands < 1 || n_iters < 1 || reps < 1)
+        return mfail(m, GS_ERR_INVALID_ARG, "gs_multi_autotune: NULL pointer, or n_cands/n_iters/reps < 1");
+    // snapshot every instance's current buffer
+    const int n = (int)m->inst.size();
+    std::vector<void*> snap(n, nullptr), cur(n, nullptr);
+    std::vector<size_t> bytes(n, 0);
+    gs_status fatal = GS_OK;
+    for (int i = 0; i < n && fatal == GS_OK; ++i) {
+        int64_t pitch;
+        ctx_field(m->inst[i], m->parity ? GS_FIELD_T1 : GS_FIELD_T0, &cur[i], &pitch);
+        void* pp;
+        int64_t ppitch;
+        ctx_field(m->inst[i], GS_FIELD_P, &pp, &ppitch);
+        void* other;
+        int64_t opitch;
+        ctx_field(m->inst[i], m->parity ? GS_FIELD_T0 : GS_FIELD_T1, &other, &opitch);
+        if (!cur[i] || !pp || !other) {
+            fatal = mfail(m, GS_ERR_STATE, "gs_multi_autotune: instance " + std::to_string(i) + ": unbound field");
+            break;
+        }
+        bytes[i] = (size_t)pitch * (size_t)m->ny[i] * ctx_elem_bytes(m->inst[i]);
+        cudaError_t e = cudaMalloc(&snap[i], bytes[i]);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(snap[i], cur[i], bytes[i], cudaMemcpyDeviceToDevice, m->stream);
+        if (e != cudaSuccess) fatal = mcuda(m, e, "gs_multi_autotune snapshot");
+    }
+    if (fatal == GS_OK) {
+        cudaError_t e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) fatal = mcuda(m, e, "gs_multi_autotune snapshot");
+    }
+    if (fatal != GS_OK) {
+        for (void* b : snap)
+            if (b) cudaFree(b);
+        return fatal;
+    }
+    const gs_multi_plan saved = m->plan;
+    const int saved_parity = m->parity;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    double best_total = INFINITY;
+    int32_t best = -1;
+    for (int32_t c = 0; c < n_cands && fatal == GS_OK; ++c) {
+        gs_multi_tune_result& r = results[c];
+        r = gs_multi_tune_result{};
+        r.plan = cands[c].plan;
+        r.batch_size = cands[c].batch_size;
+        r.exec_ms_per_iter = INFINITY;
+        r.total_ms = INFINITY;
+        const int64_t S = cands[c].batch_size;
+        gs_status rs = (S < 0) ? GS_ERR_INVALID_ARG : gs_multi_set_plan(m, &cands[c].plan);
+        r.status = rs;
+        if (rs != GS_OK) continue;  // not runnable: skipped
+        r.plan = m->plan;
+        if (S > 0) {
+            cudaError_t e = cudaStreamSynchronize(m->stream);
+            const auto t0 = std::chrono::steady_clock::now();
+            rs = (e == cudaSuccess) ? capture_for_run(m, n_iters, S) : mcuda(m, e, "gs_multi_autotune");
+            if (rs == GS_OK) {
+                e = cudaStreamSynchronize(m->stream);
+                if (e != cudaSuccess) rs = mcuda(m, e, "gs_multi_autotune build");
+            }
+            r.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+        // warm-up run, then timed runs
+        if (rs == GS_OK) rs = gs_multi_step(m, n_iters, S, GS_MULTI_FUSED);
+        if (rs == GS_OK) rs = gs_multi_sync(m);
+        double best_ms = INFINITY;
+        for (int32_t k = 0; k < reps && rs == GS_OK; ++k) {
+            cudaEventRecord(ev0, m->stream);
+            rs = gs_multi_step(m, n_iters, S, GS_MULTI_FUSED);
+            cudaEventRecord(ev1, m->stream);
+            if (rs != GS_OK) break;
+            cudaError_t e = cudaEventSynchronize(ev1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+            if (e != cudaSuccess) {
+                rs = mcuda(m, e, "gs_multi_autotune timing");
+                break;
+            }
+            best_ms = std::min(best_ms, (double)ms);
+        }
+        r.status = rs;
+        if (rs != GS_OK) {
+            if (rs == GS_ERR_CUDA || rs == GS_ERR_OOM) fatal = rs;
+            continue;
+        }
+        r.exec_ms_per_iter = best_ms / (double)n_iters;
+        r.total_ms = r.build_seconds * 1e3 + best_ms;
+        if (r.total_ms < best_total) {
+            best_total = r.total_ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    // restore the plan, the parity and every instance's state
+    const std::string fatal_msg = m->err;
+    gs_multi_set_plan(m, &saved);
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    m->parity = saved_parity;
+    for (gs_ctx* c : m->inst) gs_set_parity(c, saved_parity);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(cur[i], snap[i], bytes[i], cudaMemcpyDeviceToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    for (void* b : snap) cudaFree(b);
+    if (fatal != GS_OK) return mfail(m, fatal, fatal_msg);
+    if (e != cudaSuccess) return mcuda(m, e, "gs_multi_autotune restore");
+    if (best_index) *best_index = best;
+    if (best < 0) return mfail(m, GS_ERR_UNSUPPORTED, "gs_multi_autotune: no candidate could run");
     return GS_OK;
 }
 

@@ -78,6 +78,8 @@ def test_hbm_roofline_of_arithmetic():
 def test_column_geometry_of_the_default_workload():
     # 3D 512x512x8, COLUMN rows 4: 4 x 128 blocks of 32 x 4 threads
     assert bench.column_geometry(bench.WORKLOADS["heat3d-512x512x8"], dict(kernel=4, rows=4), 1) == (512, 128)
+    # at depth 2 (block_x 64): 19 x 64 blocks of 32 x 2 threads (28 cells, 4 rows a warp)
+    assert bench.column_geometry(bench.WORKLOADS["heat3d-512x512x8"], dict(kernel=4, block_x=64), 2) == (1216, 64)
     assert bench.column_geometry(bench.WORKLOADS["fdtd-128"], dict(kernel=4), 1) is None
 
 

@@ -114,7 +114,7 @@ def test_remainder_graphs_of_one_size_are_kept():
 
 
 @pytest.mark.parametrize("shape", [(96, 64, 1), (77, 45, 1), (300, 37, 1), (40, 33, 8), (21, 19, 3), (250, 20, 16),
-                                   (500, 130, 1), (3, 2, 1)])
+                                   (500, 130, 1), (3, 2, 1), (40, 33, 4), (130, 9, 5), (64, 70, 2), (29, 3, 8)])
 @pytest.mark.parametrize("depth", [1, 2, 4])
 def test_temporal_blocking_bit_identical(shape, depth):
     import paper_2501_09398_gb300 as g
@@ -138,10 +138,10 @@ def test_temporal_blocking_bit_identical(shape, depth):
                 continue
             assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"column {kern} rows={rows}"
             assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column {kern} graph rows={rows}"
-    if depth > 1:  # column kernel at depth 2 / 4: no march, levels in registers (2D only)
-        for bx in (32, 64, 256):
-            plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_COLUMN, block_x=bx)
-            if nz > 1:
+    if depth > 1:  # column kernel at depth 2 / 4: no march, levels in registers (2D, and stacks of <= 8 planes)
+        for bx, rows in ((32, 0), (64, 2), (256, 0)):
+            plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_COLUMN, block_x=bx, rows=rows)
+            if nz > 8:
                 with pytest.raises(g.GsError):
                     heat_gpu(T0, P, n, S=0, plan=plan)
                 continue

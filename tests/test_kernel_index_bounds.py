@@ -9,6 +9,8 @@ stores).  For every thread of every block of the launch the library makes,
 every global load and store must lie inside its buffer and inside its row
 (the pitch), every shared-memory access inside the launch's allocation, and
 the stores of a launch must cover every cell of the field exactly once.
+The 3D depth-t COLUMN kernel (one cell a lane, every plane of the column)
+is re-traced the same way.
 The formulas restate the kernels' address computations (csrc/heat.cu,
 csrc/fdtd.cu, csrc/multi.cu) for ragged shapes, so that a change to either
 is checked here before it runs on a GPU."""
@@ -152,6 +154,54 @@ def test_temporal_column_kernel_addresses(nx, ny, esize, depth, block_x):
     cells = np.zeros((ny, pitch), dtype=bool)
     cells[:, :nx] = True
     assert np.array_equal(covered.reshape(ny, pitch) == 1, cells)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(512, 24, 8), (97, 41, 8), (40, 33, 7), (30, 9, 4), (29, 5, 3), (1, 9, 2),
+                                      (57, 1, 8), (3, 2, 5), (2, 3, 1)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("depth,rows", [(2, 4), (2, 2), (4, 4)])
+@pytest.mark.parametrize("block_x", [32, 128, 256])
+def test_temporal_column3_kernel_addresses(nx, ny, nz, esize, depth, rows, block_x):
+    # one cell a lane, 32 - 2t stored lanes a warp, R rows a warp row (4 at
+    # depth 2 unless plan.rows is 2; 2 at depth 4), loads of rows y0-t ..
+    # y0+R+t-1 of every plane at clamped coordinates; EXACT kernels hold nz
+    # planes (nz 4 or 8), the others eight
+    R = 4 if (depth == 2 and rows != 2) else 2
+    BY = max(1, min(block_x // 32, 8))
+    span = 32 - 2 * depth
+    grid = (-(-nx // span), -(-ny // (R * BY)), 1)
+    NZM = nz if nz in (4, 8) else 8
+    pitch = pitch_of(nx, esize)
+    plane = pitch * ny
+    size = plane * nz
+    bx, by, bz, lane, ty, tz = threads(grid, (32, BY, 1))
+    xs = bx * span - depth
+    x = xs + lane
+    xc = np.minimum(np.maximum(x, 0), nx - 1)
+    y0 = (by * BY + ty) * R
+    NR = R + 2 * depth
+    for k in range(NR):
+        yk = np.clip(y0 - depth + k, 0, ny - 1)
+        for z in range(NZM):
+            zc = min(z, nz - 1)
+            check_vec(zc * plane + yk * pitch + xc, 1, zc * plane + yk * pitch, pitch, size)
+    for k in range(1, NR - 1):  # P rows (one plane)
+        yk = np.clip(y0 - depth + k, 0, ny - 1)
+        check_vec(yk * pitch + xc, 1, yk * pitch, pitch, pitch * ny)
+    covered = np.zeros(size, dtype=np.int64)
+    st = (lane >= depth) & (lane < 32 - depth) & (x < nx)
+    for j in range(depth, depth + R):
+        yg = y0 - depth + j
+        m = st & (yg < ny)
+        for z in range(min(NZM, nz)):
+            addr = (z * plane + yg * pitch + x)[m]
+            check_vec(addr, 1, (z * plane + yg * pitch)[m], pitch, size)
+            np.add.at(covered, addr, 1)
+    cells = np.zeros((nz, ny, pitch), dtype=bool)
+    cells[:, :, :nx] = True
+    assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
+    assert covered.max() <= 1
+    every_block_stores(st & (y0 < ny), bx, by, bz)
 
 
 # ---------------------------------------------------------------- FDTD ----

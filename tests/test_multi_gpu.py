@@ -133,3 +133,49 @@ def test_config3_batch(oracle):
         T, P = fields_np[i]
         err = max_rel(fused[i], oracle.heat_run(T, P, n, oracle.HEAT_COEFFS_2D))
         assert err <= HEAT_RTOL, (i, sides[i], err)
+
+
+def test_multi_autotune_restores_state_and_returns_its_argmin():
+    """gs_multi_autotune over the library's candidate list: every candidate
+    runs (or is skipped with its status), the best index is the argmin of
+    the returned totals, and the batch's fields, parity and plan are as they
+    were (a step after tuning equals a step of an untuned batch)."""
+    import torch
+
+    import paper_2501_09398_gb300 as g
+
+    dims = [(130, 17), (5, 9), (64, 64), (200, 3), (77, 120), (300, 40)]
+    fields_np = [gs_inputs.heat_fields(w, h, 1, seed=700 + i) for i, (w, h) in enumerate(dims)]
+    nx, ny = [d[0] for d in dims], [d[1] for d in dims]
+    stream = torch.cuda.Stream()
+    ref, _ = _run(None, fields_np, 7 + 30, 0, g.GS_MULTI_FUSED, stream=stream, dims=dims)
+
+    m = g.gs_multi_create(nx, ny, g.GS_F32, g.GS_BC_CLAMP, stream.cuda_stream)
+    bufs = g.MultiFields(m, nx, ny)
+    try:
+        for i, (T, P) in enumerate(fields_np):
+            g.gs_multi_upload(m, i, g.GS_FIELD_T, T)
+            g.gs_multi_upload(m, i, g.GS_FIELD_P, P)
+        g.gs_multi_step(m, 7, 0, g.GS_MULTI_FUSED)  # odd: the state sits in T1
+        plan0 = g.gs_multi_get_plan(m)
+        cands = g.gs_multi_candidates(m)
+        assert len(cands) == 56 and all(S in (0, 10, 100, 1000) for _, S in cands)
+        res, best = g.gs_multi_autotune(m, 30, cands, reps=2)
+        ok = [i for i, r in enumerate(res) if r["status"] == g.GS_OK]
+        assert len(ok) == len(cands)  # every candidate of the list runs on these grids
+        assert best == min(ok, key=lambda i: res[i]["total_ms"])
+        for r, (plan, S) in zip(res, cands):
+            assert r["batch_size"] == S and r["exec_ms_per_iter"] > 0
+            assert (r["build_seconds"] > 0) == (S > 0)
+            for k in ("kernel", "rows", "temporal_depth"):
+                assert r["plan"][k] == plan[k]
+        assert g.gs_multi_get_plan(m) == plan0 and g.gs_multi_get_parity(m) == 1
+        g.gs_multi_step(m, 30, 0, g.GS_MULTI_FUSED)
+        got = [g.gs_multi_read_field(m, i, g.GS_FIELD_T, np.empty_like(T)) for i, (T, _) in enumerate(fields_np)]
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+        # the tuned plan runs bit-identically too
+        g.gs_multi_set_plan(m, **res[best]["plan"])
+    finally:
+        g.gs_multi_destroy(m)
+        del bufs

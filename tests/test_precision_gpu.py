@@ -133,7 +133,7 @@ def test_config2_reduced_precision(fdtd_config2_ref, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-@pytest.mark.parametrize("shape", [(300, 37, 1), (130, 45, 8), (60, 20, 17)])
+@pytest.mark.parametrize("shape", [(300, 37, 1), (130, 45, 8), (60, 20, 17), (70, 33, 5)])
 def test_temporal_blocking_rounds_every_level(dtype, shape):
     # a depth-t launch rounds each level it computes to the storage type, as
     # t depth-1 launches store (and so round) every step: same bits
@@ -146,7 +146,7 @@ def test_temporal_blocking_rounds_every_level(dtype, shape):
     plans = [dict(kernel=g.GS_KERNEL_TILE, tile_x=16, tile_y=8)]
     if nz <= 16:
         plans.append(dict(kernel=g.GS_KERNEL_WAVE, rows=3, block_x=64))
-    if nz == 1:
+    if nz <= 8:
         plans.append(dict(kernel=g.GS_KERNEL_COLUMN, block_x=64))
     for depth in (2, 4):
         for plan in plans:
