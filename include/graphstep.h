@@ -557,6 +557,30 @@ gs_status gs_candidates(const gs_workload *w, gs_tune_candidate *out, int32_t ca
 gs_status gs_pick(gs_mlp *const *models, int32_t k, const gs_workload *w, gs_tune_candidate *best,
                   float *pred_ms_per_iter);
 
+/* The trained ensemble compiled into the library: GS_MLP_BUILTIN_MEMBERS
+ * models trained with the library's own kernels on the GB300 sweep the
+ * package ships (gs_mlp_builtin_info() names the sweep, epochs and losses).
+ * gs_mlp_create_builtin creates member `member` (weights and normalisation
+ * set) on `stream` (NULL: its own).  Errors: GS_ERR_INVALID_ARG (member out
+ * of range), GS_ERR_UNSUPPORTED (a build without a trained ensemble), and
+ * those of gs_mlp_create; message in gs_last_error(NULL). */
+#define GS_MLP_BUILTIN_MEMBERS 3
+gs_status gs_mlp_create_builtin(gs_mlp **out, int32_t member, void *stream);
+const char *gs_mlp_builtin_info(void);
+
+/* The learned choice for a context, with the library's own ensemble: the
+ * candidate (plan, batch size) gs_pick chooses for a run of n_iters
+ * iterations of ctx's workload (kind, storage type, grid) with the
+ * compiled-in models, applied with gs_set_plan (the candidate's block_x,
+ * rows, temporal_depth and kernel; its other plan fields 0).  *plan_out (may
+ * be NULL) receives the applied plan, *batch_out the batch size to pass to
+ * gs_step (0: per-step launches), *pred_ms_per_iter (may be NULL) the
+ * prediction.  Runs nothing of the workload.  Synchronous (on ctx's stream).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_UNSUPPORTED (skeleton contexts, a build
+ * without a trained ensemble, no candidate fits), GS_ERR_NUMERIC,
+ * GS_ERR_CUDA / GS_ERR_OOM; message in gs_last_error(ctx). */
+gs_status gs_pick_ctx(gs_ctx *ctx, int64_t n_iters, gs_plan *plan_out, int64_t *batch_out, float *pred_ms_per_iter);
+
 /* The paper's choice (Sec. III-B): on ctx at its current plan, measure graph
  * creation and execution for the batch sizes 1, 10, 50, 100, 500, 1000 that
  * do not exceed n_iters (gs_model_calibrate: reps timed runs of n_iters
@@ -828,6 +852,25 @@ typedef struct gs_instance {
 gs_status gs_multi_step_noalloc(const gs_instance *inst, int32_t n_inst, int32_t parity, int64_t n_iters,
                                 const gs_heat_coeffs *coeffs, gs_dtype storage, gs_bc bc, void *stream,
                                 int32_t *parity_out);
+
+/* --------------------------------------------------- fault injection -- */
+
+/* Host-side fault injection for tests of the library's error paths (the
+ * paper has no counterpart).  Every device allocation of the library
+ * (contexts' scratch, instance-batch tables, slab fields, tuner snapshots,
+ * cost-model buffers) and every kernel node it adds to a graph goes through
+ * a wrapper; gs_debug_inject_failure(call, after) lets the next `after`
+ * calls of that kind succeed and makes the one after them fail, once
+ * (GS_INJECT_MALLOC: as cudaErrorMemoryAllocation; GS_INJECT_GRAPH_NODE: as
+ * cudaErrorInvalidValue), with no CUDA call made for it; the injection is
+ * then disarmed.  GS_INJECT_NONE disarms.  Process-wide; meant for a test
+ * that owns the process's library calls while armed.  Nothing on the GPU
+ * faults: the failure is a returned status.  gs_debug_injection_pending
+ * tells whether an armed failure has not fired yet.  Errors:
+ * GS_ERR_INVALID_ARG (unknown kind, after < 0, NULL). */
+typedef enum gs_inject { GS_INJECT_NONE = 0, GS_INJECT_MALLOC = 1, GS_INJECT_GRAPH_NODE = 2 } gs_inject;
+gs_status gs_debug_inject_failure(gs_inject call, int64_t after);
+gs_status gs_debug_injection_pending(int32_t *pending);
 
 #ifdef __cplusplus
 }

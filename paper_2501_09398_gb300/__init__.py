@@ -516,6 +516,36 @@ def gs_pick(models, workload: dict):
     return {f: getattr(best.plan, f) for f in _SHAPE}, best.batch_size, pred.value
 
 
+_sig("gs_mlp_create_builtin", [ctypes.POINTER(_vp), _i32, _vp])
+_sig("gs_mlp_builtin_info", [], ctypes.c_char_p)
+_sig("gs_pick_ctx", [_vp, _i64, ctypes.POINTER(gs_plan), ctypes.POINTER(_i64), _fp])
+GS_MLP_BUILTIN_MEMBERS = 3
+
+
+def gs_mlp_create_builtin(member: int, stream=None):
+    """Member `member` of the trained ensemble compiled into the library."""
+    h = _vp()
+    st = _lib.gs_mlp_create_builtin(ctypes.byref(h), member, _vp(stream) if stream else None)
+    if st != GS_OK:
+        raise GsError(st, _lib.gs_last_error(None).decode(errors="replace"))
+    return h
+
+
+def gs_mlp_builtin_info() -> str:
+    return _lib.gs_mlp_builtin_info().decode(errors="replace")
+
+
+def gs_pick_ctx(ctx, n_iters: int):
+    """The learned choice for a run of n_iters iterations of ctx's workload
+    with the library's own ensemble, applied to ctx: (plan dict as applied,
+    S, predicted ms per iteration)."""
+    p = gs_plan()
+    S = _i64()
+    pred = ctypes.c_float()
+    _check(_lib.gs_pick_ctx(ctx, int(n_iters), ctypes.byref(p), ctypes.byref(S), ctypes.byref(pred)), ctx)
+    return {n: getattr(p, n) for n, _ in gs_plan._fields_}, S.value, pred.value
+
+
 def gs_pick_analytic(ctx, n_iters: int, reps: int = 2):
     """The paper's choice on a context at its current plan: (S, fitted model)."""
     S = _i64()
@@ -764,6 +794,23 @@ def gs_multi_step_noalloc(instances, parity: int, n_iters: int, coeffs=None, dty
     _check(_lib.gs_multi_step_noalloc(arr, n, parity, n_iters, ctypes.byref(c), dtype, bc,
                                       _vp(stream) if stream else None, ctypes.byref(out)))
     return out.value
+
+
+# ------------------------------------------------------- fault injection --
+GS_INJECT_NONE, GS_INJECT_MALLOC, GS_INJECT_GRAPH_NODE = range(3)
+_sig("gs_debug_inject_failure", [ctypes.c_int, _i64])
+_sig("gs_debug_injection_pending", [ctypes.POINTER(_i32)])
+
+
+def gs_debug_inject_failure(call: int, after: int = 0) -> None:
+    """Make the library's (after+1)-th next call of kind `call` fail once."""
+    _check(_lib.gs_debug_inject_failure(call, after))
+
+
+def gs_debug_injection_pending() -> bool:
+    v = _i32()
+    _check(_lib.gs_debug_injection_pending(ctypes.byref(v)))
+    return bool(v.value)
 
 
 def raw_call(name: str, *args) -> int:

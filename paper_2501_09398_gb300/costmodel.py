@@ -24,6 +24,13 @@ learned model:
    needs the workload's own timings at several batch sizes, the learned
    picker none) and a fixed S = 100 ("approximately 100 nodes", Sec. IV-A).
 
+6. ``write_builtin``: the trained ensemble as the source file the library
+   compiles in (``gs_mlp_create_builtin``, ``gs_pick_ctx``).
+7. ``measured_regret``: the learned pick checked by running it: on held-out
+   workloads, whole runs of I_k iterations (graph creation included, CUDA
+   events on the stream) of the pick of the compiled-in ensemble, of the
+   sweep's best candidate and of the analytic pick.
+
 Run ``python -m paper_2501_09398_gb300.costmodel --help``.
 """
 from __future__ import annotations
@@ -36,10 +43,11 @@ import time
 import numpy as np
 
 from . import (GS_BC_CLAMP, GS_BC_PEC, GS_F32, GS_FDTD3D, GS_FIELD_P, GS_FIELD_T, GS_HEAT2D, GS_HEAT3D,
-               GS_KERNEL_COLUMN, FDTD_FIELDS, FdtdFields, HeatFields, gs_autotune, gs_create,
-               gs_candidates, gs_destroy, gs_features, gs_model_fit, gs_model_pick, gs_mlp_argmin_ensemble, gs_mlp_create,
-               gs_mlp_destroy, gs_mlp_fit_normalization, gs_mlp_loss_grad, gs_mlp_train, gs_set_fdtd_params,
-               gs_upload)
+               GS_KERNEL_COLUMN, GS_MLP_INPUTS, FDTD_FIELDS, FdtdFields, HeatFields, gs_autotune, gs_create,
+               gs_candidates, gs_destroy, gs_features, gs_graph_destroy, gs_model_fit, gs_model_pick,
+               gs_mlp_argmin_ensemble, gs_mlp_create, gs_mlp_create_builtin, gs_mlp_destroy,
+               gs_mlp_fit_normalization, gs_mlp_get_normalization, gs_mlp_get_params, gs_mlp_loss_grad,
+               gs_mlp_train, gs_pick, gs_set_fdtd_params, gs_set_plan, gs_set_time, gs_step, gs_upload)
 
 KINDS = ("heat2d", "heat3d", "fdtd")
 KIND_ID = {"heat2d": GS_HEAT2D, "heat3d": GS_HEAT3D, "fdtd": GS_FDTD3D}
@@ -275,6 +283,130 @@ def summarize(reg):
                     max=float(np.max(v)), within_5pct=float(np.mean(np.array(v) <= 0.05))) for k, v in reg.items()}
 
 
+BUILTIN = __import__("os").path.join(__import__("os").path.dirname(__file__), "csrc", "costmodel_weights.inc")
+
+
+def write_builtin(models, path: str, info: str) -> None:
+    """Write the ensemble's parameters and normalisation as the C++ include
+    the library compiles in (exact float32 values, 9 significant digits)."""
+    def arr(v):
+        return ",".join("%.9g" % float(x) for x in v)
+
+    params = [gs_mlp_get_params(m) for m in models]
+    norms = [np.concatenate(gs_mlp_get_normalization(m)) for m in models]
+    lines = ["// The cost-model ensemble compiled into the library (see mlp.cu,",
+             "// gs_mlp_create_builtin), written by",
+             "// `python -m paper_2501_09398_gb300.costmodel --write-builtin FILE`.",
+             "constexpr int kBuiltinTrained = 1;",
+             "constexpr int kBuiltinMembers = %d;" % len(models),
+             "static const float kBuiltinParams[kBuiltinMembers][GS_MLP_PARAMS] = {"]
+    lines += ["    {%s}," % arr(p) for p in params]
+    lines += ["};", "static const float kBuiltinNorm[kBuiltinMembers][2 * GS_MLP_INPUTS] = {"]
+    lines += ["    {%s}," % arr(n) for n in norms]
+    lines += ["};", "static const char kBuiltinInfo[] = %s;" % json.dumps(info)]
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+def builtin_models(stream=None):
+    return [gs_mlp_create_builtin(k, stream) for k in range(3)]
+
+
+def _reset(ctx, w):
+    """Seeded initial state of the workload's fields (outside any timing)."""
+    import gs_inputs
+
+    if w["kind"] == "fdtd":
+        z = np.zeros((w["nx"] + 1,) * 3, dtype=np.float32)
+        for fid in FDTD_FIELDS:
+            gs_upload(ctx, fid, z)
+        gs_set_time(ctx, 0)
+    else:
+        T, P = gs_inputs.heat_fields(w["nx"], w["ny"], w["nz"], seed=0)
+        gs_upload(ctx, GS_FIELD_T, T)
+        gs_upload(ctx, GS_FIELD_P, P)
+
+
+def whole_run_ms(w, plan, S, stream, reps=3):
+    """Median over `reps` runs (after one untimed run) of a whole run of
+    w["n_iters"] iterations with (plan, S) from a fresh state: graph
+    creation (T_C) and execution, CUDA events on the context's stream (the
+    GPU waits for the host's graph build between them)."""
+    import torch
+
+    ctx, keep = _context(w, stream)
+    try:
+        gs_set_plan(ctx, **plan)
+        st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.current_stream()
+        times = []
+        for r in range(reps + 1):
+            _reset(ctx, w)
+            gs_graph_destroy(ctx)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            gs_step(ctx, w["n_iters"], S)
+            b.record(st)
+            torch.cuda.synchronize()
+            if r > 0:
+                times.append(a.elapsed_time(b))
+    finally:
+        gs_destroy(ctx)
+        del keep
+    return float(np.median(times))
+
+
+def measured_regret(models, held, n=30, seed=7, stream=None, reps=3, max_run_ms=400.0):
+    """Whole-run regret of the learned pick, measured: for n held-out
+    workloads (a seeded choice, equal numbers of each kind, runs the sweep
+    predicts under max_run_ms), run the learned pick (gs_pick with
+    `models`), the sweep's best candidate and the analytic pick, each a
+    whole run of I_k iterations; regret = T(pick) / min over the three - 1.
+    Returns per-workload records and the composed-time regrets (from the
+    sweep's T_C and ms per iteration) of the same picks."""
+    rng = np.random.default_rng(seed)
+    by_kind = {k: [] for k in KINDS}
+    for w, tab in held:
+        ok = [r for r in tab if r["status"] == 0 and math.isfinite(r["ms_per_iter"])]
+        if ok and min(run_ms(r, w["n_iters"]) for r in ok) < max_run_ms:
+            by_kind[w["kind"]].append((w, tab))
+    chosen = []
+    for k in KINDS:
+        idx = rng.permutation(len(by_kind[k]))[: n // len(KINDS)]
+        chosen += [by_kind[k][i] for i in sorted(idx)]
+    recs = []
+    for w, tab in chosen:
+        plan_l, S_l, _ = gs_pick(models, _fw(w))
+        ok = [r for r in tab if r["status"] == 0 and math.isfinite(r["ms_per_iter"])]
+        best = min(ok, key=lambda r: run_ms(r, w["n_iters"]))
+        ana = pick_analytic(w, tab)
+        picks = {"learned": (plan_l, S_l), "swept_best": (best["plan"], best["S"]), "analytic": (ana["plan"], ana["S"])}
+        meas = {}
+        for name, (plan, S) in picks.items():
+            key = (tuple(sorted(plan.items())), S)
+            same = [m for m in meas.values() if m["key"] == key]
+            meas[name] = dict(key=key, ms=same[0]["ms"] if same else whole_run_ms(w, plan, S, stream, reps))
+        lo = min(m["ms"] for m in meas.values())
+        learned_row = next((r for r in ok if r["plan"] == plan_l and r["S"] == S_l), None)
+        recs.append(dict(workload=w, ms={k: v["ms"] for k, v in meas.items()},
+                         measured_regret={k: v["ms"] / lo - 1.0 for k, v in meas.items()},
+                         composed_regret_learned=(regret(w, tab, learned_row) if learned_row else None),
+                         picks={k: dict(plan=v[0], S=v[1]) for k, v in picks.items()}))
+    return recs
+
+
+def summarize_measured(recs):
+    out = {}
+    for name in ("learned", "swept_best", "analytic"):
+        v = np.array([r["measured_regret"][name] for r in recs])
+        out[name] = dict(mean=float(v.mean()), median=float(np.median(v)), p95=float(np.percentile(v, 95)),
+                         within_5pct=float(np.mean(v <= 0.05)))
+    comp = [r["composed_regret_learned"] for r in recs if r["composed_regret_learned"] is not None]
+    out["learned_composed_same_workloads"] = dict(mean=float(np.mean(comp)), n=len(comp))
+    out["workloads"] = len(recs)
+    return out
+
+
 def main():
     import torch
 
@@ -290,11 +422,34 @@ def main():
     ap.add_argument("--batch-rows", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--members", type=int, default=ENSEMBLE, help="models in the ensemble")
+    ap.add_argument("--write-builtin", default="",
+                    help="write the trained ensemble as the include the library compiles in (e.g. " + BUILTIN + ")")
+    ap.add_argument("--measure-regret", type=int, default=0,
+                    help="only measure whole-run regret of the compiled-in ensemble on this many held-out workloads "
+                         "(--tables gives the sweep)")
+    ap.add_argument("--regret-seed", type=int, default=7, help="seed of the workload choice of --measure-regret")
+    ap.add_argument("--regret-max-ms", type=float, default=400.0,
+                    help="--measure-regret takes workloads whose swept best run is shorter than this")
+    ap.add_argument("--regret-reps", type=int, default=3, help="timed runs per pick (median)")
     args = ap.parse_args()
     torch.cuda.set_device(0)
     st = torch.cuda.Stream()
     torch.cuda.set_stream(st)
     t0 = time.time()
+    if args.measure_regret:
+        _, held_pairs = load_tables(DATA if args.tables in ("", "packaged") else args.tables)
+        models = builtin_models(st.cuda_stream)
+        try:
+            recs = measured_regret(models, held_pairs, n=args.measure_regret, seed=args.regret_seed,
+                                   stream=st.cuda_stream, reps=args.regret_reps, max_run_ms=args.regret_max_ms)
+        finally:
+            for m in models:
+                gs_mlp_destroy(m)
+        report = dict(summary=summarize_measured(recs), records=recs, seconds=time.time() - t0)
+        with open(args.out, "w") as f:
+            json.dump(report, f, indent=1, default=str)
+        print(json.dumps(report["summary"]))
+        return
     if args.tables:
         train_pairs, held_pairs = load_tables(DATA if args.tables == "packaged" else args.tables)
         train_pairs, held_pairs = train_pairs[:args.train], held_pairs[:args.heldout]
@@ -311,6 +466,12 @@ def main():
     models, l0, loss = train(X, y, epochs=args.epochs, batch_rows=args.batch_rows, lr=args.lr, members=args.members)
     try:
         reg = evaluate(models, held_pairs)
+        if args.write_builtin:
+            info = ("GB300 ensemble of %d MLPs (seeds 0..%d), %d epochs, batch %d, lr %g, trained on %d rows from %d "
+                    "swept workloads (seed 1); final losses %s; held-out mean regret %.4f (composed from the sweep)"
+                    % (len(models), len(models) - 1, args.epochs, args.batch_rows, args.lr, X.shape[0],
+                       len(train_pairs), ", ".join("%.4f" % v for v in loss), float(np.mean(reg["learned"]))))
+            write_builtin(models, args.write_builtin, info)
     finally:
         for m in models:
             gs_mlp_destroy(m)

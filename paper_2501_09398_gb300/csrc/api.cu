@@ -1,5 +1,6 @@
 // C ABI of graphstep: contexts, field binding, per-step launches and the
 // iteration-batch graph unroller (the paper's Sec. III-A, Listings 1-3).
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -328,7 +329,7 @@ gs_status upload_media(gs_ctx* c) {
         c->h_med[m] = make_float2((float)((1.0 - ah) / (1.0 + ah)), (float)((s / r.mu_r) / (1.0 + ah)));
         c->h_med[GS_MAX_MEDIA + m] = make_float2((float)((1.0 - ae) / (1.0 + ae)), (float)((s / r.eps_r) / (1.0 + ae)));
     }
-    if (!c->d_med) GS_CUDA(c, cudaMalloc(&c->d_med, 2 * GS_MAX_MEDIA * sizeof(float2)));
+    if (!c->d_med) GS_CUDA(c, gs_malloc(&c->d_med, 2 * GS_MAX_MEDIA * sizeof(float2)));
     GS_CUDA(c, cudaMemcpyAsync(c->d_med, c->h_med.data(), 2 * GS_MAX_MEDIA * sizeof(float2), cudaMemcpyHostToDevice,
                                c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -488,10 +489,10 @@ cudaError_t add_chain(gs_ctx* c, cudaGraph_t g, int64_t S, int p, cudaGraphNode_
         np.extra = nullptr;
         cudaGraphNode_t node;
         if (c->plan.use_pdl && *prev) {
-            err = cudaGraphAddKernelNode(&node, g, nullptr, 0, &np);
+            err = gs_graph_add_kernel_node(&node, g, nullptr, 0, &np);
             if (err == cudaSuccess) err = cudaGraphAddDependencies(g, prev, &node, &edge, 1);
         } else {
-            err = cudaGraphAddKernelNode(&node, g, *prev ? prev : nullptr, *prev ? 1 : 0, &np);
+            err = gs_graph_add_kernel_node(&node, g, *prev ? prev : nullptr, *prev ? 1 : 0, &np);
         }
         *prev = node;
         ++*nodes;
@@ -542,7 +543,7 @@ gs_status build_graph(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
 // `trip` bodies with no host launch between them; the trip count is a
 // parameter of the init node, changed in the executable graph per launch.
 gs_status build_loop(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
-    if (!c->d_loop) GS_CUDA(c, cudaMalloc(&c->d_loop, sizeof(unsigned long long)));
+    if (!c->d_loop) GS_CUDA(c, gs_malloc(&c->d_loop, sizeof(unsigned long long)));
     cudaGraph_t g = nullptr;
     GS_CUDA(c, cudaGraphCreate(&g, 0));
     cudaError_t err = cudaSuccess;
@@ -556,7 +557,7 @@ gs_status build_loop(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
     ip.blockDim = dim3(1);
     ip.kernelParams = init_args;
     err = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
-    if (err == cudaSuccess) err = cudaGraphAddKernelNode(&init, g, nullptr, 0, &ip);
+    if (err == cudaSuccess) err = gs_graph_add_kernel_node(&init, g, nullptr, 0, &ip);
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -577,7 +578,7 @@ gs_status build_loop(gs_ctx* c, int64_t S, int p, GraphEntry* out) {
         kp.blockDim = dim3(1);
         kp.kernelParams = ctl_args;
         cudaGraphNode_t ctl;
-        if (err == cudaSuccess) err = cudaGraphAddKernelNode(&ctl, body, &prev, 1, &kp);
+        if (err == cudaSuccess) err = gs_graph_add_kernel_node(&ctl, body, &prev, 1, &kp);
     }
     if (err != cudaSuccess) {
         cudaGraphDestroy(g);
@@ -645,6 +646,30 @@ gs_status launch_loop(gs_ctx* c, int64_t S, int64_t count) {
     return GS_OK;
 }
 
+// Build (if missing) every graph gs_step(n, S) launches from the current
+// parity, before its first launch: a failed build then leaves the context as
+// it was (no batch launched, parity and time unchanged).
+gs_status prepare_step_graphs(gs_ctx* c, int64_t n, int64_t S) {
+    const int64_t nb = n / S, r = n - nb * S;
+    const int fl = flip_of(c, S);
+    int p = c->parity;
+    GraphEntry* e = nullptr;
+    gs_status st = GS_OK;
+    if (nb > 0) {
+        if (c->plan.graph_loop) {
+            if ((fl ? nb / 2 : nb) > 0) st = ensure_loop(c, S, p, &e);
+            if (st == GS_OK && fl && (nb & 1)) st = ensure_graph(c, S, p, &e);
+        } else {
+            st = ensure_graph(c, S, p, &e);
+            if (st == GS_OK && fl && nb > 1) st = ensure_graph(c, S, p ^ 1, &e);
+        }
+        if (st != GS_OK) return st;
+        p ^= fl & (int)(nb & 1);
+    }
+    if (r > 0) st = ensure_graph(c, r, p, &e);
+    return st;
+}
+
 // `count` batches of S: graph launches (Listing 3) or the device loop.
 gs_status run_batches(gs_ctx* c, int64_t S, int64_t count) {
     return c->plan.graph_loop ? launch_loop(c, S, count) : launch_graphs(c, S, count);
@@ -671,7 +696,7 @@ gs_status ensure_staging(gs_ctx* c, size_t bytes) {
         c->staging = nullptr;
         c->staging_bytes = 0;
     }
-    GS_CUDA(c, cudaMalloc(&c->staging, bytes));
+    GS_CUDA(c, gs_malloc(&c->staging, bytes));
     c->staging_bytes = bytes;
     return GS_OK;
 }
@@ -696,6 +721,38 @@ bool ctx_is_skel(const gs_ctx* c) { return is_skel(c); }
 cudaStream_t ctx_stream(const gs_ctx* c) { return c->stream; }
 gs_status ctx_fail(gs_ctx* c, gs_status s, const std::string& msg) { return fail(c, s, msg); }
 gs_status global_fail(gs_status s, const std::string& msg) { return fail(nullptr, s, msg); }
+
+namespace inject {
+// Armed injection: the call kind and how many more calls of it succeed
+// before the failing one (-1: disarmed).
+std::atomic<int> g_inject_kind{GS_INJECT_NONE};
+std::atomic<long long> g_inject_left{-1};
+
+bool injected(int kind) {
+    if (g_inject_kind.load() != kind) return false;
+    const long long left = g_inject_left.fetch_sub(1);
+    if (left > 0) return false;
+    if (left == 0) {  // this call fails, then the injection is disarmed
+        g_inject_kind.store(GS_INJECT_NONE);
+        return true;
+    }
+    return false;
+}
+}  // namespace inject
+
+cudaError_t gs_malloc_raw(void** p, size_t bytes) {
+    if (inject::injected(GS_INJECT_MALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t gs_graph_add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t n,
+                                     const cudaKernelNodeParams* params) {
+    if (inject::injected(GS_INJECT_GRAPH_NODE)) return cudaErrorInvalidValue;
+    return cudaGraphAddKernelNode(node, g, deps, n, params);
+}
 
 int device_sm_count() {
     int dev = 0, n = 0;
@@ -767,6 +824,26 @@ const char* gs_status_string(gs_status s) {
 
 const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
+gs_status gs_debug_inject_failure(gs_inject call, int64_t after) {
+    if (call == GS_INJECT_NONE) {
+        gs::inject::g_inject_kind.store(GS_INJECT_NONE);
+        gs::inject::g_inject_left.store(-1);
+        return GS_OK;
+    }
+    if ((call != GS_INJECT_MALLOC && call != GS_INJECT_GRAPH_NODE) || after < 0)
+        return fail(nullptr, GS_ERR_INVALID_ARG, "gs_debug_inject_failure: unknown call kind or after < 0");
+    gs::inject::g_inject_kind.store(GS_INJECT_NONE);
+    gs::inject::g_inject_left.store(after);
+    gs::inject::g_inject_kind.store(call);
+    return GS_OK;
+}
+
+gs_status gs_debug_injection_pending(int32_t* pending) {
+    if (!pending) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_debug_injection_pending: NULL argument");
+    *pending = gs::inject::g_inject_kind.load() != GS_INJECT_NONE;
+    return GS_OK;
+}
+
 gs_status gs_required_pitch(gs_dtype dtype, int64_t width, int64_t* pitch_out) {
     if (!pitch_out || width < 1 || (dtype != GS_F32 && dtype != GS_BF16 && dtype != GS_F16))
         return fail(nullptr, GS_ERR_INVALID_ARG, "gs_required_pitch: need width >= 1, a known dtype and pitch_out");
@@ -813,7 +890,7 @@ gs_status ctx_create(gs_ctx** out, gs_kind kind, int64_t nx, int64_t ny, int64_t
         }
     }
     if (e == cudaSuccess && kind == GS_FDTD3D) {
-        e = cudaMalloc(&c->d_counter, sizeof(long long));
+        e = gs_malloc(&c->d_counter, sizeof(long long));
         if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, sizeof(long long), c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
@@ -833,6 +910,16 @@ void ctx_launch_list(gs_ctx* c, int64_t n, int p, std::vector<LaunchDesc*>* out)
 }
 
 int ctx_flip(const gs_ctx* c, int64_t n) { return flip_of(c, n); }
+
+void ctx_workload(const gs_ctx* c, gs_workload* w) {
+    *w = gs_workload{};
+    w->kind = c->kind;
+    w->dtype = c->dt;
+    w->nx = c->nx;
+    w->ny = c->ny;
+    w->nz = c->nz;
+    w->n_iters = c->time;
+}
 
 cudaError_t ctx_launch(gs_ctx* c, LaunchDesc& d) { return launch_one(c, d); }
 
@@ -1077,15 +1164,17 @@ gs_status gs_step(gs_ctx* c, int64_t n_iters, int64_t batch_size) {
         // iterations, then one remainder graph of n mod S iterations.
         const int64_t nb = n_iters / batch_size;
         const int64_t r = n_iters - nb * batch_size;
+        if (r > 0 && c->rem_S != r) {
+            drop_remainder(c, batch_size);
+            c->rem_S = r;
+        }
+        st = prepare_step_graphs(c, n_iters, batch_size);
+        if (st != GS_OK) return st;
         if (nb > 0) {
             st = run_batches(c, batch_size, nb);
             if (st != GS_OK) return st;
         }
         if (r > 0) {
-            if (c->rem_S != r) {
-                drop_remainder(c, batch_size);
-                c->rem_S = r;
-            }
             st = launch_graphs(c, r, 1);
             if (st != GS_OK) return st;
         }

@@ -289,6 +289,15 @@ cudaError_t convert_from_storage(gs_dtype dt, const void* src, float* dst, long 
 
 cudaError_t skeleton_desc(gs_dtype dt, const SkeletonArgs& a, int block_x, LaunchDesc* out);
 
+// Host-side fault injection (gs_debug_inject_failure): every device
+// allocation and graph kernel-node addition of the library goes through
+// these, which fail the armed call once with cudaErrorMemoryAllocation /
+// cudaErrorInvalidValue and otherwise forward to CUDA.
+cudaError_t gs_malloc_raw(void** p, size_t bytes);
+template <typename T> cudaError_t gs_malloc(T** p, size_t bytes) { return gs_malloc_raw(reinterpret_cast<void**>(p), bytes); }
+cudaError_t gs_graph_add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t n,
+                                     const cudaKernelNodeParams* params);
+
 int device_sm_count();
 size_t device_l2_bytes();
 // Whether consecutive launches alternate their block order (gs_traverse):
@@ -316,6 +325,8 @@ gs_status ctx_prepare(gs_ctx* c);
 void ctx_launch_list(gs_ctx* c, int64_t n, int p, std::vector<LaunchDesc*>* out);
 // Buffer-parity flip of n iterations (thermal), 0 otherwise.
 int ctx_flip(const gs_ctx* c, int64_t n);
+// The context's kind, storage type and grid (n_iters: its step count).
+void ctx_workload(const gs_ctx* c, gs_workload* w);
 // One launch on the context's stream (with the plan's PDL attribute).
 cudaError_t ctx_launch(gs_ctx* c, LaunchDesc& d);
 gs_status global_fail(gs_status s, const std::string& msg);  // message for gs_last_error(NULL)

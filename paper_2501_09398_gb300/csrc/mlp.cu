@@ -16,6 +16,10 @@
 
 #include "common.cuh"
 
+namespace {
+#include "costmodel_weights.inc"
+}  // namespace
+
 using namespace gs;
 
 namespace {
@@ -334,7 +338,7 @@ gs_status ensure_partial(gs_mlp* m, int blocks) {
         m->partial = nullptr;
         m->cap_blocks = 0;
     }
-    GS_MLPC(m, cudaMalloc(&m->partial, (size_t)blocks * PSTRIDE * sizeof(float)));
+    GS_MLPC(m, gs_malloc(&m->partial, (size_t)blocks * PSTRIDE * sizeof(float)));
     m->cap_blocks = blocks;
     return GS_OK;
 }
@@ -395,15 +399,15 @@ gs_status gs_mlp_create(gs_mlp** out, uint64_t seed, void* stream) {
         e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
         m->own_stream = (e == cudaSuccess);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&m->params, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->m, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->v, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->grad, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->norm, 2 * NI * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->step, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&m->amin_idx, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&m->amin_val, sizeof(float));
+    if (e == cudaSuccess) e = gs_malloc(&m->params, NP * sizeof(float));
+    if (e == cudaSuccess) e = gs_malloc(&m->m, NP * sizeof(float));
+    if (e == cudaSuccess) e = gs_malloc(&m->v, NP * sizeof(float));
+    if (e == cudaSuccess) e = gs_malloc(&m->grad, NP * sizeof(float));
+    if (e == cudaSuccess) e = gs_malloc(&m->norm, 2 * NI * sizeof(float));
+    if (e == cudaSuccess) e = gs_malloc(&m->loss, sizeof(float));
+    if (e == cudaSuccess) e = gs_malloc(&m->step, sizeof(long long));
+    if (e == cudaSuccess) e = gs_malloc(&m->amin_idx, sizeof(long long));
+    if (e == cudaSuccess) e = gs_malloc(&m->amin_val, sizeof(float));
     if (e != cudaSuccess) {
         gs_status st = mlp_cuda(nullptr, e, "gs_mlp_create");
         gs_mlp_destroy(m);
@@ -553,8 +557,8 @@ gs_status gs_mlp_train(gs_mlp* m, const float* X, const float* y, int64_t n_rows
         p2.blockDim = dim3(256);
         p2.kernelParams = a2;
         cudaGraphNode_t n1, n2;
-        e = cudaGraphAddKernelNode(&n1, g, prev ? &prev : nullptr, prev ? 1 : 0, &p1);
-        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n2, g, &n1, 1, &p2);
+        e = gs_graph_add_kernel_node(&n1, g, prev ? &prev : nullptr, prev ? 1 : 0, &p1);
+        if (e == cudaSuccess) e = gs_graph_add_kernel_node(&n2, g, &n1, 1, &p2);
         prev = n2;
     }
     cudaGraphExec_t ex = nullptr;
@@ -588,7 +592,7 @@ gs_status ensure_pred(gs_mlp* m, int64_t n_rows) {
         m->pred = nullptr;
         m->pred_cap = 0;
     }
-    GS_MLPC(m, cudaMalloc(&m->pred, (size_t)n_rows * sizeof(float)));
+    GS_MLPC(m, gs_malloc(&m->pred, (size_t)n_rows * sizeof(float)));
     m->pred_cap = n_rows;
     return GS_OK;
 }
@@ -710,8 +714,8 @@ bool same_shape(const gs_plan& a, const gs_plan& b) {
 // workload, in sweep order.  FDTD: COLUMN with 1, 2, 4, 8 rows and two
 // k-march shapes.  Thermal: COLUMN with 2, 4, 8 rows; COLUMN_SMEM (2D and
 // stacks of at most 8 planes); three MARCH shapes; WAVE at depth 2 and 4
-// (2D and stacks of at most 16 planes); COLUMN at depth 2 and 4 (2D).  The
-// library's default plan is included.
+// (2D and stacks of at most 16 planes); COLUMN at depth 2 and 4 (2D and
+// stacks of at most 8 planes).  The library's default plan is included.
 std::vector<gs_plan> candidate_plans(const gs_workload& w) {
     const int C = GS_KERNEL_COLUMN, CS = GS_KERNEL_COLUMN_SMEM, M = GS_KERNEL_MARCH, W = GS_KERNEL_WAVE;
     std::vector<gs_plan> v;
@@ -734,7 +738,7 @@ std::vector<gs_plan> candidate_plans(const gs_workload& w) {
             v.push_back(plan_of(64, 16, 4, W));
             for (int32_t t : {2, 4}) v.push_back(plan_of(128, 32, t, W));
         }
-        if (is2d)
+        if (is2d || w.nz <= 8)
             for (int32_t t : {2, 4}) v.push_back(plan_of(64, 4, t, C));
         const bool small = w.nx * w.ny * w.nz <= (int64_t(1) << 22);
         const bool deep = w.kind == GS_HEAT3D && w.nz > 8;
@@ -795,7 +799,7 @@ gs_status gs_pick(gs_mlp* const* models, int32_t k, const gs_workload* w, gs_tun
     if (st != GS_OK) return st;
     gs_mlp* m0 = models[0];
     float* dX = nullptr;
-    GS_MLPC(m0, cudaMalloc(&dX, X.size() * sizeof(float)));
+    GS_MLPC(m0, gs_malloc(&dX, X.size() * sizeof(float)));
     // on the first model's stream, where the ensemble argmin runs
     cudaError_t e = cudaMemcpyAsync(dX, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, m0->stream);
     int64_t row = -1;
@@ -808,6 +812,59 @@ gs_status gs_pick(gs_mlp* const* models, int32_t k, const gs_workload* w, gs_tun
     if (row < 0 || row >= (int64_t)ok.size()) return mlp_fail(m0, GS_ERR_NUMERIC, "gs_pick: no finite prediction");
     *best = ok[(size_t)row];
     if (pred_ms_per_iter) *pred_ms_per_iter = std::exp(pred);
+    return GS_OK;
+}
+
+const char* gs_mlp_builtin_info(void) { return kBuiltinInfo; }
+
+gs_status gs_mlp_create_builtin(gs_mlp** out, int32_t member, void* stream) {
+    if (!out) return global_fail(GS_ERR_INVALID_ARG, "gs_mlp_create_builtin: out is NULL");
+    *out = nullptr;
+    if (member < 0 || member >= kBuiltinMembers)
+        return global_fail(GS_ERR_INVALID_ARG, "gs_mlp_create_builtin: member must be in [0, " +
+                                                   std::to_string(kBuiltinMembers) + ")");
+    if (!kBuiltinTrained) return global_fail(GS_ERR_UNSUPPORTED, "gs_mlp_create_builtin: " + std::string(kBuiltinInfo));
+    gs_mlp* m = nullptr;
+    gs_status st = gs_mlp_create(&m, 0, stream);
+    if (st != GS_OK) return st;
+    st = gs_mlp_set_params(m, kBuiltinParams[member], NP);
+    if (st == GS_OK) st = gs_mlp_set_normalization(m, kBuiltinNorm[member], kBuiltinNorm[member] + NI);
+    if (st != GS_OK) {
+        global_fail(st, "gs_mlp_create_builtin: " + m->err);
+        gs_mlp_destroy(m);
+        return st;
+    }
+    *out = m;
+    return GS_OK;
+}
+
+gs_status gs_pick_ctx(gs_ctx* ctx, int64_t n_iters, gs_plan* plan_out, int64_t* batch_out, float* pred_ms_per_iter) {
+    if (!ctx) return global_fail(GS_ERR_INVALID_ARG, "gs_pick_ctx: NULL context");
+    if (!batch_out || n_iters < 1)
+        return ctx_fail(ctx, GS_ERR_INVALID_ARG, "gs_pick_ctx: need batch_out and n_iters >= 1");
+    gs_workload w;
+    ctx_workload(ctx, &w);
+    w.n_iters = n_iters;
+    if (w.kind != GS_HEAT2D && w.kind != GS_HEAT3D && w.kind != GS_FDTD3D)
+        return ctx_fail(ctx, GS_ERR_UNSUPPORTED, "gs_pick_ctx: the learned pick covers thermal and FDTD contexts");
+    gs_mlp* models[kBuiltinMembers] = {};
+    gs_status st = GS_OK;
+    for (int k = 0; k < kBuiltinMembers && st == GS_OK; ++k)
+        st = gs_mlp_create_builtin(&models[k], k, ctx_stream(ctx));
+    gs_tune_candidate best{};
+    std::string why;
+    if (st == GS_OK) {
+        st = gs_pick(models, kBuiltinMembers, &w, &best, pred_ms_per_iter);
+        if (st != GS_OK) why = models[0]->err.empty() ? gs_last_error(nullptr) : models[0]->err;
+    } else {
+        why = gs_last_error(nullptr);
+    }
+    for (gs_mlp* m : models) gs_mlp_destroy(m);
+    if (st != GS_OK) return ctx_fail(ctx, st, "gs_pick_ctx: " + why);
+    st = gs_set_plan(ctx, &best.plan);
+    if (st != GS_OK) return st;  // message already on ctx
+    if (plan_out) gs_get_plan(ctx, plan_out);
+    *batch_out = best.batch_size;
     return GS_OK;
 }
 

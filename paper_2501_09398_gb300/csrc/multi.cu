@@ -122,7 +122,7 @@ gs_status build_table(gs_multi* m, int variant, int depth, MultiInstance** d_tab
         step_bytes += (double)ctx_elem_bytes(m->inst[i]) * ((double)pt0 * d.ny * 2 + (double)pp * d.ny);
     }
     const bool alt = traverse_alternates(m->plan.traverse, step_bytes);
-    if (!*d_table) GS_MCUDA(m, cudaMalloc(d_table, sizeof(MultiInstance) * n));
+    if (!*d_table) GS_MCUDA(m, gs_malloc(d_table, sizeof(MultiInstance) * n));
     GS_MCUDA(m, cudaMemcpyAsync(*d_table, host.data(), sizeof(MultiInstance) * n, cudaMemcpyHostToDevice,
                                 m->stream));
     GS_MCUDA(m, cudaStreamSynchronize(m->stream));
@@ -527,7 +527,7 @@ gs_status gs_multi_autotune(gs_multi* m, int64_t n_iters, int32_t reps, const gs
             break;
         }
         bytes[i] = (size_t)pitch * (size_t)m->ny[i] * ctx_elem_bytes(m->inst[i]);
-        cudaError_t e = cudaMalloc(&snap[i], bytes[i]);
+        cudaError_t e = gs_malloc(&snap[i], bytes[i]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(snap[i], cur[i], bytes[i], cudaMemcpyDeviceToDevice, m->stream);
         if (e != cudaSuccess) fatal = mcuda(m, e, "gs_multi_autotune snapshot");
     }

@@ -211,7 +211,7 @@ gs_status build_graph(gs_slab* s, int64_t S, int p, SlabGraph* out) {
             np.blockDim = d.block;
             np.sharedMemBytes = (unsigned)d.smem;
             np.kernelParams = args;
-            err = cudaGraphAddKernelNode(&cur_k[k], g, deps.empty() ? nullptr : deps.data(), deps.size(), &np);
+            err = gs_graph_add_kernel_node(&cur_k[k], g, deps.empty() ? nullptr : deps.data(), deps.size(), &np);
             ++nodes;
         }
         copies_after(s, (int64_t)j, p, &copies);
@@ -248,17 +248,39 @@ gs_status build_graph(gs_slab* s, int64_t S, int p, SlabGraph* out) {
     return GS_OK;
 }
 
+gs_status ensure_graph(gs_slab* s, int64_t S, int p) {
+    auto key = std::make_pair(S, p);
+    if (s->graphs.count(key)) return GS_OK;
+    SlabGraph e;
+    gs_status st = build_graph(s, S, p, &e);
+    if (st != GS_OK) return st;
+    s->graphs.emplace(key, e);
+    return GS_OK;
+}
+
+// Every graph gs_slab_step(n, S) launches, built before the first launch
+// (a failed build leaves the set as it was).
+gs_status prepare_graphs(gs_slab* s, int64_t n, int64_t S) {
+    const int64_t nb = n / S, r = n % S;
+    const int fl = ctx_flip(s->ctx[0], S);
+    int p = s->parity;
+    gs_status st = GS_OK;
+    if (nb > 0) {
+        st = ensure_graph(s, S, p);
+        if (st == GS_OK && fl && nb > 1) st = ensure_graph(s, S, p ^ 1);
+        if (st != GS_OK) return st;
+        p ^= fl & (int)(nb & 1);
+    }
+    if (r > 0) st = ensure_graph(s, r, p);
+    return st;
+}
+
 gs_status launch_graphs(gs_slab* s, int64_t S, int64_t count) {
     const int fl = ctx_flip(s->ctx[0], S);
     for (int64_t i = 0; i < count; ++i) {
-        auto key = std::make_pair(S, s->parity);
-        auto it = s->graphs.find(key);
-        if (it == s->graphs.end()) {
-            SlabGraph e;
-            gs_status st = build_graph(s, S, s->parity, &e);
-            if (st != GS_OK) return st;
-            it = s->graphs.emplace(key, e).first;
-        }
+        gs_status st = ensure_graph(s, S, s->parity);
+        if (st != GS_OK) return st;
+        auto it = s->graphs.find(std::make_pair(S, s->parity));
         GS_SCUDA(s, cudaGraphLaunch(it->second.exec, s->stream));
         s->stats.graph_launches += 1;
         s->stats.last_build_nodes = it->second.nodes;
@@ -407,7 +429,7 @@ gs_status gs_slab_create(gs_slab** out, gs_kind kind, int64_t nx, int64_t ny, in
     }
     for (int k = 0; k < n_slabs; ++k) {
         void* p = nullptr;
-        e = cudaMalloc(&p, per);
+        e = gs_malloc(&p, per);
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, per, s->stream);
         if (e != cudaSuccess) {
             if (p) cudaFree(p);
@@ -576,28 +598,29 @@ gs_status gs_slab_step(gs_slab* s, int64_t n_iters, int64_t batch_size) {
         if (st != GS_OK) return st;
     } else {
         const int64_t nb = n_iters / batch_size, r = n_iters % batch_size;
+        if (r > 0 && s->rem_S != r && s->rem_S != 0 && s->rem_S != batch_size) {
+            // keep one remainder size's graphs (as gs_step does)
+            cudaStreamSynchronize(s->stream);
+            for (int p = 0; p < 2; ++p) {
+                auto it = s->graphs.find(std::make_pair(s->rem_S, p));
+                if (it == s->graphs.end()) continue;
+                cudaGraphExecDestroy(it->second.exec);
+                cudaGraphDestroy(it->second.graph);
+                s->graphs.erase(it);
+            }
+        }
+        if (r > 0) s->rem_S = r;
+        const auto t0 = std::chrono::steady_clock::now();
+        const int64_t built = s->stats.graphs_built;
+        st = prepare_graphs(s, n_iters, batch_size);
+        if (st != GS_OK) return st;
+        if (s->stats.graphs_built != built)
+            s->stats.last_build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (nb > 0) {
-            const auto t0 = std::chrono::steady_clock::now();
-            const int64_t built = s->stats.graphs_built;
             st = launch_graphs(s, batch_size, nb);
             if (st != GS_OK) return st;
-            if (s->stats.graphs_built != built)
-                s->stats.last_build_seconds =
-                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         }
         if (r > 0) {
-            if (s->rem_S != r && s->rem_S != 0 && s->rem_S != batch_size) {
-                // keep one remainder size's graphs (as gs_step does)
-                cudaStreamSynchronize(s->stream);
-                for (int p = 0; p < 2; ++p) {
-                    auto it = s->graphs.find(std::make_pair(s->rem_S, p));
-                    if (it == s->graphs.end()) continue;
-                    cudaGraphExecDestroy(it->second.exec);
-                    cudaGraphDestroy(it->second.graph);
-                    s->graphs.erase(it);
-                }
-            }
-            s->rem_S = r;
             st = launch_graphs(s, r, 1);
             if (st != GS_OK) return st;
         }

@@ -44,7 +44,7 @@ cudaError_t take(gs_ctx* c, Snapshot* s) {
         ctx_field(c, id, &p, &pitch);
         const size_t b = field_bytes(c, id, pitch);
         void* copy = nullptr;
-        cudaError_t e = cudaMalloc(&copy, b);
+        cudaError_t e = gs_malloc(&copy, b);
         if (e != cudaSuccess) return e;
         s->bufs.push_back(copy);
         s->ids.push_back(id);
