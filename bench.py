@@ -1001,6 +1001,7 @@ def main():
         # depth-4 kernel's throughput
         for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(loop=True), "device_loop"),
                               ("heat3d-256", {}, "column"),
+                              ("heat3d-256", dict(depth=2, kernel=4, block_x=128), "zmarch2"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-media-256", {}, "column"),
                               ("multi-64", {}, "tuned"),

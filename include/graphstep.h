@@ -134,16 +134,22 @@ typedef struct gs_medium {
  *          every plane of its column in registers (no march, no shared
  *          memory); stacks of more than 8 planes in chunks of 8 (the planes
  *          just below and above a chunk loaded as halos); `rows` (<= 8) warps
- *          per block stacked in y.  Depth 2 or 4, 2D only: each thread owns
+ *          per block stacked in y.  Depth 2 or 4 in 2D: each thread owns
  *          one vector of cells in 4 rows (2 for bf16/f16), loads those rows
  *          and 2t halo rows at once and advances t levels in registers
  *          (lanes 0 and 31 of a warp are halo lanes); block_x/32 warps per
- *          block stacked in y.
+ *          block stacked in y.  Depth 2 or 4 in 3D with nz <= 8: each lane
+ *          owns one cell at R rows (R = 4, or 2 with rows = 2, at depth 2; 2
+ *          at depth 4) of every plane, t lanes at each warp end are halo
+ *          lanes; block_x/32 warps per block.  Depth 2 in 3D with nz > 8:
+ *          blocks march tile_y planes in z (default 32), two cells a lane,
+ *          four rows a warp, min(block_x/32, 4) warps a block.
  *   COLUMN_SMEM  as COLUMN, but each thread loads only its own row of every
  *          plane; rows y-1 / y+1 come from shared memory after one barrier
  *          (fewer registers and L2 requests).
- *   AUTO   depth 1 and 2D: COLUMN; 3D at depth > 1: WAVE for nz <= 16, else
- *          TILE. */
+ *   AUTO   depth 1, 2D, and 3D with nz <= 8: COLUMN; other 3D stacks at
+ *          depth 2: WAVE for nz <= 16, else COLUMN (the z march); at depth
+ *          4: WAVE for nz <= 16, else TILE. */
 typedef enum gs_kernel {
     GS_KERNEL_AUTO = 0,
     GS_KERNEL_MARCH = 1,
@@ -172,7 +178,9 @@ typedef enum gs_traverse { GS_TRAVERSE_AUTO = 0, GS_TRAVERSE_FORWARD = 1, GS_TRA
  *                  COLUMN at depth 1: warps per block stacked in y (more
  *                  than 8 act as 8; at depth 2/4 block_x/32 warps); FDTD
  *                  COLUMN: j rows per block; FDTD MARCH: k planes per block
- *   tile_x, tile_y output tile of the TILE kernel
+ *   tile_x, tile_y output tile of the TILE kernel; tile_y is also the z
+ *                  chunk a block marches in the depth-2 COLUMN kernel of
+ *                  stacks deeper than 8 planes
  *   temporal_depth thermal steps fused in one launch: 1, 2 or 4; a depth-t
  *                  launch is bit-identical to t depth-1 launches
  *   use_pdl        1: graph nodes (and per-step launches) use programmatic

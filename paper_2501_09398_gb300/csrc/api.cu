@@ -259,7 +259,7 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     }
     const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
     if (is_heat(c) && p->kernel == GS_KERNEL_AUTO)
-        p->kernel = (t == 1 || c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz)
+        p->kernel = (t == 1 || c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz || (t == 2 && !wave_ok))
                         ? GS_KERNEL_COLUMN
                         : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
     if (p->kernel == GS_KERNEL_MARCH && t != 1)
@@ -268,8 +268,11 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
         return fail(c, GS_ERR_INVALID_ARG, "the TILE kernel runs depth 2 or 4 only");
     if (p->kernel == GS_KERNEL_COLUMN_SMEM && t != 1)
         return fail(c, GS_ERR_INVALID_ARG, "the COLUMN_SMEM kernel runs depth 1 only");
-    if (p->kernel == GS_KERNEL_COLUMN && t != 1 && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
-        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernel runs depth 2 or 4 in 2D and for nz <= 8 only");
+    if (p->kernel == GS_KERNEL_COLUMN && t == 4 && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
+        return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN kernel runs depth 4 in 2D and for nz <= 8 only");
+    if (p->kernel == GS_KERNEL_COLUMN && t == 2 && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz &&
+        (p->tile_y < 1 || p->tile_y > (1 << 20)))
+        return fail(c, GS_ERR_INVALID_ARG, "plan.tile_y (planes a block marches) must be in [1, 2^20]");
     if (p->kernel == GS_KERNEL_COLUMN_SMEM && c->kind == GS_HEAT3D && c->nz > kColumnMaxNz)
         return fail(c, GS_ERR_UNSUPPORTED, "the COLUMN_SMEM kernel needs nz <= 8");
     if (p->kernel == GS_KERNEL_WAVE && !wave_ok)

@@ -1131,6 +1131,142 @@ __global__ void __launch_bounds__(256, R == 2 && T == 2 ? 3 : 2) heat_column3_t_
     heat_column3_t_tile<ST, BC, NZM, EXACT, T, R>(a, (int)blk.x, (int)blk.y);
 }
 
+// ------------------------------------------- z-march, depth 2 (deep 3D) ----
+//
+// Temporal blocking for deep stacks (nz > 8), where one step streams the
+// whole field from DRAM: a block marches a chunk of tile_y planes in z and
+// advances them two levels, reading T once and writing it once per two
+// steps.  Each lane owns two cells along x (an 8-byte f32 or 4-byte bf16/f16
+// access) at the R = 4 output rows of its warp; it keeps three planes of
+// level 0 (rows y0-2 .. y0+5) and three of level 1 (rows y0-1 .. y0+4) in
+// registers (the P rows, used on plane 0 only, are loaded there).  Level-0
+// plane z completes level 1 of plane z-1 and then level 2 of plane z-2,
+// which is stored.  The march is unrolled three times so that the window
+// slots are compile-time.  Measured on 256^3 (GB300): 132 us per two-step
+// launch against 20.8 us per depth-1 step of the chunked COLUMN kernel, so
+// it loses to depth 1 there: 49 M instructions a launch (the boundary
+// path runs in every warp touching an x or y edge, and 256 = 4 x 60 + 16
+// leaves a mostly idle fifth tile), 38 % issue activity, and loading the
+// next plane one step ahead (a fourth slot, 168 registers, 1.4 waves) did not
+// change the time.  It is correct and tested, and kept as a plan.  x-neighbours by
+// shuffle: a warp edge loses one cell per level, so lanes 0 and 31 are halo
+// lanes (a warp stores 60 cells; tiles overlap by two on each side).  Rows
+// and planes outside the grid are loaded at clamped coordinates and only
+// feed values that the boundary rule replaces.  Warps away from the x and y
+// edges update planes away from the z edges without selects, in packed
+// f32x2 arithmetic on the lane's cell pair.  Block (32, BY), BY <= 4.
+constexpr int kZmW = 2, kZmR = 4;
+
+// One level on one plane: input rows 0 .. NI-1 of the plane below (B),
+// itself (M) and above (A), at global rows yb .. yb+NI-1, give output rows
+// 1 .. NI-2 (into out[0 .. NI-3]).  On plane 0 the P row of each output row
+// is loaded where it is used (xc: the lane's clamped pair).
+template <typename ST, int BC, int NI>
+__device__ __forceinline__ void zm_level(const HeatArgs& a, int p, int yb, int x0, int xc, bool fast_xy,
+                                         const float (&B)[NI][kZmW], const float (&M)[NI][kZmW],
+                                         const float (&A)[NI][kZmW], float (&out)[NI - 2][kZmW]) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool fast = fast_xy && p > 0 && p + 1 < nz;  // warp-uniform
+#pragma unroll
+    for (int i = 1; i <= NI - 2; ++i) {
+        const float(&t)[kZmW] = M[i];
+        const float w0 = __shfl_up_sync(0xffffffffu, t[kZmW - 1], 1);
+        const float eW = __shfl_down_sync(0xffffffffu, t[0], 1);
+        if (fast) {
+            float xsum[kZmW], zero[kZmW] = {0.0f, 0.0f};
+            xsum[0] = __fadd_rn(w0, t[1]);
+            xsum[1] = __fadd_rn(t[0], eW);
+            heat_cell_x2<true>(t, M[i - 1], M[i + 1], xsum, B[i], A[i], zero, a.c, out[i - 1]);
+        } else {
+            const int yg = yb + i;
+            float pz[kZmW] = {0.0f, 0.0f};
+            if (p == 0)
+                load_vecw<ST, kZmW>(static_cast<const ST*>(a.P) + (long long)min(max(yg, 0), ny - 1) * a.p_pitch + xc,
+                                    pz);
+#pragma unroll
+            for (int c = 0; c < kZmW; ++c) {
+                const int x = x0 + c;
+                const float tc = t[c];
+                float w = (c == 0) ? w0 : t[c - 1];
+                float e = (c == kZmW - 1) ? eW : t[c + 1];
+                if (x == 0) w = bnd<BC>(tc);
+                if (x + 1 >= nx) e = bnd<BC>(tc);
+                const float n = (yg == 0) ? bnd<BC>(tc) : M[i - 1][c];
+                const float so = (yg + 1 >= ny) ? bnd<BC>(tc) : M[i + 1][c];
+                const float d = (p == 0) ? bnd<BC>(tc) : B[i][c];
+                const float u = (p + 1 >= nz) ? bnd<BC>(tc) : A[i][c];
+                out[i - 1][c] = heat_cell<true>(tc, n, so, w, e, d, u, pz[c], a.c);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kZmW; ++c) out[i - 1][c] = as_stored<ST>(out[i - 1][c]);
+    }
+}
+
+template <typename ST>
+__device__ __forceinline__ void zm_load(const HeatArgs& a, int z, int y0, int xc, float (&L)[kZmR + 4][kZmW]) {
+    const ST* __restrict__ base = static_cast<const ST*>(a.Tin) + (long long)z * a.plane + xc;
+#pragma unroll
+    for (int k = 0; k < kZmR + 4; ++k) {
+        const int yk = min(max(y0 - 2 + k, 0), a.ny - 1);
+        load_vecw<ST, kZmW>(base + (long long)yk * a.pitch, L[k]);
+    }
+}
+
+// Step r of the march (PH = r mod 3): level-0 plane z = zs + r arrives,
+// level 1 of plane z-1 and level 2 of plane z-2 follow.
+template <typename ST, int BC, int PH>
+__device__ __forceinline__ void zm_step(const HeatArgs& a, int r, int zs, int z0, int z1, int y0, int x0, int xc,
+                                        bool fast_xy, bool store_lane, float (&L0)[3][kZmR + 4][kZmW],
+                                        float (&L1)[3][kZmR + 2][kZmW]) {
+    constexpr int S0 = PH, S1 = (PH + 1) % 3, S2 = (PH + 2) % 3;  // slots of planes z, z-2, z-1
+    const int nz = a.nz;
+    const int z = zs + r;
+    if (z >= 0 && z < nz) zm_load<ST>(a, z, y0, xc, L0[S0]);
+    const int p1 = z - 1;
+    if (p1 >= max(z0 - 1, 0) && p1 <= min(z1, nz - 1))
+        zm_level<ST, BC, kZmR + 4>(a, p1, y0 - 2, x0, xc, fast_xy, L0[S1], L0[S2], L0[S0], L1[S2]);
+    const int p2 = z - 2;
+    if (p2 >= z0 && p2 < z1) {
+        float out[kZmR][kZmW];
+        zm_level<ST, BC, kZmR + 2>(a, p2, y0 - 1, x0, xc, fast_xy, L1[S0], L1[S1], L1[S2], out);
+        if (store_lane) {
+            ST* o = static_cast<ST*>(a.Tout) + (long long)p2 * a.plane + x0;
+            const int nv = min(kZmW, a.nx - x0);
+#pragma unroll
+            for (int i = 0; i < kZmR; ++i) {
+                const int yg = y0 + i;
+                if (yg < a.ny) store_vecw<ST, kZmW>(o + (long long)yg * a.pitch, out[i], nv);
+            }
+        }
+    }
+}
+
+template <typename ST, int BC>
+__global__ void __launch_bounds__(128, 4) heat_zmarch2_kernel(const HeatArgs a) {
+    pdl_wait_then_trigger();
+    const uint3 blk = block_index(a.rev);
+    const int lane = threadIdx.x;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int xs = (int)blk.x * (30 * kZmW) - kZmW;  // global x of lane 0's first cell
+    const int x0 = xs + lane * kZmW;
+    const int xc = min(max(x0, 0), (nx - 1) / kZmW * kZmW);
+    const int y0 = ((int)blk.y * (int)blockDim.y + (int)threadIdx.y) * kZmR;
+    const int z0 = (int)blk.z * a.tile_y;
+    const int z1 = min(z0 + a.tile_y, nz);
+    // every cell of the warp away from both x edges, no level-1 row on a y edge
+    const bool fast_xy = (xs >= 1) && (xs + 32 * kZmW < nx) && (y0 >= 2) && (y0 + kZmR + 2 <= ny);
+    const bool store_lane = lane >= 1 && lane <= 30 && x0 < nx;
+    float L0[3][kZmR + 4][kZmW], L1[3][kZmR + 2][kZmW];
+    const int zs = z0 - 2;
+    const int rend = z1 + 2 - zs;  // level-0 planes zs .. z1+1
+    for (int r = 0; r < rend; r += 3) {
+        zm_step<ST, BC, 0>(a, r, zs, z0, z1, y0, x0, xc, fast_xy, store_lane, L0, L1);
+        if (r + 1 < rend) zm_step<ST, BC, 1>(a, r + 1, zs, z0, z1, y0, x0, xc, fast_xy, store_lane, L0, L1);
+        if (r + 2 < rend) zm_step<ST, BC, 2>(a, r + 2, zs, z0, z1, y0, x0, xc, fast_xy, store_lane, L0, L1);
+    }
+}
+
 // ------------------------------------------------------------- factory ----
 
 namespace {
@@ -1227,7 +1363,7 @@ const void* pick(bool is3d, int depth, int variant, int nz, int rows) {
         return nullptr;
     }
     if (variant == GS_KERNEL_COLUMN && depth > 1 && is3d) {
-        if (nz > kColumnMaxNz) return nullptr;
+        if (nz > kColumnMaxNz) return depth == 2 ? (const void*)heat_zmarch2_kernel<ST, BC> : nullptr;
         const bool exact8 = (nz == kColumnMaxNz);
         if (depth == 2 && rows == 2)
             return exact8 ? (const void*)heat_column3_t_kernel<ST, BC, kColumnMaxNz, true, 2, 2>
@@ -1280,6 +1416,13 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
         out->grid = dim3((a.nx + block_x * V - 1) / (block_x * V), (a.ny + a.rows - 1) / a.rows,
                          is3d ? (a.nz + zb - 1) / zb : 1);
         out->smem = is3d ? (size_t)2 * (zb + 2) * block_x * V * sizeof(float) : 0;
+    } else if (variant == GS_KERNEL_COLUMN && depth == 2 && is3d && a.nz > kColumnMaxNz) {
+        const int bw = std::max(1, std::min(block_x / 32, 4));  // warps stacked in y
+        if (a.tile_y < 1) return cudaErrorInvalidValue;
+        out->block = dim3(32, bw, 1);
+        out->grid = dim3((a.nx + 30 * kZmW - 1) / (30 * kZmW), (a.ny + kZmR * bw - 1) / (kZmR * bw),
+                         (a.nz + a.tile_y - 1) / a.tile_y);
+        out->smem = 0;
     } else if (variant == GS_KERNEL_COLUMN && depth > 1 && is3d) {
         if (a.nz > kColumnMaxNz) return cudaErrorInvalidValue;
         const int bw = std::max(1, std::min(block_x / 32, 8));  // warps stacked in y

@@ -114,7 +114,8 @@ def test_remainder_graphs_of_one_size_are_kept():
 
 
 @pytest.mark.parametrize("shape", [(96, 64, 1), (77, 45, 1), (300, 37, 1), (40, 33, 8), (21, 19, 3), (250, 20, 16),
-                                   (500, 130, 1), (3, 2, 1), (40, 33, 4), (130, 9, 5), (64, 70, 2), (29, 3, 8)])
+                                   (500, 130, 1), (3, 2, 1), (40, 33, 4), (130, 9, 5), (64, 70, 2), (29, 3, 8),
+                                   (40, 33, 12), (29, 3, 13), (130, 9, 9)])
 @pytest.mark.parametrize("depth", [1, 2, 4])
 def test_temporal_blocking_bit_identical(shape, depth):
     import paper_2501_09398_gb300 as g
@@ -138,10 +139,11 @@ def test_temporal_blocking_bit_identical(shape, depth):
                 continue
             assert np.array_equal(heat_gpu(T0, P, n, S=0, plan=plan), base), f"column {kern} rows={rows}"
             assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column {kern} graph rows={rows}"
-    if depth > 1:  # column kernel at depth 2 / 4: no march, levels in registers (2D, and stacks of <= 8 planes)
-        for bx, rows in ((32, 0), (64, 2), (256, 0)):
-            plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_COLUMN, block_x=bx, rows=rows)
-            if nz > 8:
+    if depth > 1:  # column kernel at depth 2 / 4: levels in registers (2D, stacks of <= 8 planes, and at
+        # depth 2 deeper stacks marched in z chunks of tile_y planes)
+        for bx, rows, chunk in ((32, 0, 1), (64, 2, 5), (256, 0, 0)):
+            plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_COLUMN, block_x=bx, rows=rows, tile_y=chunk)
+            if nz > 8 and depth == 4:
                 with pytest.raises(g.GsError):
                     heat_gpu(T0, P, n, S=0, plan=plan)
                 continue
@@ -167,7 +169,9 @@ def test_wave_kernel_rejects_deep_stacks():
         with pytest.raises(g.GsError) as e:
             g.gs_set_plan(ctx, temporal_depth=2, kernel=g.GS_KERNEL_WAVE)
         assert e.value.status == g.GS_ERR_UNSUPPORTED
-        g.gs_set_plan(ctx, temporal_depth=2)  # AUTO picks the tile kernel
+        g.gs_set_plan(ctx, temporal_depth=2)  # AUTO picks the z-marching column kernel at depth 2
+        assert g.gs_get_plan(ctx)["kernel"] == g.GS_KERNEL_COLUMN
+        g.gs_set_plan(ctx, temporal_depth=4)  # and the tile kernel at depth 4
         assert g.gs_get_plan(ctx)["kernel"] == g.GS_KERNEL_TILE
     finally:
         g.gs_destroy(ctx)
@@ -231,6 +235,9 @@ def test_deep_stack_full_size(oracle):
     assert max_rel(got, ref) <= HEAT_RTOL
     march = heat_gpu(T0, P, n, S=0, plan=dict(kernel=g.GS_KERNEL_MARCH, block_x=64, rows=8))
     assert np.array_equal(march, got)
+    # depth 2 marched in z (chunks of 32 planes; 13 steps: 6 fused launches and one single step)
+    zm = heat_gpu(T0, P, n, S=5, plan=dict(kernel=g.GS_KERNEL_COLUMN, temporal_depth=2, block_x=128))
+    assert np.array_equal(zm, got)
 
 
 def test_large_2d_sampled(oracle):

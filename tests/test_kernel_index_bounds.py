@@ -10,7 +10,7 @@ every global load and store must lie inside its buffer and inside its row
 (the pitch), every shared-memory access inside the launch's allocation, and
 the stores of a launch must cover every cell of the field exactly once.
 The 3D depth-t COLUMN kernel (one cell a lane, every plane of the column)
-is re-traced the same way.
+and the z-marching depth-2 kernel of deep stacks are re-traced the same way.
 The formulas restate the kernels' address computations (csrc/heat.cu,
 csrc/fdtd.cu, csrc/multi.cu) for ragged shapes, so that a change to either
 is checked here before it runs on a GPU."""
@@ -202,6 +202,55 @@ def test_temporal_column3_kernel_addresses(nx, ny, nz, esize, depth, rows, block
     assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
     assert covered.max() <= 1
     every_block_stores(st & (y0 < ny), bx, by, bz)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(256, 24, 40), (97, 41, 9), (61, 9, 17), (5, 3, 33), (121, 1, 12), (2, 7, 10)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("block_x", [32, 128, 256])
+@pytest.mark.parametrize("chunk", [1, 5, 32])
+def test_zmarch2_kernel_addresses(nx, ny, nz, esize, block_x, chunk):
+    # deep stacks at depth 2: two cells a lane (pairs at even x, clamped to
+    # the last pair that starts inside the row), lanes 1..30 store, four rows
+    # a warp, blocks of BY <= 4 warps marching `chunk` planes; level-0 planes
+    # z0-2 .. z1+1 are loaded where inside the stack, rows clamped
+    W, R = 2, 4
+    BY = max(1, min(block_x // 32, 4))
+    grid = (-(-nx // (30 * W)), -(-ny // (R * BY)), -(-nz // chunk))
+    pitch = pitch_of(nx, esize)
+    plane = pitch * ny
+    size = plane * nz
+    bx, by, bz, lane, ty, tz = threads(grid, (32, BY, 1))
+    x0 = bx * 30 * W - W + lane * W
+    xc = np.minimum(np.maximum(x0, 0), (nx - 1) // W * W)
+    y0 = (by * BY + ty) * R
+    z0 = bz * chunk
+    z1 = np.minimum(z0 + chunk, nz)
+    for dz in range(-2, chunk + 2):
+        z = z0 + dz
+        m = (z >= 0) & (z < nz) & (z <= z1 + 1)
+        for k in range(R + 4):
+            yk = np.clip(y0 - 2 + k, 0, ny - 1)
+            check_vec((z * plane + yk * pitch + xc)[m], W, (z * plane + yk * pitch)[m], pitch, size)
+    for yg in range(-1, R + 5):  # P rows of plane 0 (clamped)
+        yk = np.clip(y0 + yg, 0, ny - 1)
+        check_vec(yk * pitch + xc, W, yk * pitch, pitch, pitch * ny)
+    covered = np.zeros(size, dtype=np.int64)
+    st = (lane >= 1) & (lane <= 30) & (x0 < nx)
+    nv = np.minimum(W, nx - x0)
+    for dz in range(chunk):
+        z = z0 + dz
+        for i in range(R):
+            yg = y0 + i
+            m = st & (z < z1) & (yg < ny)
+            addr = (z * plane + yg * pitch + x0)[m]
+            check_vec(addr, nv[m], (z * plane + yg * pitch)[m], pitch, size)
+            for c in range(W):
+                mc = m & (c < nv)
+                np.add.at(covered, (z * plane + yg * pitch + x0)[mc] + c, 1)
+    cells = np.zeros((nz, ny, pitch), dtype=bool)
+    cells[:, :, :nx] = True
+    assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
+    every_block_stores(st & (y0 < ny) & (z0 < nz), bx, by, bz)
 
 
 # ---------------------------------------------------------------- FDTD ----

@@ -47,7 +47,7 @@ def test_every_swept_plan_passes_the_plan_check(g, tables):
 
 
 @pytest.mark.parametrize("kind,nx,ny,nz,plan,status", [
-    ("HEAT3D", 512, 512, 9, dict(kernel=4, temporal_depth=2), "UNSUPPORTED"),  # COLUMN depth > 1: 2D or nz <= 8
+    ("HEAT3D", 512, 512, 9, dict(kernel=4, temporal_depth=4), "UNSUPPORTED"),  # COLUMN depth 4: 2D or nz <= 8
     ("HEAT3D", 64, 64, 17, dict(kernel=2, temporal_depth=2), "UNSUPPORTED"),   # WAVE needs nz <= 16
     ("HEAT3D", 64, 64, 9, dict(kernel=5), "UNSUPPORTED"),                      # COLUMN_SMEM needs nz <= 8
     ("HEAT2D", 64, 64, 1, dict(kernel=1, temporal_depth=2), "INVALID_ARG"),    # MARCH runs depth 1 only
@@ -75,8 +75,9 @@ def test_plan_check_fills_defaults_and_resolves_auto(g):
     p = g.gs_plan_check(w3, {})
     assert (p["kernel"], p["block_x"], p["rows"], p["temporal_depth"]) == (g.GS_KERNEL_COLUMN, 64, 4, 1)
     assert g.gs_plan_check(w3, dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_COLUMN  # nz <= 8: registers
-    assert g.gs_plan_check(dict(w3, nz=16), dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_WAVE
-    assert g.gs_plan_check(dict(w3, nz=17), dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_TILE
+    assert g.gs_plan_check(dict(w3, nz=16), dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_WAVE  # 9..16 planes
+    assert g.gs_plan_check(dict(w3, nz=17), dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_COLUMN  # z-march
+    assert g.gs_plan_check(dict(w3, nz=17), dict(temporal_depth=4))["kernel"] == g.GS_KERNEL_TILE
     w2 = dict(kind=g.GS_HEAT2D, dtype=g.GS_BF16, nx=4096, ny=4096, nz=1)
     assert g.gs_plan_check(w2, dict(temporal_depth=4))["kernel"] == g.GS_KERNEL_COLUMN
     assert g.gs_plan_check(w2, {})["rows"] == 8  # large grids: 8 warp rows per block

@@ -149,6 +149,9 @@ def test_temporal_blocking_rounds_every_level(dtype, shape):
     if nz <= 8:
         plans.append(dict(kernel=g.GS_KERNEL_COLUMN, block_x=64))
     for depth in (2, 4):
+        if nz > 8 and depth == 2:  # deep stacks: the z-marching depth-2 kernel
+            got = heat_gpu(T0, P, n, S=4, dtype=dtype, plan=dict(kernel=g.GS_KERNEL_COLUMN, temporal_depth=2, tile_y=7))
+            assert np.array_equal(got, base), "z-march"
         for plan in plans:
             got = heat_gpu(T0, P, n, S=4, dtype=dtype, plan=dict(plan, temporal_depth=depth))
             assert np.array_equal(got, base), (depth, plan)
