@@ -131,14 +131,17 @@ def cells_of(w):
     return w["N"] ** 3 if w["kind"] == "fdtd" else w["nx"] * w["ny"] * w["nz"]
 
 
-def algo_bytes_per_launch(w, depth, elem=4):
+def algo_bytes_per_launch(w, depth, elem=4, fused=False):
     """Algorithmic DRAM bytes of one kernel launch.
 
     Thermal depth-t launch: read T once, write T once, read the P plane once
     (2D: P is the full plane), for t cell-updates per cell.  FDTD half-step
     (H or E kernel): read 6 components, write 3, per cell, plus the 1-byte
-    material id in media."""
+    material id in media; fused FDTD step (one launch per step): read 6
+    components and write 6."""
     if w["kind"] == "fdtd":
+        if fused:
+            return cells_of(w) * 12 * elem
         return cells_of(w) * (9 * elem + (1 if w.get("media") else 0))
     if w["kind"] == "multi":
         return cells_of(w) * 3 * elem
@@ -441,6 +444,7 @@ class Runner:
             self.out_shape = T0.shape
         plan = dict(temporal_depth=depth, **plan_extra)
         g.gs_set_plan(self.ctx, **plan)
+        self.fused = plan.get("kernel") == g.GS_KERNEL_FUSED
         self.reset()
 
     def reset(self):
@@ -466,7 +470,7 @@ class Runner:
     def launches_per_step(self, S):
         it = self.w["iters"]
         if self.w["kind"] == "fdtd":
-            return 2 * it
+            return it + (it & 1) if self.fused else 2 * it
         t = self.depth
         return it // t + it % t
 
@@ -568,7 +572,8 @@ def kernel_avg_ms(run, flush, reps=6, per=16):
 
     g = run.g
     st = run.stream
-    n_iter = 1 if run.w["kind"] == "fdtd" else run.depth
+    fused = bool(getattr(run, "fused", False))
+    n_iter = (2 if fused else 1) if run.w["kind"] == "fdtd" else run.depth
     times = []
     for _ in range(reps):
         flush.zero_()
@@ -582,7 +587,8 @@ def kernel_avg_ms(run, flush, reps=6, per=16):
             b.record(st)
         torch.cuda.synchronize()
         times += [a.elapsed_time(b) for a, b in evs]
-    # FDTD: one gs_step(1) is an H launch and an E launch; report per launch
+    # FDTD: one gs_step(1) is an H launch and an E launch, one fused
+    # gs_step(2) two fused launches; report per launch
     div = 2 if run.w["kind"] == "fdtd" else 1
     return statistics.median(times) / div
 
@@ -698,6 +704,7 @@ def measure_workload(name, w, args, flush, with_e2e=True):
     finally:
         run.close()
     return dict(S=S, depth=depth, graph_ms=graph_ms, per_step_ms=per_step_ms, kern_ms=kern_ms, e2e=e2e,
+                fused=bool(getattr(run, "fused", False)),
                 paper_conv_ms=paper_conv_ms, build_s=build_s, result=result,
                 launches=run.launches_per_step(S), l2_bytes=l2, node_floor_us=floor,
                 tuned_plan=getattr(run, "tuned", None))
@@ -849,7 +856,7 @@ def bench_line(args, w, m, clk, world):
     ms_per_step = total_ms / args.steps
     per_step_value = cells * w["iters"] / (statistics.mean(m["per_step_ms"]) * 1e-3)
     peak, peak_kind = _peaks()
-    bytes_launch = algo_bytes_per_launch(w, m["depth"])
+    bytes_launch = algo_bytes_per_launch(w, m["depth"], fused=m.get("fused", False))
     # average launch duration inside the timed region: CUDA events around
     # each graph-batched step on the launching stream, divided by the
     # kernel launches in it (so inter-node gaps are charged to the kernel)
@@ -1003,6 +1010,7 @@ def main():
                               ("heat3d-256", {}, "column"),
                               ("heat3d-256", dict(depth=2, kernel=4, block_x=128), "zmarch2"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
+                              ("fdtd-128", dict(kernel=6, rows=4), "fused"), ("fdtd-256", dict(kernel=6, rows=8), "fused"),
                               ("fdtd-media-256", {}, "column"),
                               ("multi-64", {}, "tuned"),
                               ("heat2d-512", dict(depth=4, kernel=4, block_x=256), "column4"),
@@ -1015,7 +1023,7 @@ def main():
             gms = statistics.mean(mm["graph_ms"])
             gv = c / (gms * 1e-3)
             pv = c / (statistics.mean(mm["per_step_ms"]) * 1e-3)
-            bl = algo_bytes_per_launch(ww, mm["depth"])
+            bl = algo_bytes_per_launch(ww, mm["depth"], fused=mm.get("fused", False))
             bw = bl / (gms / mm["launches"] * 1e-3) / 1e9
             extra[f"{nm}/{tag}"] = {"graph_value": gv, "per_step_value": pv, "graph_speedup": gv / pv,
                                     "S": mm["S"], "depth": mm["depth"], "in_step_GBps": bw,

@@ -156,7 +156,8 @@ typedef enum gs_kernel {
     GS_KERNEL_WAVE = 2,
     GS_KERNEL_TILE = 3,
     GS_KERNEL_COLUMN = 4,
-    GS_KERNEL_COLUMN_SMEM = 5
+    GS_KERNEL_COLUMN_SMEM = 5,
+    GS_KERNEL_FUSED = 6
 } gs_kernel;
 
 /* Block traversal order of consecutive launches (gs_plan.traverse,

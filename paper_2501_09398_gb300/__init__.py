@@ -33,7 +33,8 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_STATE, GS_ERR_TIMEOUT
 GS_HEAT2D, GS_HEAT3D, GS_FDTD3D, GS_SKELETON = range(4)
 GS_F32, GS_BF16, GS_F16 = range(3)
 GS_BC_CLAMP, GS_BC_DIRICHLET0, GS_BC_PEC = range(3)
-GS_KERNEL_AUTO, GS_KERNEL_MARCH, GS_KERNEL_WAVE, GS_KERNEL_TILE, GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM = range(6)
+GS_KERNEL_AUTO, GS_KERNEL_MARCH, GS_KERNEL_WAVE, GS_KERNEL_TILE, GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM, \
+    GS_KERNEL_FUSED = range(7)
 GS_TRAVERSE_AUTO, GS_TRAVERSE_FORWARD, GS_TRAVERSE_ALTERNATE = range(3)
 (GS_FIELD_T0, GS_FIELD_T1, GS_FIELD_P, GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY,
  GS_FIELD_HZ, GS_FIELD_T, GS_FIELD_X, GS_FIELD_MAT) = range(12)

@@ -72,6 +72,12 @@ struct gs_ctx {
     float2* d_med = nullptr;                // [256] (da, db) | [256] (ca, cb)
     float* staging = nullptr;
     size_t staging_bytes = 0;
+    // FDTD fused plan: the second set of the six components (library-owned,
+    // component c at fused_set + c * fused_stride bytes) and the fused
+    // launches reading set A (the bound fields) / set B (this one)
+    char* fused_set = nullptr;
+    size_t fused_stride = 0;
+    LaunchDesc fdesc[2];
     // Launch descriptors, valid while descs_ok: thermal [0]=depth 1,
     // [1]=depth t, each per parity; FDTD [0][0]=H, [0][1]=E.
     LaunchDesc desc[2][2];
@@ -250,12 +256,14 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     if (t != 1 && t != 2 && t != 4) return fail(c, GS_ERR_INVALID_ARG, "plan.temporal_depth must be 1, 2 or 4");
     if (c->kind == GS_FDTD3D && t != 1)
         return fail(c, GS_ERR_UNSUPPORTED, "temporal blocking is provided for the thermal stencils only");
-    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_COLUMN_SMEM)
+    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_FUSED)
         return fail(c, GS_ERR_INVALID_ARG, "plan.kernel must be a gs_kernel value");
     if (c->kind == GS_FDTD3D) {
         if (p->kernel == GS_KERNEL_AUTO) p->kernel = GS_KERNEL_COLUMN;
-        if (p->kernel != GS_KERNEL_COLUMN && p->kernel != GS_KERNEL_MARCH)
-            return fail(c, GS_ERR_INVALID_ARG, "FDTD kernels: GS_KERNEL_COLUMN or GS_KERNEL_MARCH");
+        if (p->kernel != GS_KERNEL_COLUMN && p->kernel != GS_KERNEL_MARCH && p->kernel != GS_KERNEL_FUSED)
+            return fail(c, GS_ERR_INVALID_ARG, "FDTD kernels: GS_KERNEL_COLUMN, GS_KERNEL_MARCH or GS_KERNEL_FUSED");
+    } else if (p->kernel == GS_KERNEL_FUSED) {
+        return fail(c, GS_ERR_INVALID_ARG, "GS_KERNEL_FUSED is an FDTD kernel");
     }
     const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
     if (is_heat(c) && p->kernel == GS_KERNEL_AUTO)
@@ -404,6 +412,7 @@ gs_status ensure_descs(gs_ctx* c) {
         a.counter = c->d_counter;
         a.mat = nullptr;
         a.med = nullptr;
+        const bool fused = (c->plan.kernel == GS_KERNEL_FUSED);
         if (!c->media.empty()) {
             if (c->plan.kernel != GS_KERNEL_COLUMN)
                 return fail(c, GS_ERR_UNSUPPORTED, "FDTD media run on the COLUMN kernels only");
@@ -415,11 +424,34 @@ gs_status ensure_descs(gs_ctx* c) {
         // one half-step reads all six components (and the ids), writes three
         const double step_bytes = (double)ctx_elem_bytes(c) * 6.0 * (double)a.plane * (double)(c->nz + 1) +
                                   (a.mat ? (double)a.plane * (double)(c->nz + 1) : 0.0);
+        // fused: the in-place pair (COLUMN) serves an odd last step
+        const int split = fused ? (int)GS_KERNEL_COLUMN : c->plan.kernel;
         a.rev = 0;
-        cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, c->plan.kernel, &c->desc[0][0]);
+        cudaError_t e = fdtd_desc(c->dt, false, a, c->plan.block_x, split, &c->desc[0][0]);
         a.rev = traverse_alternates(c->plan.traverse, step_bytes) ? 1 : 0;
-        if (e == cudaSuccess) e = fdtd_desc(c->dt, true, a, c->plan.block_x, c->plan.kernel, &c->desc[0][1]);
+        if (e == cudaSuccess) e = fdtd_desc(c->dt, true, a, c->plan.block_x, split, &c->desc[0][1]);
         if (e != cudaSuccess) return cuda_fail(c, e, "FDTD kernel set-up");
+        if (fused) {
+            const size_t stride = (((size_t)a.plane * (size_t)(c->nz + 1) * ctx_elem_bytes(c)) + 255) / 256 * 256;
+            if (c->fused_stride != stride) {
+                if (c->fused_set) {
+                    cudaStreamSynchronize(c->stream);
+                    cudaFree(c->fused_set);
+                    c->fused_set = nullptr;
+                    c->fused_stride = 0;
+                }
+                GS_CUDA(c, gs_malloc(&c->fused_set, 6 * stride));
+                c->fused_stride = stride;
+            }
+            FdtdArgs b = a;
+            for (int f = 0; f < 6; ++f) b.g[f] = c->fused_set + (size_t)f * stride;
+            b.rev = 0;
+            e = fdtd_desc(c->dt, false, b, c->plan.block_x, GS_KERNEL_FUSED, &c->fdesc[0]);
+            for (int f = 0; f < 6; ++f) std::swap(b.f[f], b.g[f]);
+            b.rev = traverse_alternates(c->plan.traverse, step_bytes) ? 1 : 0;
+            if (e == cudaSuccess) e = fdtd_desc(c->dt, false, b, c->plan.block_x, GS_KERNEL_FUSED, &c->fdesc[1]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "FDTD fused kernel set-up");
+        }
     }
     c->descs_ok = true;
     return GS_OK;
@@ -440,6 +472,11 @@ void for_each_launch(gs_ctx* c, int64_t n, int p, F&& f) {
         const int64_t r = n - q * t;
         for (int64_t i = 0; i < q; ++i) { f(c->desc[1][p]); p ^= 1; }
         for (int64_t i = 0; i < r; ++i) { f(c->desc[0][p]); p ^= 1; }
+    } else if (c->plan.kernel == GS_KERNEL_FUSED) {
+        // pairs of fused steps (A -> B, B -> A), so the state ends in A;
+        // an odd last step runs the in-place H and E launches
+        for (int64_t i = 0; i < n / 2; ++i) { f(c->fdesc[0]); f(c->fdesc[1]); }
+        if (n & 1) { f(c->desc[0][0]); f(c->desc[0][1]); }
     } else {
         for (int64_t i = 0; i < n; ++i) { f(c->desc[0][0]); f(c->desc[0][1]); }
     }
@@ -447,7 +484,7 @@ void for_each_launch(gs_ctx* c, int64_t n, int p, F&& f) {
 
 int64_t launches_for(const gs_ctx* c, int64_t n) {
     if (is_skel(c)) return n;
-    if (!is_heat(c)) return 2 * n;
+    if (!is_heat(c)) return c->plan.kernel == GS_KERNEL_FUSED ? n + (n & 1) : 2 * n;
     const int t = c->plan.temporal_depth;
     const int64_t q = (t > 1) ? n / t : 0;
     return q + (n - q * t);
@@ -938,6 +975,7 @@ gs_status gs_destroy(gs_ctx* c) {
     if (c->d_loop) cudaFree(c->d_loop);
     if (c->d_med) cudaFree(c->d_med);
     if (c->staging) cudaFree(c->staging);
+    if (c->fused_set) cudaFree(c->fused_set);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return GS_OK;

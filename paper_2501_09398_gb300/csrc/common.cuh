@@ -199,6 +199,7 @@ struct HeatArgs {
 
 struct FdtdArgs {
     void* f[6];           // Ex, Ey, Ez, Hx, Hy, Hz
+    void* g[6];           // fused step: the set written (f is read); unused otherwise
     int N;                // cells along i and j
     int Nk;               // cells along k (N for a cube; a sub-domain of a slab set may differ)
     int kc;               // k planes per block

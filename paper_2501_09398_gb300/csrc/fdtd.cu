@@ -514,6 +514,226 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_e_
         fdtd_e_column_body<ST, MAT, false, ALN>(a, s_med, lane, i0, j, k);
 }
 
+// ------------------------------------------------------------- fused ----
+//
+// One Yee step per launch: H and E of the same cells in one pass, out of
+// place (the state set a.f is read, the other set a.g written), so that no
+// block overwrites a value a neighbouring block still reads.  Each thread
+// owns four cells along i at one (j, k), as the column kernels.  It updates H
+// on its cells from E^n; the E update then needs H^{n+1/2} also at j-1 (Hz,
+// Hx), k-1 (Hy, Hx) and i-1 (Hz, Hy): the i-1 values come from the
+// neighbouring lane (lane 0 recomputes its one cell), the j-1 and k-1 values
+// are recomputed from E^n and H^{n-1/2} by the same rounded operations, on
+// the same operands, as their owners' updates, so the step equals the H
+// launch then the E launch bit for bit.  All six components are written to
+// a.g, updated or not (the walls' fixed values included); the soft source
+// is added to a.g's Ez.  Bytes per cell-step: six components read and six
+// written, against nine and nine for the two launches.  Neighbour values
+// come from loads at clamped offsets where they fall outside the arrays;
+// such values are never used (the update masks exclude them).
+// A value as a store to the storage type and a load back give it.
+template <typename ST>
+__device__ __forceinline__ float stored(float v) {
+    return to_f32(from_f32<ST>(v));
+}
+
+template <typename ST, bool FAST, bool ALN>
+__device__ __forceinline__ void fdtd_fused_body(const FdtdArgs& a, int lane, int i0, int j, int k) {
+    constexpr int V = kFdtdColumnCells;
+    const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
+    const bool act = FAST || ((i0 < M) && (j < M) && (k < Mk));
+    const long long P = a.pitch, PL = a.plane;
+    // a thread past the arrays (act false) loads at offset 0 only
+    const long long dj1 = (FAST || (act && j + 1 < M)) ? P : 0;
+    const long long dk1 = (FAST || (act && k + 1 < Mk)) ? PL : 0;
+    const long long djm = (FAST || (act && j >= 1)) ? -P : 0;
+    const long long dkm = (FAST || (act && k >= 1)) ? -PL : 0;
+    const long long o = act ? (long long)k * PL + (long long)j * P + i0 : 0;
+    const ST* Ex = static_cast<const ST*>(a.f[EX]);
+    const ST* Ey = static_cast<const ST*>(a.f[EY]);
+    const ST* Ez = static_cast<const ST*>(a.f[EZ]);
+    const ST* Hx = static_cast<const ST*>(a.f[HX]);
+    const ST* Hy = static_cast<const ST*>(a.f[HY]);
+    const ST* Hz = static_cast<const ST*>(a.f[HZ]);
+    const float s = a.s;
+    // own cells, the H update's j+1 / k+1 neighbours, and the rows j-1 and
+    // planes k-1 whose H the E update needs
+    float ex[V], ey[V], ez[V], hx[V], hy[V], hz[V], exk1[V], eyk1[V], ezj1[V], exj1[V];
+    float hzjm[V], hxjm[V], eyjm[V], exjm[V], ezjm[V], eyjmk1[V];
+    float hykm[V], hxkm[V], exkm[V], ezkm[V], eykm[V], ezj1km[V];
+    load_vecw<ST, V>(Ex + o, ex);
+    load_vecw<ST, V>(Ey + o, ey);
+    load_vecw<ST, V>(Ez + o, ez);
+    load_vecw<ST, V>(Hx + o, hx);
+    load_vecw<ST, V>(Hy + o, hy);
+    load_vecw<ST, V>(Hz + o, hz);
+    load_vecw<ST, V>(Ex + o + dk1, exk1);
+    load_vecw<ST, V>(Ey + o + dk1, eyk1);
+    load_vecw<ST, V>(Ez + o + dj1, ezj1);
+    load_vecw<ST, V>(Ex + o + dj1, exj1);
+    load_vecw<ST, V>(Hz + o + djm, hzjm);
+    load_vecw<ST, V>(Hx + o + djm, hxjm);
+    load_vecw<ST, V>(Ey + o + djm, eyjm);
+    load_vecw<ST, V>(Ex + o + djm, exjm);
+    load_vecw<ST, V>(Ez + o + djm, ezjm);
+    load_vecw<ST, V>(Ey + o + djm + dk1, eyjmk1);
+    load_vecw<ST, V>(Hy + o + dkm, hykm);
+    load_vecw<ST, V>(Hx + o + dkm, hxkm);
+    load_vecw<ST, V>(Ex + o + dkm, exkm);
+    load_vecw<ST, V>(Ez + o + dkm, ezkm);
+    load_vecw<ST, V>(Ey + o + dkm, eykm);
+    load_vecw<ST, V>(Ez + o + dkm + dj1, ezj1km);
+    // i+1 neighbours of lane 31's last cell (the next warp's first): Ez, Ey
+    // at (j, k), Ey at j-1, Ez at k-1; and, in ALN grids, what the i = N
+    // cell's Hx update reads
+    const bool has_r = (lane == 31) && (FAST || (act && i0 + V < M));
+    float ez_r = 0.f, ey_r = 0.f, eyjm_r = 0.f, ezkm_r = 0.f, ezj1_x = 0.f, eyk1_x = 0.f;
+    if (has_r) {
+        ez_r = load_scalar(Ez + o + V);
+        ey_r = load_scalar(Ey + o + V);
+        eyjm_r = load_scalar(Ey + o + djm + V);
+        ezkm_r = load_scalar(Ez + o + dkm + V);
+        if constexpr (ALN) {
+            ezj1_x = load_scalar(Ez + o + dj1 + V);
+            eyk1_x = load_scalar(Ey + o + dk1 + V);
+        }
+    }
+    // lane 0's i-1 cell (the previous warp's last), for its H at i-1
+    float hz_l = 0.f, hy_l = 0.f, ey_l = 0.f, ex_l = 0.f, ez_l = 0.f, exj1_l = 0.f, exk1_l = 0.f;
+    if (lane == 0 && i0 >= 1 && act) {
+        hz_l = load_scalar(Hz + o - 1);
+        hy_l = load_scalar(Hy + o - 1);
+        ey_l = load_scalar(Ey + o - 1);
+        ex_l = load_scalar(Ex + o - 1);
+        ez_l = load_scalar(Ez + o - 1);
+        exj1_l = load_scalar(Ex + o + dj1 - 1);
+        exk1_l = load_scalar(Ex + o + dk1 - 1);
+    }
+    const float ez_n = __shfl_down_sync(0xffffffffu, ez[0], 1);
+    const float ey_n = __shfl_down_sync(0xffffffffu, ey[0], 1);
+    const float eyjm_n = __shfl_down_sync(0xffffffffu, eyjm[0], 1);
+    const float ezkm_n = __shfl_down_sync(0xffffffffu, ezkm[0], 1);
+    const float ez_last = (lane == 31) ? ez_r : ez_n;
+    const float ey_last = (lane == 31) ? ey_r : ey_n;
+    const float eyjm_last = (lane == 31) ? eyjm_r : eyjm_n;
+    const float ezkm_last = (lane == 31) ? ezkm_r : ezkm_n;
+
+    // H^{n+1/2}: own cells, and the j-1 / k-1 values the E update reads
+    float hxn[V], hyn[V], hzn[V], hzjmn[V], hxjmn[V], hykmn[V], hxkmn[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
+        const float ey_ip = (e + 1 < V) ? ey[e + 1] : ey_last;
+        const float eyjm_ip = (e + 1 < V) ? eyjm[e + 1] : eyjm_last;
+        const float ezkm_ip = (e + 1 < V) ? ezkm[e + 1] : ezkm_last;
+        const bool iN = FAST || i < N;
+        hxn[e] = (FAST || (j < N && k < Nk)) ? curl_sub(hx[e], s, ezj1[e], ez[e], eyk1[e], ey[e]) : hx[e];
+        hyn[e] = (FAST || (iN && k < Nk)) ? curl_sub(hy[e], s, exk1[e], ex[e], ez_ip, ez[e]) : hy[e];
+        hzn[e] = (FAST || (iN && j < N)) ? curl_sub(hz[e], s, ey_ip, ey[e], exj1[e], ex[e]) : hz[e];
+        // row j-1: its j+1 row is row j (own Ex, Ez); plane k-1: its k+1
+        // plane is plane k (own Ex, Ey)
+        hzjmn[e] = iN ? curl_sub(hzjm[e], s, eyjm_ip, eyjm[e], ex[e], exjm[e]) : hzjm[e];
+        hxjmn[e] = (FAST || k < Nk) ? curl_sub(hxjm[e], s, ez[e], ezjm[e], eyjmk1[e], eyjm[e]) : hxjm[e];
+        hykmn[e] = iN ? curl_sub(hykm[e], s, ex[e], exkm[e], ezkm_ip, ezkm[e]) : hykm[e];
+        hxkmn[e] = (FAST || j < N) ? curl_sub(hxkm[e], s, ezj1km[e], ezkm[e], ey[e], eykm[e]) : hxkm[e];
+        // the E launch of the two-launch step reads H as stored: round to
+        // the storage type (identity for f32)
+        hxn[e] = stored<ST>(hxn[e]);
+        hyn[e] = stored<ST>(hyn[e]);
+        hzn[e] = stored<ST>(hzn[e]);
+        hzjmn[e] = stored<ST>(hzjmn[e]);
+        hxjmn[e] = stored<ST>(hxjmn[e]);
+        hykmn[e] = stored<ST>(hykmn[e]);
+        hxkmn[e] = stored<ST>(hxkmn[e]);
+    }
+    // i-1: the previous lane's last cell; lane 0 recomputes its own
+    float hz_first = __shfl_up_sync(0xffffffffu, hzn[V - 1], 1);
+    float hy_first = __shfl_up_sync(0xffffffffu, hyn[V - 1], 1);
+    if (lane == 0) {
+        const int im = i0 - 1;  // < N whenever i0 <= N
+        hz_first = stored<ST>((im >= 0 && (FAST || j < N)) ? curl_sub(hz_l, s, ey[0], ey_l, exj1_l, ex_l) : hz_l);
+        hy_first = stored<ST>((im >= 0 && (FAST || k < Nk)) ? curl_sub(hy_l, s, exk1_l, ex_l, ez[0], ez_l) : hy_l);
+    }
+    if (!act) return;
+
+    // E^{n+1}
+    const bool j_int = FAST || (j >= 1 && j <= N - 1);
+    const bool k_int = FAST || (k >= 1 && k <= Nk - 1);
+    float exn[V], eyn[V], ezn[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        const bool i_int = FAST ? (e > 0 || i0 > 0) : (i >= 1 && i <= N - 1);
+        const float hz_im = (e > 0) ? hzn[e - 1] : hz_first;
+        const float hy_im = (e > 0) ? hyn[e - 1] : hy_first;
+        exn[e] = ((FAST || i < N) && j_int && k_int) ? curl_add(ex[e], s, hzn[e], hzjmn[e], hyn[e], hykmn[e]) : ex[e];
+        eyn[e] = ((FAST || j < N) && i_int && k_int) ? curl_add(ey[e], s, hxn[e], hxkmn[e], hzn[e], hz_im) : ey[e];
+        ezn[e] = ((FAST || k < Nk) && i_int && j_int) ? curl_add(ez[e], s, hyn[e], hy_im, hxn[e], hxjmn[e]) : ez[e];
+    }
+    // lane 31's extra cell i = N (ALN): Hx is its one update; E, Hy, Hz copied
+    float x_ex = 0.f, x_hx = 0.f, x_hy = 0.f, x_hz = 0.f, x_ez = ez_r;
+    if (ALN && lane == 31) {
+        x_ex = load_scalar(Ex + o + V);
+        x_hx = load_scalar(Hx + o + V);
+        x_hy = load_scalar(Hy + o + V);
+        x_hz = load_scalar(Hz + o + V);
+        if (FAST || (j < N && k < Nk)) x_hx = curl_sub(x_hx, s, ezj1_x, ez_r, eyk1_x, ey_r);
+    }
+    // the soft source on the new Ez, and the step counter
+    if (j == a.sj && k == a.sk) {
+        const bool in_vec = (a.si >= i0 && a.si < i0 + V);
+        const bool in_extra = ALN && lane == 31 && a.si == i0 + V;
+        if (in_vec || in_extra) {
+            const long long n = *a.counter;
+            if (a.src_on) {
+                const float u = __fdiv_rn(__fsub_rn((float)n, a.delay), a.width);
+                const float gsrc = __fmul_rn(a.amp, expf(-u * u));
+                if (in_vec) {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (i0 + e == a.si) ezn[e] = __fadd_rn(ezn[e], gsrc);
+                } else {
+                    x_ez = __fadd_rn(x_ez, gsrc);
+                }
+            }
+            *a.counter = n + 1;
+        }
+    }
+    const int nv = FAST ? V : M - i0;
+    store_vecw<ST, V>(static_cast<ST*>(a.g[EX]) + o, exn, nv);
+    store_vecw<ST, V>(static_cast<ST*>(a.g[EY]) + o, eyn, nv);
+    store_vecw<ST, V>(static_cast<ST*>(a.g[EZ]) + o, ezn, nv);
+    store_vecw<ST, V>(static_cast<ST*>(a.g[HX]) + o, hxn, nv);
+    store_vecw<ST, V>(static_cast<ST*>(a.g[HY]) + o, hyn, nv);
+    store_vecw<ST, V>(static_cast<ST*>(a.g[HZ]) + o, hzn, nv);
+    if (ALN && lane == 31) {
+        static_cast<ST*>(a.g[EX])[o + V] = from_f32<ST>(x_ex);
+        static_cast<ST*>(a.g[EY])[o + V] = from_f32<ST>(ey_r);
+        static_cast<ST*>(a.g[EZ])[o + V] = from_f32<ST>(x_ez);
+        static_cast<ST*>(a.g[HX])[o + V] = from_f32<ST>(x_hx);
+        static_cast<ST*>(a.g[HY])[o + V] = from_f32<ST>(x_hy);
+        static_cast<ST*>(a.g[HZ])[o + V] = from_f32<ST>(x_hz);
+    }
+}
+
+template <typename ST, bool ALN>
+__global__ void __launch_bounds__(256, 2) fdtd_fused_kernel(const FdtdArgs a) {
+    constexpr int V = kFdtdColumnCells;
+    pdl_wait_then_trigger();
+    const int N = a.N;
+    const int lane = threadIdx.x;
+    const uint3 blk = block_index(a.rev);
+    const int i0 = (blk.x * 32 + lane) * V;
+    const int j = blk.y * blockDim.y + threadIdx.y;
+    const int k = blk.z * blockDim.z + threadIdx.z;
+    const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
+    if (in_x && j >= 1 && j <= N - 1 && k >= 1 && k <= a.Nk - 1)
+        fdtd_fused_body<ST, true, ALN>(a, lane, i0, j, k);
+    else
+        fdtd_fused_body<ST, false, ALN>(a, lane, i0, j, k);
+}
+
 namespace {
 
 template <typename ST, bool MAT>
@@ -531,6 +751,25 @@ const void* fdtd_func(bool e_half, bool col, bool mat, bool aln) {
 }  // namespace
 
 cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out) {
+    if (variant == GS_KERNEL_FUSED) {
+        if (a.mat) return cudaErrorNotSupported;  // media: the two-launch column kernels
+        const bool aln = (a.N % (32 * kFdtdColumnCells) == 0);
+        switch (dt) {
+            case GS_F32: out->func = aln ? (const void*)fdtd_fused_kernel<float, true> : (const void*)fdtd_fused_kernel<float, false>; break;
+            case GS_BF16: out->func = aln ? (const void*)fdtd_fused_kernel<__nv_bfloat16, true> : (const void*)fdtd_fused_kernel<__nv_bfloat16, false>; break;
+            case GS_F16: out->func = aln ? (const void*)fdtd_fused_kernel<__half, true> : (const void*)fdtd_fused_kernel<__half, false>; break;
+            default: return cudaErrorInvalidValue;
+        }
+        const int by = std::max(1, std::min(a.kc, 8));
+        const int bz = std::max(1, 8 / by);
+        const int M = a.N + 1, Mk = a.Nk + 1;
+        const int span = aln ? a.N : M;
+        out->block = dim3(32, by, bz);
+        out->grid = dim3((span + 32 * kFdtdColumnCells - 1) / (32 * kFdtdColumnCells), (M + by - 1) / by, (Mk + bz - 1) / bz);
+        out->smem = 0;
+        out->set_args(a);
+        return cudaSuccess;
+    }
     const bool col = (variant == GS_KERNEL_COLUMN);
     const int V = col ? kFdtdColumnCells : ((dt == GS_F32) ? 4 : 8);
     const int M = a.N + 1, Mk = a.Nk + 1;

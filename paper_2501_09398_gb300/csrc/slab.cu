@@ -526,6 +526,8 @@ gs_status gs_slab_set_plan(gs_slab* s, const gs_plan* plan) {
     if (!plan) return sfail(s, GS_ERR_INVALID_ARG, "NULL argument");
     if (plan->graph_loop || plan->device_launch)
         return sfail(s, GS_ERR_UNSUPPORTED, "slab sets provide neither plan.graph_loop nor plan.device_launch");
+    if (plan->kernel == GS_KERNEL_FUSED)
+        return sfail(s, GS_ERR_UNSUPPORTED, "slab sets run the FDTD half-steps as two launches (no GS_KERNEL_FUSED)");
     if (plan->temporal_depth > s->halo)
         return sfail(s, GS_ERR_UNSUPPORTED, "plan.temporal_depth " + std::to_string(plan->temporal_depth) +
                                                 " exceeds the halo of " + std::to_string(s->halo));

@@ -10,7 +10,8 @@ every global load and store must lie inside its buffer and inside its row
 (the pitch), every shared-memory access inside the launch's allocation, and
 the stores of a launch must cover every cell of the field exactly once.
 The 3D depth-t COLUMN kernel (one cell a lane, every plane of the column)
-and the z-marching depth-2 kernel of deep stacks are re-traced the same way.
+and the z-marching depth-2 kernel of deep stacks are re-traced the same way,
+and so is the fused FDTD step (H and E in one launch, out of place).
 The formulas restate the kernels' address computations (csrc/heat.cu,
 csrc/fdtd.cu, csrc/multi.cu) for ragged shapes, so that a change to either
 is checked here before it runs on a GPU."""
@@ -318,6 +319,62 @@ def test_fdtd_column_kernel_addresses(N, esize, rows):
     cells = np.zeros((M, M, pitch), dtype=bool)
     cells[:, :, :M] = True
     assert np.array_equal(owned.reshape(M, M, pitch) == 1, cells)
+
+
+@pytest.mark.parametrize("N,Nk", [(9, 9), (16, 16), (37, 37), (128, 128), (130, 130), (64, 17), (128, 33), (16, 1)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("rows", [1, 2, 8])
+def test_fdtd_fused_kernel_addresses(N, Nk, esize, rows):
+    # the fused step: own vectors and the j+1, k+1, j-1, k-1, j-1&k+1,
+    # k-1&j+1 vectors at offsets that collapse to 0 where they would leave
+    # the arrays (and for threads past them), lane 31's i+1 scalars, lane
+    # 0's i-1 scalars, the aligned layout's i = N cell; stores of all six
+    # components cover every element of the written set once
+    V = 4
+    M, Mk = N + 1, Nk + 1
+    aln = N % (32 * V) == 0
+    pitch = pitch_of(M, esize)
+    plane = pitch * M
+    size = plane * Mk
+    by_ = max(1, min(rows, 8))
+    bz_ = max(1, 8 // by_)
+    span = N if aln else M
+    grid = (-(-span // (32 * V)), -(-M // by_), -(-Mk // bz_))
+    bx, by, bz, lane, ty, tz = threads(grid, (32, by_, bz_))
+    i0 = (bx * 32 + lane) * V
+    j = by * by_ + ty
+    k = bz * bz_ + tz
+    in_x = np.ones_like(i0, dtype=bool) if aln else warp_all(i0 + V <= N, bx, by, bz, ty, tz)
+    fast = in_x & (j >= 1) & (j <= N - 1) & (k >= 1) & (k <= Nk - 1)
+    act = fast | ((i0 < M) & (j < M) & (k < Mk))
+    o = np.where(act, k * plane + j * pitch + i0, 0)
+    row = np.where(act, k * plane + j * pitch, 0)
+    dj1 = np.where(fast | (act & (j + 1 < M)), pitch, 0)
+    dk1 = np.where(fast | (act & (k + 1 < Mk)), plane, 0)
+    djm = np.where(fast | (act & (j >= 1)), -pitch, 0)
+    dkm = np.where(fast | (act & (k >= 1)), -plane, 0)
+    # vector loads of every thread (inactive ones at offset 0)
+    for d in (0, dk1, dj1, djm, djm + dk1, dkm, dkm + dj1):
+        check_vec(o + d, V, row + d, pitch, size)
+    has_r = (lane == 31) & (fast | (act & (i0 + V < M)))
+    for d in (0, djm, dkm) + ((dj1, dk1) if aln else ()):
+        check_vec((o + d + V)[has_r], 1, (row + d)[has_r], pitch, size)
+    m = (lane == 0) & (i0 >= 1) & act
+    for d in (0, dj1, dk1):
+        check_vec((o + d - 1)[m], 1, (row + d)[m], pitch, size)
+    # stores: every element of the M x M x Mk arrays once
+    owned = np.zeros(size, dtype=np.int64)
+    nv = np.where(fast, V, np.minimum(V, M - i0))
+    for c in range(V):
+        mm = act & (c < nv)
+        np.add.at(owned, o[mm] + c, 1)
+    if aln:
+        mm = act & (lane == 31)
+        assert np.all(i0[mm] + V == N)
+        np.add.at(owned, o[mm] + V, 1)
+    cells = np.zeros((Mk, M, pitch), dtype=bool)
+    cells[:, :, :M] = True
+    assert np.array_equal(owned.reshape(Mk, M, pitch) == 1, cells)
 
 
 # ---------------------------------------------------- MARCH and WAVE ----
