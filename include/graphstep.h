@@ -881,6 +881,30 @@ typedef enum gs_inject { GS_INJECT_NONE = 0, GS_INJECT_MALLOC = 1, GS_INJECT_GRA
 gs_status gs_debug_inject_failure(gs_inject call, int64_t after);
 gs_status gs_debug_injection_pending(int32_t *pending);
 
+/* Bounds-checked builds (libgraphstep_checked.so, compiled with GS_CHECKED
+ * by `python paper_2501_09398_gb300/build.py --checked`; the paper has no
+ * counterpart): every global field access of the thermal and FDTD stencil
+ * kernels (loads, stores, material ids) is checked against a table of up to
+ * GS_CHECK_MAX_RANGES byte ranges [lo, hi) of device memory the caller
+ * registers: its field buffers and the device memory a context owns
+ * (gs_debug_owned_ranges: the FDTD fused plan's second set, once a step has
+ * set it up).  An access outside every range is counted, its address
+ * recorded and the access skipped (a load gives zeros), so nothing faults.
+ * gs_debug_check_ranges replaces the table and clears the count;
+ * gs_debug_check_read returns the count of refused accesses since, and the
+ * first refused address, and clears the count.  gs_debug_checked_build
+ * returns 1 in a checked build, 0 otherwise; in an ordinary build the two
+ * calls return GS_ERR_UNSUPPORTED.  Errors: GS_ERR_INVALID_ARG (NULL, n
+ * outside [0, GS_CHECK_MAX_RANGES], lo > hi), GS_ERR_CUDA. */
+#define GS_CHECK_MAX_RANGES 128
+int gs_debug_checked_build(void);
+/* The byte ranges of device memory ctx owns that its kernels read or write
+ * (the fused FDTD plan's second set of components); *n_out gets their
+ * number, up to `capacity` are written.  Any build. */
+gs_status gs_debug_owned_ranges(const gs_ctx *ctx, uint64_t *lo, uint64_t *hi, int32_t capacity, int32_t *n_out);
+gs_status gs_debug_check_ranges(const uint64_t *lo, const uint64_t *hi, int32_t n);
+gs_status gs_debug_check_read(uint64_t *refused, uint64_t *first_refused_address);
+
 #ifdef __cplusplus
 }
 #endif

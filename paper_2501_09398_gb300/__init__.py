@@ -18,7 +18,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgraphstep.so")
+# GS_LIBRARY=checked loads the bounds-checked test build instead
+LIB_PATH = os.path.join(_HERE, "libgraphstep_checked.so" if os.environ.get("GS_LIBRARY") == "checked"
+                        else "libgraphstep.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -806,6 +808,42 @@ _sig("gs_debug_injection_pending", [ctypes.POINTER(_i32)])
 def gs_debug_inject_failure(call: int, after: int = 0) -> None:
     """Make the library's (after+1)-th next call of kind `call` fail once."""
     _check(_lib.gs_debug_inject_failure(call, after))
+
+
+_sig("gs_debug_checked_build", [], ctypes.c_int)
+_sig("gs_debug_check_ranges", [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _i32])
+_sig("gs_debug_check_read", [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)])
+_sig("gs_debug_owned_ranges", [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _i32,
+                               ctypes.POINTER(_i32)])
+GS_CHECK_MAX_RANGES = 128
+
+
+def gs_debug_owned_ranges(ctx):
+    """(lo, hi) byte ranges of the device memory ctx owns that its kernels touch."""
+    lo = (ctypes.c_uint64 * 8)()
+    hi = (ctypes.c_uint64 * 8)()
+    n = _i32()
+    _check(_lib.gs_debug_owned_ranges(ctx, lo, hi, 8, ctypes.byref(n)), ctx)
+    return [(lo[i], hi[i]) for i in range(min(n.value, 8))]
+
+
+def gs_debug_checked_build() -> bool:
+    return bool(_lib.gs_debug_checked_build())
+
+
+def gs_debug_check_ranges(ranges) -> None:
+    """ranges: (lo, hi) byte addresses of device memory the kernels may touch."""
+    n = len(ranges)
+    lo = (ctypes.c_uint64 * max(n, 1))(*[int(r[0]) for r in ranges])
+    hi = (ctypes.c_uint64 * max(n, 1))(*[int(r[1]) for r in ranges])
+    _check(_lib.gs_debug_check_ranges(lo, hi, n))
+
+
+def gs_debug_check_read():
+    """(refused accesses since the last read, first refused address)."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.gs_debug_check_read(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def gs_debug_injection_pending() -> bool:

@@ -331,13 +331,16 @@ def whole_run_ms(w, plan, S, stream, reps=3):
     """Median over `reps` runs (after one untimed run) of a whole run of
     w["n_iters"] iterations with (plan, S) from a fresh state: graph
     creation (T_C) and execution, CUDA events on the context's stream (the
-    GPU waits for the host's graph build between them)."""
+    GPU waits for the host's graph build between them).  `stream`: a CUDA
+    stream handle (not NULL), the context's and the events'."""
     import torch
+
+    assert stream, "whole_run_ms needs the stream its context and events share"
 
     ctx, keep = _context(w, stream)
     try:
         gs_set_plan(ctx, **plan)
-        st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.current_stream()
+        st = torch.cuda.ExternalStream(stream)  # the context's stream
         times = []
         for r in range(reps + 1):
             _reset(ctx, w)
@@ -364,6 +367,10 @@ def measured_regret(models, held, n=30, seed=7, stream=None, reps=3, max_run_ms=
     whole run of I_k iterations; regret = T(pick) / min over the three - 1.
     Returns per-workload records and the composed-time regrets (from the
     sweep's T_C and ms per iteration) of the same picks."""
+    import torch
+
+    if stream is None:  # the contexts and the timing events must share one stream
+        stream = torch.cuda.Stream().cuda_stream
     rng = np.random.default_rng(seed)
     by_kind = {k: [] for k in KINDS}
     for w, tab in held:

@@ -878,6 +878,57 @@ gs_status gs_debug_inject_failure(gs_inject call, int64_t after) {
     return GS_OK;
 }
 
+gs_status gs_debug_owned_ranges(const gs_ctx* c, uint64_t* lo, uint64_t* hi, int32_t capacity, int32_t* n_out) {
+    if (!c || !n_out || capacity < 0 || (capacity > 0 && (!lo || !hi)))
+        return fail(nullptr, GS_ERR_INVALID_ARG, "gs_debug_owned_ranges: bad arguments");
+    int32_t n = 0;
+    if (c->fused_set) {
+        if (n < capacity) {
+            lo[n] = reinterpret_cast<uint64_t>(c->fused_set);
+            hi[n] = lo[n] + 6 * c->fused_stride;
+        }
+        ++n;
+    }
+    *n_out = n;
+    return GS_OK;
+}
+
+int gs_debug_checked_build(void) {
+#ifdef GS_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+gs_status gs_debug_check_ranges(const uint64_t* lo, const uint64_t* hi, int32_t n) {
+    if (n < 0 || n > GS_CHECK_MAX_RANGES || (n > 0 && (!lo || !hi)))
+        return fail(nullptr, GS_ERR_INVALID_ARG, "gs_debug_check_ranges: n in [0, 128] and both arrays needed");
+    for (int32_t i = 0; i < n; ++i)
+        if (lo[i] > hi[i]) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_debug_check_ranges: lo > hi");
+    if (!gs_debug_checked_build()) return fail(nullptr, GS_ERR_UNSUPPORTED, "not a bounds-checked build");
+    static_assert(sizeof(uint64_t) == sizeof(unsigned long long), "range words");
+    const auto* l = reinterpret_cast<const unsigned long long*>(lo);
+    const auto* h = reinterpret_cast<const unsigned long long*>(hi);
+    cudaError_t e = gs::heat_check_set(l, h, n);
+    if (e == cudaSuccess) e = gs::fdtd_check_set(l, h, n);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "gs_debug_check_ranges");
+    return GS_OK;
+}
+
+gs_status gs_debug_check_read(uint64_t* refused, uint64_t* first) {
+    if (!refused || !first) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_debug_check_read: NULL argument");
+    if (!gs_debug_checked_build()) return fail(nullptr, GS_ERR_UNSUPPORTED, "not a bounds-checked build");
+    unsigned long long b1 = 0, f1 = 0, b2 = 0, f2 = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = gs::heat_check_get(&b1, &f1);
+    if (e == cudaSuccess) e = gs::fdtd_check_get(&b2, &f2);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "gs_debug_check_read");
+    *refused = b1 + b2;
+    *first = b1 ? f1 : f2;
+    return GS_OK;
+}
+
 gs_status gs_debug_injection_pending(int32_t* pending) {
     if (!pending) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_debug_injection_pending: NULL argument");
     *pending = gs::inject::g_inject_kind.load() != GS_INJECT_NONE;

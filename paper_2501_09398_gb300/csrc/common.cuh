@@ -34,9 +34,65 @@ template <> __device__ __forceinline__ float from_f32<float>(float v) { return v
 template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
 
+// ------------------------------------------------------- checked build --
+// With GS_CHECKED defined, the translation units that also define
+// GS_CHECK_THIS_UNIT (the stencil kernels) check every global field access
+// of the helpers below against a table of registered byte ranges (set from
+// the host, gs_debug_check_ranges): an access outside every range is
+// counted, its address recorded, and skipped (a load gives zeros).  Nothing
+// faults.  Each translation unit has its own table (no relocatable device
+// code), filled through its <unit>_check_set / _check_get functions.
+constexpr int kCheckRanges = 128;
+#if defined(GS_CHECKED) && defined(GS_CHECK_THIS_UNIT)
+static __device__ unsigned long long g_chk_lo[kCheckRanges], g_chk_hi[kCheckRanges];
+static __device__ int g_chk_n;
+static __device__ unsigned long long g_chk_bad, g_chk_first;
+__device__ __forceinline__ bool gs_chk(const void* p, size_t bytes) {
+    const unsigned long long lo = reinterpret_cast<unsigned long long>(p), hi = lo + bytes;
+    const int n = g_chk_n;
+    for (int i = 0; i < n; ++i)
+        if (lo >= g_chk_lo[i] && hi <= g_chk_hi[i]) return true;
+    if (atomicAdd(&g_chk_bad, 1ull) == 0ull) g_chk_first = lo;
+    return false;
+}
+#define GS_CHK(p, bytes) gs_chk((p), (bytes))
+#define GS_CHECK_UNIT(NAME)                                                                                  \
+    cudaError_t NAME##_check_set(const unsigned long long* lo, const unsigned long long* hi, int n) {         \
+        cudaError_t e = cudaMemcpyToSymbol(g_chk_lo, lo, sizeof(unsigned long long) * n);                     \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_chk_hi, hi, sizeof(unsigned long long) * n);           \
+        const unsigned long long zero = 0;                                                                    \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_chk_n, &n, sizeof(int));                               \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_chk_bad, &zero, sizeof(zero));                          \
+        return e;                                                                                             \
+    }                                                                                                         \
+    cudaError_t NAME##_check_get(unsigned long long* bad, unsigned long long* first) {                         \
+        cudaError_t e = cudaMemcpyFromSymbol(bad, g_chk_bad, sizeof(*bad));                                   \
+        if (e == cudaSuccess) e = cudaMemcpyFromSymbol(first, g_chk_first, sizeof(*first));                   \
+        const unsigned long long zero = 0;                                                                    \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_chk_bad, &zero, sizeof(zero));                          \
+        return e;                                                                                             \
+    }
+#else
+#define GS_CHK(p, bytes) true
+#define GS_CHECK_UNIT(NAME)                                                                                  \
+    cudaError_t NAME##_check_set(const unsigned long long*, const unsigned long long*, int) {                 \
+        return cudaErrorNotSupported;                                                                         \
+    }                                                                                                         \
+    cudaError_t NAME##_check_get(unsigned long long*, unsigned long long*) { return cudaErrorNotSupported; }
+#endif
+cudaError_t heat_check_set(const unsigned long long* lo, const unsigned long long* hi, int n);
+cudaError_t heat_check_get(unsigned long long* bad, unsigned long long* first);
+cudaError_t fdtd_check_set(const unsigned long long* lo, const unsigned long long* hi, int n);
+cudaError_t fdtd_check_get(unsigned long long* bad, unsigned long long* first);
+
 // 16-byte vector load through the read-only path.
 template <typename ST>
 __device__ __forceinline__ void load_vec(const ST* __restrict__ p, float (&v)[Vec<ST>::N]) {
+    if (!GS_CHK(p, 16)) {
+#pragma unroll
+        for (int i = 0; i < Vec<ST>::N; ++i) v[i] = 0.f;
+        return;
+    }
     const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
     const ST* e = reinterpret_cast<const ST*>(&raw);
 #pragma unroll
@@ -46,6 +102,11 @@ __device__ __forceinline__ void load_vec(const ST* __restrict__ p, float (&v)[Ve
 // 16-byte vector load through the coherent path (for in-place updates).
 template <typename ST>
 __device__ __forceinline__ void load_vec_rw(const ST* p, float (&v)[Vec<ST>::N]) {
+    if (!GS_CHK(p, 16)) {
+#pragma unroll
+        for (int i = 0; i < Vec<ST>::N; ++i) v[i] = 0.f;
+        return;
+    }
     const uint4 raw = *reinterpret_cast<const uint4*>(p);
     const ST* e = reinterpret_cast<const ST*>(&raw);
 #pragma unroll
@@ -56,6 +117,7 @@ __device__ __forceinline__ void load_vec_rw(const ST* p, float (&v)[Vec<ST>::N])
 template <typename ST>
 __device__ __forceinline__ void store_vec(ST* p, const float (&v)[Vec<ST>::N], int n_valid) {
     constexpr int N = Vec<ST>::N;
+    if (!GS_CHK(p, sizeof(ST) * (n_valid >= N ? N : (n_valid > 0 ? n_valid : 0)))) return;
     if (n_valid >= N) {
         uint4 raw;
         ST* e = reinterpret_cast<ST*>(&raw);
@@ -70,12 +132,29 @@ __device__ __forceinline__ void store_vec(ST* p, const float (&v)[Vec<ST>::N], i
 }
 
 template <typename ST>
-__device__ __forceinline__ float load_scalar(const ST* p) { return to_f32(__ldg(p)); }
+__device__ __forceinline__ float load_scalar(const ST* p) { return GS_CHK(p, sizeof(ST)) ? to_f32(__ldg(p)) : 0.f; }
+
+// One element through the coherent path (a value the launch may write).
+template <typename ST>
+__device__ __forceinline__ float load_scalar_rw(const ST* p) { return GS_CHK(p, sizeof(ST)) ? to_f32(*p) : 0.f; }
+
+template <typename ST>
+__device__ __forceinline__ void store_scalar(ST* p, float v) {
+    if (GS_CHK(p, sizeof(ST))) *p = from_f32<ST>(v);
+}
+
+// One uint8 material id.
+__device__ __forceinline__ unsigned load_id(const unsigned char* p) { return GS_CHK(p, 1) ? __ldg(p) : 0u; }
 
 // W elements per access, W * sizeof(ST) = 4, 8 or 16 bytes (read-only path).
 template <typename ST, int W>
 __device__ __forceinline__ void load_vecw(const ST* __restrict__ p, float (&v)[W]) {
     static_assert(W * sizeof(ST) == 4 || W * sizeof(ST) == 8 || W * sizeof(ST) == 16, "4-, 8- or 16-byte access");
+    if (!GS_CHK(p, W * sizeof(ST))) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = 0.f;
+        return;
+    }
     if constexpr (W * sizeof(ST) == 16) {
         const uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
         const ST* e = reinterpret_cast<const ST*>(&raw);
@@ -98,6 +177,11 @@ __device__ __forceinline__ void load_vecw(const ST* __restrict__ p, float (&v)[W
 template <typename ST, int W>
 __device__ __forceinline__ void load_vecw_rw(const ST* p, float (&v)[W]) {
     static_assert(W * sizeof(ST) == 8 || W * sizeof(ST) == 16, "8- or 16-byte access");
+    if (!GS_CHK(p, W * sizeof(ST))) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = 0.f;
+        return;
+    }
     if constexpr (W * sizeof(ST) == 16) {
         const uint4 raw = *reinterpret_cast<const uint4*>(p);
         const ST* e = reinterpret_cast<const ST*>(&raw);
@@ -115,6 +199,11 @@ __device__ __forceinline__ void load_vecw_rw(const ST* p, float (&v)[W]) {
 template <int W>
 __device__ __forceinline__ void load_ids(const unsigned char* __restrict__ p, unsigned (&id)[W]) {
     static_assert(W == 4 || W == 8, "4 or 8 ids");
+    if (!GS_CHK(p, W)) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) id[i] = 0u;
+        return;
+    }
     if constexpr (W == 4) {
         const unsigned raw = __ldg(reinterpret_cast<const unsigned*>(p));
 #pragma unroll
@@ -131,6 +220,7 @@ __device__ __forceinline__ void load_ids(const unsigned char* __restrict__ p, un
 
 template <typename ST, int W>
 __device__ __forceinline__ void store_vecw(ST* p, const float (&v)[W], int n_valid) {
+    if (!GS_CHK(p, sizeof(ST) * (n_valid >= W ? W : (n_valid > 0 ? n_valid : 0)))) return;
     if (n_valid >= W) {
         if constexpr (W * sizeof(ST) == 16) {
             uint4 raw;

@@ -18,6 +18,7 @@
 // (lane 31 / lane 0 load one scalar); j-neighbours are re-read (L1/L2).
 #include <algorithm>
 
+#define GS_CHECK_THIS_UNIT  // checked builds bounds-check this unit's field accesses
 #include "common.cuh"
 
 namespace gs {
@@ -253,7 +254,7 @@ __device__ __forceinline__ void fdtd_source(const FdtdArgs& a, int lane, int i0,
                 if (i0 + e == a.si) ez[e] = __fadd_rn(ez[e], g);
         } else {
             ST* Ez = static_cast<ST*>(a.f[EZ]);
-            Ez[o + V] = from_f32<ST>(__fadd_rn(to_f32(Ez[o + V]), g));
+            store_scalar(Ez + o + V, __fadd_rn(load_scalar_rw(Ez + o + V), g));
             *extra_src = true;
         }
     }
@@ -298,8 +299,8 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
             if constexpr (EXTRA) {
                 ezj1_x = load_scalar(Ez + o + a.pitch + V);
                 eyk1_x = load_scalar(Ey + o + a.plane + V);
-                hx_x = to_f32(Hx[o + V]);
-                if constexpr (MAT) id_x = __ldg(a.mat + o + V);
+                hx_x = load_scalar_rw(Hx + o + V);
+                if constexpr (MAT) id_x = load_id(a.mat + o + V);
             }
         }
     } else {
@@ -363,7 +364,7 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
         if (lane == 31) {
             if constexpr (MAT) hx_x = curl_sub_m(hx_x, s_med[id_x], ezj1_x, ez_r, eyk1_x, ey_r);
             else hx_x = curl_sub(hx_x, s, ezj1_x, ez_r, eyk1_x, ey_r);
-            Hx[o + V] = from_f32<ST>(hx_x);
+            store_scalar(Hx + o + V, hx_x);
         }
     }
 }
@@ -708,12 +709,12 @@ __device__ __forceinline__ void fdtd_fused_body(const FdtdArgs& a, int lane, int
     store_vecw<ST, V>(static_cast<ST*>(a.g[HY]) + o, hyn, nv);
     store_vecw<ST, V>(static_cast<ST*>(a.g[HZ]) + o, hzn, nv);
     if (ALN && lane == 31) {
-        static_cast<ST*>(a.g[EX])[o + V] = from_f32<ST>(x_ex);
-        static_cast<ST*>(a.g[EY])[o + V] = from_f32<ST>(ey_r);
-        static_cast<ST*>(a.g[EZ])[o + V] = from_f32<ST>(x_ez);
-        static_cast<ST*>(a.g[HX])[o + V] = from_f32<ST>(x_hx);
-        static_cast<ST*>(a.g[HY])[o + V] = from_f32<ST>(x_hy);
-        static_cast<ST*>(a.g[HZ])[o + V] = from_f32<ST>(x_hz);
+        store_scalar(static_cast<ST*>(a.g[EX]) + o + V, x_ex);
+        store_scalar(static_cast<ST*>(a.g[EY]) + o + V, ey_r);
+        store_scalar(static_cast<ST*>(a.g[EZ]) + o + V, x_ez);
+        store_scalar(static_cast<ST*>(a.g[HX]) + o + V, x_hx);
+        store_scalar(static_cast<ST*>(a.g[HY]) + o + V, x_hy);
+        store_scalar(static_cast<ST*>(a.g[HZ]) + o + V, x_hz);
     }
 }
 
@@ -799,5 +800,7 @@ cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, 
     out->set_args(a);
     return cudaSuccess;
 }
+
+GS_CHECK_UNIT(fdtd)
 
 }  // namespace gs

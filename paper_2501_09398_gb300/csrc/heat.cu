@@ -13,6 +13,7 @@
 // bit-identical.
 #include <algorithm>
 
+#define GS_CHECK_THIS_UNIT  // checked builds bounds-check this unit's field accesses
 #include "common.cuh"
 
 namespace gs {
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(512) heat_temporal_kernel(const HeatArgs a) {
         const int gx = gx0 + D + ox, gy = gy0 + D + oy;
         if (gx >= nx || gy >= ny) continue;
         const float v = bufA[iz * area + (oy + D) * IX + (ox + D)];
-        Tout[(long long)iz * a.plane + (long long)gy * a.pitch + gx] = from_f32<ST>(v);
+        store_scalar(Tout + (long long)iz * a.plane + (long long)gy * a.pitch + gx, v);
     }
 }
 
@@ -1112,7 +1113,7 @@ __device__ __forceinline__ void heat_column3_t_tile(const HeatArgs& a, int bx, i
 #pragma unroll
             for (int z = 0; z < NZM; ++z) {
                 if (!EXACT && z >= nz) break;
-                out_p[(long long)z * plane + (long long)yg * pitch + x] = from_f32<ST>(row[j][z]);
+                store_scalar(out_p + (long long)z * plane + (long long)yg * pitch + x, row[j][z]);
             }
         }
     }
@@ -1470,5 +1471,7 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
     out->set_args(a);
     return cudaSuccess;
 }
+
+GS_CHECK_UNIT(heat)
 
 }  // namespace gs

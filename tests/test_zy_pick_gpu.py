@@ -193,10 +193,8 @@ def test_measured_regret_of_the_builtin_ensemble():
     included, median of five) of 15 held-out workloads of the packaged sweep,
     five of each kind, with the compiled-in ensemble's pick, the sweep's best
     candidate and the analytic pick; the learned pick's measured mean regret
-    against the fastest of the three stays within 5 %.  (Several of these
-    runs take under a millisecond, where the host's graph build varies by
-    tens of microseconds: with the median of three runs one measurement
-    read 11.9 %, with the sweep's own best at 4.5 %.)"""
+    against the fastest of the three stays within 5 %.  The contexts run on
+    one explicit stream, the one the timing events are recorded on."""
     from paper_2501_09398_gb300 import costmodel as cm
     from paper_2501_09398_gb300 import gs_mlp_destroy
 
