@@ -718,8 +718,8 @@ SWEEP_S = (1, 10, 50, 100, 500, 1000)
 SWEEP_PLANS = {
     "heat2d-512": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=4, block_x=64, rows=4)),
                    (4, dict(kernel=4, block_x=64, rows=4))),
-    "heat3d-512x512x8": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=4, block_x=256)),
-                         (4, dict(kernel=4, block_x=256)), (2, dict(kernel=2, block_x=64, rows=4))),
+    "heat3d-512x512x8": ((1, dict(kernel=4, block_x=64, rows=4)), (2, dict(kernel=4, block_x=64)),
+                         (4, dict(kernel=4, block_x=64)), (2, dict(kernel=2, block_x=64, rows=4))),
 }
 
 
