@@ -1009,6 +1009,7 @@ def main():
         for nm, over, tag in (("heat2d-512", {}, "depth1"), ("heat2d-512", dict(loop=True), "device_loop"),
                               ("heat3d-256", {}, "column"),
                               ("heat3d-256", dict(depth=2, kernel=4, block_x=128), "zmarch2"),
+                              ("heat3d-256", dict(depth=2, kernel=7, block_x=256), "stream2"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-128", dict(kernel=6, rows=4), "fused"), ("fdtd-256", dict(kernel=6, rows=8), "fused"),
                               ("fdtd-media-256", {}, "column"),

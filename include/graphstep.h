@@ -147,9 +147,17 @@ typedef struct gs_medium {
  *   COLUMN_SMEM  as COLUMN, but each thread loads only its own row of every
  *          plane; rows y-1 / y+1 come from shared memory after one barrier
  *          (fewer registers and L2 requests).
+ *   STREAM 3D at depth 2 only: a block marches tile_y planes in z over an
+ *          x-y tile of 128 x (2W - 2) cells (W = 16 compute warps with
+ *          block_x = 512, 8 with block_x = 256; block_x must be one of the
+ *          two), each lane four cells at two rows, its level-0 planes
+ *          arriving in shared memory through the Tensor Memory Accelerator
+ *          (a ring of six plane stages), level 1 of each plane kept in
+ *          shared memory for its neighbours.  Any nz.
  *   AUTO   depth 1, 2D, and 3D with nz <= 8: COLUMN; other 3D stacks at
- *          depth 2: WAVE for nz <= 16, else COLUMN (the z march); at depth
- *          4: WAVE for nz <= 16, else TILE. */
+ *          depth 2: WAVE for nz <= 16, else STREAM (block_x 256 unless 256
+ *          or 512 is given; with another block_x, COLUMN's z march); at
+ *          depth 4: WAVE for nz <= 16, else TILE. */
 typedef enum gs_kernel {
     GS_KERNEL_AUTO = 0,
     GS_KERNEL_MARCH = 1,
@@ -157,7 +165,8 @@ typedef enum gs_kernel {
     GS_KERNEL_TILE = 3,
     GS_KERNEL_COLUMN = 4,
     GS_KERNEL_COLUMN_SMEM = 5,
-    GS_KERNEL_FUSED = 6
+    GS_KERNEL_FUSED = 6,
+    GS_KERNEL_STREAM = 7
 } gs_kernel;
 
 /* Block traversal order of consecutive launches (gs_plan.traverse,
@@ -904,6 +913,15 @@ int gs_debug_checked_build(void);
 gs_status gs_debug_owned_ranges(const gs_ctx *ctx, uint64_t *lo, uint64_t *hi, int32_t capacity, int32_t *n_out);
 gs_status gs_debug_check_ranges(const uint64_t *lo, const uint64_t *hi, int32_t n);
 gs_status gs_debug_check_read(uint64_t *refused, uint64_t *first_refused_address);
+
+/* Bounded waits inside the library's kernels (the STREAM kernel's waits for
+ * its tensor copies, the paper has no counterpart): a wait gives up after
+ * about one second of the GPU's global timer instead of hanging; its block
+ * then stops early, so the launch's results are not defined.  *count_out
+ * gets the number of blocks whose wait ran out since the previous call, and
+ * the count is cleared.  Synchronises the device.  Errors:
+ * GS_ERR_INVALID_ARG (NULL), GS_ERR_CUDA. */
+gs_status gs_wait_timeouts(uint64_t *count_out);
 
 #ifdef __cplusplus
 }

@@ -36,7 +36,7 @@ GS_HEAT2D, GS_HEAT3D, GS_FDTD3D, GS_SKELETON = range(4)
 GS_F32, GS_BF16, GS_F16 = range(3)
 GS_BC_CLAMP, GS_BC_DIRICHLET0, GS_BC_PEC = range(3)
 GS_KERNEL_AUTO, GS_KERNEL_MARCH, GS_KERNEL_WAVE, GS_KERNEL_TILE, GS_KERNEL_COLUMN, GS_KERNEL_COLUMN_SMEM, \
-    GS_KERNEL_FUSED = range(7)
+    GS_KERNEL_FUSED, GS_KERNEL_STREAM = range(8)
 GS_TRAVERSE_AUTO, GS_TRAVERSE_FORWARD, GS_TRAVERSE_ALTERNATE = range(3)
 (GS_FIELD_T0, GS_FIELD_T1, GS_FIELD_P, GS_FIELD_EX, GS_FIELD_EY, GS_FIELD_EZ, GS_FIELD_HX, GS_FIELD_HY,
  GS_FIELD_HZ, GS_FIELD_T, GS_FIELD_X, GS_FIELD_MAT) = range(12)
@@ -844,6 +844,17 @@ def gs_debug_check_read():
     a, b = ctypes.c_uint64(), ctypes.c_uint64()
     _check(_lib.gs_debug_check_read(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+_sig("gs_wait_timeouts", [ctypes.POINTER(ctypes.c_uint64)])
+
+
+def gs_wait_timeouts() -> int:
+    """Blocks of the library's kernels whose bounded wait ran out since the
+    last call (the count is cleared; synchronises the device)."""
+    n = ctypes.c_uint64()
+    _check(_lib.gs_wait_timeouts(ctypes.byref(n)))
+    return n.value
 
 
 def gs_debug_injection_pending() -> bool:

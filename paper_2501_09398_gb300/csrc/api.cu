@@ -220,6 +220,7 @@ gs_plan default_plan(const gs_ctx* c) {
 
 gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     const gs_plan d = default_plan(c);
+    const bool block_x_given = p->block_x != 0;
     if (p->block_x == 0) p->block_x = d.block_x;
     if (p->rows == 0) p->rows = d.rows;
     if (p->tile_x == 0) p->tile_x = d.tile_x;
@@ -256,7 +257,7 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     if (t != 1 && t != 2 && t != 4) return fail(c, GS_ERR_INVALID_ARG, "plan.temporal_depth must be 1, 2 or 4");
     if (c->kind == GS_FDTD3D && t != 1)
         return fail(c, GS_ERR_UNSUPPORTED, "temporal blocking is provided for the thermal stencils only");
-    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_FUSED)
+    if (p->kernel < GS_KERNEL_AUTO || p->kernel > GS_KERNEL_STREAM)
         return fail(c, GS_ERR_INVALID_ARG, "plan.kernel must be a gs_kernel value");
     if (c->kind == GS_FDTD3D) {
         if (p->kernel == GS_KERNEL_AUTO) p->kernel = GS_KERNEL_COLUMN;
@@ -265,11 +266,26 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
     } else if (p->kernel == GS_KERNEL_FUSED) {
         return fail(c, GS_ERR_INVALID_ARG, "GS_KERNEL_FUSED is an FDTD kernel");
     }
+    if (p->kernel == GS_KERNEL_STREAM) {
+        if (c->kind != GS_HEAT3D) return fail(c, GS_ERR_INVALID_ARG, "the STREAM kernel runs 3D thermal stacks only");
+        if (t != 2) return fail(c, GS_ERR_INVALID_ARG, "the STREAM kernel runs temporal depth 2 only");
+        if (p->block_x != 256 && p->block_x != 512)
+            return fail(c, GS_ERR_INVALID_ARG, "the STREAM kernel takes plan.block_x 256 or 512");
+        if (p->tile_y < 1 || p->tile_y > (1 << 20))
+            return fail(c, GS_ERR_INVALID_ARG, "plan.tile_y (planes a block marches) must be in [1, 2^20]");
+    }
     const bool wave_ok = (c->kind == GS_HEAT2D) || (c->nz <= kWaveMaxNz);
-    if (is_heat(c) && p->kernel == GS_KERNEL_AUTO)
-        p->kernel = (t == 1 || c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz || (t == 2 && !wave_ok))
-                        ? GS_KERNEL_COLUMN
-                        : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
+    if (is_heat(c) && p->kernel == GS_KERNEL_AUTO) {
+        if (t == 2 && !wave_ok && (!block_x_given || p->block_x == 256 || p->block_x == 512)) {
+            // deep stacks at depth 2: the planes streamed through shared memory
+            p->kernel = GS_KERNEL_STREAM;
+            if (!block_x_given) p->block_x = 256;
+        } else {
+            p->kernel = (t == 1 || c->kind == GS_HEAT2D || c->nz <= kColumnMaxNz || (t == 2 && !wave_ok))
+                            ? GS_KERNEL_COLUMN
+                            : (wave_ok ? GS_KERNEL_WAVE : GS_KERNEL_TILE);
+        }
+    }
     if (p->kernel == GS_KERNEL_MARCH && t != 1)
         return fail(c, GS_ERR_INVALID_ARG, "the MARCH kernel runs depth 1 only");
     if (p->kernel == GS_KERNEL_TILE && t == 1)
@@ -384,7 +400,7 @@ gs_status ensure_descs(gs_ctx* c) {
             const int v1 = (c->plan.kernel == GS_KERNEL_WAVE || c->plan.kernel == GS_KERNEL_COLUMN ||
                             c->plan.kernel == GS_KERNEL_COLUMN_SMEM)
                                ? c->plan.kernel
-                               : GS_KERNEL_MARCH;
+                               : (c->plan.kernel == GS_KERNEL_STREAM ? GS_KERNEL_COLUMN : GS_KERNEL_MARCH);
             cudaError_t e = heat_desc(c->kind, c->dt, c->bc, a, c->plan.block_x, 1, v1, &c->desc[0][par]);
             if (e != cudaSuccess) return cuda_fail(c, e, "thermal kernel set-up");
             if (t > 1) {
@@ -926,6 +942,16 @@ gs_status gs_debug_check_read(uint64_t* refused, uint64_t* first) {
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "gs_debug_check_read");
     *refused = b1 + b2;
     *first = b1 ? f1 : f2;
+    return GS_OK;
+}
+
+gs_status gs_wait_timeouts(uint64_t* count_out) {
+    if (!count_out) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_wait_timeouts: NULL argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "gs_wait_timeouts");
+    const unsigned n = gs::heat_stream_timeouts_take();
+    if (n == ~0u) return cuda_fail(nullptr, cudaGetLastError(), "gs_wait_timeouts: reading the count");
+    *count_out = n;
     return GS_OK;
 }
 

@@ -363,6 +363,11 @@ cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, in
 size_t heat_temporal_smem(int nz, int tile_x, int tile_y, int depth);
 size_t heat_wave_smem(int nz3d, int depth, int vec);
 size_t heat_scol_smem(int nzm, int rows, int vec);
+// STREAM kernel (3D, depth 2): dynamic shared memory of a block (block_x 512:
+// 16 compute warps, else 8), and the count of its bounded stage waits that
+// ran out since the last call (read and cleared; ~0u if the read failed).
+size_t heat_stream_smem(gs_dtype dt, int block_x);
+unsigned heat_stream_timeouts_take();
 // heat_multi_kernel for (dt, bc) with MARCH tiles (blockDim.x threads x
 // `rows` rows) or COLUMN tiles (32 x `rows` threads, one row per warp row),
 // the latter also at temporal depth 2 or 4 (NULL for other combinations).

@@ -13,6 +13,8 @@
 // bit-identical.
 #include <algorithm>
 
+#include <cuda.h>  // CUtensorMap (the tensor map of the STREAM kernel's copies)
+
 #define GS_CHECK_THIS_UNIT  // checked builds bounds-check this unit's field accesses
 #include "common.cuh"
 
@@ -1268,6 +1270,412 @@ __global__ void __launch_bounds__(128, 4) heat_zmarch2_kernel(const HeatArgs a) 
     }
 }
 
+// ------------------------------------------------- STREAM (TMA z-march) ----
+//
+// Temporal depth 2 for 3D stacks: a march along z through shared memory, fed
+// by the Tensor Memory Accelerator.  A block owns an x-y tile of 128 stored
+// cells along x and 2W - 2 stored rows (W compute warps, each lane four
+// cells along x at two rows) and a chunk of `tile_y` planes.  The tile's
+// level-0 planes, with a halo of two rows and one 16-byte unit of columns on
+// each side, stream through a ring of kStreamStages shared-memory stages
+// (one cp.async.bulk.tensor box per plane, its completion counted on the
+// stage's mbarrier).  For each arriving plane z the block computes level 1
+// of plane z-1 into one of two shared level-1 planes and level 2 of plane
+// z-2, which it stores.  A thread keeps its own cells' last three level-1
+// planes in registers; x/y neighbours come from shared memory (x: within a
+// lane's four cells, by shuffle between lanes, and from the halo columns at
+// the warp's edges).  One extra warp computes the level-1 cells of the two
+// halo columns (x0-1 and x0+128) and issues the copies.  One barrier per
+// plane.  Each wait on a stage is bounded by kStreamWaitNs of the global
+// timer: on a time-out the block stops, counts it in g_stream_timeouts and
+// returns after its copies in flight have landed (waits bounded the same
+// way); its stores are then incomplete.
+constexpr int kStreamTileX = 128;  // stored cells along x per block (32 lanes x 4)
+constexpr int kStreamRows = 2;     // level-1 rows per compute thread
+constexpr int kStreamStages = 6;   // level-0 planes in the shared ring
+constexpr unsigned long long kStreamWaitNs = 1000000000ull;
+
+__device__ unsigned int g_stream_timeouts;
+
+template <typename ST>
+__host__ __device__ constexpr int stream_pad() { return 16 / (int)sizeof(ST); }  // halo columns on each side of a stage row
+template <typename ST>
+__host__ __device__ constexpr int stream_cols() { return kStreamTileX + 2 * stream_pad<ST>(); }
+__host__ __device__ constexpr size_t stream_align128(size_t b) { return (b + 127) / 128 * 128; }
+template <typename ST>
+__host__ __device__ constexpr size_t stream_stage_bytes(int W) { return stream_align128((size_t)(2 * W + 2) * stream_cols<ST>() * sizeof(ST)); }
+template <typename ST>
+__host__ __device__ constexpr size_t stream_smem(int W) {
+    return kStreamStages * stream_stage_bytes<ST>(W) + (size_t)2 * (2 * W) * stream_cols<ST>() * sizeof(float) +
+           kStreamStages * sizeof(unsigned long long);
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of `parity` to complete, for at most kStreamWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < kStreamWaitNs)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// One box of the tensor map at (x, y, z) into shared memory; completion is
+// counted on `bar` (which the issuing thread armed with the box's bytes).
+__device__ __forceinline__ void tma_load_plane(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                               unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Four consecutive cells of a shared stage row (16 bytes in f32, 8 in 16-bit types).
+template <typename ST>
+__device__ __forceinline__ void stage_get4(const ST* p, float (&v)[4]) {
+    if constexpr (sizeof(ST) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const uint2 raw = *reinterpret_cast<const uint2*>(p);
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = to_f32(e[i]);
+    }
+}
+__device__ __forceinline__ void l1_get4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void l1_put4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Four cells of one row: own values t, rows n / so, planes d / u, the
+// x-neighbours wv (left of cell 0) and ev (right of cell 3), both already
+// under the boundary rule at the tile's outer edges.  `edge` (warp-uniform):
+// the row is the grid's first or last row or lies outside it, the plane is
+// the first or last, or the tile ends inside the row; then the boundary rule
+// replaces each missing neighbour and plane 0 adds P.  The arithmetic is
+// heat_cell's, in packed pairs either way.
+template <typename ST, int BC>
+__device__ __forceinline__ void stream_row(bool edge, const float (&t)[4], const float (&n)[4], const float (&so)[4],
+                                           const float (&d)[4], const float (&u)[4], float wv, float ev, int x, int y,
+                                           int p, const HeatArgs& a, float (&out)[4]) {
+    float xs[4];
+    if (!edge) {
+        float zero[2] = {0.0f, 0.0f};
+        xs[0] = __fadd_rn(wv, t[1]);
+        xs[1] = __fadd_rn(t[0], t[2]);
+        xs[2] = __fadd_rn(t[1], t[3]);
+        xs[3] = __fadd_rn(t[2], ev);
+        heat_cell_x2<true>(t, n, so, xs, d, u, zero, a.c, out);
+        heat_cell_x2<true>(t + 2, n + 2, so + 2, xs + 2, d + 2, u + 2, zero, a.c, out + 2);
+    } else {
+        const int nx = a.nx, ny = a.ny, nz = a.nz;
+        const bool top = (y == 0), bot = (y + 1 >= ny), lo = (p == 0), hi = (p + 1 >= nz);
+        float nn[4], ss[4], dd[4], uu[4], pw[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float w = (c == 0) ? wv : t[c - 1];
+            const float e = (x + c + 1 >= nx) ? bnd<BC>(t[c]) : (c == 3 ? ev : t[c + 1]);
+            xs[c] = __fadd_rn(w, e);
+            nn[c] = top ? bnd<BC>(t[c]) : n[c];
+            ss[c] = bot ? bnd<BC>(t[c]) : so[c];
+            dd[c] = lo ? bnd<BC>(t[c]) : d[c];
+            uu[c] = hi ? bnd<BC>(t[c]) : u[c];
+        }
+        if (lo) {
+            const ST* prow = static_cast<const ST*>(a.P) + (long long)min(max(y, 0), ny - 1) * a.p_pitch;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (x + c < nx) pw[c] = load_scalar_rw<ST>(prow + x + c);
+        }
+        heat_cell_x2<true>(t, nn, ss, xs, dd, uu, pw, a.c, out);
+        heat_cell_x2<true>(t + 2, nn + 2, ss + 2, xs + 2, dd + 2, uu + 2, pw + 2, a.c, out + 2);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = as_stored<ST>(out[c]);
+}
+
+struct StreamArgs {
+    CUtensorMap map;  // Tin as (nx, ny, nz) elements, box (stream_cols, 2W + 2, 1); sets the alignment
+    HeatArgs a;
+};
+
+// What one step of a block's march needs besides the thread's own state:
+// shared-memory offsets of the three level-0 stages (planes p1-1, p1, p1+1)
+// and the two level-1 planes (written: p1, read: p2 = p1-1), the planes, and
+// which of the two levels the step computes.
+struct StreamStep {
+    unsigned lo, mid, hi, l1w, l1r;  // byte offsets into the block's shared memory
+    int p1, p2;
+    bool do1, do2;
+};
+
+// What a thread of the march keeps for every step: `tb`, its element
+// offset in a stage or level-1 plane (row 2w, column PX + 4 lane); `eb`, the
+// same at column PX; `gout`, its first cell of level-2 output row
+// y0 - 1 + 2w (plane 0); `x`, its first cell's column; `fast_x`: the tile
+// ends at or before the row's end; lane0 / lane31: the lane takes its outer
+// x-neighbour from the halo column, wfix / efix: that neighbour is outside
+// the grid; row_edge[k]: row k needs the boundary rule in y; store_row[k]:
+// row k is a stored level-2 row.
+template <typename ST>
+struct StreamThread {
+    int tb, eb, x;
+    ST* gout;
+    bool fast_x, lane0, lane31, wfix, efix;
+    bool row_edge[kStreamRows], store_row[kStreamRows];
+};
+
+// The x-neighbours left of cell 0 and right of cell 3 of a lane's four
+// cells: the neighbour lanes' cells, at the warp's ends the halo column's
+// (wl, er), and the boundary rule at the grid's ends.
+template <int BC, typename ST>
+__device__ __forceinline__ void stream_xnb(const StreamThread<ST>& th, const float (&t)[4], float wl, float er,
+                                           float& wv, float& ev) {
+    wv = __shfl_up_sync(0xffffffffu, t[3], 1);
+    ev = __shfl_down_sync(0xffffffffu, t[0], 1);
+    wv = th.lane0 ? wl : wv;
+    ev = th.lane31 ? er : ev;
+    wv = th.wfix ? bnd<BC>(t[0]) : wv;
+    ev = th.efix ? bnd<BC>(t[3]) : ev;
+}
+
+// One step of the march (PH = step mod 3 names the register slots of the
+// last three level-1 planes).
+template <typename ST, int BC, int W, int PH>
+__device__ __forceinline__ void stream_step(const StreamArgs& sa, unsigned char* smem, const StreamStep& st, int x0,
+                                            int y0, const StreamThread<ST>& th, float (&ring)[3][kStreamRows][4]) {
+    constexpr int PX = stream_pad<ST>(), BWC = stream_cols<ST>(), L1R = 2 * W;
+    constexpr int S_NEW = PH, S_MID = (PH + 2) % 3, S_OLD = (PH + 1) % 3;  // slots of p1, p1-1, p1-2
+    const HeatArgs& a = sa.a;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int nx = a.nx, nz = a.nz;
+    const int tb = th.tb, eb = th.eb, x = th.x;
+    const bool fast_x = th.fast_x;
+    if (st.do1) {
+        const ST* lo = reinterpret_cast<const ST*>(smem + st.lo);
+        const ST* mid = reinterpret_cast<const ST*>(smem + st.mid);
+        const ST* hi = reinterpret_cast<const ST*>(smem + st.hi);
+        float* l1w = reinterpret_cast<float*>(smem + st.l1w);
+        const int p1 = st.p1;
+        if (w < W) {
+            const bool zedge = !fast_x || p1 <= 0 || p1 + 1 >= nz;
+            float rowv[kStreamRows + 2][4];
+#pragma unroll
+            for (int k = 0; k < kStreamRows + 2; ++k) stage_get4<ST>(mid + tb + k * BWC, rowv[k]);
+#pragma unroll
+            for (int k = 0; k < kStreamRows; ++k) {
+                float d[4], u[4];
+                stage_get4<ST>(lo + tb + (k + 1) * BWC, d);
+                stage_get4<ST>(hi + tb + (k + 1) * BWC, u);
+                const float(&t)[4] = rowv[k + 1];
+                const float wl = to_f32(mid[eb + (k + 1) * BWC - 1]);             // x0-1 (broadcast)
+                const float er = to_f32(mid[eb + (k + 1) * BWC + kStreamTileX]);  // x0+128
+                float wv, ev;
+                stream_xnb<BC>(th, t, wl, er, wv, ev);
+                float out[4];
+                stream_row<ST, BC>(zedge || th.row_edge[k], t, rowv[k], rowv[k + 2], d, u, wv, ev, x,
+                                   y0 - 1 + w * kStreamRows + k, p1, a, out);
+                l1_put4(l1w + tb + k * BWC, out);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) ring[S_NEW][k][c] = out[c];
+            }
+        } else {
+            // the halo columns x0-1 (j < L1R) and x0+128 at level-1 row i
+            const int ny = a.ny;
+#pragma unroll
+            for (int j = lane; j < 2 * L1R; j += 32) {
+                const int side = j >= L1R, i = side ? j - L1R : j, y = y0 - 1 + i;
+                const int xh = side ? x0 + kStreamTileX : x0 - 1;
+                if (xh < 0 || xh >= nx) continue;
+                const int cc = side ? PX + kStreamTileX : PX - 1;
+                const int o = (i + 1) * BWC + cc;
+                const float tc = to_f32(mid[o]);
+                const float wl = (xh == 0) ? bnd<BC>(tc) : to_f32(mid[o - 1]);
+                const float er = (xh + 1 >= nx) ? bnd<BC>(tc) : to_f32(mid[o + 1]);
+                const float nn = (y == 0) ? bnd<BC>(tc) : to_f32(mid[o - BWC]);
+                const float ss = (y + 1 >= ny) ? bnd<BC>(tc) : to_f32(mid[o + BWC]);
+                const float dd = (p1 == 0) ? bnd<BC>(tc) : to_f32(lo[o]);
+                const float uu = (p1 + 1 >= nz) ? bnd<BC>(tc) : to_f32(hi[o]);
+                float pw = 0.0f;
+                if (p1 == 0)
+                    pw = load_scalar_rw<ST>(static_cast<const ST*>(a.P) + (long long)min(max(y, 0), ny - 1) * a.p_pitch + xh);
+                l1w[i * BWC + cc] = as_stored<ST>(heat_cell<true>(tc, nn, ss, wl, er, dd, uu, pw, a.c));
+            }
+        }
+    }
+    if (st.do2 && w < W) {
+        const float* l1r = reinterpret_cast<const float*>(smem + st.l1r);  // level 1 of plane p2 (previous step)
+        const int p2 = st.p2;
+        const bool zedge = !fast_x || p2 <= 0 || p2 + 1 >= nz;
+        ST* orow = th.gout + (long long)p2 * a.plane;
+#pragma unroll
+        for (int k = 0; k < kStreamRows; ++k) {
+            if (!th.store_row[k]) continue;  // a halo row of level 1, or outside the grid (warp-uniform)
+            const int y = y0 - 1 + w * kStreamRows + k;
+            // rows i-1 / i+1: the thread's own other row from registers, the other from shared memory
+            float nb[4], sb[4];
+            if (k == 0) {
+                l1_get4(l1r + tb - BWC, nb);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sb[c] = ring[S_MID][1][c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) nb[c] = ring[S_MID][0][c];
+                l1_get4(l1r + tb + 2 * BWC, sb);
+            }
+            const float(&t)[4] = ring[S_MID][k];
+            const float wl = l1r[eb + k * BWC - 1];
+            const float er = l1r[eb + k * BWC + kStreamTileX];
+            float wv, ev;
+            stream_xnb<BC>(th, t, wl, er, wv, ev);
+            float out[4];
+            stream_row<ST, BC>(zedge || th.row_edge[k], t, nb, sb, ring[S_OLD][k], ring[S_NEW][k], wv, ev, x, y, p2,
+                               a, out);
+            if (fast_x)
+                store_vecw<ST, 4>(orow + (long long)k * a.pitch, out, 4);
+            else if (x < nx)
+                store_vecw<ST, 4>(orow + (long long)k * a.pitch, out, nx - x);
+        }
+    }
+}
+
+template <typename ST, int BC, int W>
+__global__ void __launch_bounds__(32 * (W + 1), W <= 8 ? 2 : 1) heat_stream2_kernel(const __grid_constant__ StreamArgs sa) {
+    constexpr int PX = stream_pad<ST>(), BWC = stream_cols<ST>(), L1R = 2 * W;
+    constexpr unsigned SB = (unsigned)stream_stage_bytes<ST>(W);
+    constexpr unsigned L1B = (unsigned)(L1R * BWC * sizeof(float));  // one level-1 plane
+    constexpr unsigned BOX_BYTES = (unsigned)((L1R + 2) * BWC * sizeof(ST));
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kStreamStages * SB + 2 * L1B);
+    const HeatArgs& a = sa.a;
+    const uint3 blk = block_index(a.rev);
+    const int x0 = (int)blk.x * kStreamTileX;
+    const int y0 = (int)blk.y * (L1R - 2);
+    const int z0 = (int)blk.z * a.tile_y;
+    const int z1 = min(z0 + a.tile_y, a.nz);
+    const int n0 = z1 - z0 + 4;  // level-0 planes z0-2 .. z1+1
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const bool producer = w == W && lane == 0;
+    StreamThread<ST> th;
+    th.tb = w * kStreamRows * BWC + PX + 4 * lane;
+    th.eb = w * kStreamRows * BWC + PX;
+    th.x = x0 + 4 * lane;
+    th.fast_x = x0 + kStreamTileX <= a.nx;
+    th.lane0 = lane == 0;
+    th.lane31 = lane == 31;
+    th.wfix = lane == 0 && x0 == 0;
+    th.efix = lane == 31 && x0 + kStreamTileX >= a.nx;
+#pragma unroll
+    for (int k = 0; k < kStreamRows; ++k) {
+        const int i = w * kStreamRows + k, y = y0 - 1 + i;
+        th.row_edge[k] = y <= 0 || y + 1 >= a.ny;
+        th.store_row[k] = i >= 1 && i <= L1R - 2 && y < a.ny;
+    }
+    th.gout = static_cast<ST*>(a.Tout) + (long long)(y0 - 1 + w * kStreamRows) * a.pitch + x0 + 4 * lane;
+    // level-1 planes start at zero (the halo columns outside the grid are
+    // read, never used)
+    {
+        float* l1 = reinterpret_cast<float*>(smem + kStreamStages * SB);
+        const int tid = w * 32 + lane;
+        for (int e = tid; e < 2 * L1R * BWC; e += 32 * (W + 1)) l1[e] = 0.0f;
+    }
+    if (producer) {
+        for (int s = 0; s < kStreamStages; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait_then_trigger();  // the previous step's stores are visible from here on
+    if (producer) {
+        for (int q = 0; q < kStreamStages && q < n0; ++q) {
+            mbar_expect_tx(&bar[q], BOX_BYTES);
+            tma_load_plane(smem + q * SB, &sa.map, x0 - PX, y0 - 2, z0 - 2 + q, &bar[q]);
+        }
+    }
+    float ring[3][kStreamRows][4];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int k = 0; k < kStreamRows; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ring[s][k][c] = 0.0f;
+    // steps whose level-1 plane p1 = z0-3+r is computed
+    const int r1lo = max(2, max(z0 - 1, 0) - z0 + 3), r1hi = min(z1, a.nz - 1) - z0 + 3;
+    int issued = min(kStreamStages, n0);
+    bool failed = false;
+    int si = 0;            // stage of plane r
+    unsigned parity = 0;   // phase parity of that stage's fill
+    StreamStep st;
+    st.mid = (kStreamStages - 1) * SB;
+    st.hi = 0;
+    for (int r = 0; r < n0 && !failed; r += 3) {
+#pragma unroll
+        for (int ph = 0; ph < 3; ++ph) {
+            const int rr = r + ph;
+            if (rr >= n0 || failed) break;
+            const bool ok = mbar_wait_bounded(&bar[si], parity);
+            st.lo = st.mid;
+            st.mid = st.hi;
+            st.hi = si * SB;
+            st.l1w = kStreamStages * SB + (rr & 1) * L1B;
+            st.l1r = kStreamStages * SB + ((rr & 1) ^ 1) * L1B;
+            st.p1 = z0 - 3 + rr;
+            st.p2 = st.p1 - 1;
+            st.do1 = rr >= r1lo && rr <= r1hi;
+            st.do2 = rr >= 4;
+            if (ph == 0) stream_step<ST, BC, W, 0>(sa, smem, st, x0, y0, th, ring);
+            if (ph == 1) stream_step<ST, BC, W, 1>(sa, smem, st, x0, y0, th, ring);
+            if (ph == 2) stream_step<ST, BC, W, 2>(sa, smem, st, x0, y0, th, ring);
+            failed = __syncthreads_or(!ok) != 0;
+            if (++si == kStreamStages) {
+                si = 0;
+                parity ^= 1u;
+            }
+            // the stage of plane rr-2 is free: refill it with plane rr-2+kStreamStages
+            if (producer && !failed && rr >= 2 && issued < n0) {
+                const int q = issued++;
+                const unsigned sq = (unsigned)(q % kStreamStages);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&bar[sq], BOX_BYTES);
+                tma_load_plane(smem + sq * SB, &sa.map, x0 - PX, y0 - 2, z0 - 2 + q, &bar[sq]);
+            }
+        }
+    }
+    if (failed && producer) {
+        // let every copy in flight land before the block's shared memory is released
+        for (int q = max(issued - kStreamStages, 0); q < issued; ++q)
+            mbar_wait_bounded(&bar[q % kStreamStages], (unsigned)((q / kStreamStages) & 1));
+        atomicAdd(&g_stream_timeouts, 1u);
+    }
+}
+
 // ------------------------------------------------------------- factory ----
 
 namespace {
@@ -1397,11 +1805,85 @@ const void* pick_bc(gs_bc bc, bool is3d, int depth, int variant, int nz, int row
 
 int vec_elems(gs_dtype dt) { return dt == GS_F32 ? 4 : 8; }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links only the CUDA runtime).
+using PfnEncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+PfnEncodeTiled encode_tiled() {
+    static const PfnEncodeTiled fn = []() -> PfnEncodeTiled {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PfnEncodeTiled>(p);
+    }();
+    return fn;
+}
+
+// The STREAM kernel's launch: W compute warps (block_x 512: 16, else 8),
+// the tensor map of a.Tin (the grid's nx x ny x nz elements with its pitch;
+// reads outside them are filled with zeros), one box a plane.
+template <typename ST>
+cudaError_t stream_desc(gs_bc bc, const HeatArgs& a, int block_x, CUtensorMapDataType dtype, LaunchDesc* out) {
+    const int W = block_x >= 512 ? 16 : 8;
+    if (a.tile_y < 1 || a.nz < 1) return cudaErrorInvalidValue;
+    PfnEncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    StreamArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.a = a;
+    const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)a.pitch * sizeof(ST), (cuuint64_t)a.plane * sizeof(ST)};
+    const cuuint32_t box[3] = {(cuuint32_t)stream_cols<ST>(), (cuuint32_t)(W * kStreamRows + 2), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&sa.map, dtype, 3, const_cast<void*>(a.Tin), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const bool cl = (bc == GS_BC_CLAMP);
+    const void* f = W == 16 ? (cl ? (const void*)heat_stream2_kernel<ST, GS_BC_CLAMP, 16>
+                                  : (const void*)heat_stream2_kernel<ST, GS_BC_DIRICHLET0, 16>)
+                            : (cl ? (const void*)heat_stream2_kernel<ST, GS_BC_CLAMP, 8>
+                                  : (const void*)heat_stream2_kernel<ST, GS_BC_DIRICHLET0, 8>);
+    out->func = f;
+    const int ts = W * kStreamRows - 2;  // stored rows of a block
+    out->block = dim3(32, W + 1, 1);
+    out->grid = dim3((a.nx + kStreamTileX - 1) / kStreamTileX, (a.ny + ts - 1) / ts,
+                     (a.nz + a.tile_y - 1) / a.tile_y);
+    out->smem = stream_smem<ST>(W);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+    if (e != cudaSuccess) return e;
+    out->set_args(sa);
+    return cudaSuccess;
+}
+
 }  // namespace
+
+size_t heat_stream_smem(gs_dtype dt, int block_x) {
+    const int W = block_x >= 512 ? 16 : 8;
+    return dt == GS_F32 ? stream_smem<float>(W) : stream_smem<__half>(W);
+}
+
+unsigned heat_stream_timeouts_take() {
+    unsigned n = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&n, g_stream_timeouts, sizeof(n)) != cudaSuccess) return ~0u;
+    cudaMemcpyToSymbol(g_stream_timeouts, &zero, sizeof(zero));
+    return n;
+}
 
 cudaError_t heat_desc(gs_kind kind, gs_dtype dt, gs_bc bc, const HeatArgs& a, int block_x, int depth, int variant,
                       LaunchDesc* out) {
     const bool is3d = (kind == GS_HEAT3D);
+    if (variant == GS_KERNEL_STREAM) {
+        if (!is3d || depth != 2) return cudaErrorInvalidValue;
+        switch (dt) {
+            case GS_F32: return stream_desc<float>(bc, a, block_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, out);
+            case GS_BF16: return stream_desc<__nv_bfloat16>(bc, a, block_x, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, out);
+            case GS_F16: return stream_desc<__half>(bc, a, block_x, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, out);
+        }
+        return cudaErrorInvalidValue;
+    }
     const void* f = nullptr;
     switch (dt) {
         case GS_F32: f = pick_bc<float>(bc, is3d, depth, variant, a.nz, a.rows); break;

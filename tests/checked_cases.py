@@ -90,7 +90,7 @@ def multi(g, dims, n, S, plan):
         del bufs
 
 
-K_MARCH, K_WAVE, K_TILE, K_COLUMN, K_SMEM, K_FUSED = 1, 2, 3, 4, 5, 6
+K_MARCH, K_WAVE, K_TILE, K_COLUMN, K_SMEM, K_FUSED, K_STREAM = 1, 2, 3, 4, 5, 6, 7
 
 
 def cases():
@@ -112,12 +112,18 @@ def cases():
             else:
                 plans += [dict(kernel=K_COLUMN, temporal_depth=2, block_x=128, tile_y=5),
                           dict(kernel=K_COLUMN, temporal_depth=2, block_x=32, tile_y=32)]
+            if nz > 1:  # planes streamed through shared memory (any stack depth)
+                plans += [dict(kernel=K_STREAM, temporal_depth=2, block_x=256, tile_y=3),
+                          dict(kernel=K_STREAM, temporal_depth=2, block_x=512, tile_y=32)]
             for i, p in enumerate(plans):
                 out.append((f"heat {nx}x{ny}x{nz} bc{bc} plan{i}",
                             lambda g, a=(nx, ny, nz), p=p, bc=bc: heat(g, *a, 11, 4, p, bc=bc)))
     for nx, ny, nz in ((130, 20, 1), (40, 33, 8)):
         out.append((f"heat {nx}x{ny}x{nz} bf16 column2",
                     lambda g, a=(nx, ny, nz): heat(g, *a, 9, 4, dict(kernel=K_COLUMN, temporal_depth=2), dtype="bf16")))
+    out.append(("heat 200x30x12 bf16 stream2",
+                lambda g: heat(g, 200, 30, 12, 9, 4, dict(kernel=K_STREAM, temporal_depth=2, block_x=256, tile_y=5),
+                               dtype="bf16")))
     for N in (37, 128):
         for i, p in enumerate((dict(kernel=K_COLUMN, rows=1), dict(kernel=K_COLUMN, rows=8),
                                dict(kernel=K_MARCH, rows=4, block_x=32), dict(kernel=K_FUSED, rows=2))):

@@ -169,7 +169,9 @@ def test_wave_kernel_rejects_deep_stacks():
         with pytest.raises(g.GsError) as e:
             g.gs_set_plan(ctx, temporal_depth=2, kernel=g.GS_KERNEL_WAVE)
         assert e.value.status == g.GS_ERR_UNSUPPORTED
-        g.gs_set_plan(ctx, temporal_depth=2)  # AUTO picks the z-marching column kernel at depth 2
+        g.gs_set_plan(ctx, temporal_depth=2)  # AUTO streams the planes through shared memory at depth 2
+        assert g.gs_get_plan(ctx)["kernel"] == g.GS_KERNEL_STREAM
+        g.gs_set_plan(ctx, temporal_depth=2, block_x=128)  # and marches in registers with another block shape
         assert g.gs_get_plan(ctx)["kernel"] == g.GS_KERNEL_COLUMN
         g.gs_set_plan(ctx, temporal_depth=4)  # and the tile kernel at depth 4
         assert g.gs_get_plan(ctx)["kernel"] == g.GS_KERNEL_TILE

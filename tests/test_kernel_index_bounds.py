@@ -11,7 +11,8 @@ every global load and store must lie inside its buffer and inside its row
 the stores of a launch must cover every cell of the field exactly once.
 The 3D depth-t COLUMN kernel (one cell a lane, every plane of the column)
 and the z-marching depth-2 kernel of deep stacks are re-traced the same way,
-and so is the fused FDTD step (H and E in one launch, out of place).
+and so are the fused FDTD step (H and E in one launch, out of place) and
+the STREAM kernel (its tensor-copy boxes, shared-memory ring and stores).
 The formulas restate the kernels' address computations (csrc/heat.cu,
 csrc/fdtd.cu, csrc/multi.cu) for ragged shapes, so that a change to either
 is checked here before it runs on a GPU."""
@@ -252,6 +253,98 @@ def test_zmarch2_kernel_addresses(nx, ny, nz, esize, block_x, chunk):
     cells[:, :, :nx] = True
     assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
     every_block_stores(st & (y0 < ny) & (z0 < nz), bx, by, bz)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(256, 24, 40), (97, 41, 9), (130, 9, 17), (5, 3, 33), (121, 1, 12),
+                                      (2, 7, 10), (300, 30, 3), (128, 40, 1)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("block_x", [256, 512])
+@pytest.mark.parametrize("chunk", [1, 5, 32])
+def test_stream2_kernel_addresses(nx, ny, nz, esize, block_x, chunk):
+    # the STREAM kernel (3D, depth 2): tiles of 128 x (2W - 2) stored cells,
+    # W compute warps (four cells a lane at level-1 rows 2w, 2w+1), one
+    # halo warp; stage boxes of (128 + 2 PX) x (2W + 2) elements from
+    # (x0 - PX, y0 - 2, plane); a ring of 6 stages refilled after step r
+    # with plane r - 2 + 6; two level-1 planes
+    W = 16 if block_x >= 512 else 8
+    R = 2
+    PX = 16 // esize
+    BWC = 128 + 2 * PX
+    L1R, S = W * R, 6
+    BR = L1R + 2
+    stage_bytes = -(-(BR * BWC * esize) // 128) * 128
+    smem = S * stage_bytes + 2 * L1R * BWC * 4 + 8 * S  # stages, two level-1 planes, mbarriers
+    assert smem <= 227 * 1024 and (W > 8 or 2 * smem <= 228 * 1024)
+    assert BWC <= 256 and BR <= 256 and (BWC * esize) % 16 == 0 and BR * BWC * esize < (1 << 20)
+    assert (S * stage_bytes) % 16 == 0 and (S * stage_bytes + 2 * L1R * BWC * 4) % 8 == 0
+    grid = (-(-nx // 128), -(-ny // (L1R - 2)), -(-nz // chunk))
+    pitch = pitch_of(nx, esize)
+    plane = pitch * ny
+    size = plane * nz
+    bx, by, bz = [a.ravel() for a in np.meshgrid(*[np.arange(n) for n in grid], indexing="ij")]
+    x0, y0, z0 = bx * 128, by * (L1R - 2), bz * chunk
+    z1 = np.minimum(z0 + chunk, nz)
+    assert np.all(((x0 - PX) * esize) % 16 == 0)  # the box's x coordinate: 16-byte aligned
+    assert np.all(z0 < nz)  # no empty block along z
+    # the ring: simulate the copies and waits of one block (n0 depends only on the chunk)
+    for n0 in np.unique(z1 - z0 + 4):
+        resident = {}
+        fills = [0] * S
+        for q in range(min(S, n0)):
+            resident[q % S] = q
+        issued = min(S, n0)
+        for r in range(n0):
+            assert resident[r % S] == r and (r // S) & 1 == (fills[r % S]) & 1  # waited plane and phase
+            fills[r % S] += 1
+            if r >= 2:
+                for q in (r - 2, r - 1, r):  # the planes level 1 reads
+                    assert resident[q % S] == q
+            if r >= 2 and issued < n0:
+                assert issued == r - 2 + S
+                resident[issued % S] = issued
+                issued += 1
+        assert issued == n0
+    # per thread: stage reads (compute warps: rows i..i+2 of mid, row i+1 of lo/hi, cols PX+4l..+3 and the
+    # edge columns PX-1, PX+128; halo warp: rows i..i+2, cols PX-2..PX and PX+127..PX+129), L1 reads
+    lane = np.arange(32)
+    cols = PX + 4 * lane
+    assert cols.min() >= 0 and (cols + 3).max() < BWC and PX - 1 >= 0 and PX + 128 < BWC
+    for w in range(W):
+        i0 = R * w
+        assert 0 <= i0 and i0 + R + 1 < BR  # level 1: stage rows i0 .. i0 + R + 1
+        assert 0 <= i0 - 1 or w == 0  # level 2: level-1 rows i0 - 1 (not for the block's first row) ..
+        assert i0 + R < L1R or w == W - 1  # .. i0 + R (not for its last)
+    for i in range(L1R):  # the halo warp: stage rows i .. i + 2, columns around PX - 1 and PX + 128
+        assert 0 <= i and i + 2 < BR
+        for cc in (PX - 1, PX + 128):
+            assert 0 <= cc - 1 and cc + 1 < BWC
+    # stores of level 2: rows i in [1, L1R-2] (y = y0 - 1 + i < ny), lanes with x = x0 + 4 lane < nx,
+    # planes [z0, z1); P reads at clamped coordinates
+    covered = np.zeros(size, dtype=np.int64)
+    for w in range(W):
+        for k in range(R):
+            i = w * R + k
+            if not 1 <= i <= L1R - 2:
+                continue
+            y = y0 - 1 + i
+            for l in range(32):
+                x = x0 + 4 * l
+                nv = np.minimum(4, nx - x)
+                for dz in range(chunk):
+                    z = z0 + dz
+                    m = (y < ny) & (x < nx) & (z < z1)
+                    addr = (z * plane + y * pitch + x)[m]
+                    check_vec(addr, nv[m], (z * plane + y * pitch)[m], pitch, size)
+                    for c in range(4):
+                        mc = m & (c < nv)
+                        np.add.at(covered, (z * plane + y * pitch + x)[mc] + c, 1)
+            yc = np.clip(y, 0, ny - 1)
+            assert np.all(yc * pitch + np.clip(x0 + 4 * 31 + 3, 0, nx - 1) < pitch * ny)
+    cells = np.zeros((nz, ny, pitch), dtype=bool)
+    cells[:, :, :nx] = True
+    assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
+    # every block stores something (the grid is not over-sized)
+    assert np.all((x0 < nx) & (y0 < ny) & (z0 < nz))
 
 
 # ---------------------------------------------------------------- FDTD ----

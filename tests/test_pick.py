@@ -76,7 +76,9 @@ def test_plan_check_fills_defaults_and_resolves_auto(g):
     assert (p["kernel"], p["block_x"], p["rows"], p["temporal_depth"]) == (g.GS_KERNEL_COLUMN, 64, 4, 1)
     assert g.gs_plan_check(w3, dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_COLUMN  # nz <= 8: registers
     assert g.gs_plan_check(dict(w3, nz=16), dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_WAVE  # 9..16 planes
-    assert g.gs_plan_check(dict(w3, nz=17), dict(temporal_depth=2))["kernel"] == g.GS_KERNEL_COLUMN  # z-march
+    p17 = g.gs_plan_check(dict(w3, nz=17), dict(temporal_depth=2))  # deep stacks at depth 2: planes streamed
+    assert (p17["kernel"], p17["block_x"]) == (g.GS_KERNEL_STREAM, 256)
+    assert g.gs_plan_check(dict(w3, nz=17), dict(temporal_depth=2, block_x=128))["kernel"] == g.GS_KERNEL_COLUMN  # z-march
     assert g.gs_plan_check(dict(w3, nz=17), dict(temporal_depth=4))["kernel"] == g.GS_KERNEL_TILE
     w2 = dict(kind=g.GS_HEAT2D, dtype=g.GS_BF16, nx=4096, ny=4096, nz=1)
     assert g.gs_plan_check(w2, dict(temporal_depth=4))["kernel"] == g.GS_KERNEL_COLUMN
