@@ -45,9 +45,11 @@ import gs_inputs  # noqa: E402
 # The per-step baseline always uses plain launches (use_pdl forced off).
 WORKLOADS = {
     # temporal depth 2: the register COLUMN kernel advances two steps per
-    # launch (measured 6.95e11 against 6.73e11 cell-updates/s at depth 1)
+    # launch, with programmatic-dependent-launch edges between the graph's
+    # nodes (measured 7.29e11 cell-updates/s; 6.95e11 without the edges,
+    # 6.78e11 at depth 1, where the edges cost 5 %)
     "heat3d-512x512x8": dict(kind="heat3d", nx=512, ny=512, nz=8, iters=1000, S=100, depth=2,
-                             plan=dict(kernel=4, block_x=64)),
+                             plan=dict(kernel=4, block_x=64, use_pdl=1)),
     # a deep stack (nz > 8): the column kernel in 8-plane chunks
     "heat3d-256": dict(kind="heat3d", nx=256, ny=256, nz=256, iters=200, S=100, depth=1,
                        plan=dict(kernel=4, rows=4)),
@@ -707,7 +709,7 @@ def measure_workload(name, w, args, flush, with_e2e=True):
                 fused=bool(getattr(run, "fused", False)),
                 paper_conv_ms=paper_conv_ms, build_s=build_s, result=result,
                 launches=run.launches_per_step(S), l2_bytes=l2, node_floor_us=floor,
-                tuned_plan=getattr(run, "tuned", None))
+                tuned_plan=getattr(run, "tuned", None), plan=g_plan)
 
 
 SWEEP_S = (1, 10, 50, 100, 500, 1000)
@@ -885,7 +887,7 @@ def bench_line(args, w, m, clk, world):
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**config_of(args.workload, w, m["S"], m["depth"], world),
-                   **({"tuned_plan": m["tuned_plan"]} if m.get("tuned_plan") else {})},
+                   **({"tuned_plan": m["tuned_plan"]} if m.get("tuned_plan") else {"launch_plan": m.get("plan")})},
         "roofline": roof,
         "per_step_launch": {"value": per_step_value, "ms_per_step": statistics.mean(m["per_step_ms"]),
                             "ms_per_step_std": statistics.pstdev(m["per_step_ms"]) if len(m["per_step_ms"]) > 1 else 0.0,
