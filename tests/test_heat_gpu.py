@@ -141,7 +141,7 @@ def test_temporal_blocking_bit_identical(shape, depth):
             assert np.array_equal(heat_gpu(T0, P, n, S=5, plan=plan), base), f"column {kern} graph rows={rows}"
     if depth > 1:  # column kernel at depth 2 / 4: levels in registers (2D, stacks of <= 8 planes, and at
         # depth 2 deeper stacks marched in z chunks of tile_y planes)
-        for bx, rows, chunk in ((32, 0, 1), (64, 2, 5), (256, 0, 0)):
+        for bx, rows, chunk in ((32, 0, 1), (64, 2, 5), (128, 0, 3), (256, 0, 0)):
             plan = dict(temporal_depth=depth, kernel=g.GS_KERNEL_COLUMN, block_x=bx, rows=rows, tile_y=chunk)
             if nz > 8 and depth == 4:
                 with pytest.raises(g.GsError):
