@@ -2,7 +2,8 @@
 copies between every launch must give the undivided grid's result bit for
 bit (2D thermal 512^2, 3D thermal 512x512x8, FDTD 64^3 with the source, and
 ragged splits), per-step and in batch graphs with a peeled remainder, with
-and without PDL, at temporal depths the halo allows."""
+and without PDL, at temporal depths the halo allows (a deep stack also with
+the STREAM kernel at depth 2)."""
 import numpy as np
 import pytest
 
@@ -106,6 +107,22 @@ def test_ragged_slabs_bit_identical(shape, K, dtype, bc):
     for S in (0, 5):
         got, _, _ = slab_heat(T0, P, n, S, K, dtype=dtype, bc=bc)
         assert np.array_equal(got, base), (shape, K, S)
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_deep_stack_slabs_stream_depth2(K):
+    # a deep stack split along z, each slab stepped by the STREAM kernel at
+    # depth 2 (planes streamed through shared memory), halo 2
+    import paper_2501_09398_gb300 as g
+
+    T0, P = gs_inputs.heat_fields(130, 40, 37, seed=5)
+    n = 23  # eleven depth-2 launches and one single step
+    base = heat_gpu(T0, P, n, S=0)
+    plan = dict(temporal_depth=2, kernel=g.GS_KERNEL_STREAM, block_x=256, tile_y=5)
+    for S in (0, 6):
+        got, _, _ = slab_heat(T0, P, n, S, K, halo=2, plan=plan)
+        assert np.array_equal(got, base), (K, S)
+    assert g.gs_wait_timeouts() == 0
 
 
 def slab_fdtd(N, n, S, K, src, plan=None, dtype="f32"):
