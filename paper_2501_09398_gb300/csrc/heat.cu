@@ -83,6 +83,21 @@ __device__ __forceinline__ void heat_cell_x2(const float* t, const float* n, con
     f2_unpack(f2_fma(f2_pack(c.k, c.k), acc, T), out[0], out[1]);
 }
 
+// heat_cell_x2 (3D) with the z-neighbour sums d+u already formed (scalar
+// round-to-nearest adds, as the packed add rounds each half): for a plane
+// pair the planes below and above are no aligned register pair.
+__device__ __forceinline__ void heat_cell_x2z(const float* t, const float* n, const float* s, const float* xs,
+                                              const float* zs, const float* p, const HeatCoef& c, float* out) {
+    const unsigned long long T = f2_pack(t[0], t[1]);
+    const unsigned long long M2 = f2_pack(-2.0f, -2.0f);
+    unsigned long long acc = f2_pack(p[0], p[1]);
+    acc = f2_fma(f2_pack(c.cy, c.cy), f2_fma(M2, T, f2_add(f2_pack(n[0], n[1]), f2_pack(s[0], s[1]))), acc);
+    acc = f2_fma(f2_pack(c.cx, c.cx), f2_fma(M2, T, f2_pack(xs[0], xs[1])), acc);
+    acc = f2_fma(f2_pack(c.cz, c.cz), f2_sub(f2_pack(c.t_amb, c.t_amb), T), acc);
+    acc = f2_fma(f2_pack(c.cz2, c.cz2), f2_fma(M2, T, f2_pack(zs[0], zs[1])), acc);
+    f2_unpack(f2_fma(f2_pack(c.k, c.k), acc, T), out[0], out[1]);
+}
+
 // 16-byte shared-memory row segments (V is 4 or 8 floats).
 template <int V>
 __device__ __forceinline__ void sm_put(float* p, const float (&v)[V]) {
@@ -1065,19 +1080,19 @@ __device__ __forceinline__ void heat_column3_t_tile(const HeatArgs& a, int bx, i
             const int yg = y0 - T + j;
             float out[NZM];
             if (fast) {
-                float xsum[NZM], dn[NZM], up[NZM], pz[NZM];
+                float xsum[NZM], zsum[NZM], pz[NZM];
 #pragma unroll
                 for (int z = 0; z < NZM; ++z) {
                     const float t = row[j][z];
                     xsum[z] = __fadd_rn(__shfl_up_sync(0xffffffffu, t, 1), __shfl_down_sync(0xffffffffu, t, 1));
-                    dn[z] = (z > 0) ? row[j][z > 0 ? z - 1 : 0] : bnd<BC>(t);
-                    up[z] = (z + 1 < NZM) ? row[j][z + 1 < NZM ? z + 1 : z] : bnd<BC>(t);
+                    const float dn = (z > 0) ? row[j][z > 0 ? z - 1 : 0] : bnd<BC>(t);
+                    const float up = (z + 1 < NZM) ? row[j][z + 1 < NZM ? z + 1 : z] : bnd<BC>(t);
+                    zsum[z] = __fadd_rn(dn, up);
                     pz[z] = (z == 0) ? pr[j - 1] : 0.0f;
                 }
 #pragma unroll
                 for (int z = 0; z < NZM; z += 2)
-                    heat_cell_x2<true>(&row[j][z], &prev[z], &row[j + 1][z], &xsum[z], &dn[z], &up[z], &pz[z], a.c,
-                                       &out[z]);
+                    heat_cell_x2z(&row[j][z], &prev[z], &row[j + 1][z], &xsum[z], &zsum[z], &pz[z], a.c, &out[z]);
             } else {
 #pragma unroll
                 for (int z = 0; z < NZM; ++z) {
