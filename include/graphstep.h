@@ -893,7 +893,9 @@ gs_status gs_debug_injection_pending(int32_t *pending);
 /* Bounds-checked builds (libgraphstep_checked.so, compiled with GS_CHECKED
  * by `python paper_2501_09398_gb300/build.py --checked`; the paper has no
  * counterpart): every global field access of the thermal and FDTD stencil
- * kernels (loads, stores, material ids) is checked against a table of up to
+ * kernels (loads, stores, material ids; not the STREAM kernel's tensor
+ * copies, which the tensor map itself keeps inside the field: reads outside
+ * its nx x ny x nz elements are filled with zeros) is checked against a table of up to
  * GS_CHECK_MAX_RANGES byte ranges [lo, hi) of device memory the caller
  * registers: its field buffers and the device memory a context owns
  * (gs_debug_owned_ranges: the FDTD fused plan's second set, once a step has

@@ -31,6 +31,7 @@ def test_loop_bit_identical_to_per_step(shape):
     for S in (1, 2, 3, 7, 10, 18, 37, 50):
         got = heat_gpu(T0, P, n, S=S, plan=dict(graph_loop=1))
         assert np.array_equal(got, base), f"S={S}"
+    # depth 2 resolves to COLUMN (2D, thin stacks) or STREAM (17 planes)
     for plan in (dict(graph_loop=1, use_pdl=1), dict(graph_loop=1, temporal_depth=2),
                  dict(graph_loop=1, temporal_depth=4)):
         for S in (5, 6):

@@ -27,6 +27,9 @@ def _plans(g, nz):
            dict(kernel=g.GS_KERNEL_TILE, temporal_depth=4, tile_x=16, tile_y=8)]
     if nz <= 8:
         out += [dict(kernel=g.GS_KERNEL_COLUMN, rows=4), dict(kernel=g.GS_KERNEL_COLUMN_SMEM, rows=3)]
+    if nz > 1:
+        out += [dict(kernel=g.GS_KERNEL_COLUMN, temporal_depth=2, block_x=64),
+                dict(kernel=g.GS_KERNEL_STREAM, temporal_depth=2, block_x=256, tile_y=3)]
     return out
 
 
