@@ -63,7 +63,7 @@ typedef enum gs_status {
     GS_ERR_STATE = 4,       /* call not valid in the current state (e.g. unbound field) */
     GS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
     GS_ERR_NUMERIC = 6,     /* non-finite values where finite ones are required */
-    GS_ERR_UNSUPPORTED = 7  /* valid request this build does not provide (e.g. plan too large) */
+    GS_ERR_UNSUPPORTED = 7  /* valid request the library does not provide (e.g. plan too large) */
 } gs_status;
 
 /* GS_SKELETON is the paper's skeleton application (Sec. III-C): a vector of

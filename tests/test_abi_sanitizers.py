@@ -24,7 +24,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SAN = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined", "-Xcompiler",
        "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize-recover=undefined"]
 
-# The structs the driver uses, as the binding declares them (checked below).
+# The structs the harness uses, as the binding declares them (checked below).
 STRUCTS = '''
 import ctypes
 i32, i64 = ctypes.c_int32, ctypes.c_int64
