@@ -157,7 +157,16 @@ typedef struct gs_medium {
  *   AUTO   depth 1, 2D, and 3D with nz <= 8: COLUMN; other 3D stacks at
  *          depth 2: WAVE for nz <= 16, else STREAM (block_x 256 unless 256
  *          or 512 is given; with another block_x, COLUMN's z march); at
- *          depth 4: WAVE for nz <= 16, else TILE. */
+ *          depth 4: WAVE for nz <= 16, else TILE.
+ * FDTD variants: COLUMN (default) and MARCH run the two launches of a step
+ * (H, then E).  FUSED runs one launch a step, out of place into a second set
+ * of the six components that the context allocates (steps in pairs, so the
+ * state ends in the bound fields; an odd last step runs as the two
+ * launches), bit-identical to the two launches: with tile_y = 0 a thread
+ * owns four cells along i at one (j, k) and recomputes the H values of rows
+ * j-1 and planes k-1 that its E update reads; with tile_y >= 1 a block of
+ * 32 x rows threads marches tile_y planes in k and keeps H of the plane
+ * below in registers (only row j-1 is recomputed). */
 typedef enum gs_kernel {
     GS_KERNEL_AUTO = 0,
     GS_KERNEL_MARCH = 1,
@@ -190,7 +199,9 @@ typedef enum gs_traverse { GS_TRAVERSE_AUTO = 0, GS_TRAVERSE_FORWARD = 1, GS_TRA
  *                  COLUMN: j rows per block; FDTD MARCH: k planes per block
  *   tile_x, tile_y output tile of the TILE kernel; tile_y is also the z
  *                  chunk a block marches in the depth-2 COLUMN kernel of
- *                  stacks deeper than 8 planes
+ *                  stacks deeper than 8 planes and in the STREAM kernel, and
+ *                  the k planes a block marches in the FDTD FUSED kernel (0:
+ *                  no march; range [0, 2^20])
  *   temporal_depth thermal steps fused in one launch: 1, 2 or 4; a depth-t
  *                  launch is bit-identical to t depth-1 launches
  *   use_pdl        1: graph nodes (and per-step launches) use programmatic
@@ -207,8 +218,9 @@ typedef struct gs_plan {
     int32_t use_pdl;
     int32_t device_launch;
     int32_t kernel; /* gs_kernel; FDTD: COLUMN (default: four cells along i
-                       per thread, block 32 x rows x 8/rows) or MARCH
-                       (block_x threads marching `rows` k planes) */
+                       per thread, block 32 x rows x 8/rows), MARCH
+                       (block_x threads marching `rows` k planes) or FUSED
+                       (one launch a step; see gs_kernel) */
     int32_t graph_loop; /* 0: the floor(n/S) batches are floor(n/S) graph
                            launches (Listing 3).  1: one launch of a graph
                            whose conditional while node repeats the batch on

@@ -263,6 +263,8 @@ gs_status validate_plan(gs_ctx* c, gs_plan* p) {
         if (p->kernel == GS_KERNEL_AUTO) p->kernel = GS_KERNEL_COLUMN;
         if (p->kernel != GS_KERNEL_COLUMN && p->kernel != GS_KERNEL_MARCH && p->kernel != GS_KERNEL_FUSED)
             return fail(c, GS_ERR_INVALID_ARG, "FDTD kernels: GS_KERNEL_COLUMN, GS_KERNEL_MARCH or GS_KERNEL_FUSED");
+        if (p->kernel == GS_KERNEL_FUSED && (p->tile_y < 0 || p->tile_y > (1 << 20)))
+            return fail(c, GS_ERR_INVALID_ARG, "FDTD FUSED: plan.tile_y (k planes a block marches; 0: none) must be in [0, 2^20]");
     } else if (p->kernel == GS_KERNEL_FUSED) {
         return fail(c, GS_ERR_INVALID_ARG, "GS_KERNEL_FUSED is an FDTD kernel");
     }
@@ -460,6 +462,7 @@ gs_status ensure_descs(gs_ctx* c) {
                 c->fused_stride = stride;
             }
             FdtdArgs b = a;
+            b.kmarch = c->plan.tile_y;
             for (int f = 0; f < 6; ++f) b.g[f] = c->fused_set + (size_t)f * stride;
             b.rev = 0;
             e = fdtd_desc(c->dt, false, b, c->plan.block_x, GS_KERNEL_FUSED, &c->fdesc[0]);

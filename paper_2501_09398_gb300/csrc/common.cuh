@@ -293,6 +293,7 @@ struct FdtdArgs {
     int N;                // cells along i and j
     int Nk;               // cells along k (N for a cube; a sub-domain of a slab set may differ)
     int kc;               // k planes per block
+    int kmarch;           // fused step: k planes a block marches (0: one plane a thread, no march)
     long long pitch;      // elements per row (>= N+1)
     long long plane;      // pitch * (N+1)
     float s;              // courant number

@@ -231,18 +231,21 @@ __global__ void __launch_bounds__(256) fdtd_e_kernel(const FdtdArgs a) {
 // per-cell predicates (E only keeps the i = 0 wall cell of lane 0).  The
 // general body serves the rest with per-cell predicates.  ALN grids (N a
 // multiple of the 32 V cells of a warp) cover only i in [0, N): the i = N
-// column, where only Hx has an update, is an extra scalar cell of lane 31
-// (without it every (j, k) would need a second, one-cell warp).
+// column, where only Hx has an update, is an extra scalar cell of the lane
+// 31 whose vector ends at i = N, in the last block along i (without it every
+// (j, k) would need a second, one-cell warp); the lanes 31 of the other
+// blocks end where the next block's lane 0 begins and own no extra cell.
 
 // Ez[si, sj, sk] += source(n) and the step counter: the one thread that owns
-// the source cell (lane 31's extra cell i = N in ALN grids) does both.
+// the source cell (in ALN grids with si = N, the lane 31 that owns the extra
+// cell i = N) does both.
 template <typename ST, int V, bool ALN>
 __device__ __forceinline__ void fdtd_source(const FdtdArgs& a, int lane, int i0, int j, int k, long long o,
                                             float (&ez)[V], bool* extra_src) {
     *extra_src = false;
     if (j != a.sj || k != a.sk) return;
     const bool in_vec = (a.si >= i0 && a.si < i0 + V);
-    const bool in_extra = ALN && lane == 31 && a.si == i0 + V;
+    const bool in_extra = ALN && lane == 31 && i0 + V == a.N && a.si == a.N;
     if (!in_vec && !in_extra) return;
     const long long n = *a.counter;
     if (a.src_on) {
@@ -296,7 +299,7 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
         if (lane == 31) {  // i0 + V <= N: in range
             ez_r = load_scalar(Ez + o + V);
             ey_r = load_scalar(Ey + o + V);
-            if constexpr (EXTRA) {
+            if (EXTRA && i0 + V == N) {
                 ezj1_x = load_scalar(Ez + o + a.pitch + V);
                 eyk1_x = load_scalar(Ey + o + a.plane + V);
                 hx_x = load_scalar_rw(Hx + o + V);
@@ -361,7 +364,7 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
     store_vecw<ST, V>(Hy + o, hy, nv);
     store_vecw<ST, V>(Hz + o, hz, nv);
     if constexpr (EXTRA) {
-        if (lane == 31) {
+        if (lane == 31 && i0 + V == N) {
             if constexpr (MAT) hx_x = curl_sub_m(hx_x, s_med[id_x], ezj1_x, ez_r, eyk1_x, ey_r);
             else hx_x = curl_sub(hx_x, s, ezj1_x, ez_r, eyk1_x, ey_r);
             store_scalar(Hx + o + V, hx_x);
@@ -594,7 +597,7 @@ __device__ __forceinline__ void fdtd_fused_body(const FdtdArgs& a, int lane, int
         ey_r = load_scalar(Ey + o + V);
         eyjm_r = load_scalar(Ey + o + djm + V);
         ezkm_r = load_scalar(Ez + o + dkm + V);
-        if constexpr (ALN) {
+        if (ALN && i0 + V == N) {
             ezj1_x = load_scalar(Ez + o + dj1 + V);
             eyk1_x = load_scalar(Ey + o + dk1 + V);
         }
@@ -674,7 +677,8 @@ __device__ __forceinline__ void fdtd_fused_body(const FdtdArgs& a, int lane, int
     }
     // lane 31's extra cell i = N (ALN): Hx is its one update; E, Hy, Hz copied
     float x_ex = 0.f, x_hx = 0.f, x_hy = 0.f, x_hz = 0.f, x_ez = ez_r;
-    if (ALN && lane == 31) {
+    const bool xcell = ALN && lane == 31 && i0 + V == N;
+    if (xcell) {
         x_ex = load_scalar(Ex + o + V);
         x_hx = load_scalar(Hx + o + V);
         x_hy = load_scalar(Hy + o + V);
@@ -684,7 +688,7 @@ __device__ __forceinline__ void fdtd_fused_body(const FdtdArgs& a, int lane, int
     // the soft source on the new Ez, and the step counter
     if (j == a.sj && k == a.sk) {
         const bool in_vec = (a.si >= i0 && a.si < i0 + V);
-        const bool in_extra = ALN && lane == 31 && a.si == i0 + V;
+        const bool in_extra = xcell && a.si == N;
         if (in_vec || in_extra) {
             const long long n = *a.counter;
             if (a.src_on) {
@@ -708,7 +712,7 @@ __device__ __forceinline__ void fdtd_fused_body(const FdtdArgs& a, int lane, int
     store_vecw<ST, V>(static_cast<ST*>(a.g[HX]) + o, hxn, nv);
     store_vecw<ST, V>(static_cast<ST*>(a.g[HY]) + o, hyn, nv);
     store_vecw<ST, V>(static_cast<ST*>(a.g[HZ]) + o, hzn, nv);
-    if (ALN && lane == 31) {
+    if (xcell) {
         store_scalar(static_cast<ST*>(a.g[EX]) + o + V, x_ex);
         store_scalar(static_cast<ST*>(a.g[EY]) + o + V, ey_r);
         store_scalar(static_cast<ST*>(a.g[EZ]) + o + V, x_ez);
@@ -735,6 +739,239 @@ __global__ void __launch_bounds__(256, 2) fdtd_fused_kernel(const FdtdArgs a) {
         fdtd_fused_body<ST, false, ALN>(a, lane, i0, j, k);
 }
 
+// The fused step marching in k.  A block of 32 x BY threads owns 128 cells
+// along i (four a lane) x BY rows j x kmarch planes k and walks its planes
+// upwards.  The E update of plane k reads H^{n+1/2} of plane k-1 (Hy, Hx),
+// which the same thread computed on the plane before and keeps in registers
+// (the column form recomputes it from six more loads); E^n of plane k+1,
+// loaded for the H update, is E^n of plane k on the next plane, and Ey of
+// row j-1 likewise.  The j-1 values of H^{n+1/2} (Hz, Hx) belong to another
+// warp and are recomputed from loads, the i-1 values come from the
+// neighbouring lane (lane 0 recomputes its one cell), as in the column form.
+// Every value is formed by the same rounded operations on the same operands
+// as in the two launches, so the result is the same bit for bit.  A block
+// whose first plane k0 is above the wall recomputes H^{n+1/2} of plane k0-1
+// once before its march.
+template <typename ST, bool FAST, bool ALN>
+__device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, int lane, int i0, bool act_i, int j, int k,
+                                                 float (&ex)[kFdtdColumnCells], float (&ey)[kFdtdColumnCells],
+                                                 float (&ez)[kFdtdColumnCells], float (&hykm)[kFdtdColumnCells],
+                                                 float (&hxkm)[kFdtdColumnCells], float (&eyjm)[kFdtdColumnCells]) {
+    constexpr int V = kFdtdColumnCells;
+    const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
+    const long long P = a.pitch, PL = a.plane;
+    const long long dj1 = (FAST || j + 1 < M) ? P : 0;
+    const long long dk1 = (FAST || k + 1 < Mk) ? PL : 0;
+    const long long djm = (FAST || j >= 1) ? -P : 0;
+    // lanes past the arrays (act_i false) load at the start of their row
+    const long long o = (long long)k * PL + (long long)j * P + ((FAST || act_i) ? i0 : 0);
+    const ST* Ex = static_cast<const ST*>(a.f[EX]);
+    const ST* Ey = static_cast<const ST*>(a.f[EY]);
+    const ST* Ez = static_cast<const ST*>(a.f[EZ]);
+    const ST* Hx = static_cast<const ST*>(a.f[HX]);
+    const ST* Hy = static_cast<const ST*>(a.f[HY]);
+    const ST* Hz = static_cast<const ST*>(a.f[HZ]);
+    const float s = a.s;
+    float hx[V], hy[V], hz[V], ex1[V], ey1[V], ez1[V], ezj1[V], exj1[V];
+    float hzjm[V], hxjm[V], exjm[V], ezjm[V], eyjm1[V];
+    load_vecw<ST, V>(Hx + o, hx);
+    load_vecw<ST, V>(Hy + o, hy);
+    load_vecw<ST, V>(Hz + o, hz);
+    load_vecw<ST, V>(Ex + o + dk1, ex1);
+    load_vecw<ST, V>(Ey + o + dk1, ey1);
+    load_vecw<ST, V>(Ez + o + dk1, ez1);
+    load_vecw<ST, V>(Ez + o + dj1, ezj1);
+    load_vecw<ST, V>(Ex + o + dj1, exj1);
+    load_vecw<ST, V>(Hz + o + djm, hzjm);
+    load_vecw<ST, V>(Hx + o + djm, hxjm);
+    load_vecw<ST, V>(Ex + o + djm, exjm);
+    load_vecw<ST, V>(Ez + o + djm, ezjm);
+    load_vecw<ST, V>(Ey + o + djm + dk1, eyjm1);
+    // i+1 neighbours of lane 31's last cell; the aligned layout's i = N cell
+    const bool has_r = (lane == 31) && (FAST || (act_i && i0 + V < M));
+    float ez_r = 0.f, ey_r = 0.f, eyjm_r = 0.f, ezj1_x = 0.f, eyk1_x = 0.f;
+    if (has_r) {
+        ez_r = load_scalar(Ez + o + V);
+        ey_r = load_scalar(Ey + o + V);
+        eyjm_r = load_scalar(Ey + o + djm + V);
+        if (ALN && i0 + V == N) {
+            ezj1_x = load_scalar(Ez + o + dj1 + V);
+            eyk1_x = load_scalar(Ey + o + dk1 + V);
+        }
+    }
+    // lane 0's i-1 cell, for its H at i-1
+    float hz_l = 0.f, hy_l = 0.f, ey_l = 0.f, ex_l = 0.f, ez_l = 0.f, exj1_l = 0.f, exk1_l = 0.f;
+    if (lane == 0 && i0 >= 1 && (FAST || act_i)) {
+        hz_l = load_scalar(Hz + o - 1);
+        hy_l = load_scalar(Hy + o - 1);
+        ey_l = load_scalar(Ey + o - 1);
+        ex_l = load_scalar(Ex + o - 1);
+        ez_l = load_scalar(Ez + o - 1);
+        exj1_l = load_scalar(Ex + o + dj1 - 1);
+        exk1_l = load_scalar(Ex + o + dk1 - 1);
+    }
+    const float ez_n = __shfl_down_sync(0xffffffffu, ez[0], 1);
+    const float ey_n = __shfl_down_sync(0xffffffffu, ey[0], 1);
+    const float eyjm_n = __shfl_down_sync(0xffffffffu, eyjm[0], 1);
+    const float ez_last = (lane == 31) ? ez_r : ez_n;
+    const float ey_last = (lane == 31) ? ey_r : ey_n;
+    const float eyjm_last = (lane == 31) ? eyjm_r : eyjm_n;
+
+    // H^{n+1/2} of the own cells and of row j-1
+    float hxn[V], hyn[V], hzn[V], hzjmn[V], hxjmn[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        const float ez_ip = (e + 1 < V) ? ez[e + 1] : ez_last;
+        const float ey_ip = (e + 1 < V) ? ey[e + 1] : ey_last;
+        const float eyjm_ip = (e + 1 < V) ? eyjm[e + 1] : eyjm_last;
+        const bool iN = FAST || i < N;
+        hxn[e] = stored<ST>((FAST || (j < N && k < Nk)) ? curl_sub(hx[e], s, ezj1[e], ez[e], ey1[e], ey[e]) : hx[e]);
+        hyn[e] = stored<ST>((FAST || (iN && k < Nk)) ? curl_sub(hy[e], s, ex1[e], ex[e], ez_ip, ez[e]) : hy[e]);
+        hzn[e] = stored<ST>((FAST || (iN && j < N)) ? curl_sub(hz[e], s, ey_ip, ey[e], exj1[e], ex[e]) : hz[e]);
+        hzjmn[e] = stored<ST>(iN ? curl_sub(hzjm[e], s, eyjm_ip, eyjm[e], ex[e], exjm[e]) : hzjm[e]);
+        hxjmn[e] = stored<ST>((FAST || k < Nk) ? curl_sub(hxjm[e], s, ez[e], ezjm[e], eyjm1[e], eyjm[e]) : hxjm[e]);
+    }
+    float hz_first = __shfl_up_sync(0xffffffffu, hzn[V - 1], 1);
+    float hy_first = __shfl_up_sync(0xffffffffu, hyn[V - 1], 1);
+    if (lane == 0) {
+        const int im = i0 - 1;
+        hz_first = stored<ST>((im >= 0 && (FAST || j < N)) ? curl_sub(hz_l, s, ey[0], ey_l, exj1_l, ex_l) : hz_l);
+        hy_first = stored<ST>((im >= 0 && (FAST || k < Nk)) ? curl_sub(hy_l, s, exk1_l, ex_l, ez[0], ez_l) : hy_l);
+    }
+
+    // E^{n+1}; Hy and Hx of plane k-1 from the plane before
+    const bool j_int = FAST || (j >= 1 && j <= N - 1);
+    const bool k_int = FAST || (k >= 1 && k <= Nk - 1);
+    float exn[V], eyn[V], ezn[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int i = i0 + e;
+        const bool i_int = FAST ? (e > 0 || i0 > 0) : (i >= 1 && i <= N - 1);
+        const float hz_im = (e > 0) ? hzn[e - 1] : hz_first;
+        const float hy_im = (e > 0) ? hyn[e - 1] : hy_first;
+        exn[e] = ((FAST || i < N) && j_int && k_int) ? curl_add(ex[e], s, hzn[e], hzjmn[e], hyn[e], hykm[e]) : ex[e];
+        eyn[e] = ((FAST || j < N) && i_int && k_int) ? curl_add(ey[e], s, hxn[e], hxkm[e], hzn[e], hz_im) : ey[e];
+        ezn[e] = ((FAST || k < Nk) && i_int && j_int) ? curl_add(ez[e], s, hyn[e], hy_im, hxn[e], hxjmn[e]) : ez[e];
+    }
+    float x_ex = 0.f, x_hx = 0.f, x_hy = 0.f, x_hz = 0.f, x_ez = ez_r;
+    const bool xcell = ALN && lane == 31 && i0 + V == N;
+    if (xcell) {
+        x_ex = load_scalar(Ex + o + V);
+        x_hx = load_scalar(Hx + o + V);
+        x_hy = load_scalar(Hy + o + V);
+        x_hz = load_scalar(Hz + o + V);
+        if (FAST || (j < N && k < Nk)) x_hx = curl_sub(x_hx, s, ezj1_x, ez_r, eyk1_x, ey_r);
+    }
+    if (j == a.sj && k == a.sk && (FAST || act_i)) {
+        const bool in_vec = (a.si >= i0 && a.si < i0 + V);
+        const bool in_extra = xcell && a.si == N;
+        if (in_vec || in_extra) {
+            const long long n = *a.counter;
+            if (a.src_on) {
+                const float u = __fdiv_rn(__fsub_rn((float)n, a.delay), a.width);
+                const float gsrc = __fmul_rn(a.amp, expf(-u * u));
+                if (in_vec) {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (i0 + e == a.si) ezn[e] = __fadd_rn(ezn[e], gsrc);
+                } else {
+                    x_ez = __fadd_rn(x_ez, gsrc);
+                }
+            }
+            *a.counter = n + 1;
+        }
+    }
+    if (FAST || act_i) {
+        const int nv = FAST ? V : M - i0;
+        store_vecw<ST, V>(static_cast<ST*>(a.g[EX]) + o, exn, nv);
+        store_vecw<ST, V>(static_cast<ST*>(a.g[EY]) + o, eyn, nv);
+        store_vecw<ST, V>(static_cast<ST*>(a.g[EZ]) + o, ezn, nv);
+        store_vecw<ST, V>(static_cast<ST*>(a.g[HX]) + o, hxn, nv);
+        store_vecw<ST, V>(static_cast<ST*>(a.g[HY]) + o, hyn, nv);
+        store_vecw<ST, V>(static_cast<ST*>(a.g[HZ]) + o, hzn, nv);
+        if (xcell) {
+            store_scalar(static_cast<ST*>(a.g[EX]) + o + V, x_ex);
+            store_scalar(static_cast<ST*>(a.g[EY]) + o + V, ey_r);
+            store_scalar(static_cast<ST*>(a.g[EZ]) + o + V, x_ez);
+            store_scalar(static_cast<ST*>(a.g[HX]) + o + V, x_hx);
+            store_scalar(static_cast<ST*>(a.g[HY]) + o + V, x_hy);
+            store_scalar(static_cast<ST*>(a.g[HZ]) + o + V, x_hz);
+        }
+    }
+    // carried to plane k+1
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        ex[e] = ex1[e];
+        ey[e] = ey1[e];
+        ez[e] = ez1[e];
+        hykm[e] = hyn[e];
+        hxkm[e] = hxn[e];
+        eyjm[e] = eyjm1[e];
+    }
+}
+
+template <typename ST, bool ALN>
+__global__ void __launch_bounds__(256, 2) fdtd_fused_march_kernel(const FdtdArgs a) {
+    constexpr int V = kFdtdColumnCells;
+    pdl_wait_then_trigger();
+    const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
+    const int lane = threadIdx.x;
+    const uint3 blk = block_index(a.rev);
+    const int i0 = (blk.x * 32 + lane) * V;
+    const int j = blk.y * blockDim.y + threadIdx.y;
+    if (j >= M) return;  // the whole warp: j is one per warp
+    const int k0 = blk.z * a.kmarch;
+    const int k1 = min(k0 + a.kmarch, Mk);
+    const bool act_i = ALN || i0 < M;
+    const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
+    const bool fast_j = in_x && j >= 1 && j <= N - 1;
+    const long long P = a.pitch, PL = a.plane;
+    const long long dj1 = (j + 1 < M) ? P : 0;
+    const long long djm = (j >= 1) ? -P : 0;
+    const long long o = (long long)k0 * PL + (long long)j * P + (act_i ? i0 : 0);
+    const ST* Ex = static_cast<const ST*>(a.f[EX]);
+    const ST* Ey = static_cast<const ST*>(a.f[EY]);
+    const ST* Ez = static_cast<const ST*>(a.f[EZ]);
+    float ex[V], ey[V], ez[V], eyjm[V], hykm[V], hxkm[V];
+    load_vecw<ST, V>(Ex + o, ex);
+    load_vecw<ST, V>(Ey + o, ey);
+    load_vecw<ST, V>(Ez + o, ez);
+    load_vecw<ST, V>(Ey + o + djm, eyjm);
+    if (k0 >= 1) {
+        // H^{n+1/2} of Hy and Hx on plane k0-1, as its owner computes it
+        const ST* Hx = static_cast<const ST*>(a.f[HX]);
+        const ST* Hy = static_cast<const ST*>(a.f[HY]);
+        const float s = a.s;
+        float hyo[V], hxo[V], exkm[V], ezkm[V], eykm[V], ezj1km[V];
+        load_vecw<ST, V>(Hy + o - PL, hyo);
+        load_vecw<ST, V>(Hx + o - PL, hxo);
+        load_vecw<ST, V>(Ex + o - PL, exkm);
+        load_vecw<ST, V>(Ez + o - PL, ezkm);
+        load_vecw<ST, V>(Ey + o - PL, eykm);
+        load_vecw<ST, V>(Ez + o - PL + dj1, ezj1km);
+        const bool has_r = (lane == 31) && act_i && (i0 + V < M);
+        const float ezkm_r = has_r ? load_scalar(Ez + o - PL + V) : 0.f;
+        const float ezkm_n = __shfl_down_sync(0xffffffffu, ezkm[0], 1);
+        const float ezkm_last = (lane == 31) ? ezkm_r : ezkm_n;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const float ezkm_ip = (e + 1 < V) ? ezkm[e + 1] : ezkm_last;
+            hykm[e] = stored<ST>((i0 + e < N) ? curl_sub(hyo[e], s, ex[e], exkm[e], ezkm_ip, ezkm[e]) : hyo[e]);
+            hxkm[e] = stored<ST>((j < N) ? curl_sub(hxo[e], s, ezj1km[e], ezkm[e], ey[e], eykm[e]) : hxo[e]);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) hykm[e] = hxkm[e] = 0.f;  // k = 0 is a wall: not read
+    }
+    for (int k = k0; k < k1; ++k) {
+        if (fast_j && k >= 1 && k <= Nk - 1)
+            fdtd_march_plane<ST, true, ALN>(a, lane, i0, act_i, j, k, ex, ey, ez, hykm, hxkm, eyjm);
+        else
+            fdtd_march_plane<ST, false, ALN>(a, lane, i0, act_i, j, k, ex, ey, ez, hykm, hxkm, eyjm);
+    }
+}
+
 namespace {
 
 template <typename ST, bool MAT>
@@ -755,6 +992,24 @@ cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, 
     if (variant == GS_KERNEL_FUSED) {
         if (a.mat) return cudaErrorNotSupported;  // media: the two-launch column kernels
         const bool aln = (a.N % (32 * kFdtdColumnCells) == 0);
+        if (a.kmarch > 0) {
+            // block (32, rows): one warp a row j, marching kmarch planes
+            switch (dt) {
+                case GS_F32: out->func = aln ? (const void*)fdtd_fused_march_kernel<float, true> : (const void*)fdtd_fused_march_kernel<float, false>; break;
+                case GS_BF16: out->func = aln ? (const void*)fdtd_fused_march_kernel<__nv_bfloat16, true> : (const void*)fdtd_fused_march_kernel<__nv_bfloat16, false>; break;
+                case GS_F16: out->func = aln ? (const void*)fdtd_fused_march_kernel<__half, true> : (const void*)fdtd_fused_march_kernel<__half, false>; break;
+                default: return cudaErrorInvalidValue;
+            }
+            const int by = std::max(1, std::min(a.kc, 8));
+            const int M = a.N + 1, Mk = a.Nk + 1;
+            const int span = aln ? a.N : M;
+            out->block = dim3(32, by, 1);
+            out->grid = dim3((span + 32 * kFdtdColumnCells - 1) / (32 * kFdtdColumnCells), (M + by - 1) / by,
+                             (Mk + a.kmarch - 1) / a.kmarch);
+            out->smem = 0;
+            out->set_args(a);
+            return cudaSuccess;
+        }
         switch (dt) {
             case GS_F32: out->func = aln ? (const void*)fdtd_fused_kernel<float, true> : (const void*)fdtd_fused_kernel<float, false>; break;
             case GS_BF16: out->func = aln ? (const void*)fdtd_fused_kernel<__nv_bfloat16, true> : (const void*)fdtd_fused_kernel<__nv_bfloat16, false>; break;

@@ -126,10 +126,12 @@ def cases():
                                dtype="bf16")))
     for N in (37, 128):
         for i, p in enumerate((dict(kernel=K_COLUMN, rows=1), dict(kernel=K_COLUMN, rows=8),
-                               dict(kernel=K_MARCH, rows=4, block_x=32), dict(kernel=K_FUSED, rows=2))):
+                               dict(kernel=K_MARCH, rows=4, block_x=32), dict(kernel=K_FUSED, rows=2),
+                               dict(kernel=K_FUSED, rows=4, tile_y=6))):
             out.append((f"fdtd {N} plan{i}", lambda g, N=N, p=p: fdtd(g, N, 5, 2, p)))
     out.append(("fdtd 20 media", lambda g: fdtd(g, 20, 5, 2, dict(kernel=K_COLUMN, rows=2), media=True)))
     out.append(("fdtd 16 f16 fused", lambda g: fdtd(g, 16, 7, 3, dict(kernel=K_FUSED), dtype="f16")))
+    out.append(("fdtd 16 bf16 fused march", lambda g: fdtd(g, 16, 7, 3, dict(kernel=K_FUSED, tile_y=3), dtype="bf16")))
     dims = [(130, 17), (5, 9), (64, 64)]
     for i, p in enumerate((dict(kernel=K_MARCH), dict(kernel=K_COLUMN, rows=4),
                            dict(kernel=K_COLUMN, rows=2, temporal_depth=2))):

@@ -193,6 +193,38 @@ def test_wall_column_and_wall_source(oracle, N, src):
     assert all(np.array_equal(got[k], per_step[k]) for k in FDTD_NAMES)
 
 
+@pytest.mark.parametrize("src", [(128, 128, 128), (256, 100, 100), (127, 40, 200)])
+def test_two_blocks_along_i_aligned(oracle, src):
+    # N = 256: the aligned layout with two blocks along i.  Only the last
+    # block's lane 31 owns the extra i = N cell; the lanes 31 of the first
+    # block end where the second block's lane 0 begins (i = 128), which must
+    # be updated, and fed by the source, exactly once.  From random values
+    # in every entry, against the oracle, with the step counter; the fused
+    # step (column form and k march) bit-identical to the two launches.
+    import paper_2501_09398_gb300 as g
+
+    N, n = 256, 6
+    init = gs_inputs.fdtd_random_all(N, seed=11)
+    ref = _oracle_run(oracle, N, n, src=src, init=init)
+    ctx, fields = fdtd_setup(N, "f32", dict(kernel=g.GS_KERNEL_COLUMN, rows=2), src)
+    try:
+        fdtd_upload(ctx, N, init)
+        g.gs_step(ctx, n, 4)
+        got = fdtd_read(ctx, N)
+        assert g.gs_get_time(ctx) == n
+    finally:
+        g.gs_destroy(ctx)
+        del fields
+    assert rel_l2(fdtd_concat(got), fdtd_concat(ref)) <= FDTD_RL2
+    for name in FDTD_NAMES:  # the block seam i = 128 and the i = N column, element by element
+        for i in (127, 128, N):
+            d = np.abs(got[name][:, :, i].astype(np.float64) - ref[name][:, :, i])
+            assert np.all(d <= 1e-5 * (1.0 + np.abs(ref[name][:, :, i]))), (name, i)
+    for plan in (dict(kernel=g.GS_KERNEL_FUSED, rows=8), dict(kernel=g.GS_KERNEL_FUSED, rows=8, tile_y=32)):
+        fused = _gpu_run(N, n, 4, src=src, init=init, plan=plan)
+        assert all(np.array_equal(fused[k], got[k]) for k in FDTD_NAMES), plan
+
+
 def test_driven_energy_budget_on_gpu():
     # the soft source's exact discrete energy budget on the GPU's own FP32
     # fields, one step at a time: W^{n+1} - W^n = g(n) (Ez^{n+1} + Ez^n)[src]

@@ -11,8 +11,8 @@ every global load and store must lie inside its buffer and inside its row
 the stores of a launch must cover every cell of the field exactly once.
 The 3D depth-t COLUMN kernel (one cell a lane, every plane of the column)
 and the z-marching depth-2 kernel of deep stacks are re-traced the same way,
-and so are the fused FDTD step (H and E in one launch, out of place) and
-the STREAM kernel (its tensor-copy boxes, shared-memory ring and stores).
+and so are the fused FDTD step (H and E in one launch, out of place; its
+column form and its k march) and the STREAM kernel (its tensor-copy boxes, shared-memory ring and stores).
 The formulas restate the kernels' address computations (csrc/heat.cu,
 csrc/fdtd.cu, csrc/multi.cu) for ragged shapes, so that a change to either
 is checked here before it runs on a GPU."""
@@ -349,7 +349,7 @@ def test_stream2_kernel_addresses(nx, ny, nz, esize, block_x, chunk):
 
 # ---------------------------------------------------------------- FDTD ----
 
-@pytest.mark.parametrize("N", [9, 16, 37, 128, 130])
+@pytest.mark.parametrize("N", [9, 16, 37, 128, 130, 256])
 @pytest.mark.parametrize("esize", [4, 2])
 @pytest.mark.parametrize("rows", [1, 2, 8])
 def test_fdtd_column_kernel_addresses(N, esize, rows):
@@ -385,9 +385,9 @@ def test_fdtd_column_kernel_addresses(N, esize, rows):
                 check_vec((o + d)[m], nv[m], (row + d)[m], pitch, size)
             m = a & (lane == 31) & (fast | (i0 + V < M))
             check_vec((o + V)[m], 1, row[m], pitch, size)
-            if aln:  # lane 31's i = N cell: Ez at j+1, Ey at k+1, Hx
-                m = fast & (lane == 31)
-                assert np.all(i0[m] + V == N)
+            if aln:  # the i = N cell of the last block's lane 31: Ez at j+1, Ey at k+1, Hx
+                m = fast & (lane == 31) & (i0 + V == N)
+                assert m.sum() == N * N  # one per (j, k) of the FAST H body
                 for d in (pitch, plane, 0):
                     check_vec((o + d + V)[m], 1, (row + d)[m], pitch, size)
         else:
@@ -414,7 +414,8 @@ def test_fdtd_column_kernel_addresses(N, esize, rows):
     assert np.array_equal(owned.reshape(M, M, pitch) == 1, cells)
 
 
-@pytest.mark.parametrize("N,Nk", [(9, 9), (16, 16), (37, 37), (128, 128), (130, 130), (64, 17), (128, 33), (16, 1)])
+@pytest.mark.parametrize("N,Nk", [(9, 9), (16, 16), (37, 37), (128, 128), (130, 130), (64, 17), (128, 33), (16, 1),
+                                  (256, 9)])
 @pytest.mark.parametrize("esize", [4, 2])
 @pytest.mark.parametrize("rows", [1, 2, 8])
 def test_fdtd_fused_kernel_addresses(N, Nk, esize, rows):
@@ -450,8 +451,12 @@ def test_fdtd_fused_kernel_addresses(N, Nk, esize, rows):
     for d in (0, dk1, dj1, djm, djm + dk1, dkm, dkm + dj1):
         check_vec(o + d, V, row + d, pitch, size)
     has_r = (lane == 31) & (fast | (act & (i0 + V < M)))
-    for d in (0, djm, dkm) + ((dj1, dk1) if aln else ()):
+    for d in (0, djm, dkm):
         check_vec((o + d + V)[has_r], 1, (row + d)[has_r], pitch, size)
+    if aln:
+        xr = has_r & (i0 + V == N)
+        for d in (dj1, dk1):
+            check_vec((o + d + V)[xr], 1, (row + d)[xr], pitch, size)
     m = (lane == 0) & (i0 >= 1) & act
     for d in (0, dj1, dk1):
         check_vec((o + d - 1)[m], 1, (row + d)[m], pitch, size)
@@ -461,13 +466,95 @@ def test_fdtd_fused_kernel_addresses(N, Nk, esize, rows):
     for c in range(V):
         mm = act & (c < nv)
         np.add.at(owned, o[mm] + c, 1)
-    if aln:
-        mm = act & (lane == 31)
-        assert np.all(i0[mm] + V == N)
+    if aln:  # the i = N cell: the last block's lane 31 only
+        mm = act & (lane == 31) & (i0 + V == N)
         np.add.at(owned, o[mm] + V, 1)
     cells = np.zeros((Mk, M, pitch), dtype=bool)
     cells[:, :, :M] = True
     assert np.array_equal(owned.reshape(Mk, M, pitch) == 1, cells)
+
+
+@pytest.mark.parametrize("N,Nk", [(9, 9), (16, 16), (37, 37), (128, 128), (130, 130), (64, 17), (128, 33), (16, 1),
+                                  (256, 9)])
+@pytest.mark.parametrize("esize", [4, 2])
+@pytest.mark.parametrize("rows,kmarch", [(1, 1), (2, 5), (8, 16), (4, 300)])
+def test_fdtd_fused_march_kernel_addresses(N, Nk, esize, rows, kmarch):
+    # the fused step marching kmarch planes in k (block 32 x rows, one warp
+    # a row j): the prologue's own and j-1 vectors at k0 and, above the
+    # bottom wall, the plane k0-1 vectors (and lane 31's i+1 scalar); per
+    # plane the own, k+1, j+1, j-1 and j-1&k+1 vectors at offsets that
+    # collapse to 0 where they would leave the arrays, lanes past the
+    # arrays loading at the start of their row; lane 31's i+1 scalars,
+    # lane 0's i-1 scalars, the aligned layout's i = N cell; stores of all
+    # six components cover every element of the written set once
+    V = 4
+    M, Mk = N + 1, Nk + 1
+    aln = N % (32 * V) == 0
+    pitch = pitch_of(M, esize)
+    plane = pitch * M
+    size = plane * Mk
+    by_ = max(1, min(rows, 8))
+    span = N if aln else M
+    grid = (-(-span // (32 * V)), -(-M // by_), -(-Mk // kmarch))
+    bx, by, bz, lane, ty, _ = threads(grid, (32, by_, 1))
+    i0 = (bx * 32 + lane) * V
+    j = by * by_ + ty
+    k0 = bz * kmarch
+    k1 = np.minimum(k0 + kmarch, Mk)
+    live = j < M  # warps past the last row return at once
+    act_i = np.ones_like(i0, dtype=bool) if aln else (i0 < M)
+    in_x = np.ones_like(i0, dtype=bool) if aln else warp_all(i0 + V <= N, bx, by, bz, ty, np.zeros_like(ty))
+    fast_j = in_x & (j >= 1) & (j <= N - 1)
+    # prologue
+    o = k0 * plane + j * pitch + np.where(act_i, i0, 0)
+    row = k0 * plane + j * pitch
+    djm = np.where(j >= 1, -pitch, 0)
+    dj1 = np.where(j + 1 < M, pitch, 0)
+    m = live
+    for d in (0, djm):
+        check_vec((o + d)[m], V, (row + d)[m], pitch, size)
+    m = live & (k0 >= 1)
+    for d in (-plane, -plane + dj1):
+        check_vec((o + d)[m], V, (row + d)[m], pitch, size)
+    m = m & (lane == 31) & act_i & (i0 + V < M)
+    check_vec((o - plane + V)[m], 1, (row - plane)[m], pitch, size)
+    owned = np.zeros(size, dtype=np.int64)
+    for p in range(min(kmarch, Mk)):
+        k = k0 + p
+        m0 = live & (k < k1)
+        fast = fast_j & (k >= 1) & (k <= Nk - 1)
+        dj1 = np.where(fast | (j + 1 < M), pitch, 0)
+        dk1 = np.where(fast | (k + 1 < Mk), plane, 0)
+        djm = np.where(fast | (j >= 1), -pitch, 0)
+        act = fast | act_i
+        o = k * plane + j * pitch + np.where(act, i0, 0)
+        row = k * plane + j * pitch
+        for d in (0, dk1, dj1, djm, djm + dk1):
+            check_vec((o + d)[m0], V, (row + d)[m0], pitch, size)
+        has_r = m0 & (lane == 31) & (fast | (act_i & (i0 + V < M)))
+        for d in (0, djm):
+            check_vec((o + d + V)[has_r], 1, (row + d)[has_r], pitch, size)
+        if aln:
+            xr = has_r & (i0 + V == N)
+            for d in (dj1, dk1):
+                check_vec((o + d + V)[xr], 1, (row + d)[xr], pitch, size)
+        ml = m0 & (lane == 0) & (i0 >= 1) & act
+        for d in (0, dj1, dk1):
+            check_vec((o + d - 1)[ml], 1, (row + d)[ml], pitch, size)
+        ms = m0 & act
+        nv = np.where(fast, V, np.minimum(V, M - i0))
+        for c in range(V):
+            mm = ms & (c < nv)
+            np.add.at(owned, o[mm] + c, 1)
+        if aln:  # the i = N cell: the last block's lane 31 only
+            mm = ms & (lane == 31) & (i0 + V == N)
+            check_vec((o + V)[mm], 1, row[mm], pitch, size)
+            np.add.at(owned, o[mm] + V, 1)
+    cells = np.zeros((Mk, M, pitch), dtype=bool)
+    cells[:, :, :M] = True
+    assert np.array_equal(owned.reshape(Mk, M, pitch) == 1, cells)
+    # no block is empty
+    assert np.all(((by * by_) < M) & (k0 < Mk) & (bx * 32 * V < span))
 
 
 # ---------------------------------------------------- MARCH and WAVE ----
