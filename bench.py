@@ -1014,6 +1014,8 @@ def main():
                               ("heat3d-256", dict(depth=2, kernel=7, block_x=256), "stream2"),
                               ("fdtd-128", {}, "column"), ("fdtd-256", {}, "column"),
                               ("fdtd-128", dict(kernel=6, rows=4), "fused"), ("fdtd-256", dict(kernel=6, rows=8), "fused"),
+                              ("fdtd-128", dict(kernel=6, rows=8, tile_y=8), "fused_march"),
+                              ("fdtd-256", dict(kernel=6, rows=4, tile_y=8), "fused_march"),
                               ("fdtd-media-256", {}, "column"),
                               ("multi-64", {}, "tuned"),
                               ("heat2d-512", dict(depth=4, kernel=4, block_x=256), "column4"),
