@@ -140,10 +140,10 @@ def algo_bytes_per_launch(w, depth, elem=4, fused=False):
     (2D: P is the full plane), for t cell-updates per cell.  FDTD half-step
     (H or E kernel): read 6 components, write 3, per cell, plus the 1-byte
     material id in media; fused FDTD step (one launch per step): read 6
-    components and write 6."""
+    components and write 6 (and the id once in media)."""
     if w["kind"] == "fdtd":
         if fused:
-            return cells_of(w) * 12 * elem
+            return cells_of(w) * (12 * elem + (1 if w.get("media") else 0))
         return cells_of(w) * (9 * elem + (1 if w.get("media") else 0))
     if w["kind"] == "multi":
         return cells_of(w) * 3 * elem
@@ -1016,6 +1016,7 @@ def main():
                               ("fdtd-128", dict(kernel=6, rows=4), "fused"), ("fdtd-256", dict(kernel=6, rows=8), "fused"),
                               ("fdtd-128", dict(kernel=6, rows=8, tile_y=8), "fused_march"),
                               ("fdtd-256", dict(kernel=6, rows=4, tile_y=8), "fused_march"),
+                              ("fdtd-media-256", dict(kernel=6, rows=4, tile_y=8), "fused_march"),
                               ("fdtd-media-256", {}, "column"),
                               ("multi-64", {}, "tuned"),
                               ("heat2d-512", dict(depth=4, kernel=4, block_x=256), "column4"),

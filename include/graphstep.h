@@ -311,7 +311,8 @@ gs_status gs_set_fdtd_params(gs_ctx *ctx, const gs_fdtd_params *p);
  * then not read).  Rows need finite eps_r > 0, mu_r > 0, sigma >= 0,
  * sigma_m >= 0 (else GS_ERR_INVALID_ARG / GS_ERR_NUMERIC); n > 256 gives
  * GS_ERR_INVALID_ARG.  Stepping with a table needs the map bound
- * (GS_ERR_STATE) and the COLUMN kernels (GS_ERR_UNSUPPORTED for MARCH).
+ * (GS_ERR_STATE) and the COLUMN kernels or the FUSED march (plan.tile_y
+ * >= 1); GS_ERR_UNSUPPORTED for MARCH and for FUSED with tile_y = 0.
  * The table is copied; built graphs are discarded. */
 gs_status gs_set_fdtd_media(gs_ctx *ctx, const gs_medium *table, int32_t n);
 

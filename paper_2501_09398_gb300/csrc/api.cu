@@ -432,8 +432,9 @@ gs_status ensure_descs(gs_ctx* c) {
         a.med = nullptr;
         const bool fused = (c->plan.kernel == GS_KERNEL_FUSED);
         if (!c->media.empty()) {
-            if (c->plan.kernel != GS_KERNEL_COLUMN)
-                return fail(c, GS_ERR_UNSUPPORTED, "FDTD media run on the COLUMN kernels only");
+            if (c->plan.kernel != GS_KERNEL_COLUMN && !(fused && c->plan.tile_y >= 1))
+                return fail(c, GS_ERR_UNSUPPORTED,
+                            "FDTD media run on the COLUMN kernels or the FUSED march (plan.tile_y >= 1) only");
             gs_status ms = upload_media(c);
             if (ms != GS_OK) return ms;
             a.mat = static_cast<const unsigned char*>(c->ptr[GS_FIELD_MAT]);

@@ -752,8 +752,9 @@ __global__ void __launch_bounds__(256, 2) fdtd_fused_kernel(const FdtdArgs a) {
 // as in the two launches, so the result is the same bit for bit.  A block
 // whose first plane k0 is above the wall recomputes H^{n+1/2} of plane k0-1
 // once before its march.
-template <typename ST, bool FAST, bool ALN>
-__device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, int lane, int i0, bool act_i, int j, int k,
+template <typename ST, bool FAST, bool ALN, bool MAT>
+__device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, const float2* s_mh, const float2* s_me, int lane,
+                                                 int i0, bool act_i, int j, int k,
                                                  float (&ex)[kFdtdColumnCells], float (&ey)[kFdtdColumnCells],
                                                  float (&ez)[kFdtdColumnCells], float (&hykm)[kFdtdColumnCells],
                                                  float (&hxkm)[kFdtdColumnCells], float (&eyjm)[kFdtdColumnCells]) {
@@ -787,6 +788,12 @@ __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, int lane, in
     load_vecw<ST, V>(Ex + o + djm, exjm);
     load_vecw<ST, V>(Ez + o + djm, ezjm);
     load_vecw<ST, V>(Ey + o + djm + dk1, eyjm1);
+    // media: the material ids of the own cells and of row j-1
+    unsigned id[V], idjm[V];
+    if constexpr (MAT) {
+        load_ids<V>(a.mat + o, id);
+        load_ids<V>(a.mat + o + djm, idjm);
+    }
     // i+1 neighbours of lane 31's last cell; the aligned layout's i = N cell
     const bool has_r = (lane == 31) && (FAST || (act_i && i0 + V < M));
     float ez_r = 0.f, ey_r = 0.f, eyjm_r = 0.f, ezj1_x = 0.f, eyk1_x = 0.f;
@@ -801,7 +808,9 @@ __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, int lane, in
     }
     // lane 0's i-1 cell, for its H at i-1
     float hz_l = 0.f, hy_l = 0.f, ey_l = 0.f, ex_l = 0.f, ez_l = 0.f, exj1_l = 0.f, exk1_l = 0.f;
+    unsigned id_l = 0;
     if (lane == 0 && i0 >= 1 && (FAST || act_i)) {
+        if constexpr (MAT) id_l = load_id(a.mat + o - 1);
         hz_l = load_scalar(Hz + o - 1);
         hy_l = load_scalar(Hy + o - 1);
         ey_l = load_scalar(Ey + o - 1);
@@ -826,18 +835,33 @@ __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, int lane, in
         const float ey_ip = (e + 1 < V) ? ey[e + 1] : ey_last;
         const float eyjm_ip = (e + 1 < V) ? eyjm[e + 1] : eyjm_last;
         const bool iN = FAST || i < N;
-        hxn[e] = stored<ST>((FAST || (j < N && k < Nk)) ? curl_sub(hx[e], s, ezj1[e], ez[e], ey1[e], ey[e]) : hx[e]);
-        hyn[e] = stored<ST>((FAST || (iN && k < Nk)) ? curl_sub(hy[e], s, ex1[e], ex[e], ez_ip, ez[e]) : hy[e]);
-        hzn[e] = stored<ST>((FAST || (iN && j < N)) ? curl_sub(hz[e], s, ey_ip, ey[e], exj1[e], ex[e]) : hz[e]);
-        hzjmn[e] = stored<ST>(iN ? curl_sub(hzjm[e], s, eyjm_ip, eyjm[e], ex[e], exjm[e]) : hzjm[e]);
-        hxjmn[e] = stored<ST>((FAST || k < Nk) ? curl_sub(hxjm[e], s, ez[e], ezjm[e], eyjm1[e], eyjm[e]) : hxjm[e]);
+        if constexpr (MAT) {
+            const float2 m = s_mh[id[e]], mj = s_mh[idjm[e]];
+            hxn[e] = stored<ST>((FAST || (j < N && k < Nk)) ? curl_sub_m(hx[e], m, ezj1[e], ez[e], ey1[e], ey[e]) : hx[e]);
+            hyn[e] = stored<ST>((FAST || (iN && k < Nk)) ? curl_sub_m(hy[e], m, ex1[e], ex[e], ez_ip, ez[e]) : hy[e]);
+            hzn[e] = stored<ST>((FAST || (iN && j < N)) ? curl_sub_m(hz[e], m, ey_ip, ey[e], exj1[e], ex[e]) : hz[e]);
+            hzjmn[e] = stored<ST>(iN ? curl_sub_m(hzjm[e], mj, eyjm_ip, eyjm[e], ex[e], exjm[e]) : hzjm[e]);
+            hxjmn[e] = stored<ST>((FAST || k < Nk) ? curl_sub_m(hxjm[e], mj, ez[e], ezjm[e], eyjm1[e], eyjm[e]) : hxjm[e]);
+        } else {
+            hxn[e] = stored<ST>((FAST || (j < N && k < Nk)) ? curl_sub(hx[e], s, ezj1[e], ez[e], ey1[e], ey[e]) : hx[e]);
+            hyn[e] = stored<ST>((FAST || (iN && k < Nk)) ? curl_sub(hy[e], s, ex1[e], ex[e], ez_ip, ez[e]) : hy[e]);
+            hzn[e] = stored<ST>((FAST || (iN && j < N)) ? curl_sub(hz[e], s, ey_ip, ey[e], exj1[e], ex[e]) : hz[e]);
+            hzjmn[e] = stored<ST>(iN ? curl_sub(hzjm[e], s, eyjm_ip, eyjm[e], ex[e], exjm[e]) : hzjm[e]);
+            hxjmn[e] = stored<ST>((FAST || k < Nk) ? curl_sub(hxjm[e], s, ez[e], ezjm[e], eyjm1[e], eyjm[e]) : hxjm[e]);
+        }
     }
     float hz_first = __shfl_up_sync(0xffffffffu, hzn[V - 1], 1);
     float hy_first = __shfl_up_sync(0xffffffffu, hyn[V - 1], 1);
     if (lane == 0) {
         const int im = i0 - 1;
-        hz_first = stored<ST>((im >= 0 && (FAST || j < N)) ? curl_sub(hz_l, s, ey[0], ey_l, exj1_l, ex_l) : hz_l);
-        hy_first = stored<ST>((im >= 0 && (FAST || k < Nk)) ? curl_sub(hy_l, s, exk1_l, ex_l, ez[0], ez_l) : hy_l);
+        if constexpr (MAT) {
+            const float2 m = s_mh[id_l];
+            hz_first = stored<ST>((im >= 0 && (FAST || j < N)) ? curl_sub_m(hz_l, m, ey[0], ey_l, exj1_l, ex_l) : hz_l);
+            hy_first = stored<ST>((im >= 0 && (FAST || k < Nk)) ? curl_sub_m(hy_l, m, exk1_l, ex_l, ez[0], ez_l) : hy_l);
+        } else {
+            hz_first = stored<ST>((im >= 0 && (FAST || j < N)) ? curl_sub(hz_l, s, ey[0], ey_l, exj1_l, ex_l) : hz_l);
+            hy_first = stored<ST>((im >= 0 && (FAST || k < Nk)) ? curl_sub(hy_l, s, exk1_l, ex_l, ez[0], ez_l) : hy_l);
+        }
     }
 
     // E^{n+1}; Hy and Hx of plane k-1 from the plane before
@@ -850,9 +874,16 @@ __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, int lane, in
         const bool i_int = FAST ? (e > 0 || i0 > 0) : (i >= 1 && i <= N - 1);
         const float hz_im = (e > 0) ? hzn[e - 1] : hz_first;
         const float hy_im = (e > 0) ? hyn[e - 1] : hy_first;
-        exn[e] = ((FAST || i < N) && j_int && k_int) ? curl_add(ex[e], s, hzn[e], hzjmn[e], hyn[e], hykm[e]) : ex[e];
-        eyn[e] = ((FAST || j < N) && i_int && k_int) ? curl_add(ey[e], s, hxn[e], hxkm[e], hzn[e], hz_im) : ey[e];
-        ezn[e] = ((FAST || k < Nk) && i_int && j_int) ? curl_add(ez[e], s, hyn[e], hy_im, hxn[e], hxjmn[e]) : ez[e];
+        if constexpr (MAT) {
+            const float2 m = s_me[id[e]];
+            exn[e] = ((FAST || i < N) && j_int && k_int) ? curl_add_m(ex[e], m, hzn[e], hzjmn[e], hyn[e], hykm[e]) : ex[e];
+            eyn[e] = ((FAST || j < N) && i_int && k_int) ? curl_add_m(ey[e], m, hxn[e], hxkm[e], hzn[e], hz_im) : ey[e];
+            ezn[e] = ((FAST || k < Nk) && i_int && j_int) ? curl_add_m(ez[e], m, hyn[e], hy_im, hxn[e], hxjmn[e]) : ez[e];
+        } else {
+            exn[e] = ((FAST || i < N) && j_int && k_int) ? curl_add(ex[e], s, hzn[e], hzjmn[e], hyn[e], hykm[e]) : ex[e];
+            eyn[e] = ((FAST || j < N) && i_int && k_int) ? curl_add(ey[e], s, hxn[e], hxkm[e], hzn[e], hz_im) : ey[e];
+            ezn[e] = ((FAST || k < Nk) && i_int && j_int) ? curl_add(ez[e], s, hyn[e], hy_im, hxn[e], hxjmn[e]) : ez[e];
+        }
     }
     float x_ex = 0.f, x_hx = 0.f, x_hy = 0.f, x_hz = 0.f, x_ez = ez_r;
     const bool xcell = ALN && lane == 31 && i0 + V == N;
@@ -861,7 +892,10 @@ __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, int lane, in
         x_hx = load_scalar(Hx + o + V);
         x_hy = load_scalar(Hy + o + V);
         x_hz = load_scalar(Hz + o + V);
-        if (FAST || (j < N && k < Nk)) x_hx = curl_sub(x_hx, s, ezj1_x, ez_r, eyk1_x, ey_r);
+        if (FAST || (j < N && k < Nk)) {
+            if constexpr (MAT) x_hx = curl_sub_m(x_hx, s_mh[load_id(a.mat + o + V)], ezj1_x, ez_r, eyk1_x, ey_r);
+            else x_hx = curl_sub(x_hx, s, ezj1_x, ez_r, eyk1_x, ey_r);
+        }
     }
     if (j == a.sj && k == a.sk && (FAST || act_i)) {
         const bool in_vec = (a.si >= i0 && a.si < i0 + V);
@@ -931,16 +965,26 @@ __device__ __forceinline__ void march_prefetch_l2(const FdtdArgs& a, long long r
         asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const ST*>(a.f[f]) + o1));
 }
 
-template <typename ST, bool ALN>
+template <typename ST, bool ALN, bool MAT>
 __global__ void __launch_bounds__(256, 2) fdtd_fused_march_kernel(const FdtdArgs a) {
     constexpr int V = kFdtdColumnCells;
     pdl_wait_then_trigger();
+    // media: the H rows (da, db) and the E rows (ca, cb) of the table
+    __shared__ float2 s_mh[MAT ? 256 : 1], s_me[MAT ? 256 : 1];
+    if constexpr (MAT) {
+        const int nt = 32 * blockDim.y;
+        for (int t = threadIdx.x + 32 * threadIdx.y; t < 256; t += nt) {
+            s_mh[t] = __ldg(a.med + t);
+            s_me[t] = __ldg(a.med + 256 + t);
+        }
+        __syncthreads();
+    }
     const int N = a.N, M = N + 1, Nk = a.Nk, Mk = Nk + 1;
     const int lane = threadIdx.x;
     const uint3 blk = block_index(a.rev);
     const int i0 = (blk.x * 32 + lane) * V;
     const int j = blk.y * blockDim.y + threadIdx.y;
-    if (j >= M) return;  // the whole warp: j is one per warp
+    if (j >= M) return;  // the whole warp: j is one per warp (after the block's one barrier)
     const int k0 = blk.z * a.kmarch;
     const int k1 = min(k0 + a.kmarch, Mk);
     const bool act_i = ALN || i0 < M;
@@ -974,11 +1018,19 @@ __global__ void __launch_bounds__(256, 2) fdtd_fused_march_kernel(const FdtdArgs
         const float ezkm_r = has_r ? load_scalar(Ez + o - PL + V) : 0.f;
         const float ezkm_n = __shfl_down_sync(0xffffffffu, ezkm[0], 1);
         const float ezkm_last = (lane == 31) ? ezkm_r : ezkm_n;
+        unsigned idkm[V];
+        if constexpr (MAT) load_ids<V>(a.mat + o - PL, idkm);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             const float ezkm_ip = (e + 1 < V) ? ezkm[e + 1] : ezkm_last;
-            hykm[e] = stored<ST>((i0 + e < N) ? curl_sub(hyo[e], s, ex[e], exkm[e], ezkm_ip, ezkm[e]) : hyo[e]);
-            hxkm[e] = stored<ST>((j < N) ? curl_sub(hxo[e], s, ezj1km[e], ezkm[e], ey[e], eykm[e]) : hxo[e]);
+            if constexpr (MAT) {
+                const float2 m = s_mh[idkm[e]];
+                hykm[e] = stored<ST>((i0 + e < N) ? curl_sub_m(hyo[e], m, ex[e], exkm[e], ezkm_ip, ezkm[e]) : hyo[e]);
+                hxkm[e] = stored<ST>((j < N) ? curl_sub_m(hxo[e], m, ezj1km[e], ezkm[e], ey[e], eykm[e]) : hxo[e]);
+            } else {
+                hykm[e] = stored<ST>((i0 + e < N) ? curl_sub(hyo[e], s, ex[e], exkm[e], ezkm_ip, ezkm[e]) : hyo[e]);
+                hxkm[e] = stored<ST>((j < N) ? curl_sub(hxo[e], s, ezj1km[e], ezkm[e], ey[e], eykm[e]) : hxo[e]);
+            }
         }
     } else {
 #pragma unroll
@@ -991,13 +1043,19 @@ __global__ void __launch_bounds__(256, 2) fdtd_fused_march_kernel(const FdtdArgs
     for (int k = k0; k < k1; ++k) {
         if (k + kMarchPrefetch < k1) march_prefetch_l2<ST>(a, row_o, k + kMarchPrefetch);
         if (fast_j && k >= 1 && k <= Nk - 1)
-            fdtd_march_plane<ST, true, ALN>(a, lane, i0, act_i, j, k, ex, ey, ez, hykm, hxkm, eyjm);
+            fdtd_march_plane<ST, true, ALN, MAT>(a, s_mh, s_me, lane, i0, act_i, j, k, ex, ey, ez, hykm, hxkm, eyjm);
         else
-            fdtd_march_plane<ST, false, ALN>(a, lane, i0, act_i, j, k, ex, ey, ez, hykm, hxkm, eyjm);
+            fdtd_march_plane<ST, false, ALN, MAT>(a, s_mh, s_me, lane, i0, act_i, j, k, ex, ey, ez, hykm, hxkm, eyjm);
     }
 }
 
 namespace {
+
+template <typename ST>
+const void* fdtd_march_func(bool aln, bool mat) {
+    if (mat) return aln ? (const void*)fdtd_fused_march_kernel<ST, true, true> : (const void*)fdtd_fused_march_kernel<ST, false, true>;
+    return aln ? (const void*)fdtd_fused_march_kernel<ST, true, false> : (const void*)fdtd_fused_march_kernel<ST, false, false>;
+}
 
 template <typename ST, bool MAT>
 const void* fdtd_column_func(bool e_half, bool aln) {
@@ -1015,14 +1073,15 @@ const void* fdtd_func(bool e_half, bool col, bool mat, bool aln) {
 
 cudaError_t fdtd_desc(gs_dtype dt, bool e_half, const FdtdArgs& a, int block_x, int variant, LaunchDesc* out) {
     if (variant == GS_KERNEL_FUSED) {
-        if (a.mat) return cudaErrorNotSupported;  // media: the two-launch column kernels
         const bool aln = (a.N % (32 * kFdtdColumnCells) == 0);
+        if (a.mat && a.kmarch < 1) return cudaErrorNotSupported;  // media: the march or the two launches
         if (a.kmarch > 0) {
             // block (32, rows): one warp a row j, marching kmarch planes
+            const bool mat = (a.mat != nullptr);
             switch (dt) {
-                case GS_F32: out->func = aln ? (const void*)fdtd_fused_march_kernel<float, true> : (const void*)fdtd_fused_march_kernel<float, false>; break;
-                case GS_BF16: out->func = aln ? (const void*)fdtd_fused_march_kernel<__nv_bfloat16, true> : (const void*)fdtd_fused_march_kernel<__nv_bfloat16, false>; break;
-                case GS_F16: out->func = aln ? (const void*)fdtd_fused_march_kernel<__half, true> : (const void*)fdtd_fused_march_kernel<__half, false>; break;
+                case GS_F32: out->func = fdtd_march_func<float>(aln, mat); break;
+                case GS_BF16: out->func = fdtd_march_func<__nv_bfloat16>(aln, mat); break;
+                case GS_F16: out->func = fdtd_march_func<__half>(aln, mat); break;
                 default: return cudaErrorInvalidValue;
             }
             const int by = std::max(1, std::min(a.kc, 8));

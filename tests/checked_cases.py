@@ -130,6 +130,8 @@ def cases():
                                dict(kernel=K_FUSED, rows=4, tile_y=6))):
             out.append((f"fdtd {N} plan{i}", lambda g, N=N, p=p: fdtd(g, N, 5, 2, p)))
     out.append(("fdtd 20 media", lambda g: fdtd(g, 20, 5, 2, dict(kernel=K_COLUMN, rows=2), media=True)))
+    out.append(("fdtd 20 media fused march",
+                lambda g: fdtd(g, 20, 5, 2, dict(kernel=K_FUSED, rows=2, tile_y=4), media=True)))
     out.append(("fdtd 16 f16 fused", lambda g: fdtd(g, 16, 7, 3, dict(kernel=K_FUSED), dtype="f16")))
     out.append(("fdtd 16 bf16 fused march", lambda g: fdtd(g, 16, 7, 3, dict(kernel=K_FUSED, tile_y=3), dtype="bf16")))
     dims = [(130, 17), (5, 9), (64, 64)]

@@ -2,7 +2,8 @@
 
 A material map (uint8 ids, one per component location) and a table of
 (eps_r, sigma, mu_r, sigma_m) rows drive the lossy-medium Yee update in the
-column kernels.  Checked: parity with the oracle (relative L2 <= 1e-4, the
+column kernels and in the fused step's k march.  Checked: parity with the
+oracle (relative L2 <= 1e-4, the
 FDTD bar) on ragged cube sizes with the driven source and from a random
 field, bit-identity of graph batches and the device loop with per-step
 launches, a vacuum table reproducing the vacuum kernels bit for bit, the
@@ -95,6 +96,25 @@ def test_media_graphs_bit_identical():
     for S, plan in ((1, None), (7, None), (45, None), (9, dict(use_pdl=1)), (9, dict(rows=1)), (9, dict(rows=8)),
                     (6, dict(graph_loop=1))):
         got = _gpu(N, n, S, media=media, src=src, plan=plan)
+        assert all(np.array_equal(got[k], base[k]) for k in FDTD_NAMES), (S, plan)
+
+
+@pytest.mark.parametrize("N,src", [(21, (7, 11, 5)), (128, (128, 40, 70)), (256, (128, 100, 60))])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_media_fused_march_bit_identical(N, src, dtype):
+    # the fused step marching in k with the media coefficients (per-cell
+    # ids, the table's H and E rows in shared memory) against the two-launch
+    # column kernels, from random values in every entry: ragged, aligned,
+    # and aligned with two blocks along i
+    import paper_2501_09398_gb300 as g
+
+    media = gs_inputs.fdtd_media(N, n_mat=6, n_boxes=12, seed=N)
+    init = gs_inputs.fdtd_random_all(N, seed=N + 3)
+    n = 7
+    base = _gpu(N, n, 0, media=media, src=src, init=init, dtype=dtype)
+    for S, plan in ((0, dict(rows=4, tile_y=1)), (3, dict(rows=2, tile_y=5)), (7, dict(rows=8, tile_y=300))):
+        got = _gpu(N, n, S, media=media, src=src, init=init, dtype=dtype,
+                   plan=dict(kernel=g.GS_KERNEL_FUSED, **plan))
         assert all(np.array_equal(got[k], base[k]) for k in FDTD_NAMES), (S, plan)
 
 

@@ -486,7 +486,10 @@ def test_fdtd_fused_march_kernel_addresses(N, Nk, esize, rows, kmarch):
     # collapse to 0 where they would leave the arrays, lanes past the
     # arrays loading at the start of their row; lane 31's i+1 scalars,
     # lane 0's i-1 scalars, the aligned layout's i = N cell; stores of all
-    # six components cover every element of the written set once
+    # six components cover every element of the written set once.  In media
+    # the uint8 ids are read at the own, j-1 and k0-1 vectors' offsets and
+    # the i-1 and i = N scalars' (the map has the fields' pitch in
+    # elements), so the same checks cover them.
     V = 4
     M, Mk = N + 1, Nk + 1
     aln = N % (32 * V) == 0
