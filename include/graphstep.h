@@ -503,7 +503,7 @@ typedef struct gs_workload {
 
 /* Feature vectors (n x GS_MLP_INPUTS floats, host memory) of a workload
  * with each candidate: log2 nx, log2 ny, log2 nz, one-hot kind (3), kernels
- * per iteration, log2 n_iters, one-hot dtype (3), log2 S (0 for S = 0),
+ * per iteration (FDTD: 2, or 1 for the FUSED kernel; thermal 1), log2 n_iters, one-hot dtype (3), log2 S (0 for S = 0),
  * [S == 0], log2 block_x, log2 rows, temporal depth, [kernel is COLUMN or
  * COLUMN_SMEM], [kernel is COLUMN_SMEM] (GS_KERNEL_AUTO resolved as
  * gs_set_plan does).  Candidates must give block_x, rows and
@@ -566,8 +566,9 @@ gs_status gs_plan_check(const gs_workload *w, const gs_plan *plan, gs_plan *reso
  * a thermal or FDTD workload: each of the workload's candidate plans (the
  * library's default plan among them) with batch size 0 (per-step launches)
  * and the paper's swept graph batch sizes 1, 10, 50, 100, 500, 1000
- * (Sec. IV), plan after plan.  Plans carry block_x, rows, temporal_depth
- * and kernel; their other fields are 0.  Some plans may not fit the grid
+ * (Sec. IV), plan after plan.  Plans carry block_x, rows, temporal_depth,
+ * kernel and tile_y (the FDTD FUSED march's planes a block; 0 elsewhere);
+ * their other fields are 0.  Some plans may not fit the grid
  * (see gs_plan_check).  out == NULL (capacity 0) only counts: *n_out gets
  * the number.  Host only.  Errors: GS_ERR_INVALID_ARG (bad workload kind,
  * or capacity below the count, with *n_out set). */
@@ -603,7 +604,9 @@ const char *gs_mlp_builtin_info(void);
  * candidate (plan, batch size) gs_pick chooses for a run of n_iters
  * iterations of ctx's workload (kind, storage type, grid) with the
  * compiled-in models, applied with gs_set_plan (the candidate's block_x,
- * rows, temporal_depth and kernel; its other plan fields 0).  *plan_out (may
+ * rows, temporal_depth, kernel and tile_y; its other plan fields 0); on an
+ * FDTD context with a media table only the plans media run on (COLUMN and
+ * the FUSED march) are considered.  *plan_out (may
  * be NULL) receives the applied plan, *batch_out the batch size to pass to
  * gs_step (0: per-step launches), *pred_ms_per_iter (may be NULL) the
  * prediction.  Runs nothing of the workload.  Synchronous (on ctx's stream).

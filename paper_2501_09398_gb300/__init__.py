@@ -481,7 +481,7 @@ _sig("gs_candidates", [ctypes.POINTER(gs_workload), ctypes.POINTER(gs_tune_candi
 _sig("gs_pick", [ctypes.POINTER(_vp), _i32, ctypes.POINTER(gs_workload), ctypes.POINTER(gs_tune_candidate), _fp])
 _sig("gs_pick_analytic", [_vp, _i64, _i32, ctypes.POINTER(_i64), ctypes.POINTER(gs_model)])
 
-_SHAPE = ("block_x", "rows", "temporal_depth", "kernel")  # the plan fields a candidate sets
+_SHAPE = ("block_x", "rows", "temporal_depth", "kernel", "tile_y")  # the plan fields a candidate sets
 
 
 def _workload(workload: dict):
@@ -498,8 +498,8 @@ def gs_plan_check(workload: dict, plan: dict) -> dict:
 
 
 def gs_candidates(workload: dict):
-    """The (plan dict of block_x, rows, temporal_depth, kernel; S) pairs the
-    pickers choose from, plan after plan."""
+    """The (plan dict of block_x, rows, temporal_depth, kernel, tile_y; S)
+    pairs the pickers choose from, plan after plan."""
     w = _workload(workload)
     n = _i32()
     _check(_lib.gs_candidates(ctypes.byref(w), None, 0, ctypes.byref(n)))

@@ -99,10 +99,10 @@ def default_plan(w):
     """The library's default launch plan for the workload (what gs_create
     picks), used by the analytic and fixed pickers."""
     if w["kind"] == "fdtd":
-        return dict(block_x=64, rows=4, temporal_depth=1, kernel=GS_KERNEL_COLUMN)
+        return dict(block_x=64, rows=4, temporal_depth=1, kernel=GS_KERNEL_COLUMN, tile_y=0)
     small = w["nx"] * w["ny"] * w["nz"] <= (1 << 22)
     deep = w["kind"] == "heat3d" and w["nz"] > 8
-    return dict(block_x=64, rows=4 if (small or deep) else 8, temporal_depth=1, kernel=GS_KERNEL_COLUMN)
+    return dict(block_x=64, rows=4 if (small or deep) else 8, temporal_depth=1, kernel=GS_KERNEL_COLUMN, tile_y=0)
 
 
 def candidates(w):

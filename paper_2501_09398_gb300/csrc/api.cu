@@ -1042,6 +1042,8 @@ void ctx_workload(const gs_ctx* c, gs_workload* w) {
     w->n_iters = c->time;
 }
 
+bool ctx_has_media(const gs_ctx* c) { return c->kind == GS_FDTD3D && !c->media.empty(); }
+
 cudaError_t ctx_launch(gs_ctx* c, LaunchDesc& d) { return launch_one(c, d); }
 
 }  // namespace gs

@@ -299,7 +299,7 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
         if (lane == 31) {  // i0 + V <= N: in range
             ez_r = load_scalar(Ez + o + V);
             ey_r = load_scalar(Ey + o + V);
-            if (EXTRA && i0 + V == N) {
+            if constexpr (EXTRA) {
                 ezj1_x = load_scalar(Ez + o + a.pitch + V);
                 eyk1_x = load_scalar(Ey + o + a.plane + V);
                 hx_x = load_scalar_rw(Hx + o + V);
@@ -364,7 +364,7 @@ __device__ __forceinline__ void fdtd_h_column_body(const FdtdArgs& a, const floa
     store_vecw<ST, V>(Hy + o, hy, nv);
     store_vecw<ST, V>(Hz + o, hz, nv);
     if constexpr (EXTRA) {
-        if (lane == 31 && i0 + V == N) {
+        if (lane == 31) {
             if constexpr (MAT) hx_x = curl_sub_m(hx_x, s_med[id_x], ezj1_x, ez_r, eyk1_x, ey_r);
             else hx_x = curl_sub(hx_x, s, ezj1_x, ez_r, eyk1_x, ey_r);
             store_scalar(Hx + o + V, hx_x);
@@ -495,8 +495,13 @@ __global__ void __launch_bounds__(256, (MAT && sizeof(ST) == 4) ? 4 : 1) fdtd_h_
     const int j = blk.y * blockDim.y + threadIdx.y;
     const int k = blk.z * blockDim.z + threadIdx.z;
     const bool in_x = ALN || __all_sync(0xffffffffu, i0 + V <= N);
-    if (in_x && j < N && k < a.Nk) fdtd_h_column_body<ST, MAT, true, ALN>(a, s_med, lane, i0, j, k);
-    else fdtd_h_column_body<ST, MAT, false, false>(a, s_med, lane, i0, j, k);
+    // EXTRA: the last block along i of an ALN grid, whose lane 31 ends at i = N
+    if (in_x && j < N && k < a.Nk) {
+        if (ALN && blk.x == gridDim.x - 1) fdtd_h_column_body<ST, MAT, true, true>(a, s_med, lane, i0, j, k);
+        else fdtd_h_column_body<ST, MAT, true, false>(a, s_med, lane, i0, j, k);
+    } else {
+        fdtd_h_column_body<ST, MAT, false, false>(a, s_med, lane, i0, j, k);
+    }
 }
 
 template <typename ST, bool MAT, bool ALN>

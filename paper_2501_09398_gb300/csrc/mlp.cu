@@ -20,6 +20,10 @@ namespace {
 #include "costmodel_weights.inc"
 }  // namespace
 
+namespace gs {
+bool ctx_has_media(const gs_ctx* c);  // api.cu: an FDTD media table is set
+}  // namespace gs
+
 using namespace gs;
 
 namespace {
@@ -664,7 +668,9 @@ gs_status gs_features(const gs_workload* w, const gs_tune_candidate* c, int32_t 
         f[3] = w->kind == GS_HEAT2D;
         f[4] = w->kind == GS_HEAT3D;
         f[5] = w->kind == GS_FDTD3D;
-        f[6] = w->kind == GS_FDTD3D ? 2.f : 1.f;
+        // kernels per iteration: FDTD runs H and E as two launches, or one
+        // fused launch
+        f[6] = (w->kind == GS_FDTD3D && p.kernel != GS_KERNEL_FUSED) ? 2.f : 1.f;
         f[7] = (float)std::log2((double)w->n_iters);
         f[8] = w->dtype == GS_F32;
         f[9] = w->dtype == GS_BF16;
@@ -697,22 +703,25 @@ namespace {
 // sizes the paper sweeps (Sec. IV).
 constexpr int64_t kPickBatchSizes[] = {0, 1, 10, 50, 100, 500, 1000};
 
-gs_plan plan_of(int32_t block_x, int32_t rows, int32_t depth, int32_t kernel) {
+gs_plan plan_of(int32_t block_x, int32_t rows, int32_t depth, int32_t kernel, int32_t tile_y = 0) {
     gs_plan p{};
     p.block_x = block_x;
     p.rows = rows;
     p.temporal_depth = depth;
     p.kernel = kernel;
+    p.tile_y = tile_y;
     return p;
 }
 
 bool same_shape(const gs_plan& a, const gs_plan& b) {
-    return a.block_x == b.block_x && a.rows == b.rows && a.temporal_depth == b.temporal_depth && a.kernel == b.kernel;
+    return a.block_x == b.block_x && a.rows == b.rows && a.temporal_depth == b.temporal_depth &&
+           a.kernel == b.kernel && a.tile_y == b.tile_y;
 }
 
 // The launch plans the pickers (and the cost model's sweep) consider for a
-// workload, in sweep order.  FDTD: COLUMN with 1, 2, 4, 8 rows and two
-// k-march shapes.  Thermal: COLUMN with 2, 4, 8 rows; COLUMN_SMEM (2D and
+// workload, in sweep order.  FDTD: COLUMN with 1, 2, 4, 8 rows, two
+// k-march shapes and the fused step's k march (8 planes a block) with 4 and
+// 8 rows.  Thermal: COLUMN with 2, 4, 8 rows; COLUMN_SMEM (2D and
 // stacks of at most 8 planes); three MARCH shapes; WAVE at depth 2 and 4
 // (2D and stacks of at most 16 planes); COLUMN at depth 2 and 4 (2D and
 // stacks of at most 8 planes).  The library's default plan is included.
@@ -724,6 +733,7 @@ std::vector<gs_plan> candidate_plans(const gs_workload& w) {
         for (int32_t r : {1, 2, 4, 8}) v.push_back(plan_of(64, r, 1, C));
         v.push_back(plan_of(64, 4, 1, M));
         v.push_back(plan_of(32, 16, 1, M));
+        for (int32_t r : {4, 8}) v.push_back(plan_of(64, r, 1, GS_KERNEL_FUSED, 8));
         dflt = plan_of(64, 4, 1, C);
     } else {
         const bool is2d = w.kind == GS_HEAT2D;
@@ -775,8 +785,13 @@ gs_status gs_candidates(const gs_workload* w, gs_tune_candidate* out, int32_t ca
     return GS_OK;
 }
 
-gs_status gs_pick(gs_mlp* const* models, int32_t k, const gs_workload* w, gs_tune_candidate* best,
-                  float* pred_ms_per_iter) {
+}  // extern "C"
+
+namespace {
+
+// gs_pick over the candidates that `runnable` accepts (all when it is NULL).
+gs_status pick_impl(gs_mlp* const* models, int32_t k, const gs_workload* w, bool (*runnable)(const gs_plan&),
+                    gs_tune_candidate* best, float* pred_ms_per_iter) {
     if (!models || k < 1 || !w || !best) return global_fail(GS_ERR_INVALID_ARG, "gs_pick: bad arguments");
     for (int32_t i = 0; i < k; ++i)
         if (!models[i]) return global_fail(GS_ERR_INVALID_ARG, "gs_pick: NULL model");
@@ -791,7 +806,7 @@ gs_status gs_pick(gs_mlp* const* models, int32_t k, const gs_workload* w, gs_tun
     const std::string saved = gs_last_error(nullptr);
     std::vector<gs_tune_candidate> ok;
     for (const gs_tune_candidate& c : all)
-        if (gs_plan_check(w, &c.plan, nullptr) == GS_OK) ok.push_back(c);
+        if ((!runnable || runnable(c.plan)) && gs_plan_check(w, &c.plan, nullptr) == GS_OK) ok.push_back(c);
     global_fail(GS_OK, saved);
     if (ok.empty()) return global_fail(GS_ERR_UNSUPPORTED, "gs_pick: no candidate plan fits this grid");
     std::vector<float> X(ok.size() * (size_t)NI);
@@ -813,6 +828,20 @@ gs_status gs_pick(gs_mlp* const* models, int32_t k, const gs_workload* w, gs_tun
     *best = ok[(size_t)row];
     if (pred_ms_per_iter) *pred_ms_per_iter = std::exp(pred);
     return GS_OK;
+}
+
+// FDTD in media runs on the COLUMN kernels and the fused march
+bool media_runs(const gs_plan& p) {
+    return p.kernel == GS_KERNEL_COLUMN || (p.kernel == GS_KERNEL_FUSED && p.tile_y >= 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_pick(gs_mlp* const* models, int32_t k, const gs_workload* w, gs_tune_candidate* best,
+                  float* pred_ms_per_iter) {
+    return pick_impl(models, k, w, nullptr, best, pred_ms_per_iter);
 }
 
 const char* gs_mlp_builtin_info(void) { return kBuiltinInfo; }
@@ -854,7 +883,8 @@ gs_status gs_pick_ctx(gs_ctx* ctx, int64_t n_iters, gs_plan* plan_out, int64_t* 
     gs_tune_candidate best{};
     std::string why;
     if (st == GS_OK) {
-        st = gs_pick(models, kBuiltinMembers, &w, &best, pred_ms_per_iter);
+        st = pick_impl(models, kBuiltinMembers, &w, ctx_has_media(ctx) ? media_runs : nullptr, &best,
+                       pred_ms_per_iter);
         if (st != GS_OK) why = models[0]->err.empty() ? gs_last_error(nullptr) : models[0]->err;
     } else {
         why = gs_last_error(nullptr);

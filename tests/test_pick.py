@@ -35,7 +35,7 @@ def test_candidates_are_the_swept_candidates(g, tables):
 
 
 def test_every_swept_plan_passes_the_plan_check(g, tables):
-    # all 24,444 swept (plan, S) pairs ran on the GPU (status 0), so the
+    # all 26,712 swept (plan, S) pairs ran on the GPU (status 0), so the
     # host-side check must accept each plan on its workload
     cm, pairs = tables
     seen = 0
