@@ -176,6 +176,38 @@ def test_pick_ctx_applies_the_builtin_ensembles_choice(w):
         del fields
 
 
+@pytest.mark.parametrize("N", [40, 128, 256])
+def test_pick_ctx_in_media_takes_a_plan_media_run_on(N):
+    # an FDTD context with a media table: the pick is among the plans media
+    # run on (COLUMN, the fused march), never the k-march kernels, and the
+    # context steps with it, bit for bit as the per-step COLUMN launches
+    import gs_inputs
+    import paper_2501_09398_gb300 as g
+    from gsutil import FDTD_NAMES, fdtd_read, fdtd_setup, fdtd_upload
+
+    media = gs_inputs.fdtd_media(N, n_mat=4, n_boxes=6, seed=N)
+    init = gs_inputs.fdtd_random_all(N, seed=N + 1)
+    src, n = (N // 2, N // 3, N // 2), 9
+    outs = []
+    for pick in (True, False):
+        ctx, fields = fdtd_setup(N, "f32", None, src, media=media)
+        try:
+            fdtd_upload(ctx, N, init)
+            if pick:
+                plan, S, pred = g.gs_pick_ctx(ctx, 1000)
+                assert plan["kernel"] == g.GS_KERNEL_COLUMN or \
+                    (plan["kernel"] == g.GS_KERNEL_FUSED and plan["tile_y"] >= 1), plan
+                assert math.isfinite(pred) and pred > 0
+            else:
+                S = 0
+            g.gs_step(ctx, n, S)
+            outs.append(fdtd_read(ctx, N))
+        finally:
+            g.gs_destroy(ctx)
+            del fields
+    assert all(np.array_equal(outs[0][k], outs[1][k]) for k in FDTD_NAMES)
+
+
 def test_pick_ctx_refuses_a_skeleton_context():
     import paper_2501_09398_gb300 as g
 
