@@ -964,10 +964,10 @@ __device__ __forceinline__ void march_prefetch_l2(const FdtdArgs& a, long long r
     const long long o1 = (k + 1 < Mk) ? o + a.plane : o;
 #pragma unroll
     for (int f = HX; f <= HZ; ++f)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const ST*>(a.f[f]) + o));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(static_cast<const ST*>(a.f[f]) + o)));
 #pragma unroll
     for (int f = EX; f <= EZ; ++f)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const ST*>(a.f[f]) + o1));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(static_cast<const ST*>(a.f[f]) + o1)));
 }
 
 template <typename ST, bool ALN, bool MAT>
