@@ -970,6 +970,38 @@ __device__ __forceinline__ void march_prefetch_l2(const FdtdArgs& a, long long r
         asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(static_cast<const ST*>(a.f[f]) + o1)));
 }
 
+// A vector load whose lines L2 keeps ahead of normally cached ones (an
+// evict_last cache policy): the planes at a chunk's lower edge, which the
+// block of the chunk below reads again at the end of its march, one block's
+// run later.
+template <typename ST, int W>
+__device__ __forceinline__ void load_vecw_keep(const ST* p, float (&v)[W], unsigned long long pol) {
+    static_assert(W * sizeof(ST) == 8 || W * sizeof(ST) == 16, "8- or 16-byte access");
+    if (!GS_CHK(p, W * sizeof(ST))) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = 0.f;
+        return;
+    }
+    const size_t g = __cvta_generic_to_global(p);
+    if constexpr (W * sizeof(ST) == 16) {
+        uint4 raw;
+        asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(raw.x), "=r"(raw.y), "=r"(raw.z), "=r"(raw.w)
+                     : "l"(g), "l"(pol));
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
+    } else {
+        uint2 raw;
+        asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                     : "=r"(raw.x), "=r"(raw.y)
+                     : "l"(g), "l"(pol));
+        const ST* e = reinterpret_cast<const ST*>(&raw);
+#pragma unroll
+        for (int i = 0; i < W; ++i) v[i] = to_f32(e[i]);
+    }
+}
+
 template <typename ST, bool ALN, bool MAT>
 __global__ void __launch_bounds__(256, 2) fdtd_fused_march_kernel(const FdtdArgs a) {
     constexpr int V = kFdtdColumnCells;
@@ -1002,23 +1034,25 @@ __global__ void __launch_bounds__(256, 2) fdtd_fused_march_kernel(const FdtdArgs
     const ST* Ex = static_cast<const ST*>(a.f[EX]);
     const ST* Ey = static_cast<const ST*>(a.f[EY]);
     const ST* Ez = static_cast<const ST*>(a.f[EZ]);
+    unsigned long long keep;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
     float ex[V], ey[V], ez[V], eyjm[V], hykm[V], hxkm[V];
-    load_vecw<ST, V>(Ex + o, ex);
-    load_vecw<ST, V>(Ey + o, ey);
-    load_vecw<ST, V>(Ez + o, ez);
-    load_vecw<ST, V>(Ey + o + djm, eyjm);
+    load_vecw_keep<ST, V>(Ex + o, ex, keep);
+    load_vecw_keep<ST, V>(Ey + o, ey, keep);
+    load_vecw_keep<ST, V>(Ez + o, ez, keep);
+    load_vecw_keep<ST, V>(Ey + o + djm, eyjm, keep);
     if (k0 >= 1) {
         // H^{n+1/2} of Hy and Hx on plane k0-1, as its owner computes it
         const ST* Hx = static_cast<const ST*>(a.f[HX]);
         const ST* Hy = static_cast<const ST*>(a.f[HY]);
         const float s = a.s;
         float hyo[V], hxo[V], exkm[V], ezkm[V], eykm[V], ezj1km[V];
-        load_vecw<ST, V>(Hy + o - PL, hyo);
-        load_vecw<ST, V>(Hx + o - PL, hxo);
-        load_vecw<ST, V>(Ex + o - PL, exkm);
-        load_vecw<ST, V>(Ez + o - PL, ezkm);
-        load_vecw<ST, V>(Ey + o - PL, eykm);
-        load_vecw<ST, V>(Ez + o - PL + dj1, ezj1km);
+        load_vecw_keep<ST, V>(Hy + o - PL, hyo, keep);
+        load_vecw_keep<ST, V>(Hx + o - PL, hxo, keep);
+        load_vecw_keep<ST, V>(Ex + o - PL, exkm, keep);
+        load_vecw_keep<ST, V>(Ez + o - PL, ezkm, keep);
+        load_vecw_keep<ST, V>(Ey + o - PL, eykm, keep);
+        load_vecw_keep<ST, V>(Ez + o - PL + dj1, ezj1km, keep);
         const bool has_r = (lane == 31) && act_i && (i0 + V < M);
         const float ezkm_r = has_r ? load_scalar(Ez + o - PL + V) : 0.f;
         const float ezkm_n = __shfl_down_sync(0xffffffffu, ezkm[0], 1);
