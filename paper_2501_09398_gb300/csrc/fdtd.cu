@@ -45,6 +45,41 @@ __device__ __forceinline__ float curl_add_m(float f, float2 m, float a, float b,
     return __fmaf_rn(m.y, __fsub_rn(__fsub_rn(a, b), __fsub_rn(c, d)), __fmul_rn(m.x, f));
 }
 
+// curl_sub / curl_add of two adjacent cells in Blackwell's packed FP32 pair
+// operations (sub/fma .rn.f32x2), each half rounded as the scalar form
+// rounds it, in the same order: ((a - b) - (c - d)), then the fused
+// multiply-add.  An operand pair is two adjacent cells of a register array;
+// a difference whose operands are shifted by one cell (an i-neighbour) is
+// formed by scalar subtractions and passed in as a pair.
+namespace {
+__device__ __forceinline__ unsigned long long p2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void p2_out(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long p2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long p2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// sc * (t1 - t2) + f for a cell pair (sc = -s: curl_sub; s: curl_add)
+__device__ __forceinline__ void curl2(const float* f, float sc, unsigned long long t1, unsigned long long t2, float* out) {
+    p2_out(p2_fma(p2(sc, sc), p2_sub(t1, t2), p2(f[0], f[1])), out[0], out[1]);
+}
+// a - b for a cell pair of register arrays
+__device__ __forceinline__ unsigned long long d2(const float* a, const float* b) {
+    return p2_sub(p2(a[0], a[1]), p2(b[0], b[1]));
+}
+}  // namespace
+
 template <typename ST>
 __global__ void __launch_bounds__(256) fdtd_h_kernel(const FdtdArgs a) {
     constexpr int V = Vec<ST>::N;
@@ -833,6 +868,32 @@ __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, const float2
 
     // H^{n+1/2} of the own cells and of row j-1
     float hxn[V], hyn[V], hzn[V], hzjmn[V], hxjmn[V];
+    if constexpr (FAST && !MAT) {
+        // every cell updates: packed pairs; the i-shifted differences scalar
+        float dz[V], dy[V], dyj[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            dz[e] = __fsub_rn((e + 1 < V) ? ez[e + 1] : ez_last, ez[e]);
+            dy[e] = __fsub_rn((e + 1 < V) ? ey[e + 1] : ey_last, ey[e]);
+            dyj[e] = __fsub_rn((e + 1 < V) ? eyjm[e + 1] : eyjm_last, eyjm[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < V; e += 2) {
+            curl2(&hx[e], -s, d2(&ezj1[e], &ez[e]), d2(&ey1[e], &ey[e]), &hxn[e]);
+            curl2(&hy[e], -s, d2(&ex1[e], &ex[e]), p2(dz[e], dz[e + 1]), &hyn[e]);
+            curl2(&hz[e], -s, p2(dy[e], dy[e + 1]), d2(&exj1[e], &ex[e]), &hzn[e]);
+            curl2(&hzjm[e], -s, p2(dyj[e], dyj[e + 1]), d2(&ex[e], &exjm[e]), &hzjmn[e]);
+            curl2(&hxjm[e], -s, d2(&ez[e], &ezjm[e]), d2(&eyjm1[e], &eyjm[e]), &hxjmn[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            hxn[e] = stored<ST>(hxn[e]);
+            hyn[e] = stored<ST>(hyn[e]);
+            hzn[e] = stored<ST>(hzn[e]);
+            hzjmn[e] = stored<ST>(hzjmn[e]);
+            hxjmn[e] = stored<ST>(hxjmn[e]);
+        }
+    } else
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const int i = i0 + e;
@@ -873,6 +934,26 @@ __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, const float2
     const bool j_int = FAST || (j >= 1 && j <= N - 1);
     const bool k_int = FAST || (k >= 1 && k <= Nk - 1);
     float exn[V], eyn[V], ezn[V];
+    if constexpr (FAST && !MAT) {
+        // packed pairs; only the i = 0 wall cell (lane 0 of the first
+        // block) keeps its Ey and Ez
+        float dzi[V], dyi[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            dzi[e] = __fsub_rn(hzn[e], (e > 0) ? hzn[e - 1] : hz_first);
+            dyi[e] = __fsub_rn(hyn[e], (e > 0) ? hyn[e - 1] : hy_first);
+        }
+#pragma unroll
+        for (int e = 0; e < V; e += 2) {
+            curl2(&ex[e], s, d2(&hzn[e], &hzjmn[e]), d2(&hyn[e], &hykm[e]), &exn[e]);
+            curl2(&ey[e], s, d2(&hxn[e], &hxkm[e]), p2(dzi[e], dzi[e + 1]), &eyn[e]);
+            curl2(&ez[e], s, p2(dyi[e], dyi[e + 1]), d2(&hxn[e], &hxjmn[e]), &ezn[e]);
+        }
+        if (i0 == 0) {
+            eyn[0] = ey[0];
+            ezn[0] = ez[0];
+        }
+    } else
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const int i = i0 + e;
