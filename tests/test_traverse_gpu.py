@@ -57,8 +57,9 @@ def test_fdtd_traversal_order_bit_identical(media):
     med = gs_inputs.fdtd_media(N, n_mat=4, seed=23) if media else None
     res = []
     for tr in (g.GS_TRAVERSE_FORWARD, g.GS_TRAVERSE_ALTERNATE):
-        for plan in (dict(rows=2), dict(kernel=g.GS_KERNEL_MARCH, block_x=64, rows=4)):
-            if media and plan.get("kernel") == g.GS_KERNEL_MARCH:
+        for plan in (dict(rows=2), dict(kernel=g.GS_KERNEL_MARCH, block_x=64, rows=4),
+                     dict(kernel=g.GS_KERNEL_FUSED, rows=2), dict(kernel=g.GS_KERNEL_FUSED, rows=4, tile_y=5)):
+            if media and (plan.get("kernel") == g.GS_KERNEL_MARCH or plan == dict(kernel=g.GS_KERNEL_FUSED, rows=2)):
                 continue
             ctx, fields = fdtd_setup(N, plan=dict(plan, traverse=tr), src=(10, 20, 30), media=med)
             try:
