@@ -61,6 +61,9 @@ def test_every_swept_plan_passes_the_plan_check(g, tables):
     ("HEAT3D", 64, 64, 8, dict(kernel=3, temporal_depth=4, tile_x=256, tile_y=256), "UNSUPPORTED"),  # tile too big
     ("HEAT2D", 64, 64, 2, dict(), "INVALID_ARG"),                              # gs_create refuses the grid
     ("FDTD3D", 32, 32, 31, dict(), "INVALID_ARG"),
+    ("FDTD3D", 32, 32, 32, dict(kernel=6, tile_y=-1), "INVALID_ARG"),        # FUSED march: tile_y in [0, 2^20]
+    ("FDTD3D", 32, 32, 32, dict(kernel=6, tile_y=(1 << 20) + 1), "INVALID_ARG"),
+    ("HEAT2D", 64, 64, 1, dict(kernel=6), "INVALID_ARG"),                      # FUSED is an FDTD kernel
 ])
 def test_plan_check_refuses_what_set_plan_refuses(g, kind, nx, ny, nz, plan, status):
     w = dict(kind=getattr(g, "GS_" + kind), dtype=g.GS_F32, nx=nx, ny=ny, nz=nz)
@@ -85,6 +88,25 @@ def test_plan_check_fills_defaults_and_resolves_auto(g):
     assert g.gs_plan_check(w2, {})["rows"] == 8  # large grids: 8 warp rows per block
     wf = dict(kind=g.GS_FDTD3D, dtype=g.GS_F16, nx=128, ny=128, nz=128)
     assert g.gs_plan_check(wf, {})["kernel"] == g.GS_KERNEL_COLUMN
+    pf = g.gs_plan_check(wf, dict(kernel=g.GS_KERNEL_FUSED, rows=4, tile_y=8))  # the fused march
+    assert (pf["kernel"], pf["rows"], pf["tile_y"]) == (g.GS_KERNEL_FUSED, 4, 8)
+    assert g.gs_plan_check(wf, dict(kernel=g.GS_KERNEL_FUSED))["tile_y"] == 0  # its column form
+
+
+def test_fdtd_candidates_include_the_fused_march(g):
+    # FDTD: the fused step's k march (8 planes a block, 4 and 8 rows) among
+    # the plans, each with the seven batch sizes; kernels per iteration is 1
+    # in its features (2 for the two-launch plans)
+    w = dict(kind=g.GS_FDTD3D, dtype=g.GS_F32, nx=256, ny=256, nz=256, n_iters=500)
+    cands = g.gs_candidates(w)
+    fused = [(p, S) for p, S in cands if p["kernel"] == g.GS_KERNEL_FUSED]
+    assert sorted({(p["rows"], p["tile_y"]) for p, _ in fused}) == [(4, 8), (8, 8)]
+    assert sorted(S for p, S in fused if p["rows"] == 4) == [0, 1, 10, 50, 100, 500, 1000]
+    F = g.gs_features(w, cands)
+    for (p, _), f in zip(cands, F):
+        assert f[6] == (1.0 if p["kernel"] == g.GS_KERNEL_FUSED else 2.0)
+    w2 = dict(kind=g.GS_HEAT2D, dtype=g.GS_F32, nx=512, ny=512, nz=1, n_iters=500)
+    assert all(p["kernel"] != g.GS_KERNEL_FUSED and p["tile_y"] == 0 for p, _ in g.gs_candidates(w2))
 
 
 def test_candidates_argument_checks(g):
