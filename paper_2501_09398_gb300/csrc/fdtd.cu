@@ -789,9 +789,11 @@ __global__ void __launch_bounds__(256, 2) fdtd_fused_kernel(const FdtdArgs a) {
 // warp and are recomputed from loads, the i-1 values come from the
 // neighbouring lane (lane 0 recomputes its one cell), as in the column form.
 // Every value is formed by the same rounded operations on the same operands
-// as in the two launches, so the result is the same bit for bit.  A block
-// whose first plane k0 is above the wall recomputes H^{n+1/2} of plane k0-1
-// once before its march.
+// as in the two launches, so the result is the same bit for bit (interior
+// warps in vacuum take the operations in packed pairs, each half rounded as
+// the scalar form; in media each cell's coefficients come from the table
+// rows the block holds in shared memory).  A block whose first plane k0 is
+// above the wall recomputes H^{n+1/2} of plane k0-1 once before its march.
 template <typename ST, bool FAST, bool ALN, bool MAT>
 __device__ __forceinline__ void fdtd_march_plane(const FdtdArgs& a, const float2* s_mh, const float2* s_me, int lane,
                                                  int i0, bool act_i, int j, int k,
