@@ -6,7 +6,7 @@ Eqs. 1-6) and names automatic characterisation and selection as future work
 learned model:
 
 1. ``sample_workloads``: seeded stepping problems over 2D 64^2-4096^2, 3D
-   64^3-256^3 and thin 3D stacks, Yee FDTD 32^3-160^3, three storage types,
+   64^3-256^3 and thin 3D stacks, Yee FDTD 32^3-256^3, three storage types,
    run lengths I_k of 100-10000 iterations.
 2. ``candidates``: per workload, the launch plans x batch sizes
    S in {per-step, 1, 10, 50, 100, 500, 1000}.
@@ -90,7 +90,7 @@ def sample_workloads(n: int, seed: int):
             else:  # thin stack (Hotspot3D-like chips): few layers, wide planes
                 nx, ny, nz = lu(128, 1024), lu(128, 1024), int(rng.choice([2, 4, 8, 16]))
         else:
-            nx = ny = nz = lu(32, 160)
+            nx = ny = nz = lu(32, 256)
         out.append(dict(kind=kind, dtype=dtype, nx=nx, ny=ny, nz=nz, n_iters=n_iters))
     return out
 
