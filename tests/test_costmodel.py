@@ -77,3 +77,81 @@ def test_documented_regrets_of_the_pickers_that_need_no_gpu(cm):
             # each figure as the table prints it: within half a unit of its last digit
             half = 0.5 * 10.0 ** -(len(d.split(".")[1]) if "." in d else 0)
             assert abs(g - float(d)) <= half + 1e-9, (name, got)
+
+
+def _builtin_members():
+    """The compiled-in ensemble's parameters and input normalisation, read
+    from the include the library compiles (csrc/costmodel_weights.inc)."""
+    import os
+    import re
+
+    import numpy as np
+
+    path = os.path.join(os.path.dirname(__file__), "..", "paper_2501_09398_gb300", "csrc", "costmodel_weights.inc")
+    with open(path) as f:
+        src = f.read()
+
+    def arrays(name):
+        body = src[src.index(name):]
+        body = body[body.index("{") + 1:body.index("};")]
+        return [np.array([float(v) for v in row.split(",") if v.strip()]) for row in re.findall(r"\{([^{}]*)\}", body)]
+
+    return arrays("kBuiltinParams"), arrays("kBuiltinNorm")
+
+
+def _forward(p, norm, X):
+    # the 18-32-32-1 ReLU network of mlp.cu, in float64: standardised
+    # inputs, W1 [32][18] | b1 | W2 [32][32] | b2 | W3 [32] | b3
+    import numpy as np
+
+    ni, nh = 18, 32
+    xh = (X - norm[:ni]) * norm[ni:]
+    o = 0
+    W1 = p[o:o + nh * ni].reshape(nh, ni)
+    o += nh * ni
+    b1 = p[o:o + nh]
+    o += nh
+    W2 = p[o:o + nh * nh].reshape(nh, nh)
+    o += nh * nh
+    b2 = p[o:o + nh]
+    o += nh
+    W3 = p[o:o + nh]
+    b3 = p[o + nh]
+    h = np.maximum(xh @ W1.T + b1, 0.0)
+    return np.maximum(h @ W2.T + b2, 0.0) @ W3 + b3
+
+
+def test_documented_regret_of_the_compiled_in_ensemble(cm):
+    # the learned row of the design notes' composed table, reproduced on the
+    # CPU: the shipped ensemble (three members, the weights the library
+    # compiles in) scores each held-out workload's candidates that fit its
+    # grid (gs_features, gs_plan_check: host code), the smallest mean
+    # prediction is the pick; and the training record the library reports
+    # names the same regret
+    import numpy as np
+
+    import paper_2501_09398_gb300 as g
+
+    P, Nm = _builtin_members()
+    assert len(P) == len(Nm) == 3
+    _, held = cm.load_tables()
+    reg = []
+    for w, tab in held:
+        cands = []
+        for r in tab:
+            if r["status"] != 0 or not math.isfinite(r["ms_per_iter"]):
+                continue
+            try:
+                g.gs_plan_check(cm._fw(w), r["plan"])
+            except g.GsError:
+                continue
+            cands.append(r)
+        X = g.gs_features(cm._fw(w), [(r["plan"], r["S"]) for r in cands]).astype(np.float64)
+        pred = np.mean([_forward(P[i], Nm[i], X) for i in range(3)], axis=0)
+        reg.append(cm.regret(w, tab, cands[int(np.argmin(pred))]))
+    r = 100 * np.array(reg)
+    got = (r.mean(), np.median(r), np.percentile(r, 95), 100 * np.mean(r <= 5.0))
+    for gv, d in zip(got, ("3.1", "1.2", "14.2", "84.5")):
+        assert abs(gv - float(d)) <= 0.05 + 1e-9, got
+    info = g.gs_mlp_builtin_info()
+    assert "held-out mean regret %.4f" % (r.mean() / 100) in info, info
