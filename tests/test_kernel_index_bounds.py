@@ -949,3 +949,49 @@ def test_scol_kernel_addresses(nx, ny, nz, esize, rows):
     cells = np.zeros((nz, ny, pitch), dtype=bool)
     cells[:, :, :nx] = True
     assert np.array_equal(covered.reshape(nz, ny, pitch) == 1, cells)
+
+
+def _fused_march_owned_exactly(N, rows, kmarch, extra_in_every_block=False):
+    """Whether the fused march's stores cover every element of the written
+    set exactly once (f32); `extra_in_every_block` plants the mistake of
+    giving every block's lane 31 the aligned layout's extra i = N cell."""
+    V, esize = 4, 4
+    M = Mk = N + 1
+    aln = N % (32 * V) == 0
+    pitch = pitch_of(M, esize)
+    plane = pitch * M
+    by_ = max(1, min(rows, 8))
+    span = N if aln else M
+    grid = (-(-span // (32 * V)), -(-M // by_), -(-Mk // kmarch))
+    bx, by, bz, lane, ty, _ = threads(grid, (32, by_, 1))
+    i0 = (bx * 32 + lane) * V
+    j = by * by_ + ty
+    k0 = bz * kmarch
+    k1 = np.minimum(k0 + kmarch, Mk)
+    act_i = np.ones_like(i0, dtype=bool) if aln else (i0 < M)
+    owned = np.zeros(plane * Mk, dtype=np.int64)
+    for p in range(min(kmarch, Mk)):
+        k = k0 + p
+        m = (j < M) & (k < k1) & act_i
+        o = k * plane + j * pitch + i0
+        nv = np.minimum(V, M - i0)
+        for c in range(V):
+            mc = m & (c < nv)
+            np.add.at(owned, o[mc] + c, 1)
+        if aln:
+            mx = m & (lane == 31) & (extra_in_every_block | (i0 + V == N))
+            np.add.at(owned, o[mx] + V, 1)
+    cells = np.zeros((Mk, M, pitch), dtype=bool)
+    cells[:, :, :M] = True
+    return np.array_equal(owned.reshape(Mk, M, pitch) == 1, cells)
+
+
+def test_planted_seam_mistake_fails_the_coverage_check():
+    # the re-trace tells the aligned layout's extra cell apart: owned by the
+    # last block's lane 31 the stores cover each element once; owned by
+    # every block's lane 31 (two blocks along i at N = 256) the first
+    # column of the second block is written twice
+    assert _fused_march_owned_exactly(256, 4, 64)
+    assert not _fused_march_owned_exactly(256, 4, 64, extra_in_every_block=True)
+    # with one block along i (N = 128) the two rules agree
+    assert _fused_march_owned_exactly(128, 4, 64, extra_in_every_block=True)
